@@ -1,0 +1,158 @@
+"""Pins of the oracle's Hamiltonian, energy, NLCG, Anderson mixing and fixed point
+(Sec. 3.3.1, App. C, App. D)."""
+from math import pi, sqrt
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import oracle as O
+from oracle.scf import inner
+from paper_1412_8250_gb300 import workloads as W
+
+
+def _setup(cell, N=6):
+    grid = O.Grid(cell.n, cell.L, N)
+    b = O.pseudocharge(cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    return grid, b, O.poisson_solve(b, grid)
+
+
+def _u(grid, Ne, seed=1):
+    u = W.random_field(grid.shape, seed=seed, kind="smooth")
+    return u * np.sqrt(Ne / (grid.dV * np.sum(u * u)))
+
+
+@pytest.mark.parametrize("fn", [O.tfw_functional(), O.wt_functional()])
+def test_energy_gradient_is_2dV_Hu(fn):
+    cell = W.small_cell(n=(10, 11, 12), L=(7.0, 7.6, 8.2), sigma=1.0, rc=6.0, seed=3)
+    grid, b, _ = _setup(cell)
+    Ne = cell.n_electrons
+    u = _u(grid, Ne)
+    V_LR = 0.3 * W.random_field(grid.shape, seed=4)
+    # include an r_s < 1 region so both PZ branches are exercised
+    u[0, 0, :3] = 0.9
+    energy = lambda w: O.inner_energy(w, O.poisson_solve(w * w + b, grid), b, V_LR, grid, fn)
+    phi = O.poisson_solve(u * u + b, grid)
+    Hu = O.hamiltonian_apply(u, phi, V_LR, grid, fn)
+    v = W.random_field(grid.shape, seed=5)
+    e = 1e-5
+    fd = (energy(u + e * v) - energy(u - e * v)) / (2 * e)
+    assert abs(fd - 2 * grid.dV * np.sum(Hu * v)) < 1e-7 * abs(fd)
+
+
+def test_line_energy_by_linearity_equals_fresh_poisson():
+    cell = W.small_cell(n=(12, 12, 12), seed=2)
+    grid, b, phib = _setup(cell)
+    Ne = cell.n_electrons
+    fn = O.tfw_functional()
+    u = _u(grid, Ne)
+    d = W.random_field(grid.shape, seed=8)
+    V = np.zeros(grid.shape)
+    phi = O.poisson_solve(u * u + b, grid)
+    pud, pdd = O.poisson_solve(u * d, grid), O.poisson_solve(d * d, grid)
+    for s in [0.01, -0.2, 0.7]:
+        w = u + s * d
+        c2 = Ne / inner(w, w, grid)
+        us = sqrt(c2) * w
+        phis = c2 * (phi - phib + 2 * s * pud + s * s * pdd) + phib
+        direct = O.poisson_solve(us * us + b, grid)
+        assert np.max(np.abs(phis - direct)) < 1e-11 * np.max(np.abs(direct))
+
+
+def test_nlcg_reaches_the_lbfgs_minimum():
+    cell = W.small_cell(n=(10, 10, 10), sigma=1.0, rc=6.0, seed=11)
+    grid, b, phib = _setup(cell)
+    Ne = cell.n_electrons
+    fn = O.tfw_functional()
+    V = np.zeros(grid.shape)
+    u0 = np.full(grid.shape, sqrt(Ne / grid.volume))
+    u, phi, info = O.nlcg(u0, V, b, phib, grid, fn, Ne, tol=1e-7, max_iter=3000)
+    assert info.converged
+    e_nlcg = O.inner_energy(u, phi, b, V, grid, fn)
+    assert abs(inner(u, u, grid) - Ne) < 1e-10 * Ne
+    assert u.min() > 0
+
+    def f(w):
+        w = w.reshape(grid.shape)
+        nw = sqrt(inner(w, w, grid))
+        us = sqrt(Ne) * w / nw
+        ph = O.poisson_solve(us * us + b, grid)
+        E = O.inner_energy(us, ph, b, V, grid, fn)
+        gu = 2 * grid.dV * O.hamiltonian_apply(us, ph, V, grid, fn)
+        gw = (sqrt(Ne) / nw) * (gu - us * np.sum(gu * us) * grid.dV / Ne)
+        return E, gw.ravel()
+
+    res = minimize(f, u0.ravel(), jac=True, method="L-BFGS-B",
+                   options=dict(maxiter=5000, gtol=1e-12, ftol=1e-16, maxcor=30))
+    assert abs(res.fun - e_nlcg) < 1e-9 * abs(e_nlcg)
+    w = res.x.reshape(grid.shape)
+    ul = sqrt(Ne) * w / sqrt(inner(w, w, grid))
+    assert np.max(np.abs(ul - u)) < 1e-4 * u.max()
+
+
+def _gmres_iterate(A, rhs, x0, k):
+    r0 = rhs - A @ x0
+    if k == 0:
+        return x0
+    K = [r0]
+    for _ in range(k - 1):
+        K.append(A @ K[-1])
+    Q, _ = np.linalg.qr(np.stack(K, axis=1))
+    y = np.linalg.lstsq(A @ Q, r0, rcond=None)[0]
+    return x0 + Q @ y
+
+
+def test_anderson_equals_gmres_on_linear_fixed_point():
+    # Walker & Ni (2011): for g(x) = Gx + c, Anderson with unbounded history and zeta = 1
+    # satisfies x_{k+1}^AA = g(x_k^GMRES) for (I - G) x = c.
+    rng = np.random.default_rng(0)
+    n = 24
+    G = rng.normal(size=(n, n))
+    G *= 0.8 / np.max(np.abs(np.linalg.eigvals(G)))
+    c = rng.normal(size=n)
+    x0 = rng.normal(size=n)
+    A = np.eye(n) - G
+    Vh, fh = [x0], [G @ x0 + c - x0]
+    for k in range(8):
+        x_next = O.anderson_update(Vh, fh, 1.0, 100)
+        ref = G @ _gmres_iterate(A, c, x0, k) + c
+        assert np.max(np.abs(x_next - ref)) < 1e-9 * np.max(np.abs(ref))
+        Vh.append(x_next)
+        fh.append(G @ x_next + c - x_next)
+
+
+def test_anderson_limited_history_and_damping_solve_linear_problem():
+    rng = np.random.default_rng(1)
+    n = 30
+    G = rng.normal(size=(n, n))
+    G = G + G.T
+    G *= 0.9 / np.max(np.abs(np.linalg.eigvalsh(G)))
+    c = rng.normal(size=n)
+    x = np.zeros(n)
+    Vh, fh = [], []
+    for k in range(200):
+        f = G @ x + c - x
+        Vh.append(x)
+        fh.append(f)
+        if np.linalg.norm(f) < 1e-12:
+            break
+        x = O.anderson_update(Vh, fh, 0.3, 7)
+    assert np.linalg.norm(G @ x + c - x) < 1e-10
+
+
+@pytest.mark.slow
+def test_fixed_point_ground_state_wt_small():
+    cell = W.al4_lr_cell(points_per_cell=12)
+    grid = O.Grid(cell.n, cell.L, 6)
+    res = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.wt_functional(),
+                             nlcg_tol=1e-8, fp_tol=1e-6, anderson_m=7, zeta=0.3)
+    assert res.fp_errors[-1] < 1e-6
+    # at the fixed point, u is the ground state of the full functional: the gradient with
+    # the self-consistent V_LR vanishes
+    b = O.pseudocharge(cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    kf2 = O.kf2_of(cell.n_electrons, grid.volume)
+    V, T, _, _ = O.lr_potential(res.u, grid, O.wt_functional(), kf2)
+    Hu = O.hamiltonian_apply(res.u, res.phi, V, grid, O.wt_functional())
+    eta = inner(res.u, Hu, grid) / cell.n_electrons
+    r = Hu - eta * res.u
+    assert sqrt(inner(r, r, grid) / cell.n_electrons) < 1e-5
