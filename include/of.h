@@ -1,0 +1,186 @@
+/*
+ * of.h -- C ABI of the GB300 library for periodic orbital-free DFT with higher-order finite
+ * differences (Ghosh & Suryanarayana, arXiv:1412.8250).
+ *
+ * Conventions for every entry point:
+ *  - A field on the n1 x n2 x n3 grid is an array of n1*n2*n3 values, x fastest:
+ *    f[i + n1*(j + n2*k)] is the value at x = (i h1, j h2, k h3), h_d = L_d / n_d (Sec. 4).
+ *  - Complex fields are interleaved (re, im) pairs of doubles, 2*n1*n2*n3 doubles.
+ *  - Field pointers are DEVICE pointers owned by the caller; the library never frees them.
+ *    Atom data (of_system), coefficient arrays and force outputs are HOST pointers.
+ *  - All device work is enqueued on the stream given to of_grid_create.  Calls that return
+ *    host scalars (energies, iteration counts, forces) synchronise that stream before
+ *    returning; the others are asynchronous.
+ *  - Atomic units throughout (bohr, hartree).
+ *  - Errors: every call returns an of_status; on failure of_last_error() gives a message
+ *    (thread-local).  No C++ exception crosses this boundary.  A solver that stops at its
+ *    iteration limit returns OF_ENOCONV with its best iterate written to the output.
+ *  - A grid handle holds device workspace (allocated at create and on the first call that
+ *    needs more) and is used by one host thread at a time.
+ */
+#ifndef OF_H
+#define OF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OF_OK = 0,
+    OF_EINVAL = 1,       /* invalid argument (null pointer, size, unsupported order) */
+    OF_ENOMEM = 2,       /* device or host allocation failed */
+    OF_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    OF_ENOCONV = 4,      /* iteration limit reached before the tolerance */
+    OF_EBREAKDOWN = 5,   /* Krylov breakdown (zero curvature / zero bilinear form) */
+    OF_ETIMEOUT = 6      /* a bounded device wait gave up */
+} of_status;
+
+typedef enum {
+    OF_F64 = 0,          /* plain FP64 */
+    OF_F32 = 1           /* FP32 sweeps; in solvers: FP32 inner Krylov + FP64 refinement */
+} of_dtype;
+
+typedef struct of_grid of_grid;
+
+/* Krylov solve options.  tol is the target of the true FP64 relative residual
+ * ||b - A x|| / ||b||.  precision OF_F64: CG/COCG entirely in FP64.  OF_F32: iterative
+ * refinement -- FP64 residual, FP32 Krylov solve of the correction to inner_tol, FP64
+ * update -- repeated until tol.  Zero fields take defaults (tol 1e-10, max_iter 20000,
+ * inner_tol 1e-5, check_every 8). */
+typedef struct {
+    double tol;
+    int max_iter;
+    int precision;
+    double inner_tol;
+    int check_every;
+} of_solve_opts;
+
+typedef struct {
+    int iterations;        /* Krylov iterations (all passes) */
+    int refinements;       /* FP64 residual evaluations */
+    double rel_residual;   /* final true FP64 relative residual */
+} of_solve_info;
+
+/* Ions: positions R[3*M] (x, y, z per ion, bohr), charges Z[M]; each carries the Gaussian
+ * charge density b_J(r) = -Z_J (2 pi sigma^2)^{-3/2} exp(-r^2 / (2 sigma^2)) for r <= rc,
+ * the stand-in for the pseudopotential charge of Sec. 3.2.  Host pointers. */
+typedef struct {
+    int n_atoms;
+    const double* R;
+    const double* Z;
+    double sigma;
+    double rc;
+} of_system;
+
+/* Kinetic functional T_TF + lambda T_vW + mu T_LR (Eq. KineticEnergyComponents).  For the
+ * kernel term (mu != 0) only the density-independent m = n = 0 term of Eq.
+ * LR:KineticEnergy:Linearized is used, with exponents alpha, beta and n_terms rational
+ * terms (P_r, Q_r) of the fitted kernel (Sec. 3.1, App. A), interleaved re/im. */
+typedef struct {
+    double lambda;
+    double mu;
+    double alpha;
+    double beta;
+    int n_terms;
+    double P[16];
+    double Q[16];
+} of_functional;
+
+typedef struct {
+    double nlcg_tol;        /* normalised residual ||r|| / sqrt(N_e) (App. C); default 1e-7 */
+    int nlcg_max_iter;      /* per inner minimisation; default 5000 */
+    int nlcg_restart;       /* N_restart; default 50 */
+    double fp_tol;          /* fixed-point error ||f_k|| / ||V^_k|| (Sec. 5.3); default 1e-7 */
+    int fp_max_iter;        /* default 60 */
+    int anderson_m;         /* mixing history m (App. D); default 7 */
+    double anderson_zeta;   /* mixing parameter zeta; default 0.3 */
+    int precision;          /* OF_F64 plain, or OF_F32 mixed (Poisson and kernel solves) */
+    of_solve_opts poisson;  /* defaults: tol 1e-10 */
+    of_solve_opts kernel;   /* defaults: tol 1e-10 */
+    int verbose;            /* 1: one line per outer iteration on stderr */
+} of_scf_opts;
+
+typedef struct {
+    double energy;          /* Eq. GroundStateEnergy */
+    double e_tf, e_vw, e_lr, e_xc, e_es, e_self, e_corr;
+    double fp_error;
+    double nlcg_residual;
+    int outer_iterations;
+    int nlcg_iterations;    /* summed over outer iterations */
+    int poisson_iterations;
+    int kernel_iterations;
+    int line_evaluations;
+    int converged;
+} of_scf_result;
+
+/* Fill defaults.  Always succeed. */
+void of_default_solve_opts(of_solve_opts* o);
+void of_default_scf_opts(of_scf_opts* o);
+
+/* Uniform periodic grid of Sec. 4: n_d points of spacing h_d = L_d / n_d per axis, finite
+ * differences of order 2N with N = fd_half_order in {1, 3, 6}.  stream is a cudaStream_t
+ * (NULL = legacy default stream); the device is the current CUDA device.  Allocates the
+ * base workspace.  OF_EINVAL for n_d < 1, L_d <= 0, unsupported N, null out. */
+of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3,
+                         int fd_half_order, void* stream, of_grid** out);
+of_status of_grid_destroy(of_grid* g);
+
+/* y = L_h x: the order-2N central-difference Laplacian of Eq. FD:Laplacian, indices wrapped
+ * periodically (Sec. 4).  dtype OF_F64: x, y are double*; OF_F32: float*.  x != y. */
+of_status of_laplacian_apply(of_grid* g, of_dtype dtype, const void* x, void* y);
+
+/* Periodic Poisson problem of Eq. Poisson: -(1/4pi) L_h phi = rho, solved by CG on the
+ * mean-free part of rho; phi returns with zero mean (Sec. 4).  phi: in = initial guess,
+ * out = solution.  rho and phi are double*, n points. */
+of_status of_poisson_solve(of_grid* g, const double* rho, double* phi,
+                           const of_solve_opts* opts, of_solve_info* info);
+
+/* Shifted solves of Eqs. Helmholtz:beta / Helmholtz:alpha:
+ *   -(1/kf2) L_h W_s + Q_s W_s = P_s f,   s = 0 .. nshift-1,
+ * by COCG (complex symmetric CG).  f: real double* (n); P, Q: host double[2*nshift]
+ * (re, im); W: device complex, nshift consecutive fields of 2n doubles, in = guess,
+ * out = solution.  info (optional) sums over the shifts. */
+of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double* P,
+                          const double* Q, double kf2, double* W, const of_solve_opts* opts,
+                          of_solve_info* info);
+
+/* b = sum over ions and periodic images of b_J (Sec. 3.2) on the grid (device double*),
+ * and the self-energy term -(1/2) sum_J int b_J V_J (host double, may be NULL). */
+of_status of_pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self);
+
+/* H u = -(lambda/2) L_h u + (V_TF + mu V_LR + V_xc + phi) u (Eq. EulerLagrange).
+ * vlr may be NULL when mu == 0.  All device double*. */
+of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double* u,
+                               const double* phi, const double* vlr, double* hu);
+
+/* The kernel map V[u] of Eq. MVF (m = n = 0 term, Eq. VLinearResponse:local): builds
+ * f = -(1/kf2) L_h u^{2e} for e = alpha, beta, solves the n_terms shifted systems of each
+ * (conjugate pairs solved once), writes V_LR (device double*) and T_LR (host double, may be
+ * NULL).  n_terms must be even, terms (0,1), (2,3), ... complex-conjugate pairs.  W_ws:
+ * device workspace and warm start of n_terms complex fields (one per pair and exponent);
+ * NULL uses the handle's own workspace with a zero start. */
+of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const double* u,
+                          double* vlr, double* t_lr, double* W_ws, const of_solve_opts* opts,
+                          of_solve_info* info);
+
+/* Ground state (Sec. 3.3.1): fixed point V_LR = V[U(V_LR)] with Anderson mixing (App. D),
+ * U by the constrained NLCG of App. C.  u: device double*, in = initial guess (any positive
+ * field; it is normalised to N_e = sum Z), out = ground state sqrt(rho).  phi: device
+ * double*, out = electrostatic potential.  The energy and its terms go to res. */
+of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functional* fn,
+                              const of_scf_opts* opts, double* u, double* phi,
+                              of_scf_result* res);
+
+/* Hellmann-Feynman forces of Eq. Force:Nuclei with the overlap correction f^c of App. B:
+ * F[3*J + c] (host) for ion J, component c.  phi: device, the ground-state potential.
+ * u is accepted for the interface of the paper's statement and not read. */
+of_status of_forces(of_grid* g, const of_system* sys, const double* u, const double* phi,
+                    double* F);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* of_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OF_H */

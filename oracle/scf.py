@@ -82,6 +82,8 @@ def line_minimum(f, s_try, max_expand=60, max_shrink=60):
             k += 1
         if fc < fb:
             return c
+        if not fc > fb:                     # flat to rounding between b and c
+            return b
     else:
         c, fc = b, fb
         b = c / (1.0 + GOLD)

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of include/of.h: the same entry points, argument marshalling only.
+
+Field arguments may be torch CUDA tensors (their data_ptr is passed) or integer device
+addresses; host arrays (ion positions, charges, forces) are numpy float64 arrays.  Every
+computation happens in libof.so; this module never falls back to anything else and raises
+if the library cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build_lib
+
+OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ENOCONV, OF_EBREAKDOWN, OF_ETIMEOUT = range(7)
+OF_F64, OF_F32 = 0, 1
+STATUS_NAMES = {0: "OF_OK", 1: "OF_EINVAL", 2: "OF_ENOMEM", 3: "OF_ECUDA", 4: "OF_ENOCONV",
+                5: "OF_EBREAKDOWN", 6: "OF_ETIMEOUT"}
+
+
+class of_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
+                ("inner_tol", C.c_double), ("check_every", C.c_int)]
+
+
+class of_solve_info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
+                ("rel_residual", C.c_double)]
+
+
+class of_system(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("R", C.POINTER(C.c_double)),
+                ("Z", C.POINTER(C.c_double)), ("sigma", C.c_double), ("rc", C.c_double)]
+
+
+class of_functional(C.Structure):
+    _fields_ = [("lambda_", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
+                ("beta", C.c_double), ("n_terms", C.c_int), ("P", C.c_double * 16),
+                ("Q", C.c_double * 16)]
+
+
+class of_scf_opts(C.Structure):
+    _fields_ = [("nlcg_tol", C.c_double), ("nlcg_max_iter", C.c_int),
+                ("nlcg_restart", C.c_int), ("fp_tol", C.c_double), ("fp_max_iter", C.c_int),
+                ("anderson_m", C.c_int), ("anderson_zeta", C.c_double),
+                ("precision", C.c_int), ("poisson", of_solve_opts), ("kernel", of_solve_opts),
+                ("verbose", C.c_int)]
+
+
+class of_scf_result(C.Structure):
+    _fields_ = [("energy", C.c_double), ("e_tf", C.c_double), ("e_vw", C.c_double),
+                ("e_lr", C.c_double), ("e_xc", C.c_double), ("e_es", C.c_double),
+                ("e_self", C.c_double), ("e_corr", C.c_double), ("fp_error", C.c_double),
+                ("nlcg_residual", C.c_double), ("outer_iterations", C.c_int),
+                ("nlcg_iterations", C.c_int), ("poisson_iterations", C.c_int),
+                ("kernel_iterations", C.c_int), ("line_evaluations", C.c_int),
+                ("converged", C.c_int)]
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+_SIGNATURES = {
+    "of_default_solve_opts": (None, [C.POINTER(of_solve_opts)]),
+    "of_default_scf_opts": (None, [C.POINTER(of_scf_opts)]),
+    "of_grid_create": (_I, [_I, _I, _I, _D, _D, _D, _I, _P, C.POINTER(_P)]),
+    "of_grid_destroy": (_I, [_P]),
+    "of_laplacian_apply": (_I, [_P, _I, _P, _P]),
+    "of_poisson_solve": (_I, [_P, _P, _P, C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_kernel_solve": (_I, [_P, _P, _I, C.POINTER(_D), C.POINTER(_D), _D, _P,
+                             C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_pseudocharge": (_I, [_P, C.POINTER(of_system), _P, C.POINTER(_D)]),
+    "of_hamiltonian_apply": (_I, [_P, C.POINTER(of_functional), _P, _P, _P, _P]),
+    "of_lr_potential": (_I, [_P, C.POINTER(of_functional), _D, _P, _P, C.POINTER(_D), _P,
+                             C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_scf_ground_state": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional),
+                                 C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
+    "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
+    "of_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libof.so (building it first when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        build_lib.build()
+    if not os.path.exists(build_lib.LIB):
+        raise RuntimeError(f"{build_lib.LIB} is missing: build the CUDA library first")
+    lib = C.CDLL(build_lib.LIB)
+    for name, (res, args) in _SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGNATURES)
+
+
+class OfError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = load().of_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+def _check(status, where, allow=()):
+    if status != OF_OK and status not in allow:
+        raise OfError(status, where)
+    return status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("field arguments must be contiguous CUDA tensors")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x)} as a device pointer")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------- the entry points
+def of_default_solve_opts():
+    o = of_solve_opts()
+    load().of_default_solve_opts(C.byref(o))
+    return o
+
+
+def of_default_scf_opts():
+    o = of_scf_opts()
+    load().of_default_scf_opts(C.byref(o))
+    return o
+
+
+def of_grid_create(n, L, fd_half_order=6, stream=None):
+    h = _P()
+    _check(load().of_grid_create(int(n[0]), int(n[1]), int(n[2]), float(L[0]), float(L[1]),
+                                 float(L[2]), int(fd_half_order), _stream_ptr(stream),
+                                 C.byref(h)), "of_grid_create")
+    return h
+
+
+def of_grid_destroy(h):
+    return _check(load().of_grid_destroy(h), "of_grid_destroy")
+
+
+def of_laplacian_apply(h, dtype, x, y):
+    return _check(load().of_laplacian_apply(h, int(dtype), _ptr(x), _ptr(y)),
+                  "of_laplacian_apply")
+
+
+def of_poisson_solve(h, rho, phi, opts=None, allow=()):
+    info = of_solve_info()
+    st = load().of_poisson_solve(h, _ptr(rho), _ptr(phi), C.byref(opts) if opts else None,
+                                 C.byref(info))
+    _check(st, "of_poisson_solve", allow)
+    return info
+
+
+def of_kernel_solve(h, f, P, Q, kf2, W, opts=None, allow=()):
+    P = np.ascontiguousarray(np.asarray(P, dtype=np.complex128))
+    Q = np.ascontiguousarray(np.asarray(Q, dtype=np.complex128))
+    Pd = P.view(np.float64)
+    Qd = Q.view(np.float64)
+    info = of_solve_info()
+    st = load().of_kernel_solve(h, _ptr(f), int(P.size), Pd.ctypes.data_as(C.POINTER(_D)),
+                                Qd.ctypes.data_as(C.POINTER(_D)), float(kf2), _ptr(W),
+                                C.byref(opts) if opts else None, C.byref(info))
+    _check(st, "of_kernel_solve", allow)
+    return info
+
+
+def make_system(R, Z, sigma, rc):
+    """of_system from numpy arrays (kept alive on the returned object)."""
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
+    Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
+    s = of_system(int(Z.size), R.ctypes.data_as(C.POINTER(_D)), Z.ctypes.data_as(C.POINTER(_D)),
+                  float(sigma), float(rc))
+    s._keep = (R, Z)
+    return s
+
+
+def make_functional(lam, mu, alpha=0.0, beta=0.0, P=(), Q=()):
+    f = of_functional()
+    f.lambda_, f.mu, f.alpha, f.beta = float(lam), float(mu), float(alpha), float(beta)
+    f.n_terms = len(P)
+    for k, (p, q) in enumerate(zip(P, Q)):
+        f.P[2 * k], f.P[2 * k + 1] = complex(p).real, complex(p).imag
+        f.Q[2 * k], f.Q[2 * k + 1] = complex(q).real, complex(q).imag
+    return f
+
+
+def of_pseudocharge(h, sys, b):
+    e = _D()
+    _check(load().of_pseudocharge(h, C.byref(sys), _ptr(b), C.byref(e)), "of_pseudocharge")
+    return e.value
+
+
+def of_hamiltonian_apply(h, fn, u, phi, vlr, hu):
+    return _check(load().of_hamiltonian_apply(h, C.byref(fn), _ptr(u), _ptr(phi), _ptr(vlr),
+                                              _ptr(hu)), "of_hamiltonian_apply")
+
+
+def of_lr_potential(h, fn, kf2, u, vlr, W=None, opts=None):
+    t = _D()
+    info = of_solve_info()
+    _check(load().of_lr_potential(h, C.byref(fn), float(kf2), _ptr(u), _ptr(vlr), C.byref(t),
+                                  _ptr(W), C.byref(opts) if opts else None, C.byref(info)),
+           "of_lr_potential")
+    return t.value, info
+
+
+def of_scf_ground_state(h, sys, fn, opts, u, phi, allow=()):
+    res = of_scf_result()
+    st = load().of_scf_ground_state(h, C.byref(sys), C.byref(fn), C.byref(opts), _ptr(u),
+                                    _ptr(phi), C.byref(res))
+    _check(st, "of_scf_ground_state", allow)
+    return res
+
+
+def of_forces(h, sys, u, phi):
+    F = np.zeros((sys.n_atoms, 3))
+    _check(load().of_forces(h, C.byref(sys), _ptr(u), _ptr(phi),
+                            F.ctypes.data_as(C.POINTER(_D))), "of_forces")
+    return F
+
+
+def of_last_error():
+    return load().of_last_error().decode(errors="replace")

@@ -1,0 +1,311 @@
+// Ion terms: charge density of the nuclei (Sec. 3.2), self energy, the overlap correction
+// E_c^* and f^c (App. B) and the Hellmann-Feynman forces (Eq. Force:Nuclei).
+//
+// Each ion carries a Gaussian charge b_J(r) = -Z_J (2 pi s^2)^{-3/2} exp(-r^2/(2 s^2)),
+// r <= r_c, whose potential is V_J(r) = -Z_J erf(r/(sqrt2 s))/r.  Work is organised as one
+// CUDA block per (ion, z-plane of the ion's bounding box); the box is addressed with
+// unwrapped grid indices, each of which is one periodic image of the ion (Sec. 4: indices
+// outside the grid map to their periodic image).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "of_stencil.cuh"
+
+namespace of {
+
+struct AtomBox {
+    double R[3];
+    double Z;
+    int lo[3];
+    int len[3];
+};
+
+struct AtomSet {
+    AtomBox* d_boxes;   // device
+    int n_atoms;
+    int max_planes;     // max box extent along z
+    std::vector<AtomBox> h;
+};
+
+static AtomSet upload_atoms(of_grid* g, const of_system* sys) {
+    OF_REQUIRE(sys && sys->n_atoms >= 1 && sys->R && sys->Z && sys->sigma > 0 && sys->rc > 0,
+               OF_EINVAL, "invalid of_system");
+    AtomSet a;
+    a.n_atoms = sys->n_atoms;
+    a.h.resize(a.n_atoms);
+    a.max_planes = 0;
+    for (int J = 0; J < a.n_atoms; ++J) {
+        AtomBox& b = a.h[J];
+        b.Z = sys->Z[J];
+        for (int c = 0; c < 3; ++c) {
+            b.R[c] = sys->R[3 * J + c];
+            OF_REQUIRE(std::isfinite(b.R[c]), OF_EINVAL, "ion %d has a non-finite position", J);
+            const int lo = (int)std::ceil((b.R[c] - sys->rc) / g->h[c]);
+            const int hi = (int)std::floor((b.R[c] + sys->rc) / g->h[c]);
+            b.lo[c] = lo;
+            b.len[c] = hi - lo + 1;
+        }
+        a.max_planes = std::max(a.max_planes, a.h[J].len[2]);
+    }
+    a.d_boxes = (AtomBox*)ws(g, WS_ATOM, sizeof(AtomBox) * a.n_atoms);
+    OF_CUDA(cudaMemcpyAsync(a.d_boxes, a.h.data(), sizeof(AtomBox) * a.n_atoms,
+                            cudaMemcpyHostToDevice, g->stream));
+    return a;
+}
+
+struct Gauss {
+    double sigma, rc, norm, inv2s2, erfscale, v0;
+};
+
+static Gauss gauss(const of_system* sys) {
+    Gauss q;
+    q.sigma = sys->sigma;
+    q.rc = sys->rc;
+    q.norm = std::pow(2.0 * M_PI * sys->sigma * sys->sigma, -1.5);
+    q.inv2s2 = 1.0 / (2.0 * sys->sigma * sys->sigma);
+    q.erfscale = 1.0 / (std::sqrt(2.0) * sys->sigma);
+    q.v0 = std::sqrt(2.0 / M_PI) / sys->sigma;
+    return q;
+}
+
+__device__ __forceinline__ double gauss_b(double r2, double Z, const Gauss& q) {
+    return -Z * q.norm * exp(-r2 * q.inv2s2);
+}
+__device__ __forceinline__ double gauss_V(double r, double Z, const Gauss& q) {
+    return r < 1e-12 ? -Z * q.v0 : -Z * erf(r * q.erfscale) / r;
+}
+
+// Block (J, plane): scatter b_J into b (atomic: boxes of different ions overlap) and reduce
+// dV * sum b_J V_J for the self energy.
+__global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double h2, double h3,
+                                                      const AtomBox* boxes, Gauss q, double* b,
+                                                      double* e_self_part, int max_planes) {
+    const int J = blockIdx.x, pl = blockIdx.y;
+    const AtomBox B = boxes[J];
+    double acc = 0.0;
+    if (pl < B.len[2]) {
+        const int k = B.lo[2] + pl;
+        const double dz = k * h3 - B.R[2];
+        const int kw = wrap_index(k, d.n3);
+        const int nxy = B.len[0] * B.len[1];
+        const double rc2 = q.rc * q.rc;
+        for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+            const int jj = t / B.len[0];
+            const int i = B.lo[0] + (t - jj * B.len[0]);
+            const int j = B.lo[1] + jj;
+            const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 <= rc2) {
+                const double bj = gauss_b(r2, B.Z, q);
+                const long long idx = wrap_index(i, d.n1) +
+                                      (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+                atomicAdd(b + idx, bj);
+                acc += bj * gauss_V(sqrt(r2), B.Z, q);
+            }
+        }
+    }
+    acc = warp_sum(acc);
+    __shared__ double sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        e_self_part[(long long)J * max_planes + pl] = s;
+    }
+}
+
+// Block (J, plane): dV * sum grad b_J (phi - V_J) over the plane, 3 components.
+__global__ void __launch_bounds__(256) k_forces(Dims d, double h1, double h2, double h3,
+                                                const AtomBox* boxes, Gauss q, const double* phi,
+                                                double* part, int max_planes) {
+    const int J = blockIdx.x, pl = blockIdx.y;
+    const AtomBox B = boxes[J];
+    double f[3] = {0.0, 0.0, 0.0};
+    if (pl < B.len[2]) {
+        const int k = B.lo[2] + pl;
+        const double dz = k * h3 - B.R[2];
+        const int kw = wrap_index(k, d.n3);
+        const int nxy = B.len[0] * B.len[1];
+        const double rc2 = q.rc * q.rc;
+        const double inv_s2 = 2.0 * q.inv2s2;
+        for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+            const int jj = t / B.len[0];
+            const int i = B.lo[0] + (t - jj * B.len[0]);
+            const int j = B.lo[1] + jj;
+            const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 <= rc2) {
+                const long long idx = wrap_index(i, d.n1) +
+                                      (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+                // grad b_J = -b_J (x - R_J) / sigma^2
+                const double w = -gauss_b(r2, B.Z, q) * inv_s2 * (phi[idx] - gauss_V(sqrt(r2), B.Z, q));
+                f[0] += w * dx;
+                f[1] += w * dy;
+                f[2] += w * dz;
+            }
+        }
+    }
+    __shared__ double sh[8][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double s = warp_sum(f[c]);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+        part[((long long)J * max_planes + pl) * 3 + threadIdx.x] = s;
+    }
+}
+
+// out[J*stride + c] = scale * sum over planes of part[(J*max_planes + pl)*stride + c]
+__global__ void k_sum_planes(int n_atoms, int max_planes, int stride, const double* part,
+                             double scale, double* out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_atoms * stride) return;
+    const int J = t / stride, c = t - J * stride;
+    double s = 0.0;
+    for (int pl = 0; pl < max_planes; ++pl) s += part[((long long)J * max_planes + pl) * stride + c];
+    out[t] = scale * s;
+}
+
+// E_c^* (per-ion halves) and f^c for Gaussian charges with point reference charges:
+// E_c^* = 1/2 sum_I sum_{(J,T) != (I,0)} Z_I Z_J erfc(r/(2s))/r, f^c_I = -dE_c^*/dR_I.
+__global__ void k_overlap(int M, const AtomBox* boxes, double L1, double L2, double L3,
+                          double sigma, double cutoff, int t1, int t2, int t3, double* e_part,
+                          double* fc) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= M) return;
+    const AtomBox A = boxes[I];
+    double e = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    const double inv2s = 1.0 / (2.0 * sigma), c2 = cutoff * cutoff;
+    const double gp0 = 1.0 / (sigma * sqrt(M_PI));
+    for (int J = 0; J < M; ++J) {
+        const AtomBox B = boxes[J];
+        for (int a = -t1; a <= t1; ++a)
+            for (int bb = -t2; bb <= t2; ++bb)
+                for (int c = -t3; c <= t3; ++c) {
+                    if (J == I && a == 0 && bb == 0 && c == 0) continue;
+                    const double dx = A.R[0] - B.R[0] - a * L1;
+                    const double dy = A.R[1] - B.R[1] - bb * L2;
+                    const double dz = A.R[2] - B.R[2] - c * L3;
+                    const double r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 > c2) continue;
+                    const double r = sqrt(r2);
+                    const double ec = erfc(r * inv2s);
+                    e += 0.5 * A.Z * B.Z * ec / r;
+                    // g'(r) = -exp(-r^2/(4 s^2)) / (s sqrt(pi) r) - erfc(r/2s)/r^2
+                    const double gp = -exp(-r2 * inv2s * inv2s) * gp0 / r - ec / r2;
+                    const double w = -A.Z * B.Z * gp / r;
+                    f0 += w * dx;
+                    f1 += w * dy;
+                    f2 += w * dz;
+                }
+    }
+    e_part[I] = e;
+    fc[3 * I + 0] = f0;
+    fc[3 * I + 1] = f1;
+    fc[3 * I + 2] = f2;
+}
+
+static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, double* e_self) {
+    AtomSet a = upload_atoms(g, sys);
+    Gauss q = gauss(sys);
+    const size_t nparts = (size_t)a.n_atoms * a.max_planes;
+    double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + a.n_atoms + 8));
+    OF_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * g->d.n, g->stream));
+    OF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * nparts, g->stream));
+    k_pseudocharge<<<dim3(a.n_atoms, a.max_planes), 256, 0, g->stream>>>(
+        g->d, g->h[0], g->h[1], g->h[2], a.d_boxes, q, b, part, a.max_planes);
+    OF_LAUNCH_CHECK();
+    if (e_self) {
+        double* per_atom = part + nparts;
+        k_sum_planes<<<(a.n_atoms + 127) / 128, 128, 0, g->stream>>>(a.n_atoms, a.max_planes, 1,
+                                                                    part, -0.5 * g->dV, per_atom);
+        k_sum_product<<<1, 256, 0, g->stream>>>(a.n_atoms, per_atom, nullptr, red_ctx(g, 119));
+        OF_LAUNCH_CHECK();
+        fetch_scalars(g, 119, 1, e_self);
+    }
+}
+
+// E_c^* and f^c into host outputs (either may be null)
+void overlap_correction(of_grid* g, const of_system* sys, double* e_c, double* fc_host) {
+    AtomSet a = upload_atoms(g, sys);
+    const int M = a.n_atoms;
+    const double cutoff = 14.0 * sys->sigma;
+    const int t1 = (int)std::ceil(cutoff / g->L[0]) + 1;
+    const int t2 = (int)std::ceil(cutoff / g->L[1]) + 1;
+    const int t3 = (int)std::ceil(cutoff / g->L[2]) + 1;
+    double* buf = (double*)ws(g, WS_S14, sizeof(double) * (4 * (size_t)M + 8));
+    k_overlap<<<(M + 127) / 128, 128, 0, g->stream>>>(M, a.d_boxes, g->L[0], g->L[1], g->L[2],
+                                                     sys->sigma, cutoff, t1, t2, t3, buf, buf + M);
+    OF_LAUNCH_CHECK();
+    if (e_c) {
+        k_sum_product<<<1, 256, 0, g->stream>>>(M, buf, nullptr, red_ctx(g, 118));
+        OF_LAUNCH_CHECK();
+        fetch_scalars(g, 118, 1, e_c);
+    }
+    if (fc_host) {
+        OF_CUDA(cudaMemcpyAsync(fc_host, buf + M, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost,
+                                g->stream));
+        OF_CUDA(cudaStreamSynchronize(g->stream));
+    }
+}
+
+void pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self) {
+    pseudocharge_impl(g, sys, b, e_self);
+}
+
+void forces(of_grid* g, const of_system* sys, const double* phi, double* F) {
+    AtomSet a = upload_atoms(g, sys);
+    Gauss q = gauss(sys);
+    const int M = a.n_atoms;
+    const size_t nparts = (size_t)M * a.max_planes * 3;
+    double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + 3 * (size_t)M + 8));
+    double* per_atom = part + nparts;
+    k_forces<<<dim3(M, a.max_planes), 256, 0, g->stream>>>(g->d, g->h[0], g->h[1], g->h[2],
+                                                         a.d_boxes, q, phi, part, a.max_planes);
+    OF_LAUNCH_CHECK();
+    k_sum_planes<<<(3 * M + 127) / 128, 128, 0, g->stream>>>(M, a.max_planes, 3, part, g->dV,
+                                                            per_atom);
+    OF_LAUNCH_CHECK();
+    std::vector<double> fc(3 * (size_t)M);
+    overlap_correction(g, sys, nullptr, fc.data());   // synchronises the stream
+    OF_CUDA(cudaMemcpyAsync(F, per_atom, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, g->stream));
+    OF_CUDA(cudaStreamSynchronize(g->stream));
+    for (size_t i = 0; i < fc.size(); ++i) F[i] += fc[i];
+}
+
+}  // namespace of
+
+using namespace of;
+
+extern "C" {
+
+of_status of_pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self) {
+    if (!g || !sys || !b) { set_error("of_pseudocharge: null argument"); return OF_EINVAL; }
+    try {
+        pseudocharge(g, sys, b, e_self);
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+of_status of_forces(of_grid* g, const of_system* sys, const double* u, const double* phi,
+                    double* F) {
+    (void)u;
+    if (!g || !sys || !phi || !F) { set_error("of_forces: null argument"); return OF_EINVAL; }
+    try {
+        forces(g, sys, phi, F);
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"

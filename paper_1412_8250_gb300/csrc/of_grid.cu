@@ -1,0 +1,167 @@
+// Grid handle, workspace, error reporting and the plain Laplacian entry point.
+#include <cstdarg>
+#include <cstring>
+#include <cmath>
+
+#include "of_stencil.cuh"
+
+namespace of {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int num_sms() {
+    static int cached = 0;
+    if (!cached) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached = v > 0 ? v : 1;
+    }
+    return cached;
+}
+
+void* ws(of_grid* g, int slot, size_t bytes) {
+    Buffer& b = g->pool[slot];
+    if (b.bytes < bytes) {
+        if (b.ptr) OF_CUDA(cudaFree(b.ptr));
+        b.ptr = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.ptr, bytes);
+        if (e != cudaSuccess) {
+            set_error("cudaMalloc(%zu) for workspace slot %d: %s", bytes, slot, cudaGetErrorString(e));
+            throw Error{OF_ENOMEM};
+        }
+        b.bytes = bytes;
+    }
+    return b.ptr;
+}
+
+void fetch_scalars(of_grid* g, int first, int count, double* out) {
+    OF_CUDA(cudaMemcpyAsync(g->s.host + first, g->s.scalars + first, sizeof(double) * count,
+                            cudaMemcpyDeviceToHost, g->stream));
+    OF_CUDA(cudaStreamSynchronize(g->stream));
+    std::memcpy(out, g->s.host + first, sizeof(double) * count);
+}
+
+// Weights of Eq. FD:Laplacian:
+//   w_0 = -(1/h^2) sum_{q=1}^N 1/q^2,  w_p = 2 (-1)^{p+1} (N!)^2 / (h^2 p^2 (N-p)! (N+p)!).
+static void fd_weights(int N, double h, double* w) {
+    double s = 0.0;
+    for (int q = 1; q <= N; ++q) s += 1.0 / ((double)q * q);
+    w[0] = -s / (h * h);
+    for (int p = 1; p <= N; ++p) {
+        // (N!)^2 / ((N-p)! (N+p)!) = prod_{k=1}^{p} (N-p+k)/(N+k)
+        double ratio = 1.0;
+        for (int k = 1; k <= p; ++k) ratio *= (double)(N - p + k) / (double)(N + k);
+        const double sgn = (p % 2 == 1) ? 1.0 : -1.0;
+        w[p] = 2.0 * sgn * ratio / (h * h * p * p);
+    }
+    for (int p = N + 1; p <= OF_MAX_N; ++p) w[p] = 0.0;
+}
+
+// ---------------------------------------------------------------- plain Laplacian
+template <typename T>
+struct OpLap {
+    const T* x;
+    T* y;
+    __device__ bool begin() { return true; }
+    __device__ T load(long long i) const { return __ldg(x + i); }
+    __device__ void store(long long i, T, T lap) { y[i] = lap; }
+    __device__ void end() {}
+};
+
+void laplacian(of_grid* g, of_dtype dt, const void* x, void* y) {
+    if (dt == OF_F64) {
+        launch_stencil<double, 2>(g, g->w64, OpLap<double>{(const double*)x, (double*)y});
+    } else if (dt == OF_F32) {
+        launch_stencil<float, 4>(g, g->w32, OpLap<float>{(const float*)x, (float*)y});
+    } else {
+        OF_REQUIRE(false, OF_EINVAL, "unknown dtype %d", (int)dt);
+    }
+}
+
+}  // namespace of
+
+using namespace of;
+
+extern "C" {
+
+const char* of_last_error(void) { return of::g_err; }
+
+of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3,
+                         int fd_half_order, void* stream, of_grid** out) {
+    if (!out) { set_error("of_grid_create: out is NULL"); return OF_EINVAL; }
+    *out = nullptr;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || !(L1 > 0) || !(L2 > 0) || !(L3 > 0)) {
+        set_error("of_grid_create: bad sizes n=(%d,%d,%d) L=(%g,%g,%g)", n1, n2, n3, L1, L2, L3);
+        return OF_EINVAL;
+    }
+    if (fd_half_order != 1 && fd_half_order != 3 && fd_half_order != 6) {
+        set_error("of_grid_create: fd_half_order %d not in {1, 3, 6}", fd_half_order);
+        return OF_EINVAL;
+    }
+    of_grid* g = new (std::nothrow) of_grid();
+    if (!g) { set_error("of_grid_create: host allocation failed"); return OF_ENOMEM; }
+    try {
+        g->d = Dims{n1, n2, n3, (long long)n1 * n2 * n3};
+        g->L[0] = L1; g->L[1] = L2; g->L[2] = L3;
+        const int n[3] = {n1, n2, n3};
+        for (int a = 0; a < 3; ++a) g->h[a] = g->L[a] / n[a];
+        g->dV = g->h[0] * g->h[1] * g->h[2];
+        g->N = fd_half_order;
+        g->w64.centre = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            fd_weights(g->N, g->h[a], g->w64.w[a]);
+            g->w64.centre += 2.0 * g->w64.w[a][0];
+            for (int p = 0; p <= OF_MAX_N; ++p) g->w32.w[a][p] = (float)g->w64.w[a][p];
+        }
+        g->w32.centre = (float)g->w64.centre;
+        g->stream = (cudaStream_t)stream;
+        OF_CUDA(cudaGetDevice(&g->device));
+        g->pool.resize(WS_NSLOTS);
+        OF_CUDA(cudaMalloc(&g->s.partials, sizeof(double) * OF_RED_SLOTS * OF_MAX_RED_BLOCKS));
+        OF_CUDA(cudaMalloc(&g->s.counter, sizeof(unsigned int) * 4));
+        OF_CUDA(cudaMemset(g->s.counter, 0, sizeof(unsigned int) * 4));
+        OF_CUDA(cudaMalloc(&g->s.scalars, sizeof(double) * 256));
+        OF_CUDA(cudaMemset(g->s.scalars, 0, sizeof(double) * 256));
+        OF_CUDA(cudaMallocHost(&g->s.host, sizeof(double) * 256));
+        *out = g;
+        return OF_OK;
+    } catch (const Error& e) {
+        of_grid_destroy(g);
+        return e.code;
+    }
+}
+
+of_status of_grid_destroy(of_grid* g) {
+    if (!g) return OF_OK;
+    for (auto& b : g->pool)
+        if (b.ptr) cudaFree(b.ptr);
+    if (g->s.partials) cudaFree(g->s.partials);
+    if (g->s.counter) cudaFree(g->s.counter);
+    if (g->s.scalars) cudaFree(g->s.scalars);
+    if (g->s.host) cudaFreeHost(g->s.host);
+    delete g;
+    return OF_OK;
+}
+
+of_status of_laplacian_apply(of_grid* g, of_dtype dtype, const void* x, void* y) {
+    if (!g || !x || !y) { set_error("of_laplacian_apply: null argument"); return OF_EINVAL; }
+    if (x == y) { set_error("of_laplacian_apply: x and y must not alias"); return OF_EINVAL; }
+    try {
+        laplacian(g, dtype, x, y);
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/of.h"
+
+#define OF_MAX_N 6
+#define OF_RED_SLOTS 48          // scalars produced by one reduction kernel (max)
+#define OF_MAX_RED_BLOCKS 4096   // partial sums per slot
+
+namespace of {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+struct Error {
+    of_status code;
+};
+
+#define OF_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            ::of::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                   \
+                            cudaGetErrorString(e_));                                     \
+            throw ::of::Error{OF_ECUDA};                                                 \
+        }                                                                                \
+    } while (0)
+
+#define OF_LAUNCH_CHECK() OF_CUDA(cudaGetLastError())
+
+#define OF_REQUIRE(cond, code, ...)                                                      \
+    do {                                                                                 \
+        if (!(cond)) {                                                                   \
+            ::of::set_error(__VA_ARGS__);                                                \
+            throw ::of::Error{code};                                                     \
+        }                                                                                \
+    } while (0)
+
+// ---------------------------------------------------------------- grid
+struct Dims {
+    int n1, n2, n3;
+    long long n;
+};
+
+// Laplacian weights of Eq. FD:Laplacian per axis (index 0 = w_0), and their sum over axes of
+// the two centre terms.
+template <typename R>
+struct Weights {
+    R w[3][OF_MAX_N + 1];
+    R centre;   // 2 (w_0^x + w_0^y + w_0^z)
+};
+
+// Device scratch for deterministic two-level reductions and solver scalars.
+struct Scratch {
+    double* partials = nullptr;       // [OF_RED_SLOTS * OF_MAX_RED_BLOCKS]
+    unsigned int* counter = nullptr;  // block-arrival counter (one per reduction kernel)
+    double* scalars = nullptr;        // general device scalars [256]
+    double* host = nullptr;           // pinned host mirror [256]
+};
+
+// Growable pool of device buffers owned by a grid handle.
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace of
+
+struct of_grid {
+    of::Dims d;
+    double L[3];
+    double h[3];
+    double dV;
+    int N;
+    of::Weights<double> w64;
+    of::Weights<float> w32;
+    cudaStream_t stream;
+    int device;
+    of::Scratch s;
+    std::vector<of::Buffer> pool;    // named workspace slots, see of::ws()
+};
+
+namespace of {
+
+// Workspace slot ids (each a device buffer of at least the requested bytes).
+enum Slot {
+    WS_K0 = 0,   // Krylov vectors 0..7 (FP64 or FP32 / complex)
+    WS_K1, WS_K2, WS_K3, WS_K4, WS_K5, WS_K6, WS_K7,
+    WS_S0, WS_S1, WS_S2, WS_S3, WS_S4, WS_S5, WS_S6, WS_S7,   // SCF vectors
+    WS_S8, WS_S9, WS_S10, WS_S11, WS_S12, WS_S13, WS_S14, WS_S15,
+    WS_LR,       // kernel-solve warm starts
+    WS_AND,      // Anderson history
+    WS_ATOM,     // per-atom device data
+    WS_NSLOTS
+};
+
+void* ws(of_grid* g, int slot, size_t bytes);   // grow-only
+
+// Reduction bookkeeping: how many blocks a grid-sized kernel uses
+inline int red_blocks(long long work_items, int per_block) {
+    long long b = (work_items + per_block - 1) / per_block;
+    if (b > OF_MAX_RED_BLOCKS) b = OF_MAX_RED_BLOCKS;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// Reads `count` device scalars (starting at index first of g->s.scalars) to host.
+void fetch_scalars(of_grid* g, int first, int count, double* out);
+
+// ----------------------------------------------------------------------- device helpers
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic grid-wide sum of K per-thread values: block partials are stored in
+// `partials[k * OF_MAX_RED_BLOCKS + block]`; the last block to finish adds them in block
+// order and writes out[k].  Requires blockDim.x * blockDim.y * blockDim.z <= 1024 and a
+// multiple of 32; every thread of the block must call it.
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], double* partials,
+                                            unsigned int* counter, double* out) {
+    __shared__ double sh[32][K > 0 ? K : 1];
+    __shared__ bool last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = nthreads >> 5;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = lane < nwarps ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) partials[k * OF_MAX_RED_BLOCKS + bid] = s;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+        unsigned int prev = atomicAdd(counter, 1u);
+        last = (prev == (unsigned int)nblocks - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int b = tid; b < nblocks; b += nthreads)
+            s += ((volatile double*)partials)[k * OF_MAX_RED_BLOCKS + b];
+        s = warp_sum(s);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double s = lane < nwarps ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) {
+                out[k] = s;
+                v[k] = s;   // thread 0 of the last block also gets the totals
+            }
+        }
+    }
+    if (tid == 0) *counter = 0u;
+    return true;
+}
+
+// ------------------------------------------------------------- entry points of the units
+void laplacian(of_grid* g, of_dtype dt, const void* x, void* y);
+
+struct KrylovOpts {
+    double tol;
+    int max_iter;
+    int precision;
+    double inner_tol;
+    int check_every;
+};
+KrylovOpts krylov_opts(const of_solve_opts* o);
+
+// Poisson: -(1/4pi) L phi = rho (mean removed), phi mean-free on return.
+of_status poisson(of_grid* g, const double* rho, double* phi, const KrylovOpts& o,
+                  of_solve_info* info);
+// Poisson with rhs given as rho = a*b (elementwise product of two fields), used by NLCG.
+of_status poisson_product(of_grid* g, const double* a, const double* b, double* phi,
+                          const KrylovOpts& o, of_solve_info* info);
+// Shifted: (-(1/kf2) L + Q) W = P f, complex W interleaved.
+of_status shifted(of_grid* g, const double* f, double2 P, double2 Q, double kf2, double2* W,
+                  const KrylovOpts& o, of_solve_info* info);
+
+}  // namespace of

@@ -1,0 +1,562 @@
+// Krylov solvers driven by the FD Laplacian.
+//
+//  * Poisson (Eq. Poisson): -(1/4pi) L_h phi = rho, i.e. A phi = 4 pi (rho - mean rho) with
+//    A = -L_h symmetric positive semi-definite; CG on the mean-free subspace (the paper uses
+//    GMRES; CG is the natural choice for this SPD operator).
+//  * Shifted (Eqs. Helmholtz:beta / Helmholtz:alpha): (-(1/kf2) L_h + Q) W = P f with complex
+//    Q: the matrix is complex symmetric (A^T = A), so COCG (CG with the bilinear form r^T r)
+//    is used in place of the paper's GMRES on the real/imaginary split.
+//
+// Both run either in FP64, or as iterative refinement: an FP64 residual, an FP32 Krylov
+// solve of the correction to a loose relative tolerance, an FP64 update -- repeated until the
+// true FP64 residual meets the tolerance.
+//
+// Every iteration is two kernels: the stencil sweep forms p = r + beta p on the fly (halo
+// points included), writes p and A p and reduces p^T A p; the update kernel applies alpha,
+// updates x and r and reduces r^T r and |r|^2.  alpha, beta and the stopping flag live in
+// device memory, so the host only synchronises every `check_every` iterations.
+#include <cmath>
+#include <cstring>
+
+#include "of_stencil.cuh"
+
+namespace of {
+
+// Device solver state, all doubles so it can be fetched with fetch_scalars.
+struct KState {
+    double rr;                  // 0  Hermitian |r|^2
+    double tol2;                // 1  stop when rr <= tol2
+    double rho_re, rho_im;      // 2  bilinear r^T r (= rr for real fields)
+    double pAp_re, pAp_im;      // 4
+    double alpha_re, alpha_im;  // 6
+    double beta_re, beta_im;    // 8
+    double done;                // 10
+    double iters;               // 11
+    double maxit;               // 12
+    double breakdown;           // 13
+    double red[4];              // 14 reduction outputs
+};
+constexpr int KSTATE_DOUBLES = sizeof(KState) / sizeof(double);
+constexpr int KS64 = 128;   // offsets in g->s.scalars
+constexpr int KS32 = 160;
+
+static KState* kstate(of_grid* g, int off) { return (KState*)(g->s.scalars + off); }
+
+template <typename T> struct KT;
+template <> struct KT<double> { static constexpr bool cplx = false; using R = double; };
+template <> struct KT<float> { static constexpr bool cplx = false; using R = float; };
+template <> struct KT<double2> { static constexpr bool cplx = true; using R = double; };
+template <> struct KT<float2> { static constexpr bool cplx = true; using R = float; };
+
+// complex-or-real helpers: a scalar s (re, im) times a field value
+__device__ __forceinline__ double cs_mul(double2 s, double v) { return s.x * v; }
+__device__ __forceinline__ float cs_mul(double2 s, float v) { return (float)s.x * v; }
+__device__ __forceinline__ double2 cs_mul(double2 s, double2 v) {
+    return make_double2(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
+}
+__device__ __forceinline__ float2 cs_mul(double2 s, float2 v) {
+    const float a = (float)s.x, b = (float)s.y;
+    return make_float2(a * v.x - b * v.y, a * v.y + b * v.x);
+}
+__device__ __forceinline__ double hn2(double v) { return v * v; }
+__device__ __forceinline__ double hn2(float v) { return (double)v * v; }
+__device__ __forceinline__ double hn2(double2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double hn2(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
+__device__ __forceinline__ double2 bil(double a, double b) { return make_double2(a * b, 0.0); }
+__device__ __forceinline__ double2 bil(float a, float b) { return make_double2((double)a * b, 0.0); }
+__device__ __forceinline__ double2 bil(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 bil(float2 a, float2 b) {
+    return make_double2((double)a.x * b.x - (double)a.y * b.y, (double)a.x * b.y + (double)a.y * b.x);
+}
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+
+// Operator A v = a (-L v) + Q v
+template <typename T>
+__device__ __forceinline__ T apply_A(T c, T lap, typename KT<T>::R a, double2 Q) {
+    return vadd(vmul(-a, lap), cs_mul(Q, c));
+}
+
+// ---------------------------------------------------------------- fused stencil ops
+// r = b - A x ; reduces |r|^2 and r^T r into the state and resets the iteration scalars.
+template <typename T>
+struct OpResidual {
+    const T* x;
+    const T* b;
+    T* r;
+    KState* st;
+    RedCtx rc;
+    typename KT<T>::R a;
+    double2 Q;
+    double acc[3];
+    __device__ bool begin() { acc[0] = acc[1] = acc[2] = 0.0; return true; }
+    __device__ T load(long long i) const { return x[i]; }
+    __device__ void store(long long i, T c, T lap) {
+        const T rv = vsub(b[i], apply_A(c, lap, a, Q));
+        r[i] = rv;
+        acc[0] += hn2(rv);
+        const double2 s = bil(rv, rv);
+        acc[1] += s.x;
+        acc[2] += s.y;
+    }
+    __device__ void end() {
+        if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) &&
+            threadIdx.x == 0 && threadIdx.y == 0) {
+            st->rr = acc[0];
+            st->rho_re = acc[1];
+            st->rho_im = acc[2];
+            st->beta_re = st->beta_im = 0.0;
+            st->breakdown = 0.0;
+            st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
+        }
+    }
+};
+
+// p_out = r + beta p_in (halo included), Ap = A p_out; reduces p^T A p and sets alpha.
+template <typename T>
+struct OpKrylovA {
+    const T* r;
+    const T* pin;
+    T* pout;
+    T* Ap;
+    KState* st;
+    RedCtx rc;
+    typename KT<T>::R a;
+    double2 Q;
+    double2 beta;
+    double acc[2];
+    __device__ bool begin() {
+        if (st->done != 0.0) return false;
+        beta = make_double2(st->beta_re, st->beta_im);
+        acc[0] = acc[1] = 0.0;
+        return true;
+    }
+    __device__ T load(long long i) const { return vadd(r[i], cs_mul(beta, pin[i])); }
+    __device__ void store(long long i, T c, T lap) {
+        pout[i] = c;
+        const T av = apply_A(c, lap, a, Q);
+        Ap[i] = av;
+        const double2 s = bil(c, av);
+        acc[0] += s.x;
+        acc[1] += s.y;
+    }
+    __device__ void end() {
+        if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) &&
+            threadIdx.x == 0 && threadIdx.y == 0) {
+            const double2 pAp = make_double2(acc[0], acc[1]);
+            st->pAp_re = pAp.x;
+            st->pAp_im = pAp.y;
+            const double mag = fabs(pAp.x) + fabs(pAp.y);
+            const bool bad = KT<T>::cplx ? !(mag > 0.0) : !(pAp.x > 0.0);
+            if (bad) {
+                st->breakdown = 1.0;
+                st->done = 1.0;
+            } else {
+                const double2 al = cdiv(make_double2(st->rho_re, st->rho_im), pAp);
+                st->alpha_re = al.x;
+                st->alpha_im = al.y;
+            }
+        }
+    }
+};
+
+// x += alpha p ; r -= alpha Ap ; reduces |r|^2 and r^T r ; sets beta, iteration count, done.
+template <typename T>
+__global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict__ x,
+                                                     T* __restrict__ r, const T* __restrict__ p,
+                                                     const T* __restrict__ Ap, KState* st,
+                                                     RedCtx rc) {
+    if (st->done != 0.0) return;
+    const double2 al = make_double2(st->alpha_re, st->alpha_im);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        x[i] = vadd(x[i], cs_mul(al, p[i]));
+        const T rv = vsub(r[i], cs_mul(al, Ap[i]));
+        r[i] = rv;
+        acc[0] += hn2(rv);
+        const double2 s = bil(rv, rv);
+        acc[1] += s.x;
+        acc[2] += s.y;
+    }
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        const double2 rho_new = make_double2(acc[1], acc[2]);
+        const double2 rho_old = make_double2(st->rho_re, st->rho_im);
+        st->rr = acc[0];
+        st->iters += 1.0;
+        if (acc[0] <= st->tol2 || st->iters >= st->maxit) {
+            st->done = 1.0;
+        } else if (!(fabs(rho_old.x) + fabs(rho_old.y) > 0.0)) {
+            st->breakdown = 1.0;
+            st->done = 1.0;
+        } else {
+            const double2 be = cdiv(rho_new, rho_old);
+            st->beta_re = be.x;
+            st->beta_im = be.y;
+        }
+        st->rho_re = rho_new.x;
+        st->rho_im = rho_new.y;
+    }
+}
+
+// ---------------------------------------------------------------- small vector kernels
+// sum of a[i] * (b ? b[i] : 1) over the grid into out[0]
+__global__ void __launch_bounds__(256) k_sum_product(long long n, const double* a, const double* b,
+                                                     RedCtx rc) {
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc[0] += b ? a[i] * b[i] : a[i];
+    grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// y = scale * (a*b - mean), mean = *sum_dev / n ; b may be null (then a alone)
+__global__ void k_form_rhs(long long n, const double* a, const double* b, const double* sum_dev,
+                           double scale, double* y) {
+    const double mean = *sum_dev / (double)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = scale * ((b ? a[i] * b[i] : a[i]) - mean);
+}
+
+__global__ void k_sub_mean(long long n, double* x, const double* sum_dev) {
+    const double mean = *sum_dev / (double)n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] -= mean;
+}
+
+// complex rhs b = P f
+__global__ void k_scale_complex(long long n, const double* f, double2 P, double2* b) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = make_double2(P.x * f[i], P.y * f[i]);
+}
+
+// |b|^2 into state tol2 (times tol^2) -- Hermitian norm of a real or complex field
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm_to_tol(long long n, const T* b, double tol,
+                                                     KState* st, RedCtx rc) {
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc[0] += hn2(b[i]);
+    if (grid_reduce<1>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        st->tol2 = tol * tol * acc[0];
+        st->red[1] = acc[0];
+    }
+}
+
+// FP64 residual -> FP32 right-hand side; fresh inner state with rr, r^T r in FP64
+template <typename T64, typename T32>
+__global__ void __launch_bounds__(256) k_demote(long long n, const T64* r64, T32* r32, T32* e32,
+                                                double inner_tol, const KState* outer, KState* st,
+                                                int maxit, RedCtx rc);
+
+template <>
+__global__ void __launch_bounds__(256) k_demote<double, float>(long long n, const double* r64, float* r32,
+                                                               float* e32, double inner_tol,
+                                                               const KState* outer, KState* st,
+                                                               int maxit, RedCtx rc) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = (float)r64[i];
+        r32[i] = v;
+        e32[i] = 0.0f;
+        acc[0] += (double)v * v;
+    }
+    acc[1] = acc[0];
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        st->rr = acc[0];
+        st->rho_re = acc[0];
+        st->rho_im = 0.0;
+        st->tol2 = inner_tol * inner_tol * outer->rr;
+        st->beta_re = st->beta_im = 0.0;
+        st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
+        st->iters = 0.0;
+        st->maxit = maxit;
+        st->breakdown = 0.0;
+    }
+}
+
+template <>
+__global__ void __launch_bounds__(256) k_demote<double2, float2>(long long n, const double2* r64,
+                                                                 float2* r32, float2* e32,
+                                                                 double inner_tol,
+                                                                 const KState* outer, KState* st,
+                                                                 int maxit, RedCtx rc) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = make_float2((float)r64[i].x, (float)r64[i].y);
+        r32[i] = v;
+        e32[i] = make_float2(0.0f, 0.0f);
+        acc[0] += hn2(v);
+        const double2 s = bil(v, v);
+        acc[1] += s.x;
+        acc[2] += s.y;
+    }
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        st->rr = acc[0];
+        st->rho_re = acc[1];
+        st->rho_im = acc[2];
+        st->tol2 = inner_tol * inner_tol * outer->rr;
+        st->beta_re = st->beta_im = 0.0;
+        st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
+        st->iters = 0.0;
+        st->maxit = maxit;
+        st->breakdown = 0.0;
+    }
+}
+
+__global__ void k_promote_add(long long n, double* x, const float* e) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] += (double)e[i];
+}
+__global__ void k_promote_add(long long n, double2* x, const float2* e) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = make_double2(x[i].x + (double)e[i].x, x[i].y + (double)e[i].y);
+}
+
+__global__ void k_init_state(KState* st, int maxit) {
+    st->iters = 0.0;
+    st->maxit = maxit;
+    st->done = 0.0;
+    st->breakdown = 0.0;
+}
+
+// ---------------------------------------------------------------- host drivers
+static int vec_blocks(long long n) { return red_blocks(n, 256 * 4); }
+
+KrylovOpts krylov_opts(const of_solve_opts* o) {
+    KrylovOpts k{1e-10, 20000, OF_F64, 1e-5, 8};
+    if (o) {
+        if (o->tol > 0) k.tol = o->tol;
+        if (o->max_iter > 0) k.max_iter = o->max_iter;
+        k.precision = o->precision;
+        if (o->inner_tol > 0) k.inner_tol = o->inner_tol;
+        if (o->check_every > 0) k.check_every = o->check_every;
+    }
+    return k;
+}
+
+// Arena of Krylov vectors: FP64 (r, pa, pb, Ap, b) and FP32 (r, pa, pb, Ap, e), complex-sized.
+struct Arena {
+    void* r64; void* pa64; void* pb64; void* Ap64; void* b64;
+    void* r32; void* pa32; void* pb32; void* Ap32; void* e32;
+};
+
+static Arena arena(of_grid* g) {
+    const size_t n = (size_t)g->d.n;
+    const size_t s64 = ((n * sizeof(double2) + 255) / 256) * 256;
+    const size_t s32 = ((n * sizeof(float2) + 255) / 256) * 256;
+    char* base = (char*)ws(g, WS_K0, 5 * s64 + 5 * s32);
+    Arena a;
+    a.r64 = base; a.pa64 = base + s64; a.pb64 = base + 2 * s64; a.Ap64 = base + 3 * s64;
+    a.b64 = base + 4 * s64;
+    char* b32 = base + 5 * s64;
+    a.r32 = b32; a.pa32 = b32 + s32; a.pb32 = b32 + 2 * s32; a.Ap32 = b32 + 3 * s32;
+    a.e32 = b32 + 4 * s32;
+    return a;
+}
+
+// Runs Krylov iterations on state `st` until its done flag is set.  Returns host copy.
+template <typename T>
+static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
+                      typename KT<T>::R a, double2 Q, const Weights<typename KT<T>::R>& W,
+                      int check_every) {
+    KState* st = kstate(g, st_off);
+    const long long n = g->d.n;
+    constexpr int RY = KT<T>::cplx ? 1 : (sizeof(typename KT<T>::R) == 8 ? 2 : 4);
+    OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(T) * n, g->stream));
+    T* p[2] = {pa, pb};
+    int ping = 0;
+    KState h;
+    for (;;) {
+        for (int k = 0; k < check_every; ++k) {
+            OpKrylovA<T> op{r, p[ping], p[1 - ping], Ap, st, red_ctx(g, 0), a, Q};
+            launch_stencil<T, RY>(g, W, op);
+            krylov_update<T><<<vec_blocks(n), 256, 0, g->stream>>>(n, x, r, p[1 - ping], Ap, st,
+                                                                    red_ctx(g, 0));
+            OF_LAUNCH_CHECK();
+            ping ^= 1;
+        }
+        fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+        if (h.done != 0.0) break;
+    }
+    return h;
+}
+
+template <typename T>
+static void residual(of_grid* g, int st_off, const T* x, const T* b, T* r, double a, double2 Q) {
+    constexpr int RY = KT<T>::cplx ? 1 : 2;
+    OpResidual<T> op{x, b, r, kstate(g, st_off), red_ctx(g, 0), (typename KT<T>::R)a, Q};
+    launch_stencil<T, RY>(g, g->w64, op);
+}
+
+// Solve A x = b (b already formed in arena b64, FP64), A = a(-L) + Q.  x: FP64 guess/solution.
+template <typename T64, typename T32>
+static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const KrylovOpts& o,
+                              of_solve_info* info) {
+    Arena ar = arena(g);
+    const long long n = g->d.n;
+    KState* st = kstate(g, KS64);
+    T64* b = (T64*)ar.b64;
+    T64* r = (T64*)ar.r64;
+    k_init_state<<<1, 1, 0, g->stream>>>(st, o.max_iter);
+    k_norm_to_tol<T64><<<vec_blocks(n), 256, 0, g->stream>>>(n, b, o.tol, st, red_ctx(g, 0));
+    OF_LAUNCH_CHECK();
+    residual<T64>(g, KS64, x, b, r, a, Q);
+    KState h;
+    fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
+    const double bb = h.tol2 / (o.tol * o.tol);
+    int total_iters = 0, refinements = 1;
+    of_status status = OF_OK;
+    if (!(bb > 0.0)) {   // zero right-hand side: the solution is zero
+        OF_CUDA(cudaMemsetAsync(x, 0, sizeof(T64) * n, g->stream));
+        h.rr = 0.0;
+    }
+    while (bb > 0.0 && h.rr > h.tol2) {
+        if (total_iters >= o.max_iter || refinements > 200) { status = OF_ENOCONV; break; }
+        if (o.precision == OF_F32) {
+            KState* s32 = kstate(g, KS32);
+            T32* r32 = (T32*)ar.r32;
+            T32* e32 = (T32*)ar.e32;
+            k_demote<T64, T32><<<vec_blocks(n), 256, 0, g->stream>>>(
+                n, r, r32, e32, o.inner_tol, st, s32, o.max_iter - total_iters, red_ctx(g, 0));
+            OF_LAUNCH_CHECK();
+            KState hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
+                                     (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
+            total_iters += (int)hi.iters;
+            k_promote_add<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, e32);
+            OF_LAUNCH_CHECK();
+            if (hi.breakdown != 0.0 && hi.iters == 0) { status = OF_EBREAKDOWN; break; }
+        } else {
+            KState hi = iterate<T64>(g, KS64, x, r, (T64*)ar.pa64, (T64*)ar.pb64, (T64*)ar.Ap64,
+                                     a, Q, g->w64, o.check_every);
+            total_iters = (int)hi.iters;
+            if (hi.breakdown != 0.0 && hi.rr > hi.tol2) { status = OF_EBREAKDOWN; break; }
+        }
+        residual<T64>(g, KS64, x, b, r, a, Q);   // true residual; restarts the recurrence
+        ++refinements;
+        fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
+    }
+    if (info) {
+        info->iterations += total_iters;
+        info->refinements += refinements;
+        info->rel_residual = bb > 0 ? std::sqrt(h.rr / bb) : 0.0;
+    }
+    if (status == OF_ENOCONV)
+        set_error("Krylov solve: %d iterations, relative residual %.3e > tol %.1e", total_iters,
+                  bb > 0 ? std::sqrt(h.rr / bb) : 0.0, o.tol);
+    if (status == OF_EBREAKDOWN) set_error("Krylov solve: breakdown after %d iterations", total_iters);
+    return status;
+}
+
+static void remove_mean(of_grid* g, double* x) {
+    const long long n = g->d.n;
+    k_sum_product<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, nullptr, red_ctx(g, 120));
+    k_sub_mean<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, g->s.scalars + 120);
+    OF_LAUNCH_CHECK();
+}
+
+static of_status poisson_impl(of_grid* g, const double* a, const double* b, double* phi,
+                              const KrylovOpts& o, of_solve_info* info) {
+    const long long n = g->d.n;
+    Arena ar = arena(g);
+    k_sum_product<<<vec_blocks(n), 256, 0, g->stream>>>(n, a, b, red_ctx(g, 120));
+    k_form_rhs<<<vec_blocks(n), 256, 0, g->stream>>>(n, a, b, g->s.scalars + 120, 4.0 * M_PI,
+                                                     (double*)ar.b64);
+    OF_LAUNCH_CHECK();
+    of_status st = solve_formed<double, float>(g, phi, 1.0, make_double2(0.0, 0.0), o, info);
+    remove_mean(g, phi);
+    return st;
+}
+
+of_status poisson(of_grid* g, const double* rho, double* phi, const KrylovOpts& o,
+                  of_solve_info* info) {
+    return poisson_impl(g, rho, nullptr, phi, o, info);
+}
+
+of_status poisson_product(of_grid* g, const double* a, const double* b, double* phi,
+                          const KrylovOpts& o, of_solve_info* info) {
+    return poisson_impl(g, a, b, phi, o, info);
+}
+
+of_status shifted(of_grid* g, const double* f, double2 P, double2 Q, double kf2, double2* W,
+                  const KrylovOpts& o, of_solve_info* info) {
+    const long long n = g->d.n;
+    Arena ar = arena(g);
+    k_scale_complex<<<vec_blocks(n), 256, 0, g->stream>>>(n, f, P, (double2*)ar.b64);
+    OF_LAUNCH_CHECK();
+    return solve_formed<double2, float2>(g, W, 1.0 / kf2, Q, o, info);
+}
+
+}  // namespace of
+
+using namespace of;
+
+extern "C" {
+
+void of_default_solve_opts(of_solve_opts* o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 20000;
+    o->precision = OF_F64;
+    o->inner_tol = 1e-5;
+    o->check_every = 8;
+}
+
+of_status of_poisson_solve(of_grid* g, const double* rho, double* phi, const of_solve_opts* opts,
+                           of_solve_info* info) {
+    if (!g || !rho || !phi) { set_error("of_poisson_solve: null argument"); return OF_EINVAL; }
+    try {
+        if (info) std::memset(info, 0, sizeof(*info));
+        return poisson(g, rho, phi, krylov_opts(opts), info);
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double* P,
+                          const double* Q, double kf2, double* W, const of_solve_opts* opts,
+                          of_solve_info* info) {
+    if (!g || !f || !P || !Q || !W || nshift < 1 || !(kf2 > 0)) {
+        set_error("of_kernel_solve: bad argument");
+        return OF_EINVAL;
+    }
+    try {
+        if (info) std::memset(info, 0, sizeof(*info));
+        KrylovOpts o = krylov_opts(opts);
+        of_status worst = OF_OK;
+        for (int s = 0; s < nshift; ++s) {
+            of_solve_info one{};
+            of_status st = shifted(g, f, make_double2(P[2 * s], P[2 * s + 1]),
+                                   make_double2(Q[2 * s], Q[2 * s + 1]), kf2,
+                                   (double2*)W + (size_t)s * g->d.n, o, &one);
+            if (info) {
+                info->iterations += one.iterations;
+                info->refinements += one.refinements;
+                info->rel_residual = std::max(info->rel_residual, one.rel_residual);
+            }
+            if (st != OF_OK && worst == OF_OK) worst = st;
+        }
+        return worst;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,849 @@
+// Electronic ground state (Sec. 3.3.1): the constrained non-linear CG of App. C for the inner
+// minimisation at fixed V_LR, the kernel map V[u] of Eq. MVF via the shifted solves of Sec. 3.1,
+// Anderson mixing of App. D on the fixed point V_LR = V[U(V_LR)], and the ground-state energy
+// of Eq. GroundStateEnergy.
+//
+// Discrete choices shared with the paper's statement:
+//  * inner products <a, b> = dV sum a b; the constraint dV sum u^2 = N_e;
+//  * vW energy -(lambda/2) <u, L_h u>, so that dE/du = 2 dV H u exactly on the grid;
+//  * the NLCG moves along the conjugate direction d_q, restarts every N_restart steps and when
+//    the Polak-Ribiere xi <= 0 or d is not a descent direction;
+//  * the line energy E(s) of u(s) = sqrt(N_e) (u + s d)/||u + s d|| is exact: by linearity
+//    of the Poisson problem phi(s) = c^2 (phi_uu + 2 s phi_ud + s^2 phi_dd) + phi_b, so the
+//    Hartree, vW and V_LR parts are polynomials in s times powers of c^2 built from one
+//    fused multi-dot pass; only the TF + xc part needs a grid pass per trial s;
+//  * Brent's method (own implementation) on a bracket grown from the previous step.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "of_functional.cuh"
+#include "of_stencil.cuh"
+
+namespace of {
+
+// indices into g->s.scalars for reduction outputs of this unit
+enum {
+    SC_UHU = 0, SC_ULU = 1,
+    SC_RR = 2, SC_RRP = 3,
+    SC_RD = 4, SC_UD = 5, SC_DD = 6, SC_UU = 7,
+    SC_DLD = 8, SC_ULD = 9,
+    SC_MD = 10,        // 13 line-search moments
+    SC_LINE = 25,
+    SC_EN = 26,        // 4 energy sums
+    SC_TLR = 30,
+    SC_FP = 32,        // |f|^2, |Vhat|^2
+    SC_GRAM = 40       // Anderson Gram entries
+};
+
+static inline int vb(long long n) { return red_blocks(n, 256 * 4); }
+
+#define GRID_LOOP(i, n) \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
+         i += (long long)gridDim.x * blockDim.x)
+
+struct FnParams {
+    double lam, mu, alpha, beta;
+};
+
+// ---------------------------------------------------------------- Hamiltonian (stencil op)
+// Hu = -(lam/2) L u + (V_TF + V_xc + phi + mu V) u ; Lu = L u ; sums <u,Hu>, <u,Lu>
+struct OpHamiltonian {
+    const double* u;
+    const double* phi;
+    const double* V;   // may be null
+    double* Hu;
+    double* Lu;        // may be null
+    FnParams fn;
+    RedCtx rc;
+    double acc[2];
+    __device__ bool begin() { acc[0] = acc[1] = 0.0; return true; }
+    __device__ double load(long long i) const { return __ldg(u + i); }
+    __device__ void store(long long i, double c, double lap) {
+        const double rho = c * c;
+        double etf, vtf, exc, vxc;
+        thomas_fermi(rho, etf, vtf);
+        lda_xc(rho, exc, vxc);
+        double pot = vtf + vxc + phi[i];
+        if (V) pot += fn.mu * V[i];
+        const double h = -0.5 * fn.lam * lap + pot * c;
+        Hu[i] = h;
+        if (Lu) Lu[i] = lap;
+        acc[0] += c * h;
+        acc[1] += c * lap;
+    }
+    __device__ void end() { grid_reduce<2>(acc, rc.partials, rc.counter, rc.out); }
+};
+
+// Ld = L d ; sums <d, Ld>, <u, Ld>
+struct OpLapDot {
+    const double* d;
+    const double* u;
+    double* Ld;
+    RedCtx rc;
+    double acc[2];
+    __device__ bool begin() { acc[0] = acc[1] = 0.0; return true; }
+    __device__ double load(long long i) const { return __ldg(d + i); }
+    __device__ void store(long long i, double c, double lap) {
+        Ld[i] = lap;
+        acc[0] += c * lap;
+        acc[1] += u[i] * lap;
+    }
+    __device__ void end() { grid_reduce<2>(acc, rc.partials, rc.counter, rc.out); }
+};
+
+// y = scale * L x (no reduction)
+struct OpScaledLap {
+    const double* x;
+    double* y;
+    double scale;
+    __device__ bool begin() { return true; }
+    __device__ double load(long long i) const { return __ldg(x + i); }
+    __device__ void store(long long i, double, double lap) { y[i] = scale * lap; }
+    __device__ void end() {}
+};
+
+// Energy sums at u: [C_F rho^{5/3}, u L u, eps_xc rho, (rho + b) phi]
+struct OpEnergy {
+    const double* u;
+    const double* b;
+    const double* phi;
+    RedCtx rc;
+    double acc[4];
+    __device__ bool begin() { acc[0] = acc[1] = acc[2] = acc[3] = 0.0; return true; }
+    __device__ double load(long long i) const { return __ldg(u + i); }
+    __device__ void store(long long i, double c, double lap) {
+        const double rho = c * c;
+        double etf, vtf, exc, vxc;
+        thomas_fermi(rho, etf, vtf);
+        lda_xc(rho, exc, vxc);
+        acc[0] += etf;
+        acc[1] += c * lap;
+        acc[2] += exc;
+        acc[3] += (rho + b[i]) * phi[i];
+    }
+    __device__ void end() { grid_reduce<4>(acc, rc.partials, rc.counter, rc.out); }
+};
+
+// ---------------------------------------------------------------- elementwise kernels
+// r = -2 (Hu - eta u) ; sums |r|^2, <r, r_prev>
+__global__ void __launch_bounds__(256) k_gradient(long long n, const double* Hu, const double* u,
+                                                  const double* eta_raw, double inv_ne_dv,
+                                                  const double* rprev, double* r, RedCtx rc) {
+    const double eta = (*eta_raw) * inv_ne_dv;
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double v = -2.0 * (Hu[i] - eta * u[i]);
+        r[i] = v;
+        acc[0] += v * v;
+        if (rprev) acc[1] += v * rprev[i];
+    }
+    grid_reduce<2>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// d = r + xi d_prev ; sums <r,d>, <u,d>, <d,d>, <u,u>
+__global__ void __launch_bounds__(256) k_direction(long long n, const double* r, const double* dprev,
+                                                   double xi, const double* u, double* d, RedCtx rc) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double v = (xi != 0.0 && dprev) ? r[i] + xi * dprev[i] : r[i];
+        d[i] = v;
+        acc[0] += r[i] * v;
+        acc[1] += u[i] * v;
+        acc[2] += v * v;
+        acc[3] += u[i] * u[i];
+    }
+    grid_reduce<4>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// Line-search moments (all raw sums): with A = phi - D, q0 = u^2, q1 = u d, q2 = d^2:
+// [q0.A, q0.B, q0.C, q1.B, q1.C, q2.C, q0.D, q1.D, q2.D, V.q0, V.q1, V.q2, b.D]
+__global__ void __launch_bounds__(256) k_line_moments(long long n, const double* u, const double* d,
+                                                      const double* V, const double* phi,
+                                                      const double* D, const double* B,
+                                                      const double* C, const double* b, RedCtx rc) {
+    double acc[13];
+#pragma unroll
+    for (int k = 0; k < 13; ++k) acc[k] = 0.0;
+    GRID_LOOP(i, n) {
+        const double uu = u[i], dd = d[i];
+        const double q0 = uu * uu, q1 = uu * dd, q2 = dd * dd;
+        const double Di = D[i], Ai = phi[i] - Di, Bi = B[i], Ci = C[i];
+        acc[0] += q0 * Ai;
+        acc[1] += q0 * Bi;
+        acc[2] += q0 * Ci;
+        acc[3] += q1 * Bi;
+        acc[4] += q1 * Ci;
+        acc[5] += q2 * Ci;
+        acc[6] += q0 * Di;
+        acc[7] += q1 * Di;
+        acc[8] += q2 * Di;
+        if (V) {
+            const double v = V[i];
+            acc[9] += v * q0;
+            acc[10] += v * q1;
+            acc[11] += v * q2;
+        }
+        acc[12] += b[i] * Di;
+    }
+    grid_reduce<13>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// sum of TF + xc energy densities at rho = c2 (u + s d)^2
+__global__ void __launch_bounds__(256) k_line_energy(long long n, const double* u, const double* d,
+                                                     double s, double c2, RedCtx rc) {
+    double acc[1] = {0.0};
+    GRID_LOOP(i, n) {
+        const double w = u[i] + s * d[i];
+        acc[0] += tf_xc_energy(c2 * w * w);
+    }
+    grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// u <- c (u + s d) ; phi <- c^2 (phi - D + 2 s B + s^2 C) + D
+__global__ void k_step(long long n, double* u, const double* d, double* phi, const double* D,
+                       const double* B, const double* C, double s, double c) {
+    const double c2 = c * c;
+    GRID_LOOP(i, n) {
+        u[i] = c * (u[i] + s * d[i]);
+        const double Di = D[i];
+        phi[i] = c2 * (phi[i] - Di + 2.0 * s * B[i] + s * s * C[i]) + Di;
+    }
+}
+
+__global__ void k_scale(long long n, double* x, double a) {
+    GRID_LOOP(i, n) x[i] *= a;
+}
+
+// y = u^2 + b
+__global__ void k_density_plus(long long n, const double* u, const double* b, double* y) {
+    GRID_LOOP(i, n) y[i] = u[i] * u[i] + b[i];
+}
+
+// g_a = max(u, floor)^{2 alpha}, g_b = max(u, floor)^{2 beta}
+__global__ void k_powers(long long n, const double* u, double two_a, double two_b, double* ga,
+                         double* gb) {
+    GRID_LOOP(i, n) {
+        const double uf = fmax(u[i], OF_U_FLOOR);
+        ga[i] = pow(uf, two_a);
+        gb[i] = pow(uf, two_b);
+    }
+}
+
+// V_LR = C_F [alpha u^{2(alpha-1)} V_beta + beta u^{2(beta-1)} V_alpha], V_e = sum over
+// conjugate pairs of 2 Re W ; sum of u^{2 alpha} V_beta + u^{2 beta} V_alpha.
+struct PairPtrs {
+    const double2* Wa[4];
+    const double2* Wb[4];
+    int npairs;
+};
+__global__ void __launch_bounds__(256) k_lr_assemble(long long n, const double* u, PairPtrs W,
+                                                     double alpha, double beta, double* vlr,
+                                                     RedCtx rc) {
+    double acc[1] = {0.0};
+    GRID_LOOP(i, n) {
+        double Va = 0.0, Vb = 0.0;
+        for (int k = 0; k < W.npairs; ++k) {
+            Va += 2.0 * W.Wa[k][i].x;
+            Vb += 2.0 * W.Wb[k][i].x;
+        }
+        const double uf = fmax(u[i], OF_U_FLOOR);
+        const double ra = pow(uf, 2.0 * alpha), rb = pow(uf, 2.0 * beta);
+        vlr[i] = OF_CF * (alpha * (ra / (uf * uf)) * Vb + beta * (rb / (uf * uf)) * Va);
+        acc[0] += ra * Vb + rb * Va;
+    }
+    grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// f = Vhat - V ; sums |f|^2, |Vhat|^2
+__global__ void __launch_bounds__(256) k_fp_residual(long long n, const double* Vhat, const double* V,
+                                                     double* f, RedCtx rc) {
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double v = Vhat[i] - V[i];
+        f[i] = v;
+        acc[0] += v * v;
+        acc[1] += Vhat[i] * Vhat[i];
+    }
+    grid_reduce<2>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// y = a - b
+__global__ void k_diff(long long n, const double* a, const double* b, double* y) {
+    GRID_LOOP(i, n) y[i] = a[i] - b[i];
+}
+
+struct HistPtrs {
+    const double* S[8];
+    const double* Y[8];
+    double g[8];
+    int m;
+};
+
+// Gram entries Y_a . Y_b (a <= b, row-major upper triangle) then Y_a . f
+template <int M>
+__global__ void __launch_bounds__(256) k_gram(long long n, HistPtrs H, const double* f, RedCtx rc) {
+    constexpr int K = M * (M + 1) / 2 + M;
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    GRID_LOOP(i, n) {
+        double y[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) y[a] = H.Y[a][i];
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = a; b < M; ++b) acc[k++] += y[a] * y[b];
+        const double fi = f[i];
+#pragma unroll
+        for (int a = 0; a < M; ++a) acc[k++] += y[a] * fi;
+    }
+    grid_reduce<K>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// V <- V + zeta f - sum_a g_a (S_a + zeta Y_a)
+__global__ void k_anderson_update(long long n, double* V, const double* f, double zeta, HistPtrs H) {
+    GRID_LOOP(i, n) {
+        double v = V[i] + zeta * f[i];
+        for (int a = 0; a < H.m; ++a) v -= H.g[a] * (H.S[a][i] + zeta * H.Y[a][i]);
+        V[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------- host helpers
+static double sc(of_grid* g, int i) {
+    double v;
+    fetch_scalars(g, i, 1, &v);
+    return v;
+}
+
+static FnParams fn_params(const of_functional* fn) {
+    return FnParams{fn->lambda, fn->mu, fn->alpha, fn->beta};
+}
+
+// Brent's method for a minimum inside the bracket a < b < c with f(b) < f(a), f(c)
+// (parabolic interpolation through the three best points, golden-section fallback).
+template <class F>
+static double brent_minimise(F&& f, double a, double b, double c, double fb, double tol,
+                             int max_iter, int& evals) {
+    const double cgold = 0.3819660112501051;
+    double lo = std::min(a, c), hi = std::max(a, c);
+    double x = b, w = b, v = b, fx = fb, fw = fb, fv = fb;
+    double e = 0.0, step = 0.0;
+    for (int it = 0; it < max_iter; ++it) {
+        const double xm = 0.5 * (lo + hi);
+        const double tol1 = tol * std::fabs(x) + 1e-11, tol2 = 2.0 * tol1;
+        if (std::fabs(x - xm) <= tol2 - 0.5 * (hi - lo)) break;
+        bool golden = true;
+        if (std::fabs(e) > tol1) {
+            double r = (x - w) * (fx - fv);
+            double q = (x - v) * (fx - fw);
+            double p = (x - v) * q - (x - w) * r;
+            q = 2.0 * (q - r);
+            if (q > 0.0) p = -p;
+            q = std::fabs(q);
+            const double etemp = e;
+            if (std::fabs(p) < std::fabs(0.5 * q * etemp) && p > q * (lo - x) && p < q * (hi - x)) {
+                e = step;
+                step = p / q;
+                const double u = x + step;
+                if (u - lo < tol2 || hi - u < tol2) step = (xm - x >= 0) ? tol1 : -tol1;
+                golden = false;
+            }
+        }
+        if (golden) {
+            e = (x >= xm) ? lo - x : hi - x;
+            step = cgold * e;
+        }
+        const double u = (std::fabs(step) >= tol1) ? x + step : x + (step >= 0 ? tol1 : -tol1);
+        const double fu = f(u);
+        ++evals;
+        if (fu <= fx) {
+            if (u >= x) lo = x; else hi = x;
+            v = w; fv = fw;
+            w = x; fw = fx;
+            x = u; fx = fu;
+        } else {
+            if (u < x) lo = u; else hi = u;
+            if (fu <= fw || w == x) {
+                v = w; fv = fw;
+                w = u; fw = fu;
+            } else if (fu <= fv || v == x || v == w) {
+                v = u; fv = fu;
+            }
+        }
+    }
+    return x;
+}
+
+// Bracket from s = 0 along increasing s (golden expansion while f decreases, shrink while it
+// does not), then Brent.  Returns 0 when no decrease is found.
+template <class F>
+static double line_minimum(F&& f, double s_try, int& evals) {
+    const double gold = 1.618033988749895;
+    const double f0 = f(0.0);
+    double b = std::fabs(s_try), fb = f(b);
+    double a = 0.0, c, fc;
+    evals += 2;
+    if (fb < f0) {
+        c = b * (1.0 + gold);
+        fc = f(c);
+        ++evals;
+        int k = 0;
+        while (fc < fb && k < 60) {
+            a = b;
+            b = c; fb = fc;
+            c = b + gold * (b - a);
+            fc = f(c);
+            ++evals;
+            ++k;
+        }
+        if (fc < fb) return c;
+        if (!(fc > fb)) return b;   // flat to rounding between b and c
+    } else {
+        c = b; fc = fb;
+        b = c / (1.0 + gold);
+        fb = f(b);
+        ++evals;
+        int k = 0;
+        while (fb >= f0 && k < 60) {
+            c = b; fc = fb;
+            b = c / (1.0 + gold);
+            fb = f(b);
+            ++evals;
+            ++k;
+        }
+        if (fb >= f0) return 0.0;
+        a = 0.0;
+    }
+    return brent_minimise(f, a, b, c, fb, 1e-8, 100, evals);
+}
+
+// Device vectors used by the ground-state driver.
+struct ScfVecs {
+    double *Hu, *Lu, *r, *rp, *d, *dp, *B, *C, *Ld, *b, *D, *rho, *V, *Vhat;
+};
+
+static ScfVecs scf_vecs(of_grid* g) {
+    const size_t bytes = sizeof(double) * (size_t)g->d.n;
+    ScfVecs v;
+    double** p[] = {&v.Hu, &v.Lu, &v.r, &v.rp, &v.d, &v.dp, &v.B, &v.C, &v.Ld, &v.b, &v.D,
+                    &v.rho, &v.V, &v.Vhat};
+    for (int k = 0; k < 14; ++k) *p[k] = (double*)ws(g, WS_S0 + k, bytes);
+    return v;
+}
+
+struct ScfStats {
+    int nlcg = 0, poisson = 0, kernel = 0, line = 0;
+    double last_residual = 0.0;
+};
+
+// Poisson solve of rho = a*b (or a when b == null) with warm start in phi.
+static void poisson_into(of_grid* g, const double* a, const double* b, double* phi,
+                         const KrylovOpts& o, ScfStats& st) {
+    of_solve_info info{};
+    of_status s = b ? poisson_product(g, a, b, phi, o, &info) : poisson(g, a, phi, o, &info);
+    st.poisson += info.iterations;
+    if (s != OF_OK && s != OF_ENOCONV) throw Error{s};
+}
+
+// Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
+static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
+                 const double* V, double tol, int max_iter, int n_restart, const KrylovOpts& po,
+                 ScfStats& st) {
+    const long long n = g->d.n;
+    const double dV = g->dV;
+    const int nb = vb(n);
+    // normalise u and solve for its potential
+    k_sum_product<<<nb, 256, 0, g->stream>>>(n, u, u, red_ctx(g, SC_UU));
+    OF_LAUNCH_CHECK();
+    const double uu0 = sc(g, SC_UU) * dV;
+    OF_REQUIRE(uu0 > 0 && std::isfinite(uu0), OF_EINVAL, "initial u has zero or non-finite norm");
+    k_scale<<<nb, 256, 0, g->stream>>>(n, u, std::sqrt(Ne / uu0));
+    k_density_plus<<<nb, 256, 0, g->stream>>>(n, u, v.b, v.rho);
+    OF_LAUNCH_CHECK();
+    poisson_into(g, v.rho, nullptr, phi, po, st);
+
+    double rr_prev = 0.0, s_prev = 1e-2;
+    bool converged = false;
+    for (int q = 0; q <= max_iter; ++q) {
+        launch_stencil<double, 2>(g, g->w64,
+                                  OpHamiltonian{u, phi, fn.mu != 0.0 ? V : nullptr, v.Hu, v.Lu, fn,
+                                                red_ctx(g, SC_UHU)});
+        k_gradient<<<nb, 256, 0, g->stream>>>(n, v.Hu, u, g->s.scalars + SC_UHU, dV / Ne,
+                                              q > 0 ? v.rp : nullptr, v.r, red_ctx(g, SC_RR));
+        OF_LAUNCH_CHECK();
+        double h[4];
+        fetch_scalars(g, SC_UHU, 4, h);
+        const double rr = h[2], rrp = h[3];
+        st.last_residual = std::sqrt(dV * rr / Ne);
+        if (st.last_residual < tol) { converged = true; break; }
+        if (q == max_iter) break;
+        double xi = 0.0;
+        if (q > 0 && q % n_restart != 0) {
+            xi = (rr - rrp) / rr_prev;
+            if (!(xi > 0.0)) xi = 0.0;
+        }
+        k_direction<<<nb, 256, 0, g->stream>>>(n, v.r, v.dp, xi, u, v.d, red_ctx(g, SC_RD));
+        OF_LAUNCH_CHECK();
+        double m[4];
+        fetch_scalars(g, SC_RD, 4, m);
+        if (!(m[0] > 0.0) && xi != 0.0) {   // not a descent direction: restart along r
+            xi = 0.0;
+            k_direction<<<nb, 256, 0, g->stream>>>(n, v.r, v.dp, 0.0, u, v.d, red_ctx(g, SC_RD));
+            OF_LAUNCH_CHECK();
+            fetch_scalars(g, SC_RD, 4, m);
+        }
+        poisson_into(g, u, v.d, v.B, po, st);
+        poisson_into(g, v.d, v.d, v.C, po, st);
+        launch_stencil<double, 2>(g, g->w64, OpLapDot{v.d, u, v.Ld, red_ctx(g, SC_DLD)});
+        k_line_moments<<<nb, 256, 0, g->stream>>>(n, u, v.d, fn.mu != 0.0 ? V : nullptr, phi, v.D,
+                                                  v.B, v.C, v.b, red_ctx(g, SC_MD));
+        OF_LAUNCH_CHECK();
+        double mo[17];
+        fetch_scalars(g, SC_DLD, 15, mo);   // DLD, ULD, then the 13 moments
+        double uLu;
+        fetch_scalars(g, SC_ULU, 1, &uLu);
+        const double ud = m[1] * dV, dd = m[2] * dV, uu = m[3] * dV;
+        const double dLd = mo[0] * dV, uLd = mo[1] * dV, uLu_ = uLu * dV;
+        const double* M = mo + 2;
+        const double M00 = M[0] * dV, M01 = M[1] * dV, M02 = M[2] * dV, M11 = M[3] * dV,
+                     M12 = M[4] * dV, M22 = M[5] * dV, N0 = M[6] * dV, N1 = M[7] * dV,
+                     N2 = M[8] * dV, Vq0 = M[9] * dV, Vq1 = M[10] * dV, Vq2 = M[11] * dV,
+                     bD = M[12] * dV;
+        auto energy = [&](double s) -> double {
+            const double c2 = Ne / (uu + 2.0 * s * ud + s * s * dd);
+            k_line_energy<<<nb, 256, 0, g->stream>>>(n, u, v.d, s, c2, red_ctx(g, SC_LINE));
+            OF_LAUNCH_CHECK();
+            const double tfxc = sc(g, SC_LINE) * dV;
+            const double vw = -0.5 * fn.lam * c2 * (uLu_ + 2.0 * s * uLd + s * s * dLd);
+            const double vl = fn.mu != 0.0 ? fn.mu * c2 * (Vq0 + 2.0 * s * Vq1 + s * s * Vq2) : 0.0;
+            const double quart = M00 + 4.0 * s * M01 + 2.0 * s * s * M02 + 4.0 * s * s * M11 +
+                                 4.0 * s * s * s * M12 + s * s * s * s * M22;
+            const double hart = 0.5 * c2 * c2 * quart + c2 * (N0 + 2.0 * s * N1 + s * s * N2) + 0.5 * bD;
+            return tfxc + vw + vl + hart;
+        };
+        int evals = 0;
+        const double s = line_minimum(energy, s_prev, evals);
+        st.line += evals;
+        if (s == 0.0) break;   // energy flat to rounding along d: stagnated
+        const double c = std::sqrt(Ne / (uu + 2.0 * s * ud + s * s * dd));
+        k_step<<<nb, 256, 0, g->stream>>>(n, u, v.d, phi, v.D, v.B, v.C, s, c);
+        k_density_plus<<<nb, 256, 0, g->stream>>>(n, u, v.b, v.rho);
+        OF_LAUNCH_CHECK();
+        poisson_into(g, v.rho, nullptr, phi, po, st);   // polish (warm start is nearly exact)
+        std::swap(v.r, v.rp);
+        std::swap(v.d, v.dp);
+        rr_prev = rr;
+        s_prev = s;
+        st.nlcg += 1;
+    }
+    return converged;
+}
+
+// Kernel map V[u] (Eq. MVF, m = n = 0 term): V_LR into vlr, returns T_LR / C_F / dV sum.
+static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2, const double* u,
+                                double* vlr, double* Wws, const KrylovOpts& ko, ScfStats& st,
+                                of_solve_info* info_out) {
+    const long long n = g->d.n;
+    const int nb = vb(n);
+    OF_REQUIRE(fn->n_terms >= 2 && fn->n_terms <= 8 && fn->n_terms % 2 == 0, OF_EINVAL,
+               "kernel term needs 2..8 coefficients in conjugate pairs (got %d)", fn->n_terms);
+    for (int k = 0; k < fn->n_terms; k += 2) {
+        OF_REQUIRE(fn->P[2 * k] == fn->P[2 * k + 2] && fn->P[2 * k + 1] == -fn->P[2 * k + 3] &&
+                       fn->Q[2 * k] == fn->Q[2 * k + 2] && fn->Q[2 * k + 1] == -fn->Q[2 * k + 3],
+                   OF_EINVAL, "kernel coefficients %d and %d are not complex conjugates", k, k + 1);
+    }
+    const int npairs = fn->n_terms / 2;
+    double* scratch = (double*)ws(g, WS_LR, sizeof(double) * 4 * (size_t)n);
+    double *ga = scratch, *gb = scratch + n, *fa = scratch + 2 * n, *fb = scratch + 3 * n;
+    k_powers<<<nb, 256, 0, g->stream>>>(n, u, 2.0 * fn->alpha, 2.0 * fn->beta, ga, gb);
+    OF_LAUNCH_CHECK();
+    // f_e = -(1/kf2) L u^{2e}  (the m = n = 0 right-hand side of Sec. 3.1)
+    launch_stencil<double, 2>(g, g->w64, OpScaledLap{ga, fa, -1.0 / kf2});
+    launch_stencil<double, 2>(g, g->w64, OpScaledLap{gb, fb, -1.0 / kf2});
+    PairPtrs W{};
+    W.npairs = npairs;
+    for (int k = 0; k < npairs; ++k) {
+        const double2 P = make_double2(fn->P[4 * k], fn->P[4 * k + 1]);
+        const double2 Q = make_double2(fn->Q[4 * k], fn->Q[4 * k + 1]);
+        double2* Wa = (double2*)Wws + (size_t)(2 * k) * n;       // from u^{2 alpha}
+        double2* Wb = (double2*)Wws + (size_t)(2 * k + 1) * n;   // from u^{2 beta}
+        of_solve_info ia{}, ib{};
+        of_status s1 = shifted(g, fa, P, Q, kf2, Wa, ko, &ia);
+        of_status s2 = shifted(g, fb, P, Q, kf2, Wb, ko, &ib);
+        if (s1 != OF_OK && s1 != OF_ENOCONV) throw Error{s1};
+        if (s2 != OF_OK && s2 != OF_ENOCONV) throw Error{s2};
+        st.kernel += ia.iterations + ib.iterations;
+        if (info_out) {
+            info_out->iterations += ia.iterations + ib.iterations;
+            info_out->refinements += ia.refinements + ib.refinements;
+            info_out->rel_residual = std::max(info_out->rel_residual,
+                                              std::max(ia.rel_residual, ib.rel_residual));
+        }
+        W.Wa[k] = Wa;
+        W.Wb[k] = Wb;
+    }
+    k_lr_assemble<<<nb, 256, 0, g->stream>>>(n, u, W, fn->alpha, fn->beta, vlr, red_ctx(g, SC_TLR));
+    OF_LAUNCH_CHECK();
+    return sc(g, SC_TLR);
+}
+
+// Small dense solve G x = y (Gaussian elimination, partial pivoting); false if singular.
+static bool dense_solve(std::vector<double> G, std::vector<double> y, int m, std::vector<double>& x) {
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(G[i * m + i]));
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (std::fabs(G[r * m + c]) > std::fabs(G[piv * m + c])) piv = r;
+        if (!(std::fabs(G[piv * m + c]) > 1e-14 * scale)) return false;
+        if (piv != c) {
+            for (int k = 0; k < m; ++k) std::swap(G[c * m + k], G[piv * m + k]);
+            std::swap(y[c], y[piv]);
+        }
+        for (int r = c + 1; r < m; ++r) {
+            const double f = G[r * m + c] / G[c * m + c];
+            for (int k = c; k < m; ++k) G[r * m + k] -= f * G[c * m + k];
+            y[r] -= f * y[c];
+        }
+    }
+    x.assign(m, 0.0);
+    for (int r = m - 1; r >= 0; --r) {
+        double s = y[r];
+        for (int k = r + 1; k < m; ++k) s -= G[r * m + k] * x[k];
+        x[r] = s / G[r * m + r];
+    }
+    return true;
+}
+
+static void launch_gram(of_grid* g, int m, long long n, const HistPtrs& H, const double* f) {
+    const int nb = vb(n);
+    switch (m) {
+        case 1: k_gram<1><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 2: k_gram<2><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 3: k_gram<3><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 4: k_gram<4><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 5: k_gram<5><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 6: k_gram<6><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 7: k_gram<7><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        default: OF_REQUIRE(false, OF_EINVAL, "Anderson history %d not in 1..7", m);
+    }
+    OF_LAUNCH_CHECK();
+}
+
+static void energy_terms(of_grid* g, const of_functional* fn, const double* u, const double* b,
+                         const double* phi, double t_lr_sum, double e_self, double e_c,
+                         of_scf_result* res) {
+    launch_stencil<double, 2>(g, g->w64, OpEnergy{u, b, phi, red_ctx(g, SC_EN)});
+    double e[4];
+    fetch_scalars(g, SC_EN, 4, e);
+    const double dV = g->dV;
+    res->e_tf = e[0] * dV;   // e[0] already carries C_F
+    res->e_vw = -0.5 * fn->lambda * e[1] * dV;
+    res->e_xc = e[2] * dV;
+    res->e_es = 0.5 * e[3] * dV;
+    res->e_lr = fn->mu != 0.0 ? fn->mu * 0.5 * OF_CF * t_lr_sum * dV : 0.0;
+    res->e_self = e_self;
+    res->e_corr = e_c;
+    res->energy = res->e_tf + res->e_vw + res->e_lr + res->e_xc + res->e_es + res->e_self + res->e_corr;
+}
+
+static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const of_scf_opts* o,
+                double* u, double* phi, of_scf_result* res) {
+    const long long n = g->d.n;
+    const int nb = vb(n);
+    const double dV = g->dV;
+    double Ne = 0.0;
+    for (int J = 0; J < sys->n_atoms; ++J) Ne += sys->Z[J];
+    OF_REQUIRE(Ne > 0, OF_EINVAL, "total ionic charge must be positive");
+    const FnParams fp = fn_params(fn);
+    const bool lr = fn->mu != 0.0;
+    KrylovOpts po = krylov_opts(&o->poisson), ko = krylov_opts(&o->kernel);
+    if (o->precision == OF_F32) po.precision = ko.precision = OF_F32;
+
+    ScfVecs v = scf_vecs(g);
+    std::memset(res, 0, sizeof(*res));
+    OF_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * n, g->stream));
+    double e_self = 0.0, e_c = 0.0;
+    pseudocharge(g, sys, v.b, &e_self);
+    overlap_correction(g, sys, &e_c, nullptr);
+    ScfStats st;
+    OF_CUDA(cudaMemsetAsync(v.D, 0, sizeof(double) * n, g->stream));
+    poisson_into(g, v.b, nullptr, v.D, po, st);   // phi_b
+    for (double* p : {v.B, v.C, v.V, v.rp, v.dp})
+        OF_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * n, g->stream));
+
+    const double kf = std::cbrt(3.0 * M_PI * M_PI * Ne / (g->L[0] * g->L[1] * g->L[2]));
+    const double kf2 = 4.0 * kf * kf;
+    const int m = std::max(0, std::min(o->anderson_m, 7));
+    double* Wws = nullptr;
+    double *Shist = nullptr, *Yhist = nullptr, *Vprev = nullptr, *fcur = nullptr, *fprev = nullptr;
+    if (lr) {
+        const int npairs = fn->n_terms / 2;
+        // Anderson history (S, Y), V_{k-1}, f_k, f_{k-1}, then the kernel-solve warm starts
+        double* hist = (double*)ws(g, WS_AND, sizeof(double) * (size_t)n * (2 * m + 3 + 4 * npairs));
+        Shist = hist;
+        Yhist = hist + (size_t)m * n;
+        Vprev = hist + (size_t)2 * m * n;
+        fcur = Vprev + n;
+        fprev = fcur + n;
+        Wws = fprev + n;   // 2 * npairs complex fields = 4 * npairs doubles per point
+        OF_CUDA(cudaMemsetAsync(Wws, 0, sizeof(double) * n * 4 * npairs, g->stream));
+    }
+
+    double t_lr_sum = 0.0;
+    int hist_count = 0, hist_head = 0;
+    double err = 0.0;
+    bool inner_ok = true;
+    for (int k = 0; k < std::max(1, o->fp_max_iter); ++k) {
+        inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, o->nlcg_tol, o->nlcg_max_iter,
+                        std::max(1, o->nlcg_restart), po, st);
+        res->outer_iterations = k + 1;
+        if (!lr) { err = 0.0; break; }
+        t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, ko, st, nullptr);
+        k_fp_residual<<<nb, 256, 0, g->stream>>>(n, v.Vhat, v.V, fcur, red_ctx(g, SC_FP));
+        OF_LAUNCH_CHECK();
+        double nf[2];
+        fetch_scalars(g, SC_FP, 2, nf);
+        err = nf[1] > 0 ? std::sqrt(nf[0] / nf[1]) : 0.0;
+        if (o->verbose)
+            fprintf(stderr, "[of] outer %d: fp error %.3e, nlcg %d, poisson its %d, kernel its %d\n",
+                    k, err, st.nlcg, st.poisson, st.kernel);
+        if (err < o->fp_tol) break;
+        if (k + 1 >= o->fp_max_iter) break;
+        // history: S = V_k - V_{k-1}, Y = f_k - f_{k-1}
+        if (k > 0 && m > 0) {
+            const int slot = hist_head;
+            k_diff<<<nb, 256, 0, g->stream>>>(n, v.V, Vprev, Shist + (size_t)slot * n);
+            k_diff<<<nb, 256, 0, g->stream>>>(n, fcur, fprev, Yhist + (size_t)slot * n);
+            OF_LAUNCH_CHECK();
+            hist_head = (hist_head + 1) % m;
+            hist_count = std::min(hist_count + 1, m);
+        }
+        OF_CUDA(cudaMemcpyAsync(Vprev, v.V, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+        OF_CUDA(cudaMemcpyAsync(fprev, fcur, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+        HistPtrs H{};
+        int j = hist_count;
+        std::vector<double> gamma;
+        while (j > 0) {
+            // use the j most recent columns, oldest first
+            H.m = j;
+            for (int a = 0; a < j; ++a) {
+                const int slot = ((hist_head - j + a) % m + m) % m;
+                H.S[a] = Shist + (size_t)slot * n;
+                H.Y[a] = Yhist + (size_t)slot * n;
+            }
+            launch_gram(g, j, n, H, fcur);
+            const int K = j * (j + 1) / 2 + j;
+            std::vector<double> raw(K);
+            fetch_scalars(g, SC_GRAM, K, raw.data());
+            std::vector<double> G(j * j), y(j);
+            int idx = 0;
+            for (int a = 0; a < j; ++a)
+                for (int b = a; b < j; ++b) { G[a * j + b] = G[b * j + a] = raw[idx]; ++idx; }
+            for (int a = 0; a < j; ++a) y[a] = raw[idx++];
+            if (dense_solve(G, y, j, gamma)) break;
+            --j;   // drop the oldest column and retry
+        }
+        H.m = j;
+        for (int a = 0; a < j; ++a) H.g[a] = gamma[a];
+        k_anderson_update<<<nb, 256, 0, g->stream>>>(n, v.V, fcur, o->anderson_zeta, H);
+        OF_LAUNCH_CHECK();
+    }
+    energy_terms(g, fn, u, v.b, phi, t_lr_sum, e_self, e_c, res);
+    res->fp_error = err;
+    res->nlcg_residual = st.last_residual;
+    res->nlcg_iterations = st.nlcg;
+    res->poisson_iterations = st.poisson;
+    res->kernel_iterations = st.kernel;
+    res->line_evaluations = st.line;
+    res->converged = (inner_ok && (!lr || err < o->fp_tol)) ? 1 : 0;
+    (void)dV;
+}
+
+}  // namespace of
+
+using namespace of;
+
+extern "C" {
+
+void of_default_scf_opts(of_scf_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->nlcg_tol = 1e-7;
+    o->nlcg_max_iter = 5000;
+    o->nlcg_restart = 50;
+    o->fp_tol = 1e-7;
+    o->fp_max_iter = 60;
+    o->anderson_m = 7;
+    o->anderson_zeta = 0.3;
+    o->precision = OF_F64;
+    of_default_solve_opts(&o->poisson);
+    of_default_solve_opts(&o->kernel);
+    o->verbose = 0;
+}
+
+of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double* u,
+                               const double* phi, const double* vlr, double* hu) {
+    if (!g || !fn || !u || !phi || !hu || (fn->mu != 0.0 && !vlr)) {
+        set_error("of_hamiltonian_apply: null argument");
+        return OF_EINVAL;
+    }
+    try {
+        launch_stencil<double, 2>(g, g->w64,
+                                  OpHamiltonian{u, phi, fn->mu != 0.0 ? vlr : nullptr, hu, nullptr,
+                                                fn_params(fn), red_ctx(g, SC_UHU)});
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const double* u,
+                          double* vlr, double* t_lr, double* W_ws, const of_solve_opts* opts,
+                          of_solve_info* info) {
+    if (!g || !fn || !u || !vlr || !(kf2 > 0)) { set_error("of_lr_potential: bad argument"); return OF_EINVAL; }
+    try {
+        if (info) std::memset(info, 0, sizeof(*info));
+        double* W = W_ws;
+        if (!W) {
+            const size_t bytes = sizeof(double2) * (size_t)fn->n_terms * g->d.n;
+            W = (double*)ws(g, WS_AND, bytes);
+            OF_CUDA(cudaMemsetAsync(W, 0, bytes, g->stream));
+        }
+        ScfStats st;
+        const double s = lr_potential_impl(g, fn, kf2, u, vlr, W, krylov_opts(opts), st, info);
+        if (t_lr) *t_lr = 0.5 * OF_CF * s * g->dV;
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functional* fn,
+                              const of_scf_opts* opts, double* u, double* phi,
+                              of_scf_result* res) {
+    if (!g || !sys || !fn || !u || !phi || !res) {
+        set_error("of_scf_ground_state: null argument");
+        return OF_EINVAL;
+    }
+    try {
+        of_scf_opts o;
+        if (opts) o = *opts; else of_default_scf_opts(&o);
+        scf(g, sys, fn, &o, u, phi, res);
+        if (!res->converged) {
+            set_error("ground state not converged: nlcg residual %.3e, fixed-point error %.3e",
+                      res->nlcg_residual, res->fp_error);
+            return OF_ENOCONV;
+        }
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,193 @@
+// Order-2N periodic finite-difference Laplacian (Eq. FD:Laplacian, periodic wrap of Sec. 4)
+// as a tiled sweep with pluggable load/store "ops", so that Krylov updates, Hamiltonian
+// terms and reductions are fused into the same pass over the grid.
+//
+// Tiling: a block of 32 x 8 threads owns a 32 x (8*RY) tile of the x-y plane and marches
+// along z through `cz` planes.  Each thread keeps the 2N+1 z-neighbours of its RY points in
+// registers (a shifting queue); the x- and y-neighbours come from the current z-plane staged
+// in shared memory with an N-point halo whose periodic indices are precomputed once per
+// block.  Symmetric taps are paired: w_p (f(i+p) + f(i-p)).
+#pragma once
+
+#include "of_internal.cuh"
+
+namespace of {
+
+// ------------------------------------------------------------------ value arithmetic
+// Real scalars (float, double) and interleaved complex (float2, double2) share the same
+// real-weighted stencil arithmetic.
+template <typename T> struct Real;
+template <> struct Real<float> { using type = float; };
+template <> struct Real<double> { using type = double; };
+template <> struct Real<float2> { using type = float; };
+template <> struct Real<double2> { using type = double; };
+
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ float vfma(float w, float a, float c) { return fmaf(w, a, c); }
+__device__ __forceinline__ double vfma(double w, double a, double c) { return fma(w, a, c); }
+__device__ __forceinline__ float2 vfma(float w, float2 a, float2 c) { return make_float2(fmaf(w, a.x, c.x), fmaf(w, a.y, c.y)); }
+__device__ __forceinline__ double2 vfma(double w, double2 a, double2 c) { return make_double2(fma(w, a.x, c.x), fma(w, a.y, c.y)); }
+
+__device__ __forceinline__ float vmul(float w, float a) { return w * a; }
+__device__ __forceinline__ double vmul(double w, double a) { return w * a; }
+__device__ __forceinline__ float2 vmul(float w, float2 a) { return make_float2(w * a.x, w * a.y); }
+__device__ __forceinline__ double2 vmul(double w, double2 a) { return make_double2(w * a.x, w * a.y); }
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+constexpr int ST_BX = 32;
+constexpr int ST_BY = 8;
+constexpr int ST_THREADS = ST_BX * ST_BY;
+
+// Op interface (all __device__):
+//   bool begin()                         -- false: the whole kernel is a no-op (uniform)
+//   T load(long long i) const            -- value of the differentiated field at i
+//   void store(long long i, T c, T lap)  -- c = field at i, lap = (L_h field)(i)
+//   void end()                           -- called by every thread of every active block
+template <typename T, int N, int RY, class Op>
+__global__ void __launch_bounds__(ST_THREADS)
+stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
+    using R = typename Real<T>::type;
+    constexpr int TY = ST_BY * RY;
+    constexpr int SX = ST_BX + 2 * N;
+    constexpr int SY = TY + 2 * N;
+    constexpr int Q = 2 * N + 1;
+    __shared__ T tile[SY][SX];
+    __shared__ int xi[SX];
+    __shared__ int yi[SY];
+
+    if (!op.begin()) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + ST_BX * ty;
+    const int x0 = blockIdx.x * ST_BX;
+    const int y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * cz;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    for (int t = tid; t < SX; t += ST_THREADS) xi[t] = wrap_index(x0 - N + t, n1);
+    for (int t = tid; t < SY; t += ST_THREADS) yi[t] = wrap_index(y0 - N + t, n2);
+    __syncthreads();
+
+    const int x = x0 + tx;
+    const bool xin = x < n1;
+    const int xs = xi[tx + N];
+    const long long plane = (long long)n1 * n2;
+    long long rowoff[RY];
+    bool yin[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const int yl = ty + r * ST_BY;
+        rowoff[r] = (long long)yi[yl + N] * n1 + xs;
+        yin[r] = (y0 + yl) < n2;
+    }
+
+    T q[RY][Q];
+    const int zend = min(z0 + cz, n3);
+    if (z0 < n3) {
+#pragma unroll
+        for (int j = 0; j < 2 * N; ++j) {
+            const long long zo = (long long)wrap_index(z0 - N + j, n3) * plane;
+#pragma unroll
+            for (int r = 0; r < RY; ++r) q[r][j] = op.load(zo + rowoff[r]);
+        }
+        for (int z = z0; z < zend; ++z) {
+            {
+                const long long zo = (long long)wrap_index(z + N, n3) * plane;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) q[r][2 * N] = op.load(zo + rowoff[r]);
+            }
+            const long long zc = (long long)z * plane;
+            for (int e = tid; e < SX * SY; e += ST_THREADS) {
+                const int sy = e / SX, sx = e - sy * SX;
+                tile[sy][sx] = op.load(zc + (long long)yi[sy] * n1 + xi[sx]);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                const int ly = ty + r * ST_BY + N, lx = tx + N;
+                const T c = q[r][N];
+                T acc = vmul(W.centre, c);
+#pragma unroll
+                for (int p = 1; p <= N; ++p) {
+                    acc = vfma(W.w[2][p], vadd(q[r][N + p], q[r][N - p]), acc);
+                    acc = vfma(W.w[0][p], vadd(tile[ly][lx + p], tile[ly][lx - p]), acc);
+                    acc = vfma(W.w[1][p], vadd(tile[ly + p][lx], tile[ly - p][lx]), acc);
+                }
+                if (xin && yin[r]) op.store(zc + (long long)(y0 + ty + r * ST_BY) * n1 + x, c, acc);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int j = 0; j < 2 * N; ++j) q[r][j] = q[r][j + 1];
+        }
+    }
+    op.end();
+}
+
+// Launch geometry: z chunk chosen so the grid has at least ~4 blocks per SM when possible.
+struct StencilLaunch {
+    dim3 grid;
+    int cz;
+};
+
+inline StencilLaunch stencil_launch(const Dims& d, int RY, int num_sms) {
+    const int TY = ST_BY * RY;
+    const int bx = (d.n1 + ST_BX - 1) / ST_BX;
+    const int by = (d.n2 + TY - 1) / TY;
+    const long long target = 4LL * num_sms;
+    long long tiles = (long long)bx * by;
+    int cz = (int)((d.n3 * tiles + target - 1) / target);
+    if (cz < 1) cz = 1;
+    if (cz > d.n3) cz = d.n3;
+    if (cz < 4 && d.n3 >= 4) cz = 4;   // keep the z-halo overhead bounded
+    int bz = (d.n3 + cz - 1) / cz;
+    return {dim3(bx, by, bz), cz};
+}
+
+int num_sms();
+
+template <typename T, int RY, class Op>
+void launch_stencil(of_grid* g, const Weights<typename Real<T>::type>& W, Op op) {
+    StencilLaunch sl = stencil_launch(g->d, RY, num_sms());
+    dim3 block(ST_BX, ST_BY, 1);
+    switch (g->N) {
+        case 1: stencil_kernel<T, 1, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
+        case 3: stencil_kernel<T, 3, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
+        case 6: stencil_kernel<T, 6, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
+        default: OF_REQUIRE(false, OF_EINVAL, "unsupported finite-difference half order %d", g->N);
+    }
+    OF_LAUNCH_CHECK();
+}
+
+inline int stencil_blocks(of_grid* g, int RY) {
+    StencilLaunch sl = stencil_launch(g->d, RY, num_sms());
+    return (int)(sl.grid.x * sl.grid.y * sl.grid.z);
+}
+
+// Reduction context handed to fused ops.
+struct RedCtx {
+    double* partials;
+    unsigned int* counter;
+    double* out;
+};
+
+inline RedCtx red_ctx(of_grid* g, int out_index) {
+    return RedCtx{g->s.partials, g->s.counter, g->s.scalars + out_index};
+}
+
+// sum of a[i] * (b ? b[i] : 1) over i < n into rc.out[0] (defined in of_krylov.cu)
+__global__ void k_sum_product(long long n, const double* a, const double* b, RedCtx rc);
+
+// ion terms (of_atoms.cu)
+void pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self);
+void overlap_correction(of_grid* g, const of_system* sys, double* e_c, double* fc_host);
+void forces(of_grid* g, const of_system* sys, const double* phi, double* F);
+
+}  // namespace of
