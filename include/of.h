@@ -180,6 +180,27 @@ of_status of_forces(of_grid* g, const of_system* sys, const double* u, const dou
 /* Message of the last failure on this host thread ("" if none). */
 const char* of_last_error(void);
 
+/* ---- measurement hooks (no counterpart in the paper) ----
+ * of_launch_count: kernel launches made by this library so far in the process.
+ * of_profile_enable: time every sample_every-th launch of each kernel class on the grid's
+ * stream with CUDA events (0 stops timing, counting continues); resets the statistics.
+ * of_profile_read: synchronises the stream, fills up to max records (one per kernel class
+ * seen) and returns their number, -1 on error.  bytes_per_launch is the algorithmic traffic
+ * of one launch (fields read plus written, no halo re-reads). */
+typedef struct {
+    int kernel_class;
+    long long launches;
+    long long timed;
+    double total_ms;
+    double mean_ms;
+    double bytes_per_launch;
+} of_kernel_stat;
+
+unsigned long long of_launch_count(void);
+const char* of_kernel_class_name(int kernel_class);
+of_status of_profile_enable(of_grid* g, int sample_every);
+int of_profile_read(of_grid* g, of_kernel_stat* out, int max);
+
 #ifdef __cplusplus
 }
 #endif

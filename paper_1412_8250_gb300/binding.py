@@ -59,6 +59,12 @@ class of_scf_result(C.Structure):
                 ("converged", C.c_int)]
 
 
+class of_kernel_stat(C.Structure):
+    _fields_ = [("kernel_class", C.c_int), ("launches", C.c_longlong), ("timed", C.c_longlong),
+                ("total_ms", C.c_double), ("mean_ms", C.c_double),
+                ("bytes_per_launch", C.c_double)]
+
+
 _P = C.c_void_p
 _D = C.c_double
 _I = C.c_int
@@ -79,6 +85,10 @@ _SIGNATURES = {
                                  C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
     "of_last_error": (C.c_char_p, []),
+    "of_launch_count": (C.c_ulonglong, []),
+    "of_kernel_class_name": (C.c_char_p, [_I]),
+    "of_profile_enable": (_I, [_P, _I]),
+    "of_profile_read": (_I, [_P, C.POINTER(of_kernel_stat), _I]),
 }
 
 _lib = None
@@ -247,3 +257,26 @@ def of_forces(h, sys, u, phi):
 
 def of_last_error():
     return load().of_last_error().decode(errors="replace")
+
+
+def of_launch_count():
+    return int(load().of_launch_count())
+
+
+def of_kernel_class_name(cls):
+    return load().of_kernel_class_name(int(cls)).decode()
+
+
+def of_profile_enable(h, sample_every=1):
+    return _check(load().of_profile_enable(h, int(sample_every)), "of_profile_enable")
+
+
+def of_profile_read(h):
+    """Per-kernel-class statistics as a list of dicts (synchronises the grid's stream)."""
+    buf = (of_kernel_stat * 32)()
+    k = load().of_profile_read(h, buf, 32)
+    if k < 0:
+        raise OfError(OF_ECUDA, "of_profile_read")
+    return [dict(kernel=of_kernel_class_name(buf[i].kernel_class), launches=buf[i].launches,
+                 timed=buf[i].timed, total_ms=buf[i].total_ms, mean_ms=buf[i].mean_ms,
+                 bytes_per_launch=buf[i].bytes_per_launch) for i in range(k)]

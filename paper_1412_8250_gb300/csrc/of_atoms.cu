@@ -219,14 +219,14 @@ static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, doubl
     double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + a.n_atoms + 8));
     OF_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * g->d.n, g->stream));
     OF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * nparts, g->stream));
-    k_pseudocharge<<<dim3(a.n_atoms, a.max_planes), 256, 0, g->stream>>>(
+    launch(k_pseudocharge, dim3(a.n_atoms, a.max_planes), 256, g->stream, 
         g->d, g->h[0], g->h[1], g->h[2], a.d_boxes, q, b, part, a.max_planes);
     OF_LAUNCH_CHECK();
     if (e_self) {
         double* per_atom = part + nparts;
-        k_sum_planes<<<(a.n_atoms + 127) / 128, 128, 0, g->stream>>>(a.n_atoms, a.max_planes, 1,
+        launch(k_sum_planes, (a.n_atoms + 127) / 128, 128, g->stream, a.n_atoms, a.max_planes, 1,
                                                                     part, -0.5 * g->dV, per_atom);
-        k_sum_product<<<1, 256, 0, g->stream>>>(a.n_atoms, per_atom, nullptr, red_ctx(g, 119));
+        launch(k_sum_product, 1, 256, g->stream, a.n_atoms, per_atom, nullptr, red_ctx(g, 119));
         OF_LAUNCH_CHECK();
         fetch_scalars(g, 119, 1, e_self);
     }
@@ -241,11 +241,11 @@ void overlap_correction(of_grid* g, const of_system* sys, double* e_c, double* f
     const int t2 = (int)std::ceil(cutoff / g->L[1]) + 1;
     const int t3 = (int)std::ceil(cutoff / g->L[2]) + 1;
     double* buf = (double*)ws(g, WS_S14, sizeof(double) * (4 * (size_t)M + 8));
-    k_overlap<<<(M + 127) / 128, 128, 0, g->stream>>>(M, a.d_boxes, g->L[0], g->L[1], g->L[2],
+    launch(k_overlap, (M + 127) / 128, 128, g->stream, M, a.d_boxes, g->L[0], g->L[1], g->L[2],
                                                      sys->sigma, cutoff, t1, t2, t3, buf, buf + M);
     OF_LAUNCH_CHECK();
     if (e_c) {
-        k_sum_product<<<1, 256, 0, g->stream>>>(M, buf, nullptr, red_ctx(g, 118));
+        launch(k_sum_product, 1, 256, g->stream, M, buf, nullptr, red_ctx(g, 118));
         OF_LAUNCH_CHECK();
         fetch_scalars(g, 118, 1, e_c);
     }
@@ -267,10 +267,10 @@ void forces(of_grid* g, const of_system* sys, const double* phi, double* F) {
     const size_t nparts = (size_t)M * a.max_planes * 3;
     double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + 3 * (size_t)M + 8));
     double* per_atom = part + nparts;
-    k_forces<<<dim3(M, a.max_planes), 256, 0, g->stream>>>(g->d, g->h[0], g->h[1], g->h[2],
+    launch(k_forces, dim3(M, a.max_planes), 256, g->stream, g->d, g->h[0], g->h[1], g->h[2],
                                                          a.d_boxes, q, phi, part, a.max_planes);
     OF_LAUNCH_CHECK();
-    k_sum_planes<<<(3 * M + 127) / 128, 128, 0, g->stream>>>(M, a.max_planes, 3, part, g->dV,
+    launch(k_sum_planes, (3 * M + 127) / 128, 128, g->stream, M, a.max_planes, 3, part, g->dV,
                                                             per_atom);
     OF_LAUNCH_CHECK();
     std::vector<double> fc(3 * (size_t)M);

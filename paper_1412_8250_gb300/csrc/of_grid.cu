@@ -7,6 +7,7 @@
 
 namespace of {
 
+unsigned long long g_launch_count = 0;
 static thread_local char g_err[1024] = "";
 
 void set_error(const char* fmt, ...) {
@@ -143,6 +144,12 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
 
 of_status of_grid_destroy(of_grid* g) {
     if (!g) return OF_OK;
+    if (g->mg) mg_destroy(g->mg);
+    if (g->prof) {
+        for (auto& r : g->prof->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+        for (auto e : g->prof->pool) cudaEventDestroy(e);
+        delete g->prof;
+    }
     for (auto& b : g->pool)
         if (b.ptr) cudaFree(b.ptr);
     if (g->s.partials) cudaFree(g->s.partials);
@@ -161,6 +168,66 @@ of_status of_laplacian_apply(of_grid* g, of_dtype dtype, const void* x, void* y)
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    }
+}
+
+unsigned long long of_launch_count(void) {
+    return __atomic_load_n(&of::g_launch_count, __ATOMIC_RELAXED);
+}
+
+const char* of_kernel_class_name(int cls) {
+    static const char* names[PC_N] = {"stencil_f64", "stencil_f32", "cg_stencil_f64",
+                                      "cg_stencil_f32", "cocg_stencil_f64", "cocg_stencil_f32",
+                                      "krylov_update", "mg_smooth", "mg_transfer",
+                                      "line_energy", "ions", "other"};
+    return (cls >= 0 && cls < PC_N) ? names[cls] : "";
+}
+
+of_status of_profile_enable(of_grid* g, int sample_every) {
+    if (!g || sample_every < 0) { set_error("of_profile_enable: bad argument"); return OF_EINVAL; }
+    try {
+        if (!g->prof) g->prof = new Prof();
+        Prof& p = *g->prof;
+        OF_CUDA(cudaStreamSynchronize(g->stream));
+        for (auto& r : p.recs) { p.pool.push_back(r.e0); p.pool.push_back(r.e1); }
+        p.recs.clear();
+        for (int c = 0; c < PC_N; ++c) { p.seen[c] = p.timed[c] = 0; p.ms[c] = p.bytes[c] = 0.0; }
+        p.every = sample_every;
+        return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+int of_profile_read(of_grid* g, of_kernel_stat* out, int max) {
+    if (!g || !g->prof) return 0;
+    try {
+        Prof& p = *g->prof;
+        OF_CUDA(cudaStreamSynchronize(g->stream));
+        for (auto& r : p.recs) {
+            float ms = 0.f;
+            OF_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+            p.timed[r.cls] += 1;
+            p.ms[r.cls] += ms;
+            p.bytes[r.cls] = r.bytes;
+            p.pool.push_back(r.e0);
+            p.pool.push_back(r.e1);
+        }
+        p.recs.clear();
+        int k = 0;
+        for (int c = 0; c < PC_N && k < max; ++c) {
+            if (p.seen[c] == 0) continue;
+            out[k].kernel_class = c;
+            out[k].launches = p.seen[c];
+            out[k].timed = p.timed[c];
+            out[k].total_ms = p.ms[c];
+            out[k].mean_ms = p.timed[c] ? p.ms[c] / p.timed[c] : 0.0;
+            out[k].bytes_per_launch = p.bytes[c];
+            ++k;
+        }
+        return k;
+    } catch (const Error&) {
+        return -1;
     }
 }
 

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/of.h"
@@ -33,6 +34,48 @@ struct Error {
     } while (0)
 
 #define OF_LAUNCH_CHECK() OF_CUDA(cudaGetLastError())
+
+// Kernel launches by this library (process-wide), for the launch accounting of callers.
+extern unsigned long long g_launch_count;
+
+// Every kernel of the library is launched through this wrapper (no dynamic shared memory).
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
+                   Args&&... args) {
+    kernel<<<grid, block, 0, stream>>>(std::forward<Args>(args)...);
+    __atomic_add_fetch(&g_launch_count, 1ull, __ATOMIC_RELAXED);
+    OF_CUDA(cudaGetLastError());
+}
+
+// Sampled per-class kernel timing with CUDA events on the launching stream.
+enum ProfClass {
+    PC_STENCIL_F64 = 0, PC_STENCIL_F32, PC_CG_F64, PC_CG_F32, PC_COCG_F64, PC_COCG_F32,
+    PC_UPDATE, PC_MG_SMOOTH, PC_MG_TRANSFER, PC_LINE, PC_ATOMS, PC_OTHER, PC_N
+};
+struct ProfRec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double bytes;
+};
+struct Prof {
+    int every = 0;
+    long long seen[PC_N] = {};
+    long long timed[PC_N] = {};
+    double ms[PC_N] = {};
+    double bytes[PC_N] = {};
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            OF_CUDA(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+};
 
 #define OF_REQUIRE(cond, code, ...)                                                      \
     do {                                                                                 \
@@ -70,6 +113,9 @@ struct Buffer {
     size_t bytes = 0;
 };
 
+struct MG;
+void mg_destroy(MG* m);
+
 }  // namespace of
 
 struct of_grid {
@@ -84,7 +130,35 @@ struct of_grid {
     int device;
     of::Scratch s;
     std::vector<of::Buffer> pool;    // named workspace slots, see of::ws()
+    of::MG* mg = nullptr;            // multigrid hierarchy (built on first use)
+    of::Prof* prof = nullptr;        // kernel timing (of_profile_enable)
 };
+
+namespace of {
+struct ProfScope {
+    Prof* p = nullptr;
+    int cls;
+    double bytes;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ProfScope(of_grid* g, int cls_, double bytes_) : cls(cls_), bytes(bytes_), s(g->stream) {
+        p = g->prof;
+        if (!p) return;
+        if (p->every > 0 && (p->seen[cls] % p->every) == 0) {
+            e0 = p->get();
+            e1 = p->get();
+            OF_CUDA(cudaEventRecord(e0, s));
+        }
+        p->seen[cls]++;
+    }
+    ~ProfScope() {
+        if (e0) {
+            cudaEventRecord(e1, s);
+            p->recs.push_back(ProfRec{cls, e0, e1, bytes});
+        }
+    }
+};
+}  // namespace of
 
 namespace of {
 
@@ -97,6 +171,7 @@ enum Slot {
     WS_LR,       // kernel-solve warm starts
     WS_AND,      // Anderson history
     WS_ATOM,     // per-atom device data
+    WS_MG,       // multigrid hierarchy
     WS_NSLOTS
 };
 

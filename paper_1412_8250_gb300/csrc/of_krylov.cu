@@ -15,8 +15,10 @@
 // points included), writes p and A p and reduces p^T A p; the update kernel applies alpha,
 // updates x and r and reduces r^T r and |r|^2.  alpha, beta and the stopping flag live in
 // device memory, so the host only synchronises every `check_every` iterations.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "of_stencil.cuh"
 
@@ -90,6 +92,7 @@ __device__ __forceinline__ T apply_A(T c, T lap, typename KT<T>::R a, double2 Q)
 // r = b - A x ; reduces |r|^2 and r^T r into the state and resets the iteration scalars.
 template <typename T>
 struct OpResidual {
+    static constexpr int kClass = KT<T>::cplx ? PC_COCG_F64 : PC_STENCIL_F64, kWords = 3;
     const T* x;
     const T* b;
     T* r;
@@ -124,6 +127,9 @@ struct OpResidual {
 // p_out = r + beta p_in (halo included), Ap = A p_out; reduces p^T A p and sets alpha.
 template <typename T>
 struct OpKrylovA {
+    static constexpr int kClass = KT<T>::cplx ? (sizeof(typename KT<T>::R) == 8 ? PC_COCG_F64 : PC_COCG_F32)
+                                              : (sizeof(typename KT<T>::R) == 8 ? PC_CG_F64 : PC_CG_F32);
+    static constexpr int kWords = 4;   // read r (or z) and p, write p and A p
     const T* r;
     const T* pin;
     T* pout;
@@ -170,7 +176,7 @@ struct OpKrylovA {
 };
 
 // x += alpha p ; r -= alpha Ap ; reduces |r|^2 and r^T r ; sets beta, iteration count, done.
-template <typename T>
+template <typename T, bool PRECOND = false>
 __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict__ x,
                                                      T* __restrict__ r, const T* __restrict__ p,
                                                      const T* __restrict__ Ap, KState* st,
@@ -195,6 +201,8 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
         st->iters += 1.0;
         if (acc[0] <= st->tol2 || st->iters >= st->maxit) {
             st->done = 1.0;
+        } else if (PRECOND) {
+            return;   // beta follows from r^T z once the preconditioner has run
         } else if (!(fabs(rho_old.x) + fabs(rho_old.y) > 0.0)) {
             st->breakdown = 1.0;
             st->done = 1.0;
@@ -205,6 +213,28 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
         }
         st->rho_re = rho_new.x;
         st->rho_im = rho_new.y;
+    }
+}
+
+// PCG: rho_new = r^T z ; beta = rho_new / rho (0 on the first call) ; rho = rho_new
+__global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __restrict__ r,
+                                                  const float* __restrict__ z, bool first,
+                                                  KState* st, RedCtx rc) {
+    if (st->done != 0.0) return;
+    double acc[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc[0] += (double)r[i] * z[i];
+    if (grid_reduce<1>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        if (!(acc[0] > 0.0)) {   // M^{-1} must be positive definite on r
+            st->breakdown = 1.0;
+            st->done = 1.0;
+            return;
+        }
+        st->beta_re = first ? 0.0 : acc[0] / st->rho_re;
+        st->beta_im = 0.0;
+        st->rho_re = acc[0];
+        st->rho_im = 0.0;
     }
 }
 
@@ -319,15 +349,16 @@ __global__ void __launch_bounds__(256) k_demote<double2, float2>(long long n, co
     }
 }
 
-__global__ void k_promote_add(long long n, double* x, const float* e) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        x[i] += (double)e[i];
+__device__ __forceinline__ void add_promoted(double& x, float e) { x += (double)e; }
+__device__ __forceinline__ void add_promoted(double2& x, float2 e) {
+    x.x += (double)e.x;
+    x.y += (double)e.y;
 }
-__global__ void k_promote_add(long long n, double2* x, const float2* e) {
+template <typename T64, typename T32>
+__global__ void k_promote_add(long long n, T64* x, const T32* e) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        x[i] = make_double2(x[i].x + (double)e[i].x, x[i].y + (double)e[i].y);
+        add_promoted(x[i], e[i]);
 }
 
 __global__ void k_init_state(KState* st, int maxit) {
@@ -355,20 +386,21 @@ KrylovOpts krylov_opts(const of_solve_opts* o) {
 // Arena of Krylov vectors: FP64 (r, pa, pb, Ap, b) and FP32 (r, pa, pb, Ap, e), complex-sized.
 struct Arena {
     void* r64; void* pa64; void* pb64; void* Ap64; void* b64;
-    void* r32; void* pa32; void* pb32; void* Ap32; void* e32;
+    void* r32; void* pa32; void* pb32; void* Ap32; void* e32; void* z32;
 };
 
 static Arena arena(of_grid* g) {
     const size_t n = (size_t)g->d.n;
     const size_t s64 = ((n * sizeof(double2) + 255) / 256) * 256;
     const size_t s32 = ((n * sizeof(float2) + 255) / 256) * 256;
-    char* base = (char*)ws(g, WS_K0, 5 * s64 + 5 * s32);
+    char* base = (char*)ws(g, WS_K0, 5 * s64 + 6 * s32);
     Arena a;
     a.r64 = base; a.pa64 = base + s64; a.pb64 = base + 2 * s64; a.Ap64 = base + 3 * s64;
     a.b64 = base + 4 * s64;
     char* b32 = base + 5 * s64;
     a.r32 = b32; a.pa32 = b32 + s32; a.pb32 = b32 + 2 * s32; a.Ap32 = b32 + 3 * s32;
     a.e32 = b32 + 4 * s32;
+    a.z32 = b32 + 5 * s32;
     return a;
 }
 
@@ -388,8 +420,42 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
         for (int k = 0; k < check_every; ++k) {
             OpKrylovA<T> op{r, p[ping], p[1 - ping], Ap, st, red_ctx(g, 0), a, Q};
             launch_stencil<T, RY>(g, W, op);
-            krylov_update<T><<<vec_blocks(n), 256, 0, g->stream>>>(n, x, r, p[1 - ping], Ap, st,
+            ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(T) * (double)n);
+            launch(krylov_update<T>, vec_blocks(n), 256, g->stream, n, x, r, p[1 - ping], Ap, st,
                                                                     red_ctx(g, 0));
+            OF_LAUNCH_CHECK();
+            ping ^= 1;
+        }
+        fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+        if (h.done != 0.0) break;
+    }
+    return h;
+}
+
+// Preconditioned CG (multigrid V-cycle) on A = -L in FP32.
+static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa, float* pb,
+                          float* Ap, float* z, int check_every) {
+    KState* st = kstate(g, st_off);
+    const long long n = g->d.n;
+    OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float) * n, g->stream));
+    float* p[2] = {pa, pb};
+    int ping = 0;
+    mg_vcycle(g, r, z, &st->done);
+    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, true, st, red_ctx(g, 0));
+    OF_LAUNCH_CHECK();
+    KState h;
+    const int every = std::max(1, check_every / 4);
+    for (;;) {
+        for (int k = 0; k < every; ++k) {
+            OpKrylovA<float> op{z, p[ping], p[1 - ping], Ap, st, red_ctx(g, 0), 1.0f,
+                                make_double2(0.0, 0.0)};
+            launch_stencil<float, 4>(g, g->w32, op);
+            ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float) * (double)n);
+            launch(krylov_update<float, true>, vec_blocks(n), 256, g->stream, 
+                n, x, r, p[1 - ping], Ap, st, red_ctx(g, 0));
+            OF_LAUNCH_CHECK();
+            mg_vcycle(g, r, z, &st->done);
+            launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
             ping ^= 1;
         }
@@ -415,8 +481,8 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     KState* st = kstate(g, KS64);
     T64* b = (T64*)ar.b64;
     T64* r = (T64*)ar.r64;
-    k_init_state<<<1, 1, 0, g->stream>>>(st, o.max_iter);
-    k_norm_to_tol<T64><<<vec_blocks(n), 256, 0, g->stream>>>(n, b, o.tol, st, red_ctx(g, 0));
+    launch(k_init_state, 1, 1, g->stream, st, o.max_iter);
+    launch(k_norm_to_tol<T64>, vec_blocks(n), 256, g->stream, n, b, o.tol, st, red_ctx(g, 0));
     OF_LAUNCH_CHECK();
     residual<T64>(g, KS64, x, b, r, a, Q);
     KState h;
@@ -434,13 +500,23 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             KState* s32 = kstate(g, KS32);
             T32* r32 = (T32*)ar.r32;
             T32* e32 = (T32*)ar.e32;
-            k_demote<T64, T32><<<vec_blocks(n), 256, 0, g->stream>>>(
+            launch(k_demote<T64, T32>, vec_blocks(n), 256, g->stream, 
                 n, r, r32, e32, o.inner_tol, st, s32, o.max_iter - total_iters, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
-            KState hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
-                                     (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
+            KState hi;
+            bool pcg = false;
+            if constexpr (std::is_same<T32, float>::value)
+                pcg = (a == 1.0 && Q.x == 0.0 && Q.y == 0.0 && mg_available(g));
+            if constexpr (std::is_same<T32, float>::value) {
+                if (pcg)
+                    hi = iterate_pcg(g, KS32, e32, r32, (float*)ar.pa32, (float*)ar.pb32,
+                                     (float*)ar.Ap32, (float*)ar.z32, o.check_every);
+            }
+            if (!pcg)
+                hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
+                                  (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
             total_iters += (int)hi.iters;
-            k_promote_add<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, e32);
+            launch(k_promote_add<T64, T32>, vec_blocks(n), 256, g->stream, n, x, e32);
             OF_LAUNCH_CHECK();
             if (hi.breakdown != 0.0 && hi.iters == 0) { status = OF_EBREAKDOWN; break; }
         } else {
@@ -467,8 +543,8 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
 
 static void remove_mean(of_grid* g, double* x) {
     const long long n = g->d.n;
-    k_sum_product<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, nullptr, red_ctx(g, 120));
-    k_sub_mean<<<vec_blocks(n), 256, 0, g->stream>>>(n, x, g->s.scalars + 120);
+    launch(k_sum_product, vec_blocks(n), 256, g->stream, n, x, nullptr, red_ctx(g, 120));
+    launch(k_sub_mean, vec_blocks(n), 256, g->stream, n, x, g->s.scalars + 120);
     OF_LAUNCH_CHECK();
 }
 
@@ -476,8 +552,8 @@ static of_status poisson_impl(of_grid* g, const double* a, const double* b, doub
                               const KrylovOpts& o, of_solve_info* info) {
     const long long n = g->d.n;
     Arena ar = arena(g);
-    k_sum_product<<<vec_blocks(n), 256, 0, g->stream>>>(n, a, b, red_ctx(g, 120));
-    k_form_rhs<<<vec_blocks(n), 256, 0, g->stream>>>(n, a, b, g->s.scalars + 120, 4.0 * M_PI,
+    launch(k_sum_product, vec_blocks(n), 256, g->stream, n, a, b, red_ctx(g, 120));
+    launch(k_form_rhs, vec_blocks(n), 256, g->stream, n, a, b, g->s.scalars + 120, 4.0 * M_PI,
                                                      (double*)ar.b64);
     OF_LAUNCH_CHECK();
     of_status st = solve_formed<double, float>(g, phi, 1.0, make_double2(0.0, 0.0), o, info);
@@ -499,7 +575,7 @@ of_status shifted(of_grid* g, const double* f, double2 P, double2 Q, double kf2,
                   const KrylovOpts& o, of_solve_info* info) {
     const long long n = g->d.n;
     Arena ar = arena(g);
-    k_scale_complex<<<vec_blocks(n), 256, 0, g->stream>>>(n, f, P, (double2*)ar.b64);
+    launch(k_scale_complex, vec_blocks(n), 256, g->stream, n, f, P, (double2*)ar.b64);
     OF_LAUNCH_CHECK();
     return solve_formed<double2, float2>(g, W, 1.0 / kf2, Q, o, info);
 }

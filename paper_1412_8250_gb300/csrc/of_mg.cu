@@ -1,0 +1,347 @@
+// Geometric multigrid V-cycle used as the preconditioner of the FP32 inner CG of the Poisson
+// solve.  The paper (Sec. 5.5) names multigrid as the way to stop the Poisson iteration count
+// from growing with system size; this is that preconditioner on the periodic grid.
+//
+//  level 0   : the order-2N operator A = -L_h of Eq. FD:Laplacian (FP32)
+//  level l>0 : the second-order 7-point operator at spacing 2^l h
+//  transfer  : full weighting R = (1/8) P^T, trilinear prolongation P (periodic wrap)
+//  smoother  : Chebyshev polynomial of the Jacobi-scaled operator on [0.15, 1.05] lambda_max,
+//              degree 2 before and after the coarse correction (same polynomial both sides,
+//              so the V-cycle is symmetric and fixed: a valid CG preconditioner)
+//  coarsest  : Chebyshev over the whole non-zero spectrum, one thread block, when the grid
+//              cannot be halved further (an odd or small dimension)
+// Every kernel reads the solver's stop flag and returns at once after convergence.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "of_stencil.cuh"
+
+namespace of {
+
+struct MGLevel {
+    Dims d;
+    double h[3];
+    int N;
+    Weights<float> W;
+    float invD;
+    float lmax, lmin;
+    float *x, *b, *r, *d0, *d1;
+};
+
+struct MG {
+    std::vector<MGLevel> lv;
+    int deg = 2;
+    int deg_coarse = 16;
+    std::vector<float> ca, cb;     // smoother coefficients per step (level-independent form)
+    float theta_inv = 0.f;
+    bool ok = false;
+};
+
+void mg_destroy(MG* m) { delete m; }
+
+static void weights_for(int N, const double h[3], Weights<float>& W, double& diag) {
+    double w[3][OF_MAX_N + 1];
+    W.centre = 0.f;
+    double c = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int q = 1; q <= N; ++q) s += 1.0 / ((double)q * q);
+        w[a][0] = -s / (h[a] * h[a]);
+        for (int p = 1; p <= N; ++p) {
+            double ratio = 1.0;
+            for (int k = 1; k <= p; ++k) ratio *= (double)(N - p + k) / (double)(N + k);
+            w[a][p] = 2.0 * ((p % 2) ? 1.0 : -1.0) * ratio / (h[a] * h[a] * p * p);
+        }
+        for (int p = N + 1; p <= OF_MAX_N; ++p) w[a][p] = 0.0;
+        for (int p = 0; p <= OF_MAX_N; ++p) W.w[a][p] = (float)w[a][p];
+        c += 2.0 * w[a][0];
+    }
+    W.centre = (float)c;
+    diag = -c;   // diagonal of A = -L
+}
+
+// extreme eigenvalues of D^{-1} A on the periodic grid, from the stencil's symbol per axis
+static void spectrum(int N, const double h[3], const Dims& d, double diag, double& lmax,
+                     double& lmin_nz) {
+    lmax = 0.0;
+    double smallest_axis = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        const int n = a == 0 ? d.n1 : (a == 1 ? d.n2 : d.n3);
+        double s = 0.0;
+        for (int q = 1; q <= N; ++q) s += 1.0 / ((double)q * q);
+        double best = 0.0, small = 1e300;
+        for (int m = 0; m < n; ++m) {
+            const double th = 2.0 * M_PI * m / n;
+            double v = 2.0 * s;
+            for (int p = 1; p <= N; ++p) {
+                double ratio = 1.0;
+                for (int k = 1; k <= p; ++k) ratio *= (double)(N - p + k) / (double)(N + k);
+                v -= 2.0 * 2.0 * ((p % 2) ? 1.0 : -1.0) * ratio / (p * p) * std::cos(p * th);
+            }
+            v /= h[a] * h[a];
+            best = std::max(best, v);
+            if (m > 0) small = std::min(small, v);
+        }
+        lmax += best;
+        smallest_axis = std::min(smallest_axis, small);
+    }
+    lmax /= diag;
+    lmin_nz = smallest_axis / diag;
+}
+
+static bool build(of_grid* g, MG& m) {
+    Dims d = g->d;
+    double h[3] = {g->h[0], g->h[1], g->h[2]};
+    int N = g->N;
+    std::vector<MGLevel> lv;
+    size_t total = 0;
+    for (;;) {
+        MGLevel L{};
+        L.d = d;
+        for (int a = 0; a < 3; ++a) L.h[a] = h[a];
+        L.N = N;
+        double diag, lmax, lmin;
+        weights_for(N, h, L.W, diag);
+        spectrum(N, h, d, diag, lmax, lmin);
+        L.invD = (float)(1.0 / diag);
+        L.lmax = (float)lmax;
+        L.lmin = (float)lmin;
+        lv.push_back(L);
+        total += 5 * (size_t)d.n;
+        const bool can = d.n1 % 2 == 0 && d.n2 % 2 == 0 && d.n3 % 2 == 0 && d.n1 >= 8 &&
+                         d.n2 >= 8 && d.n3 >= 8;
+        if (!can) break;
+        d = Dims{d.n1 / 2, d.n2 / 2, d.n3 / 2, (long long)(d.n1 / 2) * (d.n2 / 2) * (d.n3 / 2)};
+        for (int a = 0; a < 3; ++a) h[a] *= 2.0;
+        N = 1;
+    }
+    if (lv.size() < 2 || lv.back().d.n > 65536) return false;
+    float* base = (float*)ws(g, WS_MG, sizeof(float) * (total + 64 * lv.size()));
+    size_t off = 0;
+    for (auto& L : lv) {
+        float** p[5] = {&L.x, &L.b, &L.r, &L.d0, &L.d1};
+        for (int k = 0; k < 5; ++k) {
+            *p[k] = base + off;
+            off += ((size_t)L.d.n + 63) / 64 * 64;
+        }
+    }
+    m.lv = lv;
+    m.ok = true;
+    const MGLevel& C = m.lv.back();
+    const double kappa = C.lmax / std::max(C.lmin, 1e-12f);
+    m.deg_coarse = std::min(96, std::max(8, (int)std::ceil(2.0 * std::sqrt(kappa))));
+    return true;
+}
+
+bool mg_available(of_grid* g) {
+    if (!g->mg) {
+        g->mg = new MG();
+        if (!build(g, *g->mg)) g->mg->ok = false;
+    }
+    return g->mg->ok;
+}
+
+// ---------------------------------------------------------------- kernels
+// One Chebyshev step on A = -L: x (+)= d ; r_out = r_in - A d ; d_out = a d + bD r_out
+struct OpCheby {
+    static constexpr int kClass = PC_MG_SMOOTH, kWords = 6;
+    const float* din;
+    float dscale;
+    float* x;
+    bool x_init;
+    const float* rin;
+    float* rout;
+    float* dout;
+    float a, bD;
+    const double* done;
+    __device__ bool begin() { return *done == 0.0; }
+    __device__ float load(long long i) const { return din[i] * dscale; }
+    __device__ void store(long long i, float c, float lap) {
+        x[i] = x_init ? c : x[i] + c;
+        const float rn = rin[i] + lap;   // r - A d, A = -L
+        rout[i] = rn;
+        if (dout) dout[i] = a * c + bD * rn;
+    }
+    __device__ void end() {}
+};
+
+// r = b - A x
+struct OpResid32 {
+    static constexpr int kClass = PC_MG_SMOOTH, kWords = 3;
+    const float* x;
+    const float* b;
+    float* r;
+    const double* done;
+    __device__ bool begin() { return *done == 0.0; }
+    __device__ float load(long long i) const { return x[i]; }
+    __device__ void store(long long i, float, float lap) { r[i] = b[i] + lap; }
+    __device__ void end() {}
+};
+
+__device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// coarse b = full weighting of fine r
+__global__ void k_restrict(Dims f, Dims c, const float* __restrict__ r, float* __restrict__ b,
+                           const double* done) {
+    if (*done != 0.0) return;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= c.n) return;
+    const int I = (int)(idx % c.n1);
+    const int J = (int)((idx / c.n1) % c.n2);
+    const int K = (int)(idx / ((long long)c.n1 * c.n2));
+    float s = 0.f;
+    const float w[3] = {0.25f, 0.5f, 0.25f};
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = wrapc(2 * K + dz, f.n3);
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = wrapc(2 * J + dy, f.n2);
+            const long long row = ((long long)z * f.n2 + y) * f.n1;
+#pragma unroll
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = wrapc(2 * I + dx, f.n1);
+                s += w[dz + 1] * w[dy + 1] * w[dx + 1] * r[row + x];
+            }
+        }
+    }
+    b[idx] = s;
+}
+
+// fine x += trilinear interpolation of coarse e
+__global__ void k_prolong_add(Dims f, Dims c, const float* __restrict__ e, float* __restrict__ x,
+                              const double* done) {
+    if (*done != 0.0) return;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= f.n) return;
+    const int i = (int)(idx % f.n1);
+    const int j = (int)((idx / f.n1) % f.n2);
+    const int k = (int)(idx / ((long long)f.n1 * f.n2));
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = (i & 1) ? wrapc(I0 + 1, c.n1) : I0;
+    const int J1 = (j & 1) ? wrapc(J0 + 1, c.n2) : J0;
+    const int K1 = (k & 1) ? wrapc(K0 + 1, c.n3) : K0;
+    const float wx = (i & 1) ? 0.5f : 1.0f, wy = (j & 1) ? 0.5f : 1.0f, wz = (k & 1) ? 0.5f : 1.0f;
+    auto at = [&](int I, int J, int K) { return e[((long long)K * c.n2 + J) * c.n1 + I]; };
+    float s = wz * (wy * (wx * at(I0, J0, K0) + (1.f - wx) * at(I1, J0, K0)) +
+                    (1.f - wy) * (wx * at(I0, J1, K0) + (1.f - wx) * at(I1, J1, K0))) +
+              (1.f - wz) * (wy * (wx * at(I0, J0, K1) + (1.f - wx) * at(I1, J0, K1)) +
+                            (1.f - wy) * (wx * at(I0, J1, K1) + (1.f - wx) * at(I1, J1, K1)));
+    // (1 - w) is the weight of the second node; for even indices both nodes coincide
+    x[idx] += s;
+}
+
+// Coarsest level: Chebyshev iteration for A x = b with the second-order operator, one block.
+__global__ void __launch_bounds__(1024) k_coarse_cheby(Dims d, float cx, float cy, float cz,
+                                                       float centre, float invD, float theta,
+                                                       float delta, int steps, const float* b,
+                                                       float* x, float* r, float* dv,
+                                                       const double* done) {
+    if (*done != 0.0) return;
+    const int n = (int)d.n;
+    const float sigma1 = theta / delta;
+    float rho = 1.f / sigma1;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = 0.f;
+        r[i] = b[i];
+        dv[i] = b[i] * invD / theta;
+    }
+    __syncthreads();
+    for (int s = 0; s < steps; ++s) {
+        const float rho_new = 1.f / (2.f * sigma1 - rho);
+        const float a = rho_new * rho, bb = 2.f * rho_new / delta;
+        // phase 1: x += d ; r -= A d  (A d = -(centre d + sum_axes c (d(+1) + d(-1))))
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int ix = i % d.n1, iy = (i / d.n1) % d.n2, iz = i / (d.n1 * d.n2);
+            const float dc = dv[i];
+            const float lap = centre * dc +
+                              cx * (dv[i - ix + wrapc(ix + 1, d.n1)] + dv[i - ix + wrapc(ix - 1, d.n1)]) +
+                              cy * (dv[i + (wrapc(iy + 1, d.n2) - iy) * d.n1] +
+                                    dv[i + (wrapc(iy - 1, d.n2) - iy) * d.n1]) +
+                              cz * (dv[i + (wrapc(iz + 1, d.n3) - iz) * d.n1 * d.n2] +
+                                    dv[i + (wrapc(iz - 1, d.n3) - iz) * d.n1 * d.n2]);
+            x[i] += dc;
+            r[i] += lap;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) dv[i] = a * dv[i] + bb * invD * r[i];
+        __syncthreads();
+        rho = rho_new;
+    }
+}
+
+// Chebyshev coefficients for steps k = 0..deg-1 on [lmin, lmax]: returned as the pair
+// (a_k, b_k) used to form d_{k+1} = a_k d_k + b_k D^{-1} r_{k+1}.
+static void cheby_coeffs(double lmin, double lmax, int deg, std::vector<float>& a,
+                         std::vector<float>& b, double& theta) {
+    theta = 0.5 * (lmax + lmin);
+    const double delta = 0.5 * (lmax - lmin);
+    const double sigma1 = theta / delta;
+    double rho = 1.0 / sigma1;
+    a.resize(deg);
+    b.resize(deg);
+    for (int k = 0; k < deg; ++k) {
+        const double rn = 1.0 / (2.0 * sigma1 - rho);
+        a[k] = (float)(rn * rho);
+        b[k] = (float)(2.0 * rn / delta);
+        rho = rn;
+    }
+}
+
+static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const double* done) {
+    std::vector<float> a, b;
+    double theta;
+    cheby_coeffs(0.15 * L.lmax, 1.05 * L.lmax, deg, a, b, theta);
+    if (!zero_guess) {
+        launch_stencil_dims<float, 4>(g, L.d, L.N, L.W, OpResid32{L.x, L.b, L.r, done});
+    }
+    float* din = zero_guess ? L.b : L.r;
+    float* dbuf[2] = {L.d0, L.d1};
+    for (int k = 0; k < deg; ++k) {
+        OpCheby op;
+        op.din = (k == 0) ? din : dbuf[(k + 1) & 1];
+        op.dscale = (k == 0) ? (float)(L.invD / theta) : 1.f;
+        op.x = L.x;
+        op.x_init = zero_guess && k == 0;
+        op.rin = (k == 0 && zero_guess) ? L.b : L.r;
+        op.rout = L.r;
+        op.dout = (k + 1 < deg) ? dbuf[k & 1] : nullptr;
+        op.a = a[k];
+        op.bD = b[k] * L.invD;
+        op.done = done;
+        launch_stencil_dims<float, 4>(g, L.d, L.N, L.W, op);
+    }
+}
+
+// z = M^{-1} r (one V-cycle); r, z fine-level FP32 fields
+void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
+    MG& m = *g->mg;
+    const int nl = (int)m.lv.size();
+    m.lv[0].b = const_cast<float*>(r);
+    m.lv[0].x = z;
+    for (int l = 0; l < nl - 1; ++l) {
+        MGLevel& L = m.lv[l];
+        MGLevel& C = m.lv[l + 1];
+        smooth(g, L, m.deg, true, done);   // x_l = S b_l, r_l = b_l - A x_l
+        launch(k_restrict, (unsigned)((C.d.n + 255) / 256), 256, g->stream, L.d, C.d, L.r, C.b, done);
+        OF_LAUNCH_CHECK();
+    }
+    {
+        MGLevel& C = m.lv[nl - 1];
+        const double theta = 0.5 * (C.lmax + C.lmin), delta = 0.5 * (C.lmax - C.lmin);
+        launch(k_coarse_cheby, 1, 1024, g->stream, C.d, C.W.w[0][1], C.W.w[1][1], C.W.w[2][1],
+                                                  C.W.centre, C.invD, (float)theta, (float)delta,
+                                                  m.deg_coarse, C.b, C.x, C.r, C.d0, done);
+        OF_LAUNCH_CHECK();
+    }
+    for (int l = nl - 2; l >= 0; --l) {
+        MGLevel& L = m.lv[l];
+        MGLevel& C = m.lv[l + 1];
+        launch(k_prolong_add, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d, C.x, L.x, done);
+        OF_LAUNCH_CHECK();
+        smooth(g, L, m.deg, false, done);
+    }
+}
+
+}  // namespace of

@@ -458,12 +458,12 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
     const double dV = g->dV;
     const int nb = vb(n);
     // normalise u and solve for its potential
-    k_sum_product<<<nb, 256, 0, g->stream>>>(n, u, u, red_ctx(g, SC_UU));
+    launch(k_sum_product, nb, 256, g->stream, n, u, u, red_ctx(g, SC_UU));
     OF_LAUNCH_CHECK();
     const double uu0 = sc(g, SC_UU) * dV;
     OF_REQUIRE(uu0 > 0 && std::isfinite(uu0), OF_EINVAL, "initial u has zero or non-finite norm");
-    k_scale<<<nb, 256, 0, g->stream>>>(n, u, std::sqrt(Ne / uu0));
-    k_density_plus<<<nb, 256, 0, g->stream>>>(n, u, v.b, v.rho);
+    launch(k_scale, nb, 256, g->stream, n, u, std::sqrt(Ne / uu0));
+    launch(k_density_plus, nb, 256, g->stream, n, u, v.b, v.rho);
     OF_LAUNCH_CHECK();
     poisson_into(g, v.rho, nullptr, phi, po, st);
 
@@ -473,7 +473,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         launch_stencil<double, 2>(g, g->w64,
                                   OpHamiltonian{u, phi, fn.mu != 0.0 ? V : nullptr, v.Hu, v.Lu, fn,
                                                 red_ctx(g, SC_UHU)});
-        k_gradient<<<nb, 256, 0, g->stream>>>(n, v.Hu, u, g->s.scalars + SC_UHU, dV / Ne,
+        launch(k_gradient, nb, 256, g->stream, n, v.Hu, u, g->s.scalars + SC_UHU, dV / Ne,
                                               q > 0 ? v.rp : nullptr, v.r, red_ctx(g, SC_RR));
         OF_LAUNCH_CHECK();
         double h[4];
@@ -487,20 +487,20 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
             xi = (rr - rrp) / rr_prev;
             if (!(xi > 0.0)) xi = 0.0;
         }
-        k_direction<<<nb, 256, 0, g->stream>>>(n, v.r, v.dp, xi, u, v.d, red_ctx(g, SC_RD));
+        launch(k_direction, nb, 256, g->stream, n, v.r, v.dp, xi, u, v.d, red_ctx(g, SC_RD));
         OF_LAUNCH_CHECK();
         double m[4];
         fetch_scalars(g, SC_RD, 4, m);
         if (!(m[0] > 0.0) && xi != 0.0) {   // not a descent direction: restart along r
             xi = 0.0;
-            k_direction<<<nb, 256, 0, g->stream>>>(n, v.r, v.dp, 0.0, u, v.d, red_ctx(g, SC_RD));
+            launch(k_direction, nb, 256, g->stream, n, v.r, v.dp, 0.0, u, v.d, red_ctx(g, SC_RD));
             OF_LAUNCH_CHECK();
             fetch_scalars(g, SC_RD, 4, m);
         }
         poisson_into(g, u, v.d, v.B, po, st);
         poisson_into(g, v.d, v.d, v.C, po, st);
         launch_stencil<double, 2>(g, g->w64, OpLapDot{v.d, u, v.Ld, red_ctx(g, SC_DLD)});
-        k_line_moments<<<nb, 256, 0, g->stream>>>(n, u, v.d, fn.mu != 0.0 ? V : nullptr, phi, v.D,
+        launch(k_line_moments, nb, 256, g->stream, n, u, v.d, fn.mu != 0.0 ? V : nullptr, phi, v.D,
                                                   v.B, v.C, v.b, red_ctx(g, SC_MD));
         OF_LAUNCH_CHECK();
         double mo[17];
@@ -516,7 +516,8 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
                      bD = M[12] * dV;
         auto energy = [&](double s) -> double {
             const double c2 = Ne / (uu + 2.0 * s * ud + s * s * dd);
-            k_line_energy<<<nb, 256, 0, g->stream>>>(n, u, v.d, s, c2, red_ctx(g, SC_LINE));
+            ProfScope ps(g, PC_LINE, 2.0 * sizeof(double) * (double)n);
+            launch(k_line_energy, nb, 256, g->stream, n, u, v.d, s, c2, red_ctx(g, SC_LINE));
             OF_LAUNCH_CHECK();
             const double tfxc = sc(g, SC_LINE) * dV;
             const double vw = -0.5 * fn.lam * c2 * (uLu_ + 2.0 * s * uLd + s * s * dLd);
@@ -531,8 +532,8 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         st.line += evals;
         if (s == 0.0) break;   // energy flat to rounding along d: stagnated
         const double c = std::sqrt(Ne / (uu + 2.0 * s * ud + s * s * dd));
-        k_step<<<nb, 256, 0, g->stream>>>(n, u, v.d, phi, v.D, v.B, v.C, s, c);
-        k_density_plus<<<nb, 256, 0, g->stream>>>(n, u, v.b, v.rho);
+        launch(k_step, nb, 256, g->stream, n, u, v.d, phi, v.D, v.B, v.C, s, c);
+        launch(k_density_plus, nb, 256, g->stream, n, u, v.b, v.rho);
         OF_LAUNCH_CHECK();
         poisson_into(g, v.rho, nullptr, phi, po, st);   // polish (warm start is nearly exact)
         std::swap(v.r, v.rp);
@@ -560,7 +561,7 @@ static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2,
     const int npairs = fn->n_terms / 2;
     double* scratch = (double*)ws(g, WS_LR, sizeof(double) * 4 * (size_t)n);
     double *ga = scratch, *gb = scratch + n, *fa = scratch + 2 * n, *fb = scratch + 3 * n;
-    k_powers<<<nb, 256, 0, g->stream>>>(n, u, 2.0 * fn->alpha, 2.0 * fn->beta, ga, gb);
+    launch(k_powers, nb, 256, g->stream, n, u, 2.0 * fn->alpha, 2.0 * fn->beta, ga, gb);
     OF_LAUNCH_CHECK();
     // f_e = -(1/kf2) L u^{2e}  (the m = n = 0 right-hand side of Sec. 3.1)
     launch_stencil<double, 2>(g, g->w64, OpScaledLap{ga, fa, -1.0 / kf2});
@@ -587,7 +588,7 @@ static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2,
         W.Wa[k] = Wa;
         W.Wb[k] = Wb;
     }
-    k_lr_assemble<<<nb, 256, 0, g->stream>>>(n, u, W, fn->alpha, fn->beta, vlr, red_ctx(g, SC_TLR));
+    launch(k_lr_assemble, nb, 256, g->stream, n, u, W, fn->alpha, fn->beta, vlr, red_ctx(g, SC_TLR));
     OF_LAUNCH_CHECK();
     return sc(g, SC_TLR);
 }
@@ -623,13 +624,13 @@ static bool dense_solve(std::vector<double> G, std::vector<double> y, int m, std
 static void launch_gram(of_grid* g, int m, long long n, const HistPtrs& H, const double* f) {
     const int nb = vb(n);
     switch (m) {
-        case 1: k_gram<1><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 2: k_gram<2><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 3: k_gram<3><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 4: k_gram<4><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 5: k_gram<5><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 6: k_gram<6><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
-        case 7: k_gram<7><<<nb, 256, 0, g->stream>>>(n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 1: launch(k_gram<1>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 2: launch(k_gram<2>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 3: launch(k_gram<3>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 4: launch(k_gram<4>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 5: launch(k_gram<5>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 6: launch(k_gram<6>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
+        case 7: launch(k_gram<7>, nb, 256, g->stream, n, H, f, red_ctx(g, SC_GRAM)); break;
         default: OF_REQUIRE(false, OF_EINVAL, "Anderson history %d not in 1..7", m);
     }
     OF_LAUNCH_CHECK();
@@ -705,7 +706,7 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
         t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, ko, st, nullptr);
-        k_fp_residual<<<nb, 256, 0, g->stream>>>(n, v.Vhat, v.V, fcur, red_ctx(g, SC_FP));
+        launch(k_fp_residual, nb, 256, g->stream, n, v.Vhat, v.V, fcur, red_ctx(g, SC_FP));
         OF_LAUNCH_CHECK();
         double nf[2];
         fetch_scalars(g, SC_FP, 2, nf);
@@ -718,8 +719,8 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         // history: S = V_k - V_{k-1}, Y = f_k - f_{k-1}
         if (k > 0 && m > 0) {
             const int slot = hist_head;
-            k_diff<<<nb, 256, 0, g->stream>>>(n, v.V, Vprev, Shist + (size_t)slot * n);
-            k_diff<<<nb, 256, 0, g->stream>>>(n, fcur, fprev, Yhist + (size_t)slot * n);
+            launch(k_diff, nb, 256, g->stream, n, v.V, Vprev, Shist + (size_t)slot * n);
+            launch(k_diff, nb, 256, g->stream, n, fcur, fprev, Yhist + (size_t)slot * n);
             OF_LAUNCH_CHECK();
             hist_head = (hist_head + 1) % m;
             hist_count = std::min(hist_count + 1, m);
@@ -751,7 +752,7 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         }
         H.m = j;
         for (int a = 0; a < j; ++a) H.g[a] = gamma[a];
-        k_anderson_update<<<nb, 256, 0, g->stream>>>(n, v.V, fcur, o->anderson_zeta, H);
+        launch(k_anderson_update, nb, 256, g->stream, n, v.V, fcur, o->anderson_zeta, H);
         OF_LAUNCH_CHECK();
     }
     energy_terms(g, fn, u, v.b, phi, t_lr_sum, e_self, e_c, res);

@@ -153,17 +153,39 @@ inline StencilLaunch stencil_launch(const Dims& d, int RY, int num_sms) {
 
 int num_sms();
 
+// Profiling class and algorithmic words moved per point of a stencil op (defaults for plain
+// Laplacian-like ops: read x, write y).
+template <class Op, class = void>
+struct OpInfo {
+    static constexpr int cls = -1;
+    static constexpr int words = 2;
+};
+template <class Op>
+struct OpInfo<Op, decltype((void)Op::kClass, void())> {
+    static constexpr int cls = Op::kClass;
+    static constexpr int words = Op::kWords;
+};
+
+template <typename T, int RY, class Op>
+void launch_stencil_dims(of_grid* g, const Dims& d, int N,
+                         const Weights<typename Real<T>::type>& W, Op op) {
+    StencilLaunch sl = stencil_launch(d, RY, num_sms());
+    dim3 block(ST_BX, ST_BY, 1);
+    const int cls = OpInfo<Op>::cls >= 0 ? OpInfo<Op>::cls
+                                         : (sizeof(typename Real<T>::type) == 8 ? PC_STENCIL_F64 : PC_STENCIL_F32);
+    ProfScope ps(g, cls, (double)OpInfo<Op>::words * sizeof(T) * (double)d.n);
+    cudaStream_t stream = g->stream;
+    switch (N) {
+        case 1: launch(stencil_kernel<T, 1, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
+        case 3: launch(stencil_kernel<T, 3, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
+        case 6: launch(stencil_kernel<T, 6, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
+        default: OF_REQUIRE(false, OF_EINVAL, "unsupported finite-difference half order %d", N);
+    }
+}
+
 template <typename T, int RY, class Op>
 void launch_stencil(of_grid* g, const Weights<typename Real<T>::type>& W, Op op) {
-    StencilLaunch sl = stencil_launch(g->d, RY, num_sms());
-    dim3 block(ST_BX, ST_BY, 1);
-    switch (g->N) {
-        case 1: stencil_kernel<T, 1, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
-        case 3: stencil_kernel<T, 3, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
-        case 6: stencil_kernel<T, 6, RY, Op><<<sl.grid, block, 0, g->stream>>>(g->d, W, sl.cz, op); break;
-        default: OF_REQUIRE(false, OF_EINVAL, "unsupported finite-difference half order %d", g->N);
-    }
-    OF_LAUNCH_CHECK();
+    launch_stencil_dims<T, RY, Op>(g, g->d, g->N, W, op);
 }
 
 inline int stencil_blocks(of_grid* g, int RY) {
@@ -184,6 +206,10 @@ inline RedCtx red_ctx(of_grid* g, int out_index) {
 
 // sum of a[i] * (b ? b[i] : 1) over i < n into rc.out[0] (defined in of_krylov.cu)
 __global__ void k_sum_product(long long n, const double* a, const double* b, RedCtx rc);
+
+// multigrid preconditioner (of_mg.cu): z = one V-cycle applied to r (FP32 fine-level fields)
+bool mg_available(of_grid* g);
+void mg_vcycle(of_grid* g, const float* r, float* z, const double* done);
 
 // ion terms (of_atoms.cu)
 void pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self);

@@ -26,7 +26,7 @@ def lib():
 
 def test_every_declared_symbol_is_exported(lib):
     names = _declared()
-    assert len(names) >= 13
+    assert len(names) >= 17
     for name in names:
         assert hasattr(lib, name), name
     assert sorted(B.exported_symbols()) == names
