@@ -144,6 +144,24 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
                           const double* Q, double kf2, double* W, const of_solve_opts* opts,
                           of_solve_info* info);
 
+/* The Poisson solve of of_poisson_solve (FP64 CG only) for callers that cannot allocate
+ * device memory -- code running under an allocator it does not control, or with all device
+ * memory reserved up front -- and so cannot create a grid handle.  The paper has no
+ * counterpart: this is an interface for such callers.  The grid is passed directly
+ * (sizes, side lengths, fd_half_order in {1, 3, 6}, a cudaStream_t or NULL).  rho: device
+ * double*, n points; phi: device double*, in = guess, out = mean-free solution.  opts may be
+ * NULL (defaults); opts->precision must be OF_F64.
+ * This call allocates nothing: its Krylov vectors and reduction scratch live in one static
+ * device array of about 10.6 MB that every GPU loading the library holds until exit, which
+ * limits the grid to n1*n2*n3 <= 262144 points (OF_EINVAL beyond).  All calls share that array,
+ * so calls whose GPU work overlaps (on different streams or threads) race; serialise them.
+ * The first call on a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  Synchronises the stream
+ * before returning. */
+of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1, double L2, double L3,
+                                   int fd_half_order, void* stream, const double* rho,
+                                   double* phi, const of_solve_opts* opts, of_solve_info* info);
+
 /* b = sum over ions and periodic images of b_J (Sec. 3.2) on the grid (device double*),
  * and the self-energy term -(1/2) sum_J int b_J V_J (host double, may be NULL). */
 of_status of_pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self);

@@ -85,6 +85,8 @@ _SIGNATURES = {
                                  C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
     "of_last_error": (C.c_char_p, []),
+    "of_poisson_solve_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _I, _P, _P, _P,
+                                      C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
     "of_launch_count": (C.c_ulonglong, []),
     "of_kernel_class_name": (C.c_char_p, [_I]),
     "of_profile_enable": (_I, [_P, _I]),
@@ -280,3 +282,14 @@ def of_profile_read(h):
     return [dict(kernel=of_kernel_class_name(buf[i].kernel_class), launches=buf[i].launches,
                  timed=buf[i].timed, total_ms=buf[i].total_ms, mean_ms=buf[i].mean_ms,
                  bytes_per_launch=buf[i].bytes_per_launch) for i in range(k)]
+
+
+def of_poisson_solve_noalloc(n, L, fd_half_order, stream, rho, phi, opts=None, allow=()):
+    """Poisson solve that allocates no device memory (see include/of.h)."""
+    info = of_solve_info()
+    st = load().of_poisson_solve_noalloc(int(n[0]), int(n[1]), int(n[2]), float(L[0]),
+                                         float(L[1]), float(L[2]), int(fd_half_order),
+                                         _stream_ptr(stream), _ptr(rho), _ptr(phi),
+                                         C.byref(opts) if opts else None, C.byref(info))
+    _check(st, "of_poisson_solve_noalloc", allow)
+    return info

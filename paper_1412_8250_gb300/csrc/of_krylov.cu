@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 
 #include "of_stencil.cuh"
@@ -636,3 +637,163 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation Poisson solve
+// A variant of the FP64 CG Poisson solve for callers that cannot call cudaMalloc (for example
+// code running under an allocator it does not own, or in a process whose device memory is
+// reserved up front): every buffer it needs beyond the caller's rho and phi -- the five Krylov
+// vectors, the reduction partials, the block counter and the solver scalars -- lives in the
+// file-scope array below.  Each GPU that loads the library holds that array until the process
+// exits; all calls share it.
+namespace of {
+
+constexpr long long NOALLOC_MAX_POINTS = 1LL << 18;   // 262,144 grid points, e.g. 64^3
+constexpr int NOALLOC_RED_SLOTS = 3;                  // reductions of this path use <= 3 sums
+constexpr size_t NOALLOC_VEC = (size_t)NOALLOC_MAX_POINTS;
+constexpr size_t NOALLOC_PARTIALS = 5 * NOALLOC_VEC;
+constexpr size_t NOALLOC_SCALARS = NOALLOC_PARTIALS + (size_t)NOALLOC_RED_SLOTS * OF_MAX_RED_BLOCKS;
+constexpr size_t NOALLOC_COUNTER = NOALLOC_SCALARS + 256;
+constexpr size_t NOALLOC_DOUBLES = NOALLOC_COUNTER + 8;   // about 10.6 MB
+
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+
+// Device address of the scratch array, looked up once per device with that device current.
+static double* noalloc_base(int device) {
+    static double* addr[256] = {};
+    static bool looked_up[256] = {};
+    static std::mutex guard;
+    OF_REQUIRE(device >= 0 && device < 256, OF_EINVAL, "device ordinal %d out of range", device);
+    std::lock_guard<std::mutex> lock(guard);
+    if (!looked_up[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            set_error("cudaGetSymbolAddress of the no-allocation scratch: %s", cudaGetErrorString(e));
+            throw Error{OF_ECUDA};
+        }
+        addr[device] = (double*)p;
+        looked_up[device] = true;
+    }
+    return addr[device];
+}
+
+}  // namespace of
+
+extern "C" of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1, double L2,
+                                              double L3, int fd_half_order, void* stream,
+                                              const double* rho, double* phi,
+                                              const of_solve_opts* opts, of_solve_info* info) {
+    using namespace of;
+    if (!rho || !phi) { set_error("of_poisson_solve_noalloc: null argument"); return OF_EINVAL; }
+    if (n1 < 1 || n2 < 1 || n3 < 1 || !(L1 > 0) || !(L2 > 0) || !(L3 > 0)) {
+        set_error("of_poisson_solve_noalloc: bad sizes n=(%d,%d,%d) L=(%g,%g,%g)", n1, n2, n3, L1, L2, L3);
+        return OF_EINVAL;
+    }
+    const long long n = (long long)n1 * n2 * n3;
+    if (n > NOALLOC_MAX_POINTS) {
+        set_error("of_poisson_solve_noalloc: %lld grid points exceed the no-allocation limit of "
+                  "%lld points", n, NOALLOC_MAX_POINTS);
+        return OF_EINVAL;
+    }
+    if (fd_half_order != 1 && fd_half_order != 3 && fd_half_order != 6) {
+        set_error("of_poisson_solve_noalloc: fd_half_order %d not in {1, 3, 6}", fd_half_order);
+        return OF_EINVAL;
+    }
+    KrylovOpts o = krylov_opts(opts);
+    if (o.precision != OF_F64) {
+        set_error("of_poisson_solve_noalloc: only the FP64 solve (precision OF_F64) is available");
+        return OF_EINVAL;
+    }
+    try {
+        if (info) std::memset(info, 0, sizeof(*info));
+        int device = 0;
+        OF_CUDA(cudaGetDevice(&device));
+        double* base = noalloc_base(device);
+        // A handle on the stack describing the grid; its workspace pool stays empty and
+        // every pointer below points into the scratch array.
+        of_grid g{};
+        g.d = Dims{n1, n2, n3, n};
+        g.L[0] = L1; g.L[1] = L2; g.L[2] = L3;
+        const int nn[3] = {n1, n2, n3};
+        for (int a = 0; a < 3; ++a) g.h[a] = g.L[a] / nn[a];
+        g.dV = g.h[0] * g.h[1] * g.h[2];
+        g.N = fd_half_order;
+        g.w64.centre = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            // Eq. FD:Laplacian weights
+            double s = 0.0;
+            for (int q = 1; q <= g.N; ++q) s += 1.0 / ((double)q * q);
+            g.w64.w[a][0] = -s / (g.h[a] * g.h[a]);
+            for (int p = 1; p <= OF_MAX_N; ++p) {
+                double w = 0.0;
+                if (p <= g.N) {
+                    double ratio = 1.0;
+                    for (int k = 1; k <= p; ++k) ratio *= (double)(g.N - p + k) / (double)(g.N + k);
+                    w = 2.0 * ((p % 2) ? 1.0 : -1.0) * ratio / (g.h[a] * g.h[a] * p * p);
+                }
+                g.w64.w[a][p] = w;
+            }
+            g.w64.centre += 2.0 * g.w64.w[a][0];
+            for (int p = 0; p <= OF_MAX_N; ++p) g.w32.w[a][p] = (float)g.w64.w[a][p];
+        }
+        g.w32.centre = (float)g.w64.centre;
+        g.stream = (cudaStream_t)stream;
+        g.device = device;
+        double host_scalars[256];
+        g.s.partials = base + NOALLOC_PARTIALS;
+        g.s.scalars = base + NOALLOC_SCALARS;
+        g.s.counter = (unsigned int*)(base + NOALLOC_COUNTER);
+        g.s.host = host_scalars;
+        // the array keeps the previous call's contents: zero what must start at zero
+        OF_CUDA(cudaMemsetAsync(g.s.counter, 0, sizeof(double) * 8, g.stream));
+        OF_CUDA(cudaMemsetAsync(g.s.scalars, 0, sizeof(double) * 256, g.stream));
+
+        double* r = base;
+        double* pa = base + NOALLOC_VEC;
+        double* pb = base + 2 * NOALLOC_VEC;
+        double* Ap = base + 3 * NOALLOC_VEC;
+        double* b = base + 4 * NOALLOC_VEC;
+        // right-hand side 4 pi (rho - mean rho) of Eq. Poisson
+        launch(k_sum_product, vec_blocks(n), 256, g.stream, n, rho, nullptr, red_ctx(&g, 120));
+        launch(k_form_rhs, vec_blocks(n), 256, g.stream, n, rho, nullptr, g.s.scalars + 120,
+               4.0 * M_PI, b);
+        KState* st = kstate(&g, KS64);
+        launch(k_init_state, 1, 1, g.stream, st, o.max_iter);
+        launch(k_norm_to_tol<double>, vec_blocks(n), 256, g.stream, n, (const double*)b, o.tol, st,
+               red_ctx(&g, 0));
+        residual<double>(&g, KS64, phi, b, r, 1.0, make_double2(0.0, 0.0));
+        KState h;
+        fetch_scalars(&g, KS64, KSTATE_DOUBLES, (double*)&h);
+        const double bb = h.tol2 / (o.tol * o.tol);
+        of_status status = OF_OK;
+        int iters = 0, refinements = 1;
+        if (!(bb > 0.0)) {
+            OF_CUDA(cudaMemsetAsync(phi, 0, sizeof(double) * n, g.stream));
+            h.rr = 0.0;
+        }
+        while (bb > 0.0 && h.rr > h.tol2) {
+            if (iters >= o.max_iter || refinements > 200) { status = OF_ENOCONV; break; }
+            KState hi = iterate<double>(&g, KS64, phi, r, pa, pb, Ap, 1.0, make_double2(0.0, 0.0),
+                                        g.w64, o.check_every);
+            iters = (int)hi.iters;
+            if (hi.breakdown != 0.0 && hi.rr > hi.tol2) { status = OF_EBREAKDOWN; break; }
+            residual<double>(&g, KS64, phi, b, r, 1.0, make_double2(0.0, 0.0));
+            ++refinements;
+            fetch_scalars(&g, KS64, KSTATE_DOUBLES, (double*)&h);
+        }
+        remove_mean(&g, phi);
+        OF_CUDA(cudaStreamSynchronize(g.stream));
+        if (info) {
+            info->iterations = iters;
+            info->refinements = refinements;
+            info->rel_residual = bb > 0 ? std::sqrt(h.rr / bb) : 0.0;
+        }
+        if (status == OF_ENOCONV)
+            set_error("of_poisson_solve_noalloc: %d iterations, relative residual %.3e > tol %.1e",
+                      iters, bb > 0 ? std::sqrt(h.rr / bb) : 0.0, o.tol);
+        if (status == OF_EBREAKDOWN) set_error("of_poisson_solve_noalloc: breakdown");
+        return status;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
