@@ -98,6 +98,10 @@ typedef struct {
     of_solve_opts poisson;  /* defaults: tol 1e-10 */
     of_solve_opts kernel;   /* defaults: tol 1e-10 */
     int verbose;            /* 1: one line per outer iteration on stderr */
+    double line_tol;        /* Brent tolerance, relative in the step length; default 1e-3 */
+    double nlcg_tol_rel;    /* > 0: inexact inner solves, outer step k stops its NLCG at
+                               max(nlcg_tol, nlcg_tol_rel * fixed-point error of step k-1);
+                               0 (default): every inner solve to nlcg_tol */
 } of_scf_opts;
 
 typedef struct {

@@ -46,7 +46,7 @@ class of_scf_opts(C.Structure):
                 ("nlcg_restart", C.c_int), ("fp_tol", C.c_double), ("fp_max_iter", C.c_int),
                 ("anderson_m", C.c_int), ("anderson_zeta", C.c_double),
                 ("precision", C.c_int), ("poisson", of_solve_opts), ("kernel", of_solve_opts),
-                ("verbose", C.c_int)]
+                ("verbose", C.c_int), ("line_tol", C.c_double), ("nlcg_tol_rel", C.c_double)]
 
 
 class of_scf_result(C.Structure):

@@ -18,16 +18,36 @@ constexpr double OF_U_FLOOR = 1e-12;     // negative powers of u use max(u, floo
 constexpr double PZ_G1 = -0.1423, PZ_B1 = 1.0529, PZ_B2 = 0.3334;
 constexpr double PZ_A1 = 0.0311, PZ_BB1 = -0.048, PZ_C1 = 0.002, PZ_D1 = -0.0116;
 
+// rho^{-1/3} by Newton's method for f(t) = t^{-3} - rho, t <- t (4 - rho t^3) / 3, from a
+// single-precision seed; the error squares each step (1e-7 -> 1e-14 -> rounding), so two
+// FP64 steps reach full double accuracy at a fraction of the cost of a double cube root.
+__device__ __forceinline__ double inv_cbrt(double rho) {
+    double t = (double)rcbrtf((float)rho);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) t = t * (4.0 - rho * t * t * t) * (1.0 / 3.0);
+    return t;
+}
+
+// sqrt(x) = x / sqrt(x) with 1/sqrt(x) from Newton's method y <- y (3 - x y^2) / 2 on a
+// single-precision seed (two FP64 steps)
+__device__ __forceinline__ double sqrt_newton(double x) {
+    double y = (double)rsqrtf((float)x);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) y = y * (1.5 - 0.5 * x * y * y);
+    return x * y;
+}
+
 // e = eps_xc(rho) * rho and v = V_xc(rho) for the exchange (Slater) and PZ correlation.
 __device__ __forceinline__ void lda_xc(double rho, double& e, double& v) {
     const double r = fmax(rho, OF_RHO_FLOOR);
-    const double c = cbrt(r);                       // rho^{1/3} = u^{2/3}
+    const double t = inv_cbrt(r);                   // rho^{-1/3}
+    const double c = r * t * t;                     // rho^{1/3} = u^{2/3}
     const double ex = -0.75 * OF_CX * c;            // eps_x
     const double vx = -OF_CX * c;                   // V_x
-    const double rs = OF_RS0 / c;
+    const double rs = OF_RS0 * t;
     double ec, vc;
     if (rs >= 1.0) {
-        const double sq = sqrt(rs);
+        const double sq = sqrt_newton(rs);
         const double den = 1.0 + PZ_B1 * sq + PZ_B2 * rs;
         ec = PZ_G1 / den;
         vc = (PZ_G1 + (7.0 / 6.0) * PZ_G1 * PZ_B1 * sq + (4.0 / 3.0) * PZ_G1 * PZ_B2 * rs) / (den * den);
@@ -43,18 +63,30 @@ __device__ __forceinline__ void lda_xc(double rho, double& e, double& v) {
 
 // Thomas-Fermi: energy density C_F rho^{5/3} and V_TF = (5/3) C_F rho^{2/3}
 __device__ __forceinline__ void thomas_fermi(double rho, double& e, double& v) {
-    const double c = cbrt(rho);
+    if (!(rho > 1e-30)) { e = 0.0; v = 0.0; return; }   // below 1e-50 Ha per point
+    const double t = inv_cbrt(rho);
+    const double c = rho * t * t;                   // rho^{1/3}
     const double c2 = c * c;
     e = OF_CF * rho * c2;
     v = (5.0 / 3.0) * OF_CF * c2;
 }
 
-// Energy densities only (line-search evaluations)
+// Energy densities only (line-search evaluations): C_F rho^{5/3} + eps_xc(rho) rho, one
+// reciprocal cube root shared by both terms.
 __device__ __forceinline__ double tf_xc_energy(double rho) {
-    double etf, vtf, exc, vxc;
-    thomas_fermi(rho, etf, vtf);
-    lda_xc(rho, exc, vxc);
-    return etf + exc;
+    const double r = fmax(rho, OF_RHO_FLOOR);
+    const double t = inv_cbrt(r);
+    const double c = r * t * t;                     // rho^{1/3}
+    const double etf = rho > 0.0 ? OF_CF * rho * c * c : 0.0;
+    const double rs = OF_RS0 * t;
+    double ec;
+    if (rs >= 1.0) {
+        ec = PZ_G1 / (1.0 + PZ_B1 * sqrt_newton(rs) + PZ_B2 * rs);
+    } else {
+        const double lr = log(rs);
+        ec = PZ_A1 * lr + PZ_BB1 + PZ_C1 * rs * lr + PZ_D1 * rs;
+    }
+    return etf + (-0.75 * OF_CX * c + ec) * r;
 }
 
 }  // namespace of

@@ -8,6 +8,8 @@
 namespace of {
 
 unsigned long long g_launch_count = 0;
+thread_local double g_capture_bytes = 0.0;
+thread_local bool g_capturing = false;
 static thread_local char g_err[1024] = "";
 
 void set_error(const char* fmt, ...) {
@@ -83,7 +85,7 @@ void laplacian(of_grid* g, of_dtype dt, const void* x, void* y) {
     if (dt == OF_F64) {
         launch_stencil<double, 2>(g, g->w64, OpLap<double>{(const double*)x, (double*)y});
     } else if (dt == OF_F32) {
-        launch_stencil<float, 4>(g, g->w32, OpLap<float>{(const float*)x, (float*)y});
+        launch_stencil<float, 2>(g, g->w32, OpLap<float>{(const float*)x, (float*)y});
     } else {
         OF_REQUIRE(false, OF_EINVAL, "unknown dtype %d", (int)dt);
     }
@@ -145,6 +147,8 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
 of_status of_grid_destroy(of_grid* g) {
     if (!g) return OF_OK;
     if (g->mg) mg_destroy(g->mg);
+    if (g->graphs) destroy_graphs(g->graphs);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     if (g->prof) {
         for (auto& r : g->prof->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         for (auto e : g->prof->pool) cudaEventDestroy(e);
@@ -179,7 +183,7 @@ const char* of_kernel_class_name(int cls) {
     static const char* names[PC_N] = {"stencil_f64", "stencil_f32", "cg_stencil_f64",
                                       "cg_stencil_f32", "cocg_stencil_f64", "cocg_stencil_f32",
                                       "krylov_update", "mg_smooth", "mg_transfer",
-                                      "line_energy", "ions", "other"};
+                                      "line_energy", "ions", "other", "pcg_iteration_pair_graph"};
     return (cls >= 0 && cls < PC_N) ? names[cls] : "";
 }
 

@@ -50,8 +50,13 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
 // Sampled per-class kernel timing with CUDA events on the launching stream.
 enum ProfClass {
     PC_STENCIL_F64 = 0, PC_STENCIL_F32, PC_CG_F64, PC_CG_F32, PC_COCG_F64, PC_COCG_F32,
-    PC_UPDATE, PC_MG_SMOOTH, PC_MG_TRANSFER, PC_LINE, PC_ATOMS, PC_OTHER, PC_N
+    PC_UPDATE, PC_MG_SMOOTH, PC_MG_TRANSFER, PC_LINE, PC_ATOMS, PC_OTHER, PC_PCG_GRAPH, PC_N
 };
+
+// While a CUDA graph is being captured, ProfScope adds the algorithmic bytes of each captured
+// launch here (per host thread), so the graph's replays can be reported with their traffic.
+extern thread_local double g_capture_bytes;
+extern thread_local bool g_capturing;
 struct ProfRec {
     int cls;
     cudaEvent_t e0, e1;
@@ -132,6 +137,8 @@ struct of_grid {
     std::vector<of::Buffer> pool;    // named workspace slots, see of::ws()
     of::MG* mg = nullptr;            // multigrid hierarchy (built on first use)
     of::Prof* prof = nullptr;        // kernel timing (of_profile_enable)
+    cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
+    void* graphs = nullptr;              // cached CUDA graphs (of_krylov.cu)
 };
 
 namespace of {
@@ -142,6 +149,10 @@ struct ProfScope {
     cudaStream_t s;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ProfScope(of_grid* g, int cls_, double bytes_) : cls(cls_), bytes(bytes_), s(g->stream) {
+        if (g_capturing) {
+            g_capture_bytes += bytes;
+            return;
+        }
         p = g->prof;
         if (!p) return;
         if (p->every > 0 && (p->seen[cls] % p->every) == 0) {

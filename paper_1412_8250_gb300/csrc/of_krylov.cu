@@ -17,6 +17,7 @@
 // device memory, so the host only synchronises every `check_every` iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -38,6 +39,8 @@ struct KState {
     double maxit;               // 12
     double breakdown;           // 13
     double red[4];              // 14 reduction outputs
+    double zshift;              // 18 mean of the preconditioned vector (projected PCG), else 0
+    double scale;               // 19 FP32 inner solve: correction = scale * FP32 solution
 };
 constexpr int KSTATE_DOUBLES = sizeof(KState) / sizeof(double);
 constexpr int KS64 = 128;   // offsets in g->s.scalars
@@ -50,6 +53,24 @@ template <> struct KT<double> { static constexpr bool cplx = false; using R = do
 template <> struct KT<float> { static constexpr bool cplx = false; using R = float; };
 template <> struct KT<double2> { static constexpr bool cplx = true; using R = double; };
 template <> struct KT<float2> { static constexpr bool cplx = true; using R = float; };
+
+// Per-thread partial sums of FP32 fields are kept in FP32 (a thread sums only a few points;
+// GB300's FP64 rate is 1/64 of FP32) and widened to FP64 for the block and grid reduction.
+template <typename R> struct AccT { using type = double; };
+template <> struct AccT<float> { using type = float; };
+
+__device__ __forceinline__ float hn2f(float v) { return v * v; }
+__device__ __forceinline__ float hn2f(float2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ double hn2f(double v) { return v * v; }
+__device__ __forceinline__ double hn2f(double2 v) { return v.x * v.x + v.y * v.y; }
+__device__ __forceinline__ float2 bilf(float a, float b) { return make_float2(a * b, 0.f); }
+__device__ __forceinline__ float2 bilf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 bilf(double a, double b) { return make_double2(a * b, 0.0); }
+__device__ __forceinline__ double2 bilf(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
 
 // complex-or-real helpers: a scalar s (re, im) times a field value
 __device__ __forceinline__ double cs_mul(double2 s, double v) { return s.x * v; }
@@ -82,6 +103,12 @@ __host__ __device__ inline double2 cdiv(double2 a, double2 b) {
     const double d = b.x * b.x + b.y * b.y;
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
+
+template <typename T> __device__ __forceinline__ T one();
+template <> __device__ __forceinline__ double one<double>() { return 1.0; }
+template <> __device__ __forceinline__ float one<float>() { return 1.f; }
+template <> __device__ __forceinline__ double2 one<double2>() { return make_double2(1.0, 0.0); }
+template <> __device__ __forceinline__ float2 one<float2>() { return make_float2(1.f, 0.f); }
 
 // Operator A v = a (-L v) + Q v
 template <typename T>
@@ -120,6 +147,7 @@ struct OpResidual {
             st->rho_im = acc[2];
             st->beta_re = st->beta_im = 0.0;
             st->breakdown = 0.0;
+            st->zshift = 0.0;
             st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
         }
     }
@@ -140,23 +168,29 @@ struct OpKrylovA {
     typename KT<T>::R a;
     double2 Q;
     double2 beta;
-    double acc[2];
+    double2 shift;
+    typename AccT<typename KT<T>::R>::type accp[2];
     __device__ bool begin() {
         if (st->done != 0.0) return false;
         beta = make_double2(st->beta_re, st->beta_im);
-        acc[0] = acc[1] = 0.0;
+        shift = make_double2(-st->zshift, 0.0);
+        accp[0] = accp[1] = 0;
         return true;
     }
-    __device__ T load(long long i) const { return vadd(r[i], cs_mul(beta, pin[i])); }
+    // p = (r - zshift) + beta p_in ; zshift is 0 except in the projected PCG
+    __device__ T load(long long i) const {
+        return vadd(vadd(r[i], cs_mul(shift, one<T>())), cs_mul(beta, pin[i]));
+    }
     __device__ void store(long long i, T c, T lap) {
         pout[i] = c;
         const T av = apply_A(c, lap, a, Q);
         Ap[i] = av;
-        const double2 s = bil(c, av);
-        acc[0] += s.x;
-        acc[1] += s.y;
+        const auto s = bilf(c, av);
+        accp[0] += s.x;
+        accp[1] += s.y;
     }
     __device__ void end() {
+        double acc[2] = {(double)accp[0], (double)accp[1]};
         if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) &&
             threadIdx.x == 0 && threadIdx.y == 0) {
             const double2 pAp = make_double2(acc[0], acc[1]);
@@ -184,17 +218,20 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
                                                      RedCtx rc) {
     if (st->done != 0.0) return;
     const double2 al = make_double2(st->alpha_re, st->alpha_im);
-    double acc[3] = {0.0, 0.0, 0.0};
+    typename AccT<typename KT<T>::R>::type a0 = 0, a1 = 0, a2 = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         x[i] = vadd(x[i], cs_mul(al, p[i]));
         const T rv = vsub(r[i], cs_mul(al, Ap[i]));
         r[i] = rv;
-        acc[0] += hn2(rv);
-        const double2 s = bil(rv, rv);
-        acc[1] += s.x;
-        acc[2] += s.y;
+        a0 += hn2f(rv);
+        if (!PRECOND) {
+            const auto s = bilf(rv, rv);
+            a1 += s.x;
+            a2 += s.y;
+        }
     }
+    double acc[3] = {(double)a0, (double)a1, (double)a2};
     if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
         const double2 rho_new = make_double2(acc[1], acc[2]);
         const double2 rho_old = make_double2(st->rho_re, st->rho_im);
@@ -217,25 +254,36 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
     }
 }
 
-// PCG: rho_new = r^T z ; beta = rho_new / rho (0 on the first call) ; rho = rho_new
+// Projected PCG on the singular periodic operator: the preconditioned vector is used with its
+// mean removed (z - zbar, zbar = mean z), so rounding in the constant mode, which the
+// preconditioner amplifies, never enters the search direction.
+// rho_new = r^T (z - zbar) ; beta = rho_new / rho (0 on the first call) ; rho = rho_new.
 __global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __restrict__ r,
                                                   const float* __restrict__ z, bool first,
                                                   KState* st, RedCtx rc) {
     if (st->done != 0.0) return;
-    double acc[1] = {0.0};
+    float prz = 0.f, pz = 0.f, pr = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        acc[0] += (double)r[i] * z[i];
-    if (grid_reduce<1>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
-        if (!(acc[0] > 0.0)) {   // M^{-1} must be positive definite on r
+         i += (long long)gridDim.x * blockDim.x) {
+        const float ri = r[i], zi = z[i];
+        prz += ri * zi;
+        pz += zi;
+        pr += ri;
+    }
+    double acc[3] = {(double)prz, (double)pz, (double)pr};
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        const double zbar = acc[1] / (double)n;
+        const double rho = acc[0] - zbar * acc[2];
+        if (!(rho > 0.0)) {   // M^{-1} must be positive definite on r
             st->breakdown = 1.0;
             st->done = 1.0;
             return;
         }
-        st->beta_re = first ? 0.0 : acc[0] / st->rho_re;
+        st->beta_re = first ? 0.0 : rho / st->rho_re;
         st->beta_im = 0.0;
-        st->rho_re = acc[0];
+        st->rho_re = rho;
         st->rho_im = 0.0;
+        st->zshift = zbar;
     }
 }
 
@@ -298,25 +346,30 @@ __global__ void __launch_bounds__(256) k_demote<double, float>(long long n, cons
                                                                float* e32, double inner_tol,
                                                                const KState* outer, KState* st,
                                                                int maxit, RedCtx rc) {
-    double acc[3] = {0.0, 0.0, 0.0};
+    // the residual is scaled to unit RMS before rounding, so tiny right-hand sides (near the
+    // end of a minimisation) stay inside the FP32 normal range
+    const double inv = outer->rr > 0.0 ? rsqrt(outer->rr / (double)n) : 1.0;
+    float part = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const float v = (float)r64[i];
+        const float v = (float)(r64[i] * inv);
         r32[i] = v;
         e32[i] = 0.0f;
-        acc[0] += (double)v * v;
+        part += v * v;
     }
-    acc[1] = acc[0];
+    double acc[3] = {(double)part, (double)part, 0.0};
     if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
         st->rr = acc[0];
         st->rho_re = acc[0];
         st->rho_im = 0.0;
-        st->tol2 = inner_tol * inner_tol * outer->rr;
+        st->scale = 1.0 / inv;
+        st->tol2 = inner_tol * inner_tol * acc[0];
         st->beta_re = st->beta_im = 0.0;
         st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
         st->iters = 0.0;
         st->maxit = maxit;
         st->breakdown = 0.0;
+        st->zshift = 0.0;
     }
 }
 
@@ -326,43 +379,50 @@ __global__ void __launch_bounds__(256) k_demote<double2, float2>(long long n, co
                                                                  double inner_tol,
                                                                  const KState* outer, KState* st,
                                                                  int maxit, RedCtx rc) {
-    double acc[3] = {0.0, 0.0, 0.0};
+    const double inv = outer->rr > 0.0 ? rsqrt(outer->rr / (double)n) : 1.0;
+    float p0 = 0.f, p1 = 0.f, p2 = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const float2 v = make_float2((float)r64[i].x, (float)r64[i].y);
+        const float2 v = make_float2((float)(r64[i].x * inv), (float)(r64[i].y * inv));
         r32[i] = v;
         e32[i] = make_float2(0.0f, 0.0f);
-        acc[0] += hn2(v);
-        const double2 s = bil(v, v);
-        acc[1] += s.x;
-        acc[2] += s.y;
+        p0 += hn2f(v);
+        const float2 s = bilf(v, v);
+        p1 += s.x;
+        p2 += s.y;
     }
+    double acc[3] = {(double)p0, (double)p1, (double)p2};
     if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
         st->rr = acc[0];
         st->rho_re = acc[1];
         st->rho_im = acc[2];
-        st->tol2 = inner_tol * inner_tol * outer->rr;
+        st->scale = 1.0 / inv;
+        st->tol2 = inner_tol * inner_tol * acc[0];
         st->beta_re = st->beta_im = 0.0;
         st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
         st->iters = 0.0;
         st->maxit = maxit;
         st->breakdown = 0.0;
+        st->zshift = 0.0;
     }
 }
 
-__device__ __forceinline__ void add_promoted(double& x, float e) { x += (double)e; }
-__device__ __forceinline__ void add_promoted(double2& x, float2 e) {
-    x.x += (double)e.x;
-    x.y += (double)e.y;
+__device__ __forceinline__ void add_promoted(double& x, float e, double s) { x += s * (double)e; }
+__device__ __forceinline__ void add_promoted(double2& x, float2 e, double s) {
+    x.x += s * (double)e.x;
+    x.y += s * (double)e.y;
 }
+// x += scale * e, scale the factor the inner right-hand side was divided by
 template <typename T64, typename T32>
-__global__ void k_promote_add(long long n, T64* x, const T32* e) {
+__global__ void k_promote_add(long long n, T64* x, const T32* e, const KState* inner) {
+    const double s = inner->scale;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
-        add_promoted(x[i], e[i]);
+        add_promoted(x[i], e[i], s);
 }
 
 __global__ void k_init_state(KState* st, int maxit) {
+    st->zshift = 0.0;
     st->iters = 0.0;
     st->maxit = maxit;
     st->done = 0.0;
@@ -412,7 +472,7 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
                       int check_every) {
     KState* st = kstate(g, st_off);
     const long long n = g->d.n;
-    constexpr int RY = KT<T>::cplx ? 1 : (sizeof(typename KT<T>::R) == 8 ? 2 : 4);
+    constexpr int RY = KT<T>::cplx ? 1 : 2;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(T) * n, g->stream));
     T* p[2] = {pa, pb};
     int ping = 0;
@@ -433,31 +493,132 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
     return h;
 }
 
-// Preconditioned CG (multigrid V-cycle) on A = -L in FP32.
+// CUDA graphs of the preconditioned CG: "init" (V-cycle + first r^T z) and "pair" (two full
+// iterations, ping and pong of the direction buffers).  Every kernel reads its scalars and the
+// stop flag from device memory, so the same executable graph serves every solve on the grid's
+// arena; it is rebuilt only if a buffer address changes.
+struct PcgGraphs {
+    const void* key[8] = {};
+    cudaGraphExec_t init = nullptr, pair = nullptr;
+    unsigned long long init_kernels = 0, pair_kernels = 0;
+    double init_bytes = 0.0, pair_bytes = 0.0;
+};
+
+void destroy_graphs(void* p) {
+    PcgGraphs* G = (PcgGraphs*)p;
+    if (!G) return;
+    if (G->init) cudaGraphExecDestroy(G->init);
+    if (G->pair) cudaGraphExecDestroy(G->pair);
+    delete G;
+}
+
+template <class Body>
+static cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kernels,
+                               double& bytes) {
+    if (!g->cap_stream) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t saved = g->stream;
+    Prof* saved_prof = g->prof;
+    g->stream = g->cap_stream;
+    g->prof = nullptr;
+    const unsigned long long c0 = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
+    cudaGraph_t graph = nullptr;
+    OF_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    g_capturing = true;
+    g_capture_bytes = 0.0;
+    try {
+        body();
+    } catch (...) {
+        g_capturing = false;
+        cudaStreamEndCapture(g->stream, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        g->stream = saved;
+        g->prof = saved_prof;
+        throw;
+    }
+    g_capturing = false;
+    bytes = g_capture_bytes;
+    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+    g->stream = saved;
+    g->prof = saved_prof;
+    OF_CUDA(e);
+    kernels = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED) - c0;
+    __atomic_sub_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);   // captured, not launched
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    OF_CUDA(e);
+    return exec;
+}
+
+static void replay(of_grid* g, cudaGraphExec_t exec, unsigned long long kernels, double bytes) {
+    ProfScope ps(g, PC_PCG_GRAPH, bytes);
+    OF_CUDA(cudaGraphLaunch(exec, g->stream));
+    __atomic_add_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);
+}
+
+static void pcg_init_body(of_grid* g, float* r, float* z, KState* st) {
+    const long long n = g->d.n;
+    mg_vcycle(g, r, z, &st->done);
+    ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
+    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, true, st, red_ctx(g, 0));
+}
+
+static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pout, float* Ap,
+                          float* z, KState* st) {
+    const long long n = g->d.n;
+    OpKrylovA<float> op{z, pin, pout, Ap, st, red_ctx(g, 0), 1.0f, make_double2(0.0, 0.0)};
+    launch_stencil<float, 2>(g, g->w32, op);
+    {
+        ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float) * (double)n);
+        launch(krylov_update<float, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
+               red_ctx(g, 0));
+    }
+    mg_vcycle(g, r, z, &st->done);
+    ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
+    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
+}
+
+// Preconditioned CG (multigrid V-cycle) on A = -L in FP32.  Without profiling the iterations
+// run as replays of captured CUDA graphs; with profiling on, as individual launches so that
+// every kernel class can be timed.
 static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa, float* pb,
                           float* Ap, float* z, int check_every) {
     KState* st = kstate(g, st_off);
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float) * n, g->stream));
+    KState h;
+    const bool use_graphs = std::getenv("OF_NO_GRAPHS") == nullptr;
+    if (use_graphs) {
+        if (!g->graphs) g->graphs = new PcgGraphs();
+        PcgGraphs& G = *(PcgGraphs*)g->graphs;
+        const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
+        if (!G.pair || std::memcmp(key, G.key, sizeof(key)) != 0) {
+            if (G.init) cudaGraphExecDestroy(G.init);
+            if (G.pair) cudaGraphExecDestroy(G.pair);
+            G.init = G.pair = nullptr;
+            G.init = capture(g, [&] { pcg_init_body(g, r, z, st); }, G.init_kernels, G.init_bytes);
+            G.pair = capture(g, [&] {
+                pcg_step_body(g, x, r, pa, pb, Ap, z, st);
+                pcg_step_body(g, x, r, pb, pa, Ap, z, st);
+            }, G.pair_kernels, G.pair_bytes);
+            std::memcpy(G.key, key, sizeof(key));
+        }
+        replay(g, G.init, G.init_kernels, G.init_bytes);
+        const int pairs = std::max(1, check_every / 8);
+        for (;;) {
+            for (int k = 0; k < pairs; ++k) replay(g, G.pair, G.pair_kernels, G.pair_bytes);
+            fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+            if (h.done != 0.0) break;
+        }
+        return h;
+    }
     float* p[2] = {pa, pb};
     int ping = 0;
-    mg_vcycle(g, r, z, &st->done);
-    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, true, st, red_ctx(g, 0));
-    OF_LAUNCH_CHECK();
-    KState h;
+    pcg_init_body(g, r, z, st);
     const int every = std::max(1, check_every / 4);
     for (;;) {
         for (int k = 0; k < every; ++k) {
-            OpKrylovA<float> op{z, p[ping], p[1 - ping], Ap, st, red_ctx(g, 0), 1.0f,
-                                make_double2(0.0, 0.0)};
-            launch_stencil<float, 4>(g, g->w32, op);
-            ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float) * (double)n);
-            launch(krylov_update<float, true>, vec_blocks(n), 256, g->stream, 
-                n, x, r, p[1 - ping], Ap, st, red_ctx(g, 0));
-            OF_LAUNCH_CHECK();
-            mg_vcycle(g, r, z, &st->done);
-            launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
-            OF_LAUNCH_CHECK();
+            pcg_step_body(g, x, r, p[ping], p[1 - ping], Ap, z, st);
             ping ^= 1;
         }
         fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
@@ -517,14 +678,26 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
                                   (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
             total_iters += (int)hi.iters;
-            launch(k_promote_add<T64, T32>, vec_blocks(n), 256, g->stream, n, x, e32);
+            launch(k_promote_add<T64, T32>, vec_blocks(n), 256, g->stream, n, x, (const T32*)e32, (const KState*)s32);
             OF_LAUNCH_CHECK();
-            if (hi.breakdown != 0.0 && hi.iters == 0) { status = OF_EBREAKDOWN; break; }
+            if (hi.breakdown != 0.0 && hi.iters == 0) {
+                status = OF_EBREAKDOWN;
+                set_error("Krylov solve (FP32 inner, %s): breakdown at the start of refinement pass "
+                          "%d: inner |r|^2 %.3e, r^T M r %.3e, p^T A p %.3e, outer |r|^2 %.3e, tol2 %.3e",
+                          pcg ? "multigrid PCG" : "CG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
+                          h.rr, h.tol2);
+                break;
+            }
         } else {
             KState hi = iterate<T64>(g, KS64, x, r, (T64*)ar.pa64, (T64*)ar.pb64, (T64*)ar.Ap64,
                                      a, Q, g->w64, o.check_every);
             total_iters = (int)hi.iters;
-            if (hi.breakdown != 0.0 && hi.rr > hi.tol2) { status = OF_EBREAKDOWN; break; }
+            if (hi.breakdown != 0.0 && hi.rr > hi.tol2) {
+                status = OF_EBREAKDOWN;
+                set_error("Krylov solve (FP64): breakdown after %d iterations: |r|^2 %.3e, p^T A p %.3e",
+                          total_iters, hi.rr, hi.pAp_re);
+                break;
+            }
         }
         residual<T64>(g, KS64, x, b, r, a, Q);   // true residual; restarts the recurrence
         ++refinements;
@@ -538,7 +711,6 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     if (status == OF_ENOCONV)
         set_error("Krylov solve: %d iterations, relative residual %.3e > tol %.1e", total_iters,
                   bb > 0 ? std::sqrt(h.rr / bb) : 0.0, o.tol);
-    if (status == OF_EBREAKDOWN) set_error("Krylov solve: breakdown after %d iterations", total_iters);
     return status;
 }
 

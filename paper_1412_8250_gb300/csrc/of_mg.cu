@@ -15,7 +15,11 @@
 #include <cmath>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "of_stencil.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace of {
 
@@ -33,10 +37,12 @@ struct MG {
     std::vector<MGLevel> lv;
     int deg = 2;
     int deg_coarse = 16;
-    std::vector<float> ca, cb;     // smoother coefficients per step (level-independent form)
-    float theta_inv = 0.f;
+    int first_small = 1;   // levels from here down run inside one thread block
     bool ok = false;
 };
+
+constexpr long long MG_SMALL_POINTS = 16384;   // levels this small run in one block
+constexpr int MG_MAX_LEVELS = 10;
 
 void mg_destroy(MG* m) { delete m; }
 
@@ -116,7 +122,8 @@ static bool build(of_grid* g, MG& m) {
         for (int a = 0; a < 3; ++a) h[a] *= 2.0;
         N = 1;
     }
-    if (lv.size() < 2 || lv.back().d.n > 65536) return false;
+    if (lv.size() < 2 || lv.size() > (size_t)MG_MAX_LEVELS || lv.back().d.n > MG_SMALL_POINTS)
+        return false;
     float* base = (float*)ws(g, WS_MG, sizeof(float) * (total + 64 * lv.size()));
     size_t off = 0;
     for (auto& L : lv) {
@@ -131,6 +138,8 @@ static bool build(of_grid* g, MG& m) {
     const MGLevel& C = m.lv.back();
     const double kappa = C.lmax / std::max(C.lmin, 1e-12f);
     m.deg_coarse = std::min(96, std::max(8, (int)std::ceil(2.0 * std::sqrt(kappa))));
+    m.first_small = (int)m.lv.size() - 1;
+    while (m.first_small > 1 && m.lv[m.first_small - 1].d.n <= MG_SMALL_POINTS) --m.first_small;
     return true;
 }
 
@@ -232,42 +241,133 @@ __global__ void k_prolong_add(Dims f, Dims c, const float* __restrict__ e, float
     x[idx] += s;
 }
 
-// Coarsest level: Chebyshev iteration for A x = b with the second-order operator, one block.
-__global__ void __launch_bounds__(1024) k_coarse_cheby(Dims d, float cx, float cy, float cz,
-                                                       float centre, float invD, float theta,
-                                                       float delta, int steps, const float* b,
-                                                       float* x, float* r, float* dv,
-                                                       const double* done) {
-    if (*done != 0.0) return;
-    const int n = (int)d.n;
-    const float sigma1 = theta / delta;
-    float rho = 1.f / sigma1;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        x[i] = 0.f;
-        r[i] = b[i];
-        dv[i] = b[i] * invD / theta;
+// ---- the small levels inside one thread block (second-order operator on all of them)
+struct SmallLevels {
+    int count;
+    int deg;
+    int deg_coarse;
+    float ctheta, cdelta;
+    Dims d[MG_MAX_LEVELS];
+    float cx[MG_MAX_LEVELS], cy[MG_MAX_LEVELS], cz[MG_MAX_LEVELS], centre[MG_MAX_LEVELS];
+    float invD[MG_MAX_LEVELS], theta[MG_MAX_LEVELS];
+    float ca[MG_MAX_LEVELS][4], cb[MG_MAX_LEVELS][4];
+    float *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS], *dv[MG_MAX_LEVELS];
+};
+
+// (L_h a)(i) for the 7-point operator of level l
+__device__ __forceinline__ float lap7(const SmallLevels& P, int l, const float* a, int i) {
+    const Dims& d = P.d[l];
+    const int ix = i % d.n1, iy = (i / d.n1) % d.n2, iz = i / (d.n1 * d.n2);
+    const int sx = d.n1, sy = d.n1 * d.n2;
+    return P.centre[l] * a[i] +
+           P.cx[l] * (a[i - ix + wrapc(ix + 1, d.n1)] + a[i - ix + wrapc(ix - 1, d.n1)]) +
+           P.cy[l] * (a[i + (wrapc(iy + 1, d.n2) - iy) * sx] + a[i + (wrapc(iy - 1, d.n2) - iy) * sx]) +
+           P.cz[l] * (a[i + (wrapc(iz + 1, d.n3) - iz) * sy] + a[i + (wrapc(iz - 1, d.n3) - iz) * sy]);
+}
+
+// The small levels run on one thread-block cluster (MG_CLUSTER CTAs of 1024 threads, one per
+// SM) that steps through the phases of the V-cycle with hardware cluster barriers.
+constexpr int MG_CLUSTER = 8;
+
+__device__ __forceinline__ int cl_tid() { return blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int cl_stride() { return gridDim.x * blockDim.x; }
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+
+// Chebyshev smoothing of level l (zero initial guess, or starting from x), whole cluster
+__device__ void blk_smooth(const SmallLevels& P, int l, bool zero) {
+    const int n = (int)P.d[l].n;
+    float *x = P.x[l], *b = P.b[l], *r = P.r[l], *dv = P.dv[l];
+    const float s0 = P.invD[l] / P.theta[l];
+    if (zero) {
+        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = b[i] * s0;
+    } else {
+        for (int i = cl_tid(); i < n; i += cl_stride()) r[i] = b[i] + lap7(P, l, x, i);
+        cl_sync();
+        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = r[i] * s0;
     }
-    __syncthreads();
-    for (int s = 0; s < steps; ++s) {
-        const float rho_new = 1.f / (2.f * sigma1 - rho);
-        const float a = rho_new * rho, bb = 2.f * rho_new / delta;
-        // phase 1: x += d ; r -= A d  (A d = -(centre d + sum_axes c (d(+1) + d(-1))))
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const int ix = i % d.n1, iy = (i / d.n1) % d.n2, iz = i / (d.n1 * d.n2);
-            const float dc = dv[i];
-            const float lap = centre * dc +
-                              cx * (dv[i - ix + wrapc(ix + 1, d.n1)] + dv[i - ix + wrapc(ix - 1, d.n1)]) +
-                              cy * (dv[i + (wrapc(iy + 1, d.n2) - iy) * d.n1] +
-                                    dv[i + (wrapc(iy - 1, d.n2) - iy) * d.n1]) +
-                              cz * (dv[i + (wrapc(iz + 1, d.n3) - iz) * d.n1 * d.n2] +
-                                    dv[i + (wrapc(iz - 1, d.n3) - iz) * d.n1 * d.n2]);
-            x[i] += dc;
-            r[i] += lap;
+    cl_sync();
+    for (int k = 0; k < P.deg; ++k) {
+        const bool first = zero && k == 0;
+        for (int i = cl_tid(); i < n; i += cl_stride()) {
+            x[i] = first ? dv[i] : x[i] + dv[i];
+            r[i] = (first ? b[i] : r[i]) + lap7(P, l, dv, i);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) dv[i] = a * dv[i] + bb * invD * r[i];
-        __syncthreads();
-        rho = rho_new;
+        cl_sync();
+        if (k + 1 < P.deg) {
+            for (int i = cl_tid(); i < n; i += cl_stride())
+                dv[i] = P.ca[l][k] * dv[i] + P.cb[l][k] * P.invD[l] * r[i];
+            cl_sync();
+        }
+    }
+}
+
+__global__ void __cluster_dims__(MG_CLUSTER, 1, 1) __launch_bounds__(1024)
+k_small_vcycle(SmallLevels P, const double* done) {
+    if (*done != 0.0) return;
+    const float w[3] = {0.25f, 0.5f, 0.25f};
+    for (int l = 0; l + 1 < P.count; ++l) {
+        blk_smooth(P, l, true);
+        const Dims f = P.d[l], c = P.d[l + 1];
+        const float* r = P.r[l];
+        for (int I = cl_tid(); I < (int)c.n; I += cl_stride()) {
+            const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
+            float s = 0.f;
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int fx = wrapc(2 * ci + dx, f.n1), fy = wrapc(2 * cj + dy, f.n2),
+                                  fz = wrapc(2 * ck + dz, f.n3);
+                        s += w[dz + 1] * w[dy + 1] * w[dx + 1] * r[(fz * f.n2 + fy) * f.n1 + fx];
+                    }
+            P.b[l + 1][I] = s;
+        }
+        cl_sync();
+    }
+    {   // coarsest: Chebyshev over the whole non-zero spectrum from a zero guess
+        const int l = P.count - 1;
+        const int n = (int)P.d[l].n;
+        float *x = P.x[l], *b = P.b[l], *r = P.r[l], *dv = P.dv[l];
+        const float sigma1 = P.ctheta / P.cdelta;
+        float rho = 1.f / sigma1;
+        for (int i = cl_tid(); i < n; i += cl_stride()) {
+            x[i] = 0.f;
+            r[i] = b[i];
+            dv[i] = b[i] * P.invD[l] / P.ctheta;
+        }
+        cl_sync();
+        for (int s = 0; s < P.deg_coarse; ++s) {
+            const float rn = 1.f / (2.f * sigma1 - rho);
+            const float a = rn * rho, bb = 2.f * rn / P.cdelta;
+            for (int i = cl_tid(); i < n; i += cl_stride()) {
+                x[i] += dv[i];
+                r[i] += lap7(P, l, dv, i);
+            }
+            cl_sync();
+            for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = a * dv[i] + bb * P.invD[l] * r[i];
+            cl_sync();
+            rho = rn;
+        }
+    }
+    for (int l = P.count - 2; l >= 0; --l) {
+        const Dims f = P.d[l], c = P.d[l + 1];
+        const float* e = P.x[l + 1];
+        float* x = P.x[l];
+        for (int i = cl_tid(); i < (int)f.n; i += cl_stride()) {
+            const int fi = i % f.n1, fj = (i / f.n1) % f.n2, fk = i / (f.n1 * f.n2);
+            const int I0 = fi >> 1, J0 = fj >> 1, K0 = fk >> 1;
+            const int I1 = (fi & 1) ? wrapc(I0 + 1, c.n1) : I0;
+            const int J1 = (fj & 1) ? wrapc(J0 + 1, c.n2) : J0;
+            const int K1 = (fk & 1) ? wrapc(K0 + 1, c.n3) : K0;
+            const float wx = (fi & 1) ? 0.5f : 1.0f, wy = (fj & 1) ? 0.5f : 1.0f,
+                        wz = (fk & 1) ? 0.5f : 1.0f;
+            auto at = [&](int I, int J, int K) { return e[(K * c.n2 + J) * c.n1 + I]; };
+            x[i] += wz * (wy * (wx * at(I0, J0, K0) + (1.f - wx) * at(I1, J0, K0)) +
+                          (1.f - wy) * (wx * at(I0, J1, K0) + (1.f - wx) * at(I1, J1, K0))) +
+                    (1.f - wz) * (wy * (wx * at(I0, J0, K1) + (1.f - wx) * at(I1, J0, K1)) +
+                                  (1.f - wy) * (wx * at(I0, J1, K1) + (1.f - wx) * at(I1, J1, K1)));
+        }
+        cl_sync();
+        blk_smooth(P, l, false);
     }
 }
 
@@ -294,7 +394,7 @@ static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const doubl
     double theta;
     cheby_coeffs(0.15 * L.lmax, 1.05 * L.lmax, deg, a, b, theta);
     if (!zero_guess) {
-        launch_stencil_dims<float, 4>(g, L.d, L.N, L.W, OpResid32{L.x, L.b, L.r, done});
+        launch_stencil_dims<float, 2>(g, L.d, L.N, L.W, OpResid32{L.x, L.b, L.r, done});
     }
     float* din = zero_guess ? L.b : L.r;
     float* dbuf[2] = {L.d0, L.d1};
@@ -310,36 +410,64 @@ static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const doubl
         op.a = a[k];
         op.bD = b[k] * L.invD;
         op.done = done;
-        launch_stencil_dims<float, 4>(g, L.d, L.N, L.W, op);
+        launch_stencil_dims<float, 2>(g, L.d, L.N, L.W, op);
     }
 }
 
-// z = M^{-1} r (one V-cycle); r, z fine-level FP32 fields
+// z = M^{-1} r (one V-cycle); r, z fine-level FP32 fields.  Levels above first_small are
+// swept by grid-wide launches, the rest by k_small_vcycle in one block.
 void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
     MG& m = *g->mg;
     const int nl = (int)m.lv.size();
+    const int fs = m.first_small;
     m.lv[0].b = const_cast<float*>(r);
     m.lv[0].x = z;
-    for (int l = 0; l < nl - 1; ++l) {
+    for (int l = 0; l < fs; ++l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
         smooth(g, L, m.deg, true, done);   // x_l = S b_l, r_l = b_l - A x_l
+        ProfScope ps(g, PC_MG_TRANSFER, sizeof(float) * (double)(L.d.n + C.d.n));
         launch(k_restrict, (unsigned)((C.d.n + 255) / 256), 256, g->stream, L.d, C.d, L.r, C.b, done);
-        OF_LAUNCH_CHECK();
     }
     {
-        MGLevel& C = m.lv[nl - 1];
-        const double theta = 0.5 * (C.lmax + C.lmin), delta = 0.5 * (C.lmax - C.lmin);
-        launch(k_coarse_cheby, 1, 1024, g->stream, C.d, C.W.w[0][1], C.W.w[1][1], C.W.w[2][1],
-                                                  C.W.centre, C.invD, (float)theta, (float)delta,
-                                                  m.deg_coarse, C.b, C.x, C.r, C.d0, done);
-        OF_LAUNCH_CHECK();
+        SmallLevels P{};
+        P.count = nl - fs;
+        P.deg = m.deg;
+        P.deg_coarse = m.deg_coarse;
+        const MGLevel& C = m.lv[nl - 1];
+        P.ctheta = 0.5f * (C.lmax + C.lmin);
+        P.cdelta = 0.5f * (C.lmax - C.lmin);
+        for (int k = 0; k < P.count; ++k) {
+            const MGLevel& L = m.lv[fs + k];
+            P.d[k] = L.d;
+            P.cx[k] = L.W.w[0][1];
+            P.cy[k] = L.W.w[1][1];
+            P.cz[k] = L.W.w[2][1];
+            P.centre[k] = L.W.centre;
+            P.invD[k] = L.invD;
+            std::vector<float> a, b;
+            double theta;
+            cheby_coeffs(0.15 * L.lmax, 1.05 * L.lmax, m.deg, a, b, theta);
+            P.theta[k] = (float)theta;
+            for (int j = 0; j < m.deg && j < 4; ++j) {
+                P.ca[k][j] = a[j];
+                P.cb[k][j] = b[j];
+            }
+            P.x[k] = L.x;
+            P.b[k] = L.b;
+            P.r[k] = L.r;
+            P.dv[k] = L.d0;
+        }
+        ProfScope ps(g, PC_MG_TRANSFER, 0.0);
+        launch(k_small_vcycle, MG_CLUSTER, 1024, g->stream, P, done);
     }
-    for (int l = nl - 2; l >= 0; --l) {
+    for (int l = fs - 1; l >= 0; --l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
-        launch(k_prolong_add, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d, C.x, L.x, done);
-        OF_LAUNCH_CHECK();
+        {
+            ProfScope ps(g, PC_MG_TRANSFER, sizeof(float) * (double)(2 * L.d.n + C.d.n));
+            launch(k_prolong_add, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d, C.x, L.x, done);
+        }
         smooth(g, L, m.deg, false, done);
     }
 }

@@ -382,7 +382,7 @@ static double brent_minimise(F&& f, double a, double b, double c, double fb, dou
 // Bracket from s = 0 along increasing s (golden expansion while f decreases, shrink while it
 // does not), then Brent.  Returns 0 when no decrease is found.
 template <class F>
-static double line_minimum(F&& f, double s_try, int& evals) {
+static double line_minimum(F&& f, double s_try, double tol, int& evals) {
     const double gold = 1.618033988749895;
     const double f0 = f(0.0);
     double b = std::fabs(s_try), fb = f(b);
@@ -419,7 +419,7 @@ static double line_minimum(F&& f, double s_try, int& evals) {
         if (fb >= f0) return 0.0;
         a = 0.0;
     }
-    return brent_minimise(f, a, b, c, fb, 1e-8, 100, evals);
+    return brent_minimise(f, a, b, c, fb, tol, 100, evals);
 }
 
 // Device vectors used by the ground-state driver.
@@ -452,8 +452,8 @@ static void poisson_into(of_grid* g, const double* a, const double* b, double* p
 
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
 static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
-                 const double* V, double tol, int max_iter, int n_restart, const KrylovOpts& po,
-                 ScfStats& st) {
+                 const double* V, double tol, int max_iter, int n_restart, double line_tol,
+                 const KrylovOpts& po, ScfStats& st) {
     const long long n = g->d.n;
     const double dV = g->dV;
     const int nb = vb(n);
@@ -528,7 +528,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
             return tfxc + vw + vl + hart;
         };
         int evals = 0;
-        const double s = line_minimum(energy, s_prev, evals);
+        const double s = line_minimum(energy, s_prev, line_tol, evals);
         st.line += evals;
         if (s == 0.0) break;   // energy flat to rounding along d: stagnated
         const double c = std::sqrt(Ne / (uu + 2.0 * s * ud + s * s * dd));
@@ -700,9 +700,14 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
     int hist_count = 0, hist_head = 0;
     double err = 0.0;
     bool inner_ok = true;
+    double prev_err = 1.0;
     for (int k = 0; k < std::max(1, o->fp_max_iter); ++k) {
-        inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, o->nlcg_tol, o->nlcg_max_iter,
-                        std::max(1, o->nlcg_restart), po, st);
+        // inexact inner solves while the outer iteration is far from its fixed point
+        const double tol_k = (lr && o->nlcg_tol_rel > 0.0)
+                                 ? std::max(o->nlcg_tol, o->nlcg_tol_rel * prev_err)
+                                 : o->nlcg_tol;
+        inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, tol_k, o->nlcg_max_iter,
+                        std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3, po, st);
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
         t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, ko, st, nullptr);
@@ -711,10 +716,11 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         double nf[2];
         fetch_scalars(g, SC_FP, 2, nf);
         err = nf[1] > 0 ? std::sqrt(nf[0] / nf[1]) : 0.0;
+        prev_err = err;
         if (o->verbose)
             fprintf(stderr, "[of] outer %d: fp error %.3e, nlcg %d, poisson its %d, kernel its %d\n",
                     k, err, st.nlcg, st.poisson, st.kernel);
-        if (err < o->fp_tol) break;
+        if (err < o->fp_tol && tol_k <= o->nlcg_tol) break;
         if (k + 1 >= o->fp_max_iter) break;
         // history: S = V_k - V_{k-1}, Y = f_k - f_{k-1}
         if (k > 0 && m > 0) {
@@ -786,6 +792,7 @@ void of_default_scf_opts(of_scf_opts* o) {
     of_default_solve_opts(&o->poisson);
     of_default_solve_opts(&o->kernel);
     o->verbose = 0;
+    o->line_tol = 1e-3;
 }
 
 of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double* u,

@@ -51,15 +51,23 @@ constexpr int ST_THREADS = ST_BX * ST_BY;
 //   T load(long long i) const            -- value of the differentiated field at i
 //   void store(long long i, T c, T lap)  -- c = field at i, lap = (L_h field)(i)
 //   void end()                           -- called by every thread of every active block
+//
+// Pipeline per z-plane (one barrier per plane): the x-y tile of plane z+1 (with its periodic
+// halo) sits in registers, loaded one plane ahead; it is written to the free half of a
+// double-buffered shared tile while plane z is computed from the other half.  The z
+// neighbours of each thread's points shift through a register queue, whose newest entry
+// (plane z+N) is also loaded one plane ahead.  In-plane offsets of the tile elements a
+// thread loads are computed once per block.
 template <typename T, int N, int RY, class Op>
 __global__ void __launch_bounds__(ST_THREADS)
 stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
-    using R = typename Real<T>::type;
     constexpr int TY = ST_BY * RY;
     constexpr int SX = ST_BX + 2 * N;
     constexpr int SY = TY + 2 * N;
+    constexpr int TILE = SX * SY;
+    constexpr int PER = (TILE + ST_THREADS - 1) / ST_THREADS;
     constexpr int Q = 2 * N + 1;
-    __shared__ T tile[SY][SX];
+    __shared__ T tile[2][SY][SX];
     __shared__ int xi[SX];
     __shared__ int yi[SY];
 
@@ -86,8 +94,23 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
         rowoff[r] = (long long)yi[yl + N] * n1 + xs;
         yin[r] = (y0 + yl) < n2;
     }
+    int goff[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = tid + k * ST_THREADS;
+        if (e < TILE) {
+            const int sy = e / SX, sx = e - sy * SX;
+            goff[k] = yi[sy] * n1 + xi[sx];
+        } else {
+            goff[k] = 0;
+        }
+    }
+    T* tile0 = &tile[0][0][0];
+    T* tile1 = &tile[1][0][0];
 
     T q[RY][Q];
+    T pre[PER];
+    T qn[RY];
     const int zend = min(z0 + cz, n3);
     if (z0 < n3) {
 #pragma unroll
@@ -96,18 +119,41 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
 #pragma unroll
             for (int r = 0; r < RY; ++r) q[r][j] = op.load(zo + rowoff[r]);
         }
-        for (int z = z0; z < zend; ++z) {
-            {
-                const long long zo = (long long)wrap_index(z + N, n3) * plane;
+        {   // plane z0 straight into buffer 0; plane z0 + 1 and queue entry z0 + N into registers
+            const long long zo = (long long)z0 * plane;
 #pragma unroll
-                for (int r = 0; r < RY; ++r) q[r][2 * N] = op.load(zo + rowoff[r]);
+            for (int k = 0; k < PER; ++k) {
+                const int e = tid + k * ST_THREADS;
+                if (e < TILE) tile0[e] = op.load(zo + goff[k]);
+            }
+            const long long z1 = (long long)wrap_index(z0 + 1, n3) * plane;
+#pragma unroll
+            for (int k = 0; k < PER; ++k) pre[k] = op.load(z1 + goff[k]);
+            const long long zq = (long long)wrap_index(z0 + N, n3) * plane;
+#pragma unroll
+            for (int r = 0; r < RY; ++r) qn[r] = op.load(zq + rowoff[r]);
+        }
+        __syncthreads();
+        int buf = 0;
+        for (int z = z0; z < zend; ++z) {
+            T* cur = buf ? tile1 : tile0;
+            T* nxt = buf ? tile0 : tile1;
+#pragma unroll
+            for (int r = 0; r < RY; ++r) q[r][2 * N] = qn[r];
+            if (z + 1 < zend) {
+#pragma unroll
+                for (int k = 0; k < PER; ++k) {
+                    const int e = tid + k * ST_THREADS;
+                    if (e < TILE) nxt[e] = pre[k];
+                }
+                const long long z2 = (long long)wrap_index(z + 2, n3) * plane;
+#pragma unroll
+                for (int k = 0; k < PER; ++k) pre[k] = op.load(z2 + goff[k]);
+                const long long zq = (long long)wrap_index(z + 1 + N, n3) * plane;
+#pragma unroll
+                for (int r = 0; r < RY; ++r) qn[r] = op.load(zq + rowoff[r]);
             }
             const long long zc = (long long)z * plane;
-            for (int e = tid; e < SX * SY; e += ST_THREADS) {
-                const int sy = e / SX, sx = e - sy * SX;
-                tile[sy][sx] = op.load(zc + (long long)yi[sy] * n1 + xi[sx]);
-            }
-            __syncthreads();
 #pragma unroll
             for (int r = 0; r < RY; ++r) {
                 const int ly = ty + r * ST_BY + N, lx = tx + N;
@@ -116,8 +162,8 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
 #pragma unroll
                 for (int p = 1; p <= N; ++p) {
                     acc = vfma(W.w[2][p], vadd(q[r][N + p], q[r][N - p]), acc);
-                    acc = vfma(W.w[0][p], vadd(tile[ly][lx + p], tile[ly][lx - p]), acc);
-                    acc = vfma(W.w[1][p], vadd(tile[ly + p][lx], tile[ly - p][lx]), acc);
+                    acc = vfma(W.w[0][p], vadd(cur[ly * SX + lx + p], cur[ly * SX + lx - p]), acc);
+                    acc = vfma(W.w[1][p], vadd(cur[(ly + p) * SX + lx], cur[(ly - p) * SX + lx]), acc);
                 }
                 if (xin && yin[r]) op.store(zc + (long long)(y0 + ty + r * ST_BY) * n1 + x, c, acc);
             }
@@ -126,6 +172,7 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
             for (int r = 0; r < RY; ++r)
 #pragma unroll
                 for (int j = 0; j < 2 * N; ++j) q[r][j] = q[r][j + 1];
+            buf ^= 1;
         }
     }
     op.end();
@@ -206,6 +253,9 @@ inline RedCtx red_ctx(of_grid* g, int out_index) {
 
 // sum of a[i] * (b ? b[i] : 1) over i < n into rc.out[0] (defined in of_krylov.cu)
 __global__ void k_sum_product(long long n, const double* a, const double* b, RedCtx rc);
+
+// cached CUDA graphs of the Krylov solvers (of_krylov.cu)
+void destroy_graphs(void* graphs);
 
 // multigrid preconditioner (of_mg.cu): z = one V-cycle applied to r (FP32 fine-level fields)
 bool mg_available(of_grid* g);

@@ -79,11 +79,12 @@ def test_tfw_config1_against_golden(prec):
     assert abs(np.sum(u * u) * np.prod(np.array(cell.L) / np.array(cell.n)) - cell.n_electrons) < 1e-10
 
 
-@pytest.mark.parametrize("prec", [B.OF_F64, B.OF_F32])
-def test_wt_small_cell_against_golden(prec):
+@pytest.mark.parametrize("prec,inexact", [(B.OF_F64, 0.0), (B.OF_F32, 0.0), (B.OF_F32, 1e-3)])
+def test_wt_small_cell_against_golden(prec, inexact):
     rec = _golden()["al4_wt"]
     cell = _cell_from(rec)
-    res, F, u, phi = _run(cell, Fn.wt(), prec)
+    res, F, u, phi = _run(cell, Fn.wt(), prec, nlcg_tol_rel=inexact, anderson_m=3,
+                          anderson_zeta=1.0)
     assert res.converged, (res.fp_error, res.nlcg_residual)
     assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
     assert abs(res.e_lr - rec["terms"]["lr"]) / cell.n_atoms <= 1e-5
