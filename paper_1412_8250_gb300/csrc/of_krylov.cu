@@ -17,6 +17,7 @@
 // device memory, so the host only synchronises every `check_every` iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -465,34 +466,6 @@ static Arena arena(of_grid* g) {
     return a;
 }
 
-// Runs Krylov iterations on state `st` until its done flag is set.  Returns host copy.
-template <typename T>
-static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
-                      typename KT<T>::R a, double2 Q, const Weights<typename KT<T>::R>& W,
-                      int check_every) {
-    KState* st = kstate(g, st_off);
-    const long long n = g->d.n;
-    constexpr int RY = KT<T>::cplx ? 1 : 2;
-    OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(T) * n, g->stream));
-    T* p[2] = {pa, pb};
-    int ping = 0;
-    KState h;
-    for (;;) {
-        for (int k = 0; k < check_every; ++k) {
-            OpKrylovA<T> op{r, p[ping], p[1 - ping], Ap, st, red_ctx(g, 0), a, Q};
-            launch_stencil<T, RY>(g, W, op);
-            ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(T) * (double)n);
-            launch(krylov_update<T>, vec_blocks(n), 256, g->stream, n, x, r, p[1 - ping], Ap, st,
-                                                                    red_ctx(g, 0));
-            OF_LAUNCH_CHECK();
-            ping ^= 1;
-        }
-        fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
-        if (h.done != 0.0) break;
-    }
-    return h;
-}
-
 // CUDA graphs of the preconditioned CG: "init" (V-cycle + first r^T z) and "pair" (two full
 // iterations, ping and pong of the direction buffers).  Every kernel reads its scalars and the
 // stop flag from device memory, so the same executable graph serves every solve on the grid's
@@ -504,12 +477,32 @@ struct PcgGraphs {
     double init_bytes = 0.0, pair_bytes = 0.0;
 };
 
+// Graphs of two plain CG / COCG iterations, keyed by buffers and operator constants.
+struct PlainGraph {
+    const void* key[8];
+    double consts[3];
+    cudaGraphExec_t exec;
+    unsigned long long kernels;
+    double bytes;
+};
+
+struct Graphs {
+    PcgGraphs pcg;
+    std::vector<PlainGraph> plain;
+};
+
 void destroy_graphs(void* p) {
-    PcgGraphs* G = (PcgGraphs*)p;
+    Graphs* G = (Graphs*)p;
     if (!G) return;
-    if (G->init) cudaGraphExecDestroy(G->init);
-    if (G->pair) cudaGraphExecDestroy(G->pair);
+    if (G->pcg.init) cudaGraphExecDestroy(G->pcg.init);
+    if (G->pcg.pair) cudaGraphExecDestroy(G->pcg.pair);
+    for (auto& e : G->plain) cudaGraphExecDestroy(e.exec);
     delete G;
+}
+
+static Graphs& graphs(of_grid* g) {
+    if (!g->graphs) g->graphs = new Graphs();
+    return *(Graphs*)g->graphs;
 }
 
 template <class Body>
@@ -550,8 +543,9 @@ static cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kern
     return exec;
 }
 
-static void replay(of_grid* g, cudaGraphExec_t exec, unsigned long long kernels, double bytes) {
-    ProfScope ps(g, PC_PCG_GRAPH, bytes);
+static void replay(of_grid* g, cudaGraphExec_t exec, unsigned long long kernels, double bytes,
+                   int cls = PC_PCG_GRAPH) {
+    ProfScope ps(g, cls, bytes);
     OF_CUDA(cudaGraphLaunch(exec, g->stream));
     __atomic_add_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);
 }
@@ -578,6 +572,69 @@ static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pou
     launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
 }
 
+// One plain CG / COCG iteration: p_out = r + beta p_in with A p_out and p^T A p in one sweep,
+// then the update of x and r with the next beta.
+template <typename T>
+static void krylov_step(of_grid* g, KState* st, T* x, T* r, T* pin, T* pout, T* Ap,
+                        typename KT<T>::R a, double2 Q, const Weights<typename KT<T>::R>& W) {
+    const long long n = g->d.n;
+    constexpr int RY = KT<T>::cplx ? 1 : 2;
+    OpKrylovA<T> op{r, pin, pout, Ap, st, red_ctx(g, 0), a, Q};
+    launch_stencil<T, RY>(g, W, op);
+    ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(T) * (double)n);
+    launch(krylov_update<T>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st, red_ctx(g, 0));
+}
+
+// Runs Krylov iterations on state `st` until its done flag is set.  Returns host copy.  Pairs
+// of iterations (ping and pong of the direction buffers) are replayed from a cached CUDA graph
+// keyed by the buffers and the operator's constants.
+template <typename T>
+static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
+                      typename KT<T>::R a, double2 Q, const Weights<typename KT<T>::R>& W,
+                      int check_every) {
+    KState* st = kstate(g, st_off);
+    const long long n = g->d.n;
+    OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(T) * n, g->stream));
+    KState h;
+    if (std::getenv("OF_NO_GRAPHS") == nullptr) {
+        Graphs& G = graphs(g);
+        const void* key[8] = {x, r, pa, pb, Ap, st, &W, (const void*)(uintptr_t)sizeof(T)};
+        const double consts[3] = {(double)a, Q.x, Q.y};
+        PlainGraph* e = nullptr;
+        for (auto& c : G.plain)
+            if (!std::memcmp(c.key, key, sizeof(key)) && !std::memcmp(c.consts, consts, sizeof(consts))) e = &c;
+        if (!e) {
+            PlainGraph c{};
+            std::memcpy(c.key, key, sizeof(key));
+            std::memcpy(c.consts, consts, sizeof(consts));
+            c.exec = capture(g, [&] {
+                krylov_step<T>(g, st, x, r, pa, pb, Ap, a, Q, W);
+                krylov_step<T>(g, st, x, r, pb, pa, Ap, a, Q, W);
+            }, c.kernels, c.bytes);
+            G.plain.push_back(c);
+            e = &G.plain.back();
+        }
+        const int pairs = std::max(1, check_every / 2);
+        for (;;) {
+            for (int k = 0; k < pairs; ++k) replay(g, e->exec, e->kernels, e->bytes, PC_KRYLOV_GRAPH);
+            fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+            if (h.done != 0.0) break;
+        }
+        return h;
+    }
+    T* p[2] = {pa, pb};
+    int ping = 0;
+    for (;;) {
+        for (int k = 0; k < check_every; ++k) {
+            krylov_step<T>(g, st, x, r, p[ping], p[1 - ping], Ap, a, Q, W);
+            ping ^= 1;
+        }
+        fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+        if (h.done != 0.0) break;
+    }
+    return h;
+}
+
 // Preconditioned CG (multigrid V-cycle) on A = -L in FP32.  Without profiling the iterations
 // run as replays of captured CUDA graphs; with profiling on, as individual launches so that
 // every kernel class can be timed.
@@ -589,8 +646,7 @@ static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa,
     KState h;
     const bool use_graphs = std::getenv("OF_NO_GRAPHS") == nullptr;
     if (use_graphs) {
-        if (!g->graphs) g->graphs = new PcgGraphs();
-        PcgGraphs& G = *(PcgGraphs*)g->graphs;
+        PcgGraphs& G = graphs(g).pcg;
         const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
         if (!G.pair || std::memcmp(key, G.key, sizeof(key)) != 0) {
             if (G.init) cudaGraphExecDestroy(G.init);
