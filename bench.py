@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--compare-f64", action="store_true",
                    help="also time one plain FP64 CG ground state and report it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the 64-cell batched-vs-sequential Poisson comparison")
     p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf"],
                    help="run only a bounded piece of the step (for profiler captures) and exit: "
                         "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil320 = "
@@ -161,6 +163,63 @@ def stencil_rates(torch, B, h, shape, reps=30):
         n = x.numel()
         out[name] = {"gpts": n / (ms * 1e-3) / 1e9, "ms": ms,
                      "gbs": 2 * n * x.element_size() / (ms * 1e-3) / 1e9}
+    return out
+
+
+def batched_compare(torch, B, W, reps=2):
+    """64 uneven cells (reps 2..4 per axis, 64-128 points per axis, half with a vacancy, seed 3):
+    the Poisson problem of each cell's initial density (uniform electrons plus its Gaussian
+    nuclear charge), solved to relative residual 1e-10 by (a) one batched call, (b) the
+    single-grid solver cell by cell with the same plain FP32 CG + FP64 refinement, (c) cell by
+    cell with the multigrid-preconditioned CG."""
+    cells = W.batched_cells()
+    stream = torch.cuda.current_stream()
+    grids, rhos, phis = [], [], []
+    for c in cells:
+        g = B.of_grid_create(c.n, c.L, 6, stream)
+        b = torch.empty(c.shape, dtype=torch.float64, device="cuda")
+        B.of_pseudocharge(g, B.make_system(c.R, c.Z, c.sigma, c.rc), b)
+        vol = c.L[0] * c.L[1] * c.L[2]
+        rhos.append(b + c.n_electrons / vol)
+        phis.append(torch.zeros(c.shape, dtype=torch.float64, device="cuda"))
+        grids.append(g)
+    o = B.of_default_solve_opts()
+    o.precision = B.OF_F32
+    o.tol = 1e-10
+    o.no_multigrid = 1
+    om = B.of_default_solve_opts()
+    om.precision = B.OF_F32
+    om.tol = 1e-10
+
+    def run_batched():
+        for p in phis:
+            p.zero_()
+        return B.of_poisson_solve_batched(grids, rhos, phis, o)
+
+    def run_seq(opts):
+        for g, r, p in zip(grids, rhos, phis):
+            p.zero_()
+            B.of_poisson_solve(g, r, p, opts)
+
+    out = {}
+    run_batched()   # tunes the blocking, captures the graph
+    run_seq(o)
+    run_seq(om)
+    for name, fn in [("batched_plain_cg_s", run_batched), ("sequential_plain_cg_s", lambda: run_seq(o)),
+                     ("sequential_multigrid_pcg_s", lambda: run_seq(om))]:
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t = time.time()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.time() - t)
+        out[name] = min(ts)
+    out["cells"] = len(cells)
+    out["points"] = int(sum(c.n_points for c in cells))
+    out["atoms"] = int(sum(c.n_atoms for c in cells))
+    for g in grids:
+        B.of_grid_destroy(g)
     return out
 
 
@@ -330,6 +389,7 @@ def main():
     d2h = 2 * out_u.numel() * 8 + F_e2e.size * 8
 
     stencil = stencil_rates(torch, B, h, cell.shape)
+    batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
     compare = None
     if args.compare_f64 and rank == 0:
         _, h64, s64, fn64, o64 = make_case(torch, B, Fn, W, "f64")
@@ -382,7 +442,7 @@ def main():
                            "poisson_iterations": res.poisson_iterations,
                            "kernel_iterations": res.kernel_iterations,
                            "fp_error": res.fp_error, "max_force": float(np.abs(F).max())},
-                "kernel_profile": prof, "step_ms": step_ms}
+                "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched}
         if compare:
             line["compare"] = compare
         print(json.dumps(line), flush=True)

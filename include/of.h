@@ -45,7 +45,8 @@ typedef struct of_grid of_grid;
 /* Krylov solve options.  tol is the target of the true FP64 relative residual
  * ||b - A x|| / ||b||.  precision OF_F64: CG/COCG entirely in FP64.  OF_F32: iterative
  * refinement -- FP64 residual, FP32 Krylov solve of the correction to inner_tol, FP64
- * update -- repeated until tol.  Zero fields take defaults (tol 1e-10, max_iter 20000,
+ * update -- repeated until tol; the FP32 Poisson CG is preconditioned by a multigrid
+ * V-cycle unless no_multigrid is set.  Zero fields take defaults (tol 1e-10, max_iter 20000,
  * inner_tol 1e-5, check_every 8). */
 typedef struct {
     double tol;
@@ -53,6 +54,7 @@ typedef struct {
     int precision;
     double inner_tol;
     int check_every;
+    int no_multigrid;      /* 1: plain FP32 CG inner solve for Poisson (no V-cycle) */
 } of_solve_opts;
 
 typedef struct {
@@ -165,6 +167,17 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
 of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1, double L2, double L3,
                                    int fd_half_order, void* stream, const double* rho,
                                    double* phi, const of_solve_opts* opts, of_solve_info* info);
+
+/* Poisson solves (as of_poisson_solve) of ncells independent cells at once: grids[c] with
+ * rho[c] and phi[c] (device double*, in = guess, out = mean-free solution).  All grids must
+ * share the stream and the finite-difference order.  Every Krylov phase of all cells is one
+ * grouped launch and the lockstep FP32 CG iterations (FP64 refinement as in the OF_F32
+ * mode, no multigrid) are replayed from one CUDA graph; the z extent of the stencil blocks is
+ * chosen per set of grid shapes by timing candidates on the first call.  infos (optional)
+ * receives one record per cell.  Synchronises the stream. */
+of_status of_poisson_solve_batched(int ncells, of_grid* const* grids, const double* const* rho,
+                                   double* const* phi, const of_solve_opts* opts,
+                                   of_solve_info* infos);
 
 /* b = sum over ions and periodic images of b_J (Sec. 3.2) on the grid (device double*),
  * and the self-energy term -(1/2) sum_J int b_J V_J (host double, may be NULL). */

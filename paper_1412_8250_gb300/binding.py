@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OF_OK", 1: "OF_EINVAL", 2: "OF_ENOMEM", 3: "OF_ECUDA", 4: "O
 
 class of_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("check_every", C.c_int)]
+                ("inner_tol", C.c_double), ("check_every", C.c_int), ("no_multigrid", C.c_int)]
 
 
 class of_solve_info(C.Structure):
@@ -86,6 +86,8 @@ _SIGNATURES = {
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
     "of_last_error": (C.c_char_p, []),
     "of_poisson_solve_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _I, _P, _P, _P,
+                                      C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_poisson_solve_batched": (_I, [_I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                       C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
     "of_launch_count": (C.c_ulonglong, []),
     "of_kernel_class_name": (C.c_char_p, [_I]),
@@ -293,3 +295,15 @@ def of_poisson_solve_noalloc(n, L, fd_half_order, stream, rho, phi, opts=None, a
                                          C.byref(opts) if opts else None, C.byref(info))
     _check(st, "of_poisson_solve_noalloc", allow)
     return info
+
+
+def of_poisson_solve_batched(grids, rhos, phis, opts=None, allow=()):
+    """Batched Poisson solves of independent cells (see include/of.h); returns the infos."""
+    nc = len(grids)
+    G = (_P * nc)(*[g.value if isinstance(g, _P) else g for g in grids])
+    R = (_P * nc)(*[_ptr(x) for x in rhos])
+    F = (_P * nc)(*[_ptr(x) for x in phis])
+    infos = (of_solve_info * nc)()
+    st = load().of_poisson_solve_batched(nc, G, R, F, C.byref(opts) if opts else None, infos)
+    _check(st, "of_poisson_solve_batched", allow)
+    return list(infos)

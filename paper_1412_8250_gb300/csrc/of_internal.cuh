@@ -276,6 +276,7 @@ struct KrylovOpts {
     int precision;
     double inner_tol;
     int check_every;
+    int no_multigrid;
 };
 KrylovOpts krylov_opts(const of_solve_opts* o);
 

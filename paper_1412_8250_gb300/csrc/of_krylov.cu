@@ -23,237 +23,9 @@
 #include <mutex>
 #include <type_traits>
 
-#include "of_stencil.cuh"
+#include "of_krylov.cuh"
 
 namespace of {
-
-// Device solver state, all doubles so it can be fetched with fetch_scalars.
-struct KState {
-    double rr;                  // 0  Hermitian |r|^2
-    double tol2;                // 1  stop when rr <= tol2
-    double rho_re, rho_im;      // 2  bilinear r^T r (= rr for real fields)
-    double pAp_re, pAp_im;      // 4
-    double alpha_re, alpha_im;  // 6
-    double beta_re, beta_im;    // 8
-    double done;                // 10
-    double iters;               // 11
-    double maxit;               // 12
-    double breakdown;           // 13
-    double red[4];              // 14 reduction outputs
-    double zshift;              // 18 mean of the preconditioned vector (projected PCG), else 0
-    double scale;               // 19 FP32 inner solve: correction = scale * FP32 solution
-};
-constexpr int KSTATE_DOUBLES = sizeof(KState) / sizeof(double);
-constexpr int KS64 = 128;   // offsets in g->s.scalars
-constexpr int KS32 = 160;
-
-static KState* kstate(of_grid* g, int off) { return (KState*)(g->s.scalars + off); }
-
-template <typename T> struct KT;
-template <> struct KT<double> { static constexpr bool cplx = false; using R = double; };
-template <> struct KT<float> { static constexpr bool cplx = false; using R = float; };
-template <> struct KT<double2> { static constexpr bool cplx = true; using R = double; };
-template <> struct KT<float2> { static constexpr bool cplx = true; using R = float; };
-
-// Per-thread partial sums of FP32 fields are kept in FP32 (a thread sums only a few points;
-// GB300's FP64 rate is 1/64 of FP32) and widened to FP64 for the block and grid reduction.
-template <typename R> struct AccT { using type = double; };
-template <> struct AccT<float> { using type = float; };
-
-__device__ __forceinline__ float hn2f(float v) { return v * v; }
-__device__ __forceinline__ float hn2f(float2 v) { return v.x * v.x + v.y * v.y; }
-__device__ __forceinline__ double hn2f(double v) { return v * v; }
-__device__ __forceinline__ double hn2f(double2 v) { return v.x * v.x + v.y * v.y; }
-__device__ __forceinline__ float2 bilf(float a, float b) { return make_float2(a * b, 0.f); }
-__device__ __forceinline__ float2 bilf(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 bilf(double a, double b) { return make_double2(a * b, 0.0); }
-__device__ __forceinline__ double2 bilf(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// complex-or-real helpers: a scalar s (re, im) times a field value
-__device__ __forceinline__ double cs_mul(double2 s, double v) { return s.x * v; }
-__device__ __forceinline__ float cs_mul(double2 s, float v) { return (float)s.x * v; }
-__device__ __forceinline__ double2 cs_mul(double2 s, double2 v) {
-    return make_double2(s.x * v.x - s.y * v.y, s.x * v.y + s.y * v.x);
-}
-__device__ __forceinline__ float2 cs_mul(double2 s, float2 v) {
-    const float a = (float)s.x, b = (float)s.y;
-    return make_float2(a * v.x - b * v.y, a * v.y + b * v.x);
-}
-__device__ __forceinline__ double hn2(double v) { return v * v; }
-__device__ __forceinline__ double hn2(float v) { return (double)v * v; }
-__device__ __forceinline__ double hn2(double2 v) { return v.x * v.x + v.y * v.y; }
-__device__ __forceinline__ double hn2(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
-__device__ __forceinline__ double2 bil(double a, double b) { return make_double2(a * b, 0.0); }
-__device__ __forceinline__ double2 bil(float a, float b) { return make_double2((double)a * b, 0.0); }
-__device__ __forceinline__ double2 bil(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 bil(float2 a, float2 b) {
-    return make_double2((double)a.x * b.x - (double)a.y * b.y, (double)a.x * b.y + (double)a.y * b.x);
-}
-__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
-__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
-__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
-__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
-    const double d = b.x * b.x + b.y * b.y;
-    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
-}
-
-template <typename T> __device__ __forceinline__ T one();
-template <> __device__ __forceinline__ double one<double>() { return 1.0; }
-template <> __device__ __forceinline__ float one<float>() { return 1.f; }
-template <> __device__ __forceinline__ double2 one<double2>() { return make_double2(1.0, 0.0); }
-template <> __device__ __forceinline__ float2 one<float2>() { return make_float2(1.f, 0.f); }
-
-// Operator A v = a (-L v) + Q v
-template <typename T>
-__device__ __forceinline__ T apply_A(T c, T lap, typename KT<T>::R a, double2 Q) {
-    return vadd(vmul(-a, lap), cs_mul(Q, c));
-}
-
-// ---------------------------------------------------------------- fused stencil ops
-// r = b - A x ; reduces |r|^2 and r^T r into the state and resets the iteration scalars.
-template <typename T>
-struct OpResidual {
-    static constexpr int kClass = KT<T>::cplx ? PC_COCG_F64 : PC_STENCIL_F64, kWords = 3;
-    const T* x;
-    const T* b;
-    T* r;
-    KState* st;
-    RedCtx rc;
-    typename KT<T>::R a;
-    double2 Q;
-    double acc[3];
-    __device__ bool begin() { acc[0] = acc[1] = acc[2] = 0.0; return true; }
-    __device__ T load(long long i) const { return x[i]; }
-    __device__ void store(long long i, T c, T lap) {
-        const T rv = vsub(b[i], apply_A(c, lap, a, Q));
-        r[i] = rv;
-        acc[0] += hn2(rv);
-        const double2 s = bil(rv, rv);
-        acc[1] += s.x;
-        acc[2] += s.y;
-    }
-    __device__ void end() {
-        if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) &&
-            threadIdx.x == 0 && threadIdx.y == 0) {
-            st->rr = acc[0];
-            st->rho_re = acc[1];
-            st->rho_im = acc[2];
-            st->beta_re = st->beta_im = 0.0;
-            st->breakdown = 0.0;
-            st->zshift = 0.0;
-            st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
-        }
-    }
-};
-
-// p_out = r + beta p_in (halo included), Ap = A p_out; reduces p^T A p and sets alpha.
-template <typename T>
-struct OpKrylovA {
-    static constexpr int kClass = KT<T>::cplx ? (sizeof(typename KT<T>::R) == 8 ? PC_COCG_F64 : PC_COCG_F32)
-                                              : (sizeof(typename KT<T>::R) == 8 ? PC_CG_F64 : PC_CG_F32);
-    static constexpr int kWords = 4;   // read r (or z) and p, write p and A p
-    const T* r;
-    const T* pin;
-    T* pout;
-    T* Ap;
-    KState* st;
-    RedCtx rc;
-    typename KT<T>::R a;
-    double2 Q;
-    double2 beta;
-    double2 shift;
-    typename AccT<typename KT<T>::R>::type accp[2];
-    __device__ bool begin() {
-        if (st->done != 0.0) return false;
-        beta = make_double2(st->beta_re, st->beta_im);
-        shift = make_double2(-st->zshift, 0.0);
-        accp[0] = accp[1] = 0;
-        return true;
-    }
-    // p = (r - zshift) + beta p_in ; zshift is 0 except in the projected PCG
-    __device__ T load(long long i) const {
-        return vadd(vadd(r[i], cs_mul(shift, one<T>())), cs_mul(beta, pin[i]));
-    }
-    __device__ void store(long long i, T c, T lap) {
-        pout[i] = c;
-        const T av = apply_A(c, lap, a, Q);
-        Ap[i] = av;
-        const auto s = bilf(c, av);
-        accp[0] += s.x;
-        accp[1] += s.y;
-    }
-    __device__ void end() {
-        double acc[2] = {(double)accp[0], (double)accp[1]};
-        if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) &&
-            threadIdx.x == 0 && threadIdx.y == 0) {
-            const double2 pAp = make_double2(acc[0], acc[1]);
-            st->pAp_re = pAp.x;
-            st->pAp_im = pAp.y;
-            const double mag = fabs(pAp.x) + fabs(pAp.y);
-            const bool bad = KT<T>::cplx ? !(mag > 0.0) : !(pAp.x > 0.0);
-            if (bad) {
-                st->breakdown = 1.0;
-                st->done = 1.0;
-            } else {
-                const double2 al = cdiv(make_double2(st->rho_re, st->rho_im), pAp);
-                st->alpha_re = al.x;
-                st->alpha_im = al.y;
-            }
-        }
-    }
-};
-
-// x += alpha p ; r -= alpha Ap ; reduces |r|^2 and r^T r ; sets beta, iteration count, done.
-template <typename T, bool PRECOND = false>
-__global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict__ x,
-                                                     T* __restrict__ r, const T* __restrict__ p,
-                                                     const T* __restrict__ Ap, KState* st,
-                                                     RedCtx rc) {
-    if (st->done != 0.0) return;
-    const double2 al = make_double2(st->alpha_re, st->alpha_im);
-    typename AccT<typename KT<T>::R>::type a0 = 0, a1 = 0, a2 = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        x[i] = vadd(x[i], cs_mul(al, p[i]));
-        const T rv = vsub(r[i], cs_mul(al, Ap[i]));
-        r[i] = rv;
-        a0 += hn2f(rv);
-        if (!PRECOND) {
-            const auto s = bilf(rv, rv);
-            a1 += s.x;
-            a2 += s.y;
-        }
-    }
-    double acc[3] = {(double)a0, (double)a1, (double)a2};
-    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
-        const double2 rho_new = make_double2(acc[1], acc[2]);
-        const double2 rho_old = make_double2(st->rho_re, st->rho_im);
-        st->rr = acc[0];
-        st->iters += 1.0;
-        if (acc[0] <= st->tol2 || st->iters >= st->maxit) {
-            st->done = 1.0;
-        } else if (PRECOND) {
-            return;   // beta follows from r^T z once the preconditioner has run
-        } else if (!(fabs(rho_old.x) + fabs(rho_old.y) > 0.0)) {
-            st->breakdown = 1.0;
-            st->done = 1.0;
-        } else {
-            const double2 be = cdiv(rho_new, rho_old);
-            st->beta_re = be.x;
-            st->beta_im = be.y;
-        }
-        st->rho_re = rho_new.x;
-        st->rho_im = rho_new.y;
-    }
-}
 
 // Projected PCG on the singular periodic operator: the preconditioned vector is used with its
 // mean removed (z - zbar, zbar = mean z), so rounding in the constant mode, which the
@@ -431,11 +203,10 @@ __global__ void k_init_state(KState* st, int maxit) {
 }
 
 // ---------------------------------------------------------------- host drivers
-static int vec_blocks(long long n) { return red_blocks(n, 256 * 4); }
-
 KrylovOpts krylov_opts(const of_solve_opts* o) {
-    KrylovOpts k{1e-10, 20000, OF_F64, 1e-5, 8};
+    KrylovOpts k{1e-10, 20000, OF_F64, 1e-5, 8, 0};
     if (o) {
+        k.no_multigrid = o->no_multigrid;
         if (o->tol > 0) k.tol = o->tol;
         if (o->max_iter > 0) k.max_iter = o->max_iter;
         k.precision = o->precision;
@@ -443,111 +214,6 @@ KrylovOpts krylov_opts(const of_solve_opts* o) {
         if (o->check_every > 0) k.check_every = o->check_every;
     }
     return k;
-}
-
-// Arena of Krylov vectors: FP64 (r, pa, pb, Ap, b) and FP32 (r, pa, pb, Ap, e), complex-sized.
-struct Arena {
-    void* r64; void* pa64; void* pb64; void* Ap64; void* b64;
-    void* r32; void* pa32; void* pb32; void* Ap32; void* e32; void* z32;
-};
-
-static Arena arena(of_grid* g) {
-    const size_t n = (size_t)g->d.n;
-    const size_t s64 = ((n * sizeof(double2) + 255) / 256) * 256;
-    const size_t s32 = ((n * sizeof(float2) + 255) / 256) * 256;
-    char* base = (char*)ws(g, WS_K0, 5 * s64 + 6 * s32);
-    Arena a;
-    a.r64 = base; a.pa64 = base + s64; a.pb64 = base + 2 * s64; a.Ap64 = base + 3 * s64;
-    a.b64 = base + 4 * s64;
-    char* b32 = base + 5 * s64;
-    a.r32 = b32; a.pa32 = b32 + s32; a.pb32 = b32 + 2 * s32; a.Ap32 = b32 + 3 * s32;
-    a.e32 = b32 + 4 * s32;
-    a.z32 = b32 + 5 * s32;
-    return a;
-}
-
-// CUDA graphs of the preconditioned CG: "init" (V-cycle + first r^T z) and "pair" (two full
-// iterations, ping and pong of the direction buffers).  Every kernel reads its scalars and the
-// stop flag from device memory, so the same executable graph serves every solve on the grid's
-// arena; it is rebuilt only if a buffer address changes.
-struct PcgGraphs {
-    const void* key[8] = {};
-    cudaGraphExec_t init = nullptr, pair = nullptr;
-    unsigned long long init_kernels = 0, pair_kernels = 0;
-    double init_bytes = 0.0, pair_bytes = 0.0;
-};
-
-// Graphs of two plain CG / COCG iterations, keyed by buffers and operator constants.
-struct PlainGraph {
-    const void* key[8];
-    double consts[3];
-    cudaGraphExec_t exec;
-    unsigned long long kernels;
-    double bytes;
-};
-
-struct Graphs {
-    PcgGraphs pcg;
-    std::vector<PlainGraph> plain;
-};
-
-void destroy_graphs(void* p) {
-    Graphs* G = (Graphs*)p;
-    if (!G) return;
-    if (G->pcg.init) cudaGraphExecDestroy(G->pcg.init);
-    if (G->pcg.pair) cudaGraphExecDestroy(G->pcg.pair);
-    for (auto& e : G->plain) cudaGraphExecDestroy(e.exec);
-    delete G;
-}
-
-static Graphs& graphs(of_grid* g) {
-    if (!g->graphs) g->graphs = new Graphs();
-    return *(Graphs*)g->graphs;
-}
-
-template <class Body>
-static cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kernels,
-                               double& bytes) {
-    if (!g->cap_stream) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-    cudaStream_t saved = g->stream;
-    Prof* saved_prof = g->prof;
-    g->stream = g->cap_stream;
-    g->prof = nullptr;
-    const unsigned long long c0 = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
-    cudaGraph_t graph = nullptr;
-    OF_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-    g_capturing = true;
-    g_capture_bytes = 0.0;
-    try {
-        body();
-    } catch (...) {
-        g_capturing = false;
-        cudaStreamEndCapture(g->stream, &graph);
-        if (graph) cudaGraphDestroy(graph);
-        g->stream = saved;
-        g->prof = saved_prof;
-        throw;
-    }
-    g_capturing = false;
-    bytes = g_capture_bytes;
-    cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
-    g->stream = saved;
-    g->prof = saved_prof;
-    OF_CUDA(e);
-    kernels = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED) - c0;
-    __atomic_sub_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);   // captured, not launched
-    cudaGraphExec_t exec = nullptr;
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    OF_CUDA(e);
-    return exec;
-}
-
-static void replay(of_grid* g, cudaGraphExec_t exec, unsigned long long kernels, double bytes,
-                   int cls = PC_PCG_GRAPH) {
-    ProfScope ps(g, cls, bytes);
-    OF_CUDA(cudaGraphLaunch(exec, g->stream));
-    __atomic_add_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);
 }
 
 static void pcg_init_body(of_grid* g, float* r, float* z, KState* st) {
@@ -634,6 +300,8 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
     }
     return h;
 }
+
+void destroy_graphs(void* p) { destroy_graphs_impl(p); }
 
 // Preconditioned CG (multigrid V-cycle) on A = -L in FP32.  Without profiling the iterations
 // run as replays of captured CUDA graphs; with profiling on, as individual launches so that
@@ -724,7 +392,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             KState hi;
             bool pcg = false;
             if constexpr (std::is_same<T32, float>::value)
-                pcg = (a == 1.0 && Q.x == 0.0 && Q.y == 0.0 && mg_available(g));
+                pcg = (a == 1.0 && Q.x == 0.0 && Q.y == 0.0 && !o.no_multigrid && mg_available(g));
             if constexpr (std::is_same<T32, float>::value) {
                 if (pcg)
                     hi = iterate_pcg(g, KS32, e32, r32, (float*)ar.pa32, (float*)ar.pb32,
@@ -822,6 +490,7 @@ void of_default_solve_opts(of_solve_opts* o) {
     o->precision = OF_F64;
     o->inner_tol = 1e-5;
     o->check_every = 8;
+    o->no_multigrid = 0;
 }
 
 of_status of_poisson_solve(of_grid* g, const double* rho, double* phi, const of_solve_opts* opts,

@@ -58,9 +58,10 @@ constexpr int ST_THREADS = ST_BX * ST_BY;
 // neighbours of each thread's points shift through a register queue, whose newest entry
 // (plane z+N) is also loaded one plane ahead.  In-plane offsets of the tile elements a
 // thread loads are computed once per block.
+// One block's share of a sweep: tile (bx, by) of the x-y plane, planes [bz*cz, bz*cz + cz).
 template <typename T, int N, int RY, class Op>
-__global__ void __launch_bounds__(ST_THREADS)
-stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
+__device__ __forceinline__ void stencil_tile(const Dims& d, const Weights<typename Real<T>::type>& W,
+                                             int cz, int bx, int by, int bz, Op& op) {
     constexpr int TY = ST_BY * RY;
     constexpr int SX = ST_BX + 2 * N;
     constexpr int SY = TY + 2 * N;
@@ -71,12 +72,11 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
     __shared__ int xi[SX];
     __shared__ int yi[SY];
 
-    if (!op.begin()) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + ST_BX * ty;
-    const int x0 = blockIdx.x * ST_BX;
-    const int y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * cz;
+    const int x0 = bx * ST_BX;
+    const int y0 = by * TY;
+    const int z0 = bz * cz;
     const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
     for (int t = tid; t < SX; t += ST_THREADS) xi[t] = wrap_index(x0 - N + t, n1);
     for (int t = tid; t < SY; t += ST_THREADS) yi[t] = wrap_index(y0 - N + t, n2);
@@ -175,6 +175,13 @@ stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
             buf ^= 1;
         }
     }
+}
+
+template <typename T, int N, int RY, class Op>
+__global__ void __launch_bounds__(ST_THREADS)
+stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
+    if (!op.begin()) return;
+    stencil_tile<T, N, RY, Op>(d, W, cz, blockIdx.x, blockIdx.y, blockIdx.z, op);
     op.end();
 }
 
