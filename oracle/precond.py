@@ -1,0 +1,153 @@
+"""Learned preconditioner: a small 3D convolutional network and its training loss.
+
+Oracle (test infrastructure only).  The paper suggests better preconditioning for its Krylov
+solves (Sec. 5.5) without specifying one; this is the reference for the network used as a
+preconditioner of the Poisson CG.  Network: three periodic 3x3x3 convolutions
+1 -> 16 -> 16 -> 1 channels with biases, GELU (exact, erf form) after the first two.
+Convolutions are cross-correlations, y[o](x) = b[o] + sum_c sum_t W[o][c][t] a[c](x + t),
+t over the 27 offsets (dz, dy, dx) in {-1,0,1}^3 in that nesting order, indices periodic.
+
+Loss for one residual r (normalised to unit RMS): the A-norm error of the correction y = net(r)
+against the exact correction e = A^{-1} r, up to the constant 1/2 e^T A e:
+    loss = 1/2 y^T A y - y^T r,   A = -L_h (Eq. FD:Laplacian),   d loss / d y = A y - r.
+
+Pins (tests/test_oracle_precond.py): every gradient against central finite differences of the
+loss; the periodic convolution against an explicit loop over offsets; the loss against the
+A-norm error of the spectral solution; the flexible CG against the spectral solution without a
+preconditioner, in one step with the exact inverse, step for step equal to CG when every
+network step is refused, and faster than CG with a linear SPD preconditioner.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import erf
+
+from .fd import Grid, laplacian
+
+OFFSETS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+CHANNELS = 16
+
+
+def init_params(seed=0, channels=CHANNELS):
+    """He-style random initial weights (float64)."""
+    rng = np.random.default_rng(seed)
+    c = channels
+    return dict(
+        W1=rng.normal(0, np.sqrt(2.0 / 27), size=(c, 1, 27)), b1=np.zeros(c),
+        W2=rng.normal(0, np.sqrt(2.0 / (27 * c)), size=(c, c, 27)), b2=np.zeros(c),
+        W3=rng.normal(0, np.sqrt(1.0 / (27 * c)), size=(1, c, 27)), b3=np.zeros(1))
+
+
+def shifted(a, t):
+    """a(x + t) for an array of shape (..., n3, n2, n1), periodic."""
+    dz, dy, dx = t
+    return np.roll(a, shift=(-dz, -dy, -dx), axis=(-3, -2, -1))
+
+
+def conv(a, W, b):
+    """Periodic 3x3x3 cross-correlation: a (C_in, n3, n2, n1) -> (C_out, n3, n2, n1)."""
+    out = np.zeros((W.shape[0],) + a.shape[1:])
+    for k, t in enumerate(OFFSETS):
+        sa = shifted(a, t)
+        out += np.einsum("oc,c...->o...", W[:, :, k], sa)
+    return out + b[:, None, None, None]
+
+
+def conv_backward(a, W, gy):
+    """Gradients of sum(gy * conv(a, W, b)) with respect to W, b and a."""
+    dW = np.zeros_like(W)
+    ga = np.zeros_like(a)
+    for k, t in enumerate(OFFSETS):
+        sa = shifted(a, t)
+        dW[:, :, k] = np.tensordot(gy, sa, axes=([1, 2, 3], [1, 2, 3]))
+        # d/da: sum_x gy[o](x) W[o][c][t] a[c](x + t)  ->  ga[c](x') += W gy[o](x' - t)
+        ga += np.einsum("oc,o...->c...", W[:, :, k], shifted(gy, tuple(-s for s in t)))
+    db = gy.reshape(gy.shape[0], -1).sum(1)
+    return dW, db, ga
+
+
+def gelu(z):
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def forward(P, r):
+    """net(r) for r of shape (n3, n2, n1); returns (y, cache)."""
+    a0 = r[None]
+    z1 = conv(a0, P["W1"], P["b1"])
+    a1 = gelu(z1)
+    z2 = conv(a1, P["W2"], P["b2"])
+    a2 = gelu(z2)
+    y = conv(a2, P["W3"], P["b3"])[0]
+    return y, (a0, z1, a1, z2, a2)
+
+
+def loss_and_grads(P, r, grid: Grid):
+    """A-norm loss of one residual (r is normalised here to unit RMS) and its parameter
+    gradients.  Returns (loss, grads dict)."""
+    r = r / np.sqrt(np.mean(r * r))
+    y, (a0, z1, a1, z2, a2) = forward(P, r)
+    Ay = -laplacian(y, grid)
+    loss = 0.5 * float(np.sum(y * Ay)) - float(np.sum(y * r))
+    gy = (Ay - r)[None]
+    dW3, db3, ga2 = conv_backward(a2, P["W3"], gy)
+    gz2 = ga2 * gelu_grad(z2)
+    dW2, db2, ga1 = conv_backward(a1, P["W2"], gz2)
+    gz1 = ga1 * gelu_grad(z1)
+    dW1, db1, _ = conv_backward(a0, P["W1"], gz1)
+    return loss, dict(W1=dW1, b1=db1, W2=dW2, b2=db2, W3=dW3, b3=db3)
+
+
+def apply(P, r):
+    """Preconditioner z = s * net(r / s), s = RMS of r (homogeneous of degree one)."""
+    s = np.sqrt(np.mean(r * r))
+    if s == 0.0:
+        return np.zeros_like(r)
+    return s * forward(P, r / s)[0]
+
+
+def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, precond=None):
+    """Flexible CG on A x = b, A = -L_h on mean-free fields.
+
+    The preconditioned vector z (the network z = s net(r / s), or `precond(r)` when given, mean
+    removed) is kept only while it is a clear descent direction, cos(r, z) > theta; otherwise
+    that iteration takes the plain direction z = r (Jacobi: the diagonal of A is a constant, so
+    its inverse is a multiple of the identity, which the step length absorbs).  Polak-Ribiere
+    beta = max(0, z^T (r - r_old) / (r_old^T z_old)), step alpha = r^T p / p^T A p.
+    Returns (x, iterations, network steps)."""
+    def choose(r):
+        if P is None and precond is None:
+            return r.copy(), False
+        z = precond(r) if precond is not None else apply(P, r)
+        z = z - z.mean()
+        nz = np.linalg.norm(z)
+        if nz > 0 and float(np.sum(r * z)) > theta * np.linalg.norm(r) * nz:
+            return z, True
+        return r.copy(), False
+
+    x = np.zeros_like(b)
+    r = b - b.mean()
+    nb = np.linalg.norm(r)
+    if nb == 0.0:
+        return x, 0, 0
+    z, used = choose(r)
+    net_steps = int(used)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    for it in range(1, max_iter + 1):
+        Ap = -laplacian(p, grid)
+        alpha = float(np.sum(r * p)) / float(np.sum(p * Ap))
+        x += alpha * p
+        r_new = r - alpha * Ap
+        if np.linalg.norm(r_new) < tol * nb:
+            return x, it, net_steps
+        z, used = choose(r_new)
+        net_steps += int(used)
+        beta = max(float(np.sum(z * (r_new - r))) / rz, 0.0)
+        rz = float(np.sum(r_new * z))
+        r = r_new
+        p = z + beta * p
+    return x, max_iter, net_steps

@@ -1,0 +1,105 @@
+"""Pins of the oracle's learned-preconditioner network: convolution, gradients, and the
+effect of a trained network on CG iterations."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import precond as NP
+from paper_1412_8250_gb300 import workloads as W
+
+
+def test_conv_matches_explicit_offsets():
+    rng = np.random.default_rng(0)
+    a = rng.normal(size=(2, 5, 6, 7))
+    Wt = rng.normal(size=(3, 2, 27))
+    b = rng.normal(size=3)
+    y = NP.conv(a, Wt, b)
+    n3, n2, n1 = a.shape[1:]
+    for (o, z, yy, x) in [(0, 0, 0, 0), (2, 4, 5, 6), (1, 2, 3, 1)]:
+        s = b[o]
+        for c in range(2):
+            for k, (dz, dy, dx) in enumerate(NP.OFFSETS):
+                s += Wt[o, c, k] * a[c, (z + dz) % n3, (yy + dy) % n2, (x + dx) % n1]
+        assert abs(y[o, z, yy, x] - s) < 1e-12
+
+
+def test_gradients_match_finite_differences():
+    grid = O.Grid((6, 7, 8), (1.5, 1.7, 1.9), 3)
+    P = NP.init_params(seed=1, channels=4)
+    for k in P:
+        P[k] = P[k] + 0.05 * np.random.default_rng(3).normal(size=P[k].shape)
+    r = W.random_field(grid.shape, seed=5)
+    loss, G = NP.loss_and_grads(P, r, grid)
+    rng = np.random.default_rng(9)
+    e = 1e-6
+    for name in P:
+        for _ in range(3):
+            idx = tuple(rng.integers(0, s) for s in P[name].shape)
+            Pp = {k: v.copy() for k, v in P.items()}
+            Pm = {k: v.copy() for k, v in P.items()}
+            Pp[name][idx] += e
+            Pm[name][idx] -= e
+            fd = (NP.loss_and_grads(Pp, r, grid)[0] - NP.loss_and_grads(Pm, r, grid)[0]) / (2 * e)
+            assert abs(fd - G[name][idx]) < 1e-5 * max(1.0, abs(fd)), (name, idx)
+
+
+def test_loss_is_a_norm_error_up_to_a_constant():
+    # 1/2 y^T A y - y^T r + 1/2 e^T A e = 1/2 (y - e)^T A (y - e) with A e = r
+    grid = O.Grid((8, 8, 8), (2.0, 2.0, 2.0), 6)
+    P = NP.init_params(seed=2, channels=4)
+    r = W.random_field(grid.shape, seed=6)
+    r -= r.mean()
+    loss, _ = NP.loss_and_grads(P, r, grid)
+    rn = r / np.sqrt(np.mean(r * r))
+    e = O.solve_shifted_spectral(rn, grid, 1.0, 0.0)
+    y, _ = NP.forward(P, rn)
+    d = y - e
+    d -= d.mean()
+    lhs = loss + 0.5 * float(np.sum(e * -O.laplacian(e, grid)))
+    rhs = 0.5 * float(np.sum(d * -O.laplacian(d, grid)))
+    # the constant mode of y is invisible to A; the y^T r term sees it only through mean(r) = 0
+    assert abs(lhs - rhs) < 1e-9 * max(1.0, abs(rhs))
+
+
+def _poisson_case(n=12, seed=11):
+    grid = O.Grid((n, n, n), (0.2375 * n,) * 3, 6)
+    b = W.random_field(grid.shape, seed=seed, kind="smooth") + 0.3 * W.random_field(grid.shape, seed=seed + 1)
+    b -= b.mean()
+    return grid, b, O.solve_shifted_spectral(b, grid, 1.0, 0.0)
+
+
+def test_flexible_cg_without_preconditioner_is_cg():
+    # no preconditioner: every step is the plain CG step; the answer is the spectral solution
+    grid, b, x_exact = _poisson_case()
+    x, its, used = NP.flexible_cg(b, grid, tol=1e-10)
+    x -= x.mean()
+    assert used == 0 and 5 < its < 500
+    assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
+
+
+def test_flexible_cg_with_exact_inverse_takes_one_step():
+    # M = A^{-1}: the first direction is the exact correction
+    grid, b, x_exact = _poisson_case()
+    inv = lambda r: O.solve_shifted_spectral(r - r.mean(), grid, 1.0, 0.0)  # noqa: E731
+    x, its, used = NP.flexible_cg(b, grid, tol=1e-10, precond=inv)
+    assert its == 1 and used == 1
+
+
+def test_flexible_cg_falls_back_on_an_ascent_direction():
+    # M r = -r is never accepted: the iteration is plain CG step for step
+    grid, b, _ = _poisson_case()
+    _, its_plain, _ = NP.flexible_cg(b, grid, tol=1e-10)
+    _, its, used = NP.flexible_cg(b, grid, tol=1e-10, precond=lambda r: -r)
+    assert used == 0 and its == its_plain
+
+
+def test_flexible_cg_with_spd_preconditioner_beats_cg():
+    # a linear SPD preconditioner (inverse of A + c) is accepted at every step with theta = 0
+    # and needs fewer iterations than CG; the answer is unchanged
+    grid, b, x_exact = _poisson_case()
+    M = lambda r: O.solve_shifted_spectral(r, grid, 1.0, 2.0)  # noqa: E731
+    _, its_plain, _ = NP.flexible_cg(b, grid, tol=1e-10)
+    x, its, used = NP.flexible_cg(b, grid, tol=1e-10, theta=0.0, precond=M)
+    x -= x.mean()
+    assert used == its and its < its_plain
+    assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
