@@ -41,13 +41,15 @@ typedef enum {
 } of_dtype;
 
 typedef struct of_grid of_grid;
+typedef struct of_precond of_precond;   /* learned preconditioner (of_precond_create) */
 
 /* Krylov solve options.  tol is the target of the true FP64 relative residual
  * ||b - A x|| / ||b||.  precision OF_F64: CG/COCG entirely in FP64.  OF_F32: iterative
  * refinement -- FP64 residual, FP32 Krylov solve of the correction to inner_tol, FP64
  * update -- repeated until tol; the FP32 Poisson CG is preconditioned by a multigrid
- * V-cycle unless no_multigrid is set.  Zero fields take defaults (tol 1e-10, max_iter 20000,
- * inner_tol 1e-5, check_every 8). */
+ * V-cycle unless no_multigrid is set, or by the learned network when precond is set (see
+ * of_precond_create).  Zero fields take defaults (tol 1e-10, max_iter 20000, inner_tol 1e-5,
+ * check_every 8, precond_theta 0.3). */
 typedef struct {
     double tol;
     int max_iter;
@@ -55,12 +57,17 @@ typedef struct {
     double inner_tol;
     int check_every;
     int no_multigrid;      /* 1: plain FP32 CG inner solve for Poisson (no V-cycle) */
+    of_precond* precond;   /* non-NULL with OF_F32: the FP32 Poisson inner solve is flexible
+                              CG preconditioned by this network (kernel solves ignore it) */
+    double precond_theta;  /* a network direction z is kept when cos(r, z) > theta, else the
+                              step is plain CG; default 0.3 */
 } of_solve_opts;
 
 typedef struct {
     int iterations;        /* Krylov iterations (all passes) */
     int refinements;       /* FP64 residual evaluations */
     double rel_residual;   /* final true FP64 relative residual */
+    int net_steps;         /* flexible-CG steps that took the learned network's direction */
 } of_solve_info;
 
 /* Ions: positions R[3*M] (x, y, z per ion, bohr), charges Z[M]; each carries the Gaussian
@@ -211,6 +218,43 @@ of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functio
  * u is accepted for the interface of the paper's statement and not read. */
 of_status of_forces(of_grid* g, const of_system* sys, const double* u, const double* phi,
                     double* F);
+
+/* ---- learned preconditioner (Sec. 5.5 asks for better preconditioning; the network is this
+ * library's answer, not the paper's) ----
+ * A three-layer periodic 3D convolutional network, 1 -> 16 -> 16 -> 1 channels, 3x3x3
+ * kernels, exact GELU after the first two layers: y(x) = b + sum_c sum_t W[o][c][t] a[c](x+t),
+ * t over (dz, dy, dx) in {-1,0,1}^3 with dz outermost and dx innermost.  Parameters are one
+ * float array of of_precond_num_params() = 7809 values: W1[16][27], b1[16], W2[16][16][27],
+ * b2[16], W3[16][27], b3.  Kernels keep weights and activations in BF16 and sum in FP32.
+ * Applied to a residual r as z = s net(r / s), s = RMS of r.  Trained on residuals r (of the
+ * grid's Poisson operator A = -L_h) with the loss 1/2 y^T A y - y^T r, y = net(r / s), which
+ * equals half the A-norm error of y against A^{-1} r up to a constant.  The handle lives on the
+ * current device; every call that takes a grid requires the grid on that device and enqueues
+ * on the grid's stream. */
+int of_precond_num_params(void);
+/* Copies params (host, 7809 floats) to a new handle.  OF_EINVAL on a wrong count. */
+of_status of_precond_create(const float* params, int nparams, of_precond** out);
+of_status of_precond_destroy(of_precond* P);
+/* Current FP32 master parameters to host params[7809]. */
+of_status of_precond_get_params(of_precond* P, float* params, int nparams);
+/* z = s net(r / s) for device float fields r, z (r != z).  Synchronises. */
+of_status of_precond_apply(of_grid* g, of_precond* P, const float* r, float* z);
+/* Loss of one device float residual r and its parameter gradient (host grad[7809], may be
+ * NULL).  Synchronises. */
+of_status of_precond_loss_grad(of_grid* g, of_precond* P, const float* r, double* loss, float* grad);
+/* Adam (beta 0.9, 0.999) for `steps` steps on mini-batches of `batch` residuals: step s uses
+ * samples[order[s * batch + k] * n], k < batch (samples: device, nsamples x n floats; order:
+ * host, steps * batch indices in [0, nsamples)).  loss_out: the last mini-batch's mean loss
+ * per point.  Synchronises. */
+of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int nsamples,
+                           const int* order, int steps, int batch, float lr, double* loss_out);
+/* Training data from the solver itself: runs FP32 CG on the grid's Poisson system for the
+ * device density rho (right-hand side 4 pi (rho - mean rho), scaled to unit RMS) and copies
+ * every stride-th residual, the first one included, to samples[k * n] (device, room for
+ * max_samples fields); stops at relative residual 1e-6 or once max_samples are taken;
+ * *count = residuals written.  Synchronises. */
+of_status of_precond_collect(of_grid* g, const double* rho, int stride, int max_samples,
+                             float* samples, int* count);
 
 /* Message of the last failure on this host thread ("" if none). */
 const char* of_last_error(void);

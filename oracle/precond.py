@@ -109,15 +109,15 @@ def apply(P, r):
     return s * forward(P, r / s)[0]
 
 
-def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, precond=None):
-    """Flexible CG on A x = b, A = -L_h on mean-free fields.
+def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, precond=None, m=4):
+    """Flexible CG on A x = b, A = -L_h on mean-free fields (truncated FCG(m) after Notay).
 
     The preconditioned vector z (the network z = s net(r / s), or `precond(r)` when given, mean
     removed) is kept only while it is a clear descent direction, cos(r, z) > theta; otherwise
     that iteration takes the plain direction z = r (Jacobi: the diagonal of A is a constant, so
-    its inverse is a multiple of the identity, which the step length absorbs).  Polak-Ribiere
-    beta = max(0, z^T (r - r_old) / (r_old^T z_old)), step alpha = r^T p / p^T A p.
-    Returns (x, iterations, network steps)."""
+    its inverse is a multiple of the identity, which the step length absorbs).  The direction
+    is z made A-conjugate to the last m directions, p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j,
+    and the step is alpha = r^T p / p^T A p.  Returns (x, iterations, network steps)."""
     def choose(r):
         if P is None and precond is None:
             return r.copy(), False
@@ -135,19 +135,20 @@ def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, preco
         return x, 0, 0
     z, used = choose(r)
     net_steps = int(used)
-    p = z.copy()
-    rz = float(np.sum(r * z))
+    p = z
+    past = []   # (p_j, A p_j, p_j^T A p_j), newest last
     for it in range(1, max_iter + 1):
         Ap = -laplacian(p, grid)
-        alpha = float(np.sum(r * p)) / float(np.sum(p * Ap))
+        pAp = float(np.sum(p * Ap))
+        alpha = float(np.sum(r * p)) / pAp
         x += alpha * p
-        r_new = r - alpha * Ap
-        if np.linalg.norm(r_new) < tol * nb:
+        r = r - alpha * Ap
+        past = (past + [(p, Ap, pAp)])[-m:]
+        if np.linalg.norm(r) < tol * nb:
             return x, it, net_steps
-        z, used = choose(r_new)
+        z, used = choose(r)
         net_steps += int(used)
-        beta = max(float(np.sum(z * (r_new - r))) / rz, 0.0)
-        rz = float(np.sum(r_new * z))
-        r = r_new
-        p = z + beta * p
+        p = z.copy()
+        for (pj, Apj, pApj) in past:
+            p -= (float(np.sum(z * Apj)) / pApj) * pj
     return x, max_iter, net_steps

@@ -22,12 +22,13 @@ STATUS_NAMES = {0: "OF_OK", 1: "OF_EINVAL", 2: "OF_ENOMEM", 3: "OF_ECUDA", 4: "O
 
 class of_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
-                ("inner_tol", C.c_double), ("check_every", C.c_int), ("no_multigrid", C.c_int)]
+                ("inner_tol", C.c_double), ("check_every", C.c_int), ("no_multigrid", C.c_int),
+                ("precond", C.c_void_p), ("precond_theta", C.c_double)]
 
 
 class of_solve_info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("refinements", C.c_int),
-                ("rel_residual", C.c_double)]
+                ("rel_residual", C.c_double), ("net_steps", C.c_int)]
 
 
 class of_system(C.Structure):
@@ -89,6 +90,14 @@ _SIGNATURES = {
                                       C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
     "of_poisson_solve_batched": (_I, [_I, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                       C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_precond_num_params": (_I, []),
+    "of_precond_create": (_I, [C.POINTER(C.c_float), _I, C.POINTER(_P)]),
+    "of_precond_destroy": (_I, [_P]),
+    "of_precond_get_params": (_I, [_P, C.POINTER(C.c_float), _I]),
+    "of_precond_apply": (_I, [_P, _P, _P, _P]),
+    "of_precond_loss_grad": (_I, [_P, _P, _P, C.POINTER(_D), C.POINTER(C.c_float)]),
+    "of_precond_train": (_I, [_P, _P, _P, _I, C.POINTER(_I), _I, _I, C.c_float, C.POINTER(_D)]),
+    "of_precond_collect": (_I, [_P, _P, _I, _I, _P, C.POINTER(_I)]),
     "of_launch_count": (C.c_ulonglong, []),
     "of_kernel_class_name": (C.c_char_p, [_I]),
     "of_profile_enable": (_I, [_P, _I]),
@@ -307,3 +316,59 @@ def of_poisson_solve_batched(grids, rhos, phis, opts=None, allow=()):
     st = load().of_poisson_solve_batched(nc, G, R, F, C.byref(opts) if opts else None, infos)
     _check(st, "of_poisson_solve_batched", allow)
     return list(infos)
+
+
+# ------------------------------------------------------------- learned preconditioner
+def of_precond_num_params():
+    return int(load().of_precond_num_params())
+
+
+def of_precond_create(params):
+    """New network handle from host FP32 parameters (W1, b1, W2, b2, W3, b3 flattened)."""
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+    h = _P()
+    _check(load().of_precond_create(p.ctypes.data_as(C.POINTER(C.c_float)), int(p.size),
+                                    C.byref(h)), "of_precond_create")
+    return h
+
+
+def of_precond_destroy(P):
+    return _check(load().of_precond_destroy(P), "of_precond_destroy")
+
+
+def of_precond_get_params(P):
+    out = np.zeros(of_precond_num_params(), dtype=np.float32)
+    _check(load().of_precond_get_params(P, out.ctypes.data_as(C.POINTER(C.c_float)), int(out.size)),
+           "of_precond_get_params")
+    return out
+
+
+def of_precond_apply(h, P, r, z):
+    return _check(load().of_precond_apply(h, P, _ptr(r), _ptr(z)), "of_precond_apply")
+
+
+def of_precond_loss_grad(h, P, r):
+    loss = _D()
+    grad = np.zeros(of_precond_num_params(), dtype=np.float32)
+    _check(load().of_precond_loss_grad(h, P, _ptr(r), C.byref(loss),
+                                       grad.ctypes.data_as(C.POINTER(C.c_float))),
+           "of_precond_loss_grad")
+    return loss.value, grad
+
+
+def of_precond_train(h, P, samples, nsamples, order, steps, batch, lr):
+    o = np.ascontiguousarray(np.asarray(order, dtype=np.int32).ravel())
+    if o.size < steps * batch:
+        raise ValueError("order needs steps * batch entries")
+    loss = _D()
+    _check(load().of_precond_train(h, P, _ptr(samples), int(nsamples),
+                                   o.ctypes.data_as(C.POINTER(_I)), int(steps), int(batch),
+                                   float(lr), C.byref(loss)), "of_precond_train")
+    return loss.value
+
+
+def of_precond_collect(h, rho, stride, max_samples, samples):
+    count = _I()
+    _check(load().of_precond_collect(h, _ptr(rho), int(stride), int(max_samples), _ptr(samples),
+                                     C.byref(count)), "of_precond_collect")
+    return count.value

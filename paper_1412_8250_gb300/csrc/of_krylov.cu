@@ -204,9 +204,11 @@ __global__ void k_init_state(KState* st, int maxit) {
 
 // ---------------------------------------------------------------- host drivers
 KrylovOpts krylov_opts(const of_solve_opts* o) {
-    KrylovOpts k{1e-10, 20000, OF_F64, 1e-5, 8, 0};
+    KrylovOpts k{1e-10, 20000, OF_F64, 1e-5, 8, 0, nullptr, 0.3};
     if (o) {
         k.no_multigrid = o->no_multigrid;
+        k.precond = o->precond;
+        if (o->precond_theta > 0) k.theta = o->precond_theta;
         if (o->tol > 0) k.tol = o->tol;
         if (o->max_iter > 0) k.max_iter = o->max_iter;
         k.precision = o->precision;
@@ -375,6 +377,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
     const double bb = h.tol2 / (o.tol * o.tol);
     int total_iters = 0, refinements = 1;
+    double net_steps = 0.0;
     of_status status = OF_OK;
     if (!(bb > 0.0)) {   // zero right-hand side: the solution is zero
         OF_CUDA(cudaMemsetAsync(x, 0, sizeof(T64) * n, g->stream));
@@ -390,15 +393,19 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 n, r, r32, e32, o.inner_tol, st, s32, o.max_iter - total_iters, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
             KState hi;
-            bool pcg = false;
-            if constexpr (std::is_same<T32, float>::value)
-                pcg = (a == 1.0 && Q.x == 0.0 && Q.y == 0.0 && !o.no_multigrid && mg_available(g));
+            bool pcg = false, fcg = false;
             if constexpr (std::is_same<T32, float>::value) {
-                if (pcg)
+                const bool poisson_op = a == 1.0 && Q.x == 0.0 && Q.y == 0.0;
+                fcg = poisson_op && o.precond != nullptr;
+                pcg = poisson_op && !fcg && !o.no_multigrid && mg_available(g);
+                if (fcg)
+                    hi = iterate_fcg(g, o.precond, o.theta, KS32, e32, r32, (float*)ar.pa32,
+                                     (float*)ar.z32, o.check_every, nullptr, &net_steps);
+                else if (pcg)
                     hi = iterate_pcg(g, KS32, e32, r32, (float*)ar.pa32, (float*)ar.pb32,
                                      (float*)ar.Ap32, (float*)ar.z32, o.check_every);
             }
-            if (!pcg)
+            if (!pcg && !fcg)
                 hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
                                   (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
             total_iters += (int)hi.iters;
@@ -408,7 +415,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 status = OF_EBREAKDOWN;
                 set_error("Krylov solve (FP32 inner, %s): breakdown at the start of refinement pass "
                           "%d: inner |r|^2 %.3e, r^T M r %.3e, p^T A p %.3e, outer |r|^2 %.3e, tol2 %.3e",
-                          pcg ? "multigrid PCG" : "CG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
+                          fcg ? "flexible CG" : pcg ? "multigrid PCG" : "CG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
                           h.rr, h.tol2);
                 break;
             }
@@ -431,6 +438,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
         info->iterations += total_iters;
         info->refinements += refinements;
         info->rel_residual = bb > 0 ? std::sqrt(h.rr / bb) : 0.0;
+        info->net_steps += (int)net_steps;
     }
     if (status == OF_ENOCONV)
         set_error("Krylov solve: %d iterations, relative residual %.3e > tol %.1e", total_iters,
@@ -491,6 +499,8 @@ void of_default_solve_opts(of_solve_opts* o) {
     o->inner_tol = 1e-5;
     o->check_every = 8;
     o->no_multigrid = 0;
+    o->precond = nullptr;
+    o->precond_theta = 0.3;
 }
 
 of_status of_poisson_solve(of_grid* g, const double* rho, double* phi, const of_solve_opts* opts,

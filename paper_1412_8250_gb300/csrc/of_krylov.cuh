@@ -265,6 +265,11 @@ inline Arena arena(of_grid* g) {
 }
 
 
+// Flexible CG with the learned preconditioner (of_precond.cu); P == nullptr: plain CG.
+struct Sink;
+KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x, float* r,
+                   float* ra, float* z, int check_every, Sink* sink, double* net_steps);
+
 // CUDA graphs of the preconditioned CG: "init" (V-cycle + first r^T z) and "pair" (two full
 // iterations, ping and pong of the direction buffers).  Every kernel reads its scalars and the
 // stop flag from device memory, so the same executable graph serves every solve on the grid's

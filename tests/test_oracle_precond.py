@@ -86,7 +86,7 @@ def test_flexible_cg_with_exact_inverse_takes_one_step():
 
 
 def test_flexible_cg_falls_back_on_an_ascent_direction():
-    # M r = -r is never accepted: the iteration is plain CG step for step
+    # M r = -r is never accepted: the iteration is the plain one step for step
     grid, b, _ = _poisson_case()
     _, its_plain, _ = NP.flexible_cg(b, grid, tol=1e-10)
     _, its, used = NP.flexible_cg(b, grid, tol=1e-10, precond=lambda r: -r)
@@ -103,3 +103,12 @@ def test_flexible_cg_with_spd_preconditioner_beats_cg():
     x -= x.mean()
     assert used == its and its < its_plain
     assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
+
+
+def test_flexible_cg_keeps_conjugacy_with_more_directions():
+    # with a linear SPD preconditioner, orthogonalising against more past directions changes
+    # nothing in exact arithmetic (PCG directions are already A-conjugate): same count
+    grid, b, _ = _poisson_case()
+    M = lambda r: O.solve_shifted_spectral(r, grid, 1.0, 2.0)  # noqa: E731
+    counts = [NP.flexible_cg(b, grid, tol=1e-10, theta=0.0, precond=M, m=m)[1] for m in (1, 4, 8)]
+    assert max(counts) - min(counts) <= 1, counts
