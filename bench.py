@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--compare-f64", action="store_true",
                    help="also time one plain FP64 CG ground state and report it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-cell batched-vs-sequential Poisson comparison")
     p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf"],
@@ -223,6 +225,86 @@ def batched_compare(torch, B, W, reps=2):
     return out
 
 
+def _initial_density(torch, B, cell):
+    """Uniform electrons plus the cell's Gaussian nuclear charge: the density of the first
+    Poisson solve of a ground-state run."""
+    g = B.of_grid_create(cell.n, cell.L, 6, torch.cuda.current_stream())
+    b = torch.empty(cell.shape, dtype=torch.float64, device="cuda")
+    B.of_pseudocharge(g, B.make_system(cell.R, cell.Z, cell.sigma, cell.rc), b)
+    B.of_grid_destroy(g)
+    return b + cell.n_electrons / (cell.L[0] * cell.L[1] * cell.L[2])
+
+
+def learned_compare(torch, B, W, steps=400, theta=0.3):
+    """Learned preconditioner: trained on the GPU on CG residuals of the Poisson problems of the
+    4-atom 32^3 and the 108-atom 96^3 cells (64 residuals each; four Adam runs per cell, batch
+    4), then used in the FP32 flexible CG of the Poisson solve of the 864-atom 6x6x6 cell,
+    192^3 grid, same spacing, to true relative residual 1e-10; against the same solve with
+    plain (Jacobi) FP32 CG, plain FP64 CG and multigrid-preconditioned FP32 CG."""
+    import numpy as np
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    net = B.of_precond_create(W.initial_network(0))
+    data = []
+    for cell, stride in ((W.al4_cell(), 4), (W.al108_cell(), 8)):
+        rho = _initial_density(torch, B, cell)
+        g = B.of_grid_create(cell.n, cell.L, 6, stream)
+        s = torch.empty((64,) + cell.shape, dtype=torch.float32, device="cuda")
+        data.append((g, s, B.of_precond_collect(g, rho, stride, 64, s)))
+    rng = np.random.default_rng(0)
+    for rnd in range(4):
+        for g, s, cnt in data:
+            st = steps // 4
+            B.of_precond_train(g, net, s, cnt, rng.integers(0, cnt, size=st * 4), st, 4,
+                               3e-3 if rnd < 3 else 1e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    for g, _, _ in data:
+        B.of_grid_destroy(g)
+    del data
+    cell = W.al864_cell()
+    rho = _initial_density(torch, B, cell)
+    g = B.of_grid_create(cell.n, cell.L, 6, stream)
+    phi = torch.zeros_like(rho)
+
+    def opts(prec, no_mg, use_net):
+        o = B.of_default_solve_opts()
+        o.tol, o.precision, o.no_multigrid, o.inner_tol = 1e-10, prec, no_mg, 1e-4
+        if use_net:
+            o.precond, o.precond_theta = net, theta
+        return o
+
+    out = {"workload": "al864 Poisson (uniform density + ions), 192^3, tol 1e-10",
+           "training_s": train_s, "training_steps": steps, "theta": theta}
+    for name, o in (("jacobi_cg_mixed", opts(B.OF_F32, 1, False)),
+                    ("learned_fcg_mixed", opts(B.OF_F32, 1, True)),
+                    ("plain_cg_f64", opts(B.OF_F64, 1, False)),
+                    ("multigrid_pcg_mixed", opts(B.OF_F32, 0, False))):
+        phi.zero_()
+        B.of_poisson_solve(g, rho, phi, o)     # workspace, graphs
+        phi.zero_()
+        torch.cuda.synchronize()
+        t = time.time()
+        info = B.of_poisson_solve(g, rho, phi, o)
+        torch.cuda.synchronize()
+        out[name] = {"s": time.time() - t, "iterations": info.iterations,
+                     "refinements": info.refinements, "network_steps": info.net_steps,
+                     "rel_residual": info.rel_residual}
+    r = torch.randn(cell.shape, dtype=torch.float32, device="cuda")
+    z = torch.empty_like(r)
+    B.of_precond_apply(g, net, r, z)
+    torch.cuda.synchronize()
+    t = time.time()
+    for _ in range(10):
+        B.of_precond_apply(g, net, r, z)
+    torch.cuda.synchronize()
+    out["network_apply_ms"] = (time.time() - t) / 10 * 1e3
+    B.of_grid_destroy(g)
+    B.of_precond_destroy(net)
+    return out
+
+
 def cpu_sample(cell, nlcg_steps_per_gs, outer_per_gs, budget_s=25.0):
     """Time the oracle on a bounded sample of the same workload and extrapolate to one
     ground state: setup (pseudocharges, Poisson of b) + NLCG steps x (oracle time per NLCG
@@ -390,6 +472,7 @@ def main():
 
     stencil = stencil_rates(torch, B, h, cell.shape)
     batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
+    learned = None if (args.no_learned or rank != 0) else learned_compare(torch, B, W)
     compare = None
     if args.compare_f64 and rank == 0:
         _, h64, s64, fn64, o64 = make_case(torch, B, Fn, W, "f64")
@@ -442,7 +525,8 @@ def main():
                            "poisson_iterations": res.poisson_iterations,
                            "kernel_iterations": res.kernel_iterations,
                            "fp_error": res.fp_error, "max_force": float(np.abs(F).max())},
-                "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched}
+                "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched,
+                "learned_preconditioner": learned}
         if compare:
             line["compare"] = compare
         print(json.dumps(line), flush=True)

@@ -47,6 +47,15 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
     OF_CUDA(cudaGetLastError());
 }
 
+// Same, with `smem` bytes of dynamic shared memory (the caller raises the kernel's limit).
+template <typename... KArgs, typename... Args>
+inline void launch_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                        cudaStream_t stream, Args&&... args) {
+    kernel<<<grid, block, smem, stream>>>(std::forward<Args>(args)...);
+    __atomic_add_fetch(&g_launch_count, 1ull, __ATOMIC_RELAXED);
+    OF_CUDA(cudaGetLastError());
+}
+
 // Sampled per-class kernel timing with CUDA events on the launching stream.
 enum ProfClass {
     PC_STENCIL_F64 = 0, PC_STENCIL_F32, PC_CG_F64, PC_CG_F32, PC_COCG_F64, PC_COCG_F32,

@@ -2,6 +2,8 @@
 //
 // Network: three periodic 3x3x3 convolutions, 1 -> 16 -> 16 -> 1 channels with biases, exact
 // (erf) GELU after the first two; weights and stored activations in BF16, every sum in FP32.
+// The forward pass runs on the tensor cores (tcgen05.mma, accumulators in tensor memory); the
+// backward pass of training on the CUDA cores.
 // Training loss for one residual r (scaled to unit RMS): the A-norm error of the correction
 // y = net(r) against the exact correction e = A^{-1} r, up to the constant 1/2 e^T A e,
 //     loss = 1/2 y^T A y - y^T r,   A = -L_h,   d loss / d y = A y - r,
@@ -98,9 +100,126 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * __expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-__device__ __forceinline__ void load16(const __nv_bfloat16* p, float (&v)[NC]) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 u0 = __ldg(q), u1 = __ldg(q + 1);
+__device__ __forceinline__ void store8(__nv_bfloat16* p, const float (&v)[8]) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
+// ---------------------------------------------------------------- forward
+// ---------------------------------------------------------------- forward on the tensor cores
+// Layer 2 is the network's dense contraction: per point z2[o] = b2[o] + sum_t sum_c
+// W2[o][c][t] a1[x+t][c], 432 multiply-adds per output channel.  Over a tile of up to 128
+// consecutive points of one x-row it is the implicit GEMM D[128 x 16] = sum_t A_t B_t^T,
+// A_t[m][c] = a1[x_m + t][c], B_t[o][c] = W2[o][c][t]: 27 tcgen05.mma of shape M=128, N=16,
+// K=16 (BF16 operands, FP32 accumulators in tensor memory), issued by one thread.  The three
+// taps dx = -1, 0, 1 of one (dz, dy) plane read the same staged rows shifted by one row, so a
+// tile stages nine plane rows of length L + 2 (x0 - 1 .. x0 + L, wrapped) and each MMA's A
+// descriptor starts dx + 1 rows into its plane.  Each plane accumulates into its own 16
+// columns (nine short chains instead of one of 27).  Layer 3 (one output channel) is the same
+// contraction with B_t row 0 = W3[.][t] and rows 1-15 zero.  The epilogue reads the
+// accumulators with tcgen05.ld and sums them: layer 2 adds b2, applies GELU and stores BF16
+// (z2 too when training); layer 3 takes column 0, adds b3 and scales.  Layer 1 (one input
+// channel) is one GEMM with the 27 taps as K, padded to 32.
+// Shared-memory operands are K-major without swizzle: core matrices of 8 rows x 16 bytes
+// (8 BF16 channels), rows 16 bytes apart throughout (stride byte offset 128 per 8-row group),
+// channels 8-15 one plane-half further (leading byte offset = ROWS * 16).
+namespace tc {
+constexpr int M = 128;                   // rows per MMA (points per tile, padded)
+constexpr int THREADS = 256;             // two threads per row: channel halves
+constexpr int ROWS = M + 2;              // staged rows per plane: x0 - 1 .. x0 + 128
+constexpr int HALF = ROWS * 16;          // bytes of one channel half of a plane (2080)
+constexpr int PLANE = 2 * HALF;          // 4160
+constexpr int A_BYTES = 9 * PLANE;       // 37440
+constexpr int B_TAP = NC * NC * 2;       // 512 bytes per tap: 16 x 16 BF16
+constexpr int B_BYTES = NT * B_TAP;      // 13824
+constexpr int SMEM = 128 + 2 * A_BYTES + B_BYTES + 64;   // layers 2 and 3: two A buffers
+constexpr int SMEM1 = 128 + A_BYTES + 2 * B_TAP + 64;      // layer 1
+constexpr int ACC_COLS = 256;   // layers 2 and 3: nine 16-column accumulators (144 used); two
+                                // CTAs per SM fill the 512 columns of tensor memory
+// layer 1: A tile 128 rows x 32 taps, four K-blocks of 8 taps (2048 bytes each), then the
+// staged FP32 planes of r
+constexpr int L1_KB = M * 16;
+constexpr int L1_STAGE = 4 * L1_KB;
+static_assert(L1_STAGE + 9 * ROWS * 4 <= A_BYTES, "layer-1 staging must fit the A buffer");
+constexpr uint32_t A_LBO = HALF, A_SBO = 128;    // B tiles: (o/8, c/8) at (o/8)*256 + (c/8)*128
+constexpr uint32_t B_LBO = 128, B_SBO = 256;
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+// both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NC >> 3) << 17) |
+                           ((uint32_t)(M >> 4) << 24);
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // give up on a completion after 2 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45),
+// descriptor version 1 (bit 46), no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait for the phase of parity `parity` of an mbarrier
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    const unsigned long long t0 = now_ns();
+    for (int k = 0; k < (1 << 22); ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+        if ((k & 63) == 63 && now_ns() - t0 > WAIT_NS) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(tmem), "l"(a), "l"(b), "r"(IDESC), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+// loads without the wait: issue several, then one wait_ld()
+__device__ __forceinline__ void ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void ld1_nowait(uint32_t taddr, uint32_t& r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+}  // namespace tc
+
+// Activations a1, a2, z1, z2 are stored channel-half planar: channel c of point i at
+// p[((c / 8) * n + i) * 8 + c % 8], so that any run of consecutive points of one half is a
+// contiguous block that a bulk copy moves straight into the MMA operand layout.
+__device__ __forceinline__ void load16p(const __nv_bfloat16* p, long long n, long long i, float (&v)[NC]) {
+    const uint4 u0 = __ldg(reinterpret_cast<const uint4*>(p + i * 8));
+    const uint4 u1 = __ldg(reinterpret_cast<const uint4*>(p + (n + i) * 8));
     const __nv_bfloat162* h0 = reinterpret_cast<const __nv_bfloat162*>(&u0);
     const __nv_bfloat162* h1 = reinterpret_cast<const __nv_bfloat162*>(&u1);
 #pragma unroll
@@ -111,115 +230,335 @@ __device__ __forceinline__ void load16(const __nv_bfloat16* p, float (&v)[NC]) {
         v[8 + 2 * k] = f1.x; v[8 + 2 * k + 1] = f1.y;
     }
 }
-
-__device__ __forceinline__ void store16(__nv_bfloat16* p, const float (&v)[NC]) {
-    uint4 u0, u1;
-    __nv_bfloat162* h0 = reinterpret_cast<__nv_bfloat162*>(&u0);
-    __nv_bfloat162* h1 = reinterpret_cast<__nv_bfloat162*>(&u1);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        h0[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-        h1[k] = __floats2bfloat162_rn(v[8 + 2 * k], v[8 + 2 * k + 1]);
-    }
-    uint4* q = reinterpret_cast<uint4*>(p);
-    q[0] = u0;
-    q[1] = u1;
+__device__ __forceinline__ float getp(const __nv_bfloat16* p, long long n, long long i, int c) {
+    return __bfloat162float(p[((long long)(c >> 3) * n + i) * 8 + (c & 7)]);
 }
 
-// ---------------------------------------------------------------- forward
-// layer 1: z1 = W1 * (sgn r / s) + b1, a1 = GELU(z1); also rn = sgn r / s (training only)
-__global__ void __launch_bounds__(256) k_net_l1(Dims d, const float* __restrict__ r, const double* rms_dev,
-                                                float sgn, const __nv_bfloat16* __restrict__ P,
-                                                __nv_bfloat16* z1, __nv_bfloat16* a1, float* rn) {
-    __shared__ float W[NT * NC + NC];   // [t][o], then b1
-    for (int k = threadIdx.x; k < NT * NC; k += blockDim.x)
-        W[k] = __bfloat162float(P[OW1 + (k % NC) * NT + k / NC]);
-    for (int k = threadIdx.x; k < NC; k += blockDim.x) W[NT * NC + k] = __bfloat162float(P[OB1 + k]);
-    __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const double rms = *rms_dev;
-    const float inv = rms > 0.0 ? sgn * (float)(1.0 / rms) : 0.f;
-    const Nb nb = neighbours(d, i);
-    float acc[NC];
-#pragma unroll
-    for (int o = 0; o < NC; ++o) acc[o] = W[NT * NC + o];
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const float v = __ldg(r + nb.at(t)) * inv;
-#pragma unroll
-        for (int o = 0; o < NC; ++o) acc[o] = fmaf(W[t * NC + o], v, acc[o]);
+// B tiles (N = 16 output channels o x K = 16), K-major, (o/8, c/8) core matrices at
+// (o/8) * 256 + (c/8) * 128: per tap t for layers 2 and 3, per half h of the 32 padded taps
+// for layer 1
+template <int LAYER>
+__device__ __forceinline__ void fill_b(unsigned char* Bs, const __nv_bfloat16* __restrict__ P, float* bias) {
+    const int ntiles_b = LAYER == 1 ? 2 : NT;
+    for (int k = threadIdx.x; k < ntiles_b * NC * NC; k += blockDim.x) {
+        const int t = k / (NC * NC), o = (k / NC) % NC, c = k % NC;
+        __nv_bfloat16 w;
+        if (LAYER == 1) {
+            const int tap = 16 * t + c;
+            w = tap < NT ? P[OW1 + o * NT + tap] : __float2bfloat16(0.f);
+        } else if (LAYER == 2) {
+            w = P[OW2 + (o * NC + c) * NT + t];
+        } else {
+            w = o == 0 ? P[OW3 + c * NT + t] : __float2bfloat16(0.f);
+        }
+        *(__nv_bfloat16*)(Bs + t * tc::B_TAP + (o >> 3) * 256 + (c >> 3) * 128 + (o & 7) * 16 + (c & 7) * 2) = w;
     }
-    if (rn) rn[i] = r[i] * inv;
-    float g[NC];
-#pragma unroll
-    for (int o = 0; o < NC; ++o) g[o] = gelu_f(acc[o]);
-    if (z1) store16(z1 + i * NC, acc);
-    store16(a1 + i * NC, g);
+    const int tid = threadIdx.x;
+    if (tid < NC)
+        bias[tid] = LAYER == 1 ? __bfloat162float(P[OB1 + tid])
+                  : LAYER == 2 ? __bfloat162float(P[OB2 + tid])
+                               : (tid == 0 ? __bfloat162float(P[OB3]) : 0.f);
 }
 
-// layer 2: z2 = W2 * a1 + b2, a2 = GELU(z2); W2 staged as [t][c][o]
-__global__ void __launch_bounds__(256) k_net_l2(Dims d, const __nv_bfloat16* __restrict__ a1,
-                                                const __nv_bfloat16* __restrict__ P,
-                                                __nv_bfloat16* z2, __nv_bfloat16* a2) {
-    __shared__ __align__(16) float W[NT * NC * NC + NC];
-    for (int k = threadIdx.x; k < NT * NC * NC; k += blockDim.x) {
-        const int t = k / (NC * NC), c = (k / NC) % NC, o = k % NC;
-        W[k] = __bfloat162float(P[OW2 + (o * NC + c) * NT + t]);
+// first point of the x-row of each plane q = 3 (dz + 1) + (dy + 1) around row (y, z)
+__device__ __forceinline__ void plane_bases(const Dims& d, int y, int z, long long (&qb)[9]) {
+    const long long plane = (long long)d.n1 * d.n2;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int zz = z + q / 3 - 1, yy = y + q % 3 - 1;
+        const int zw = zz < 0 ? zz + d.n3 : (zz >= d.n3 ? zz - d.n3 : zz);
+        const int yw = yy < 0 ? yy + d.n2 : (yy >= d.n2 ? yy - d.n2 : yy);
+        qb[q] = (long long)zw * plane + (long long)yw * d.n1;
     }
-    for (int k = threadIdx.x; k < NC; k += blockDim.x) W[NT * NC * NC + k] = __bfloat162float(P[OB2 + k]);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+}
+// tensor-memory columns (a power of two >= 32), allocated and freed by one whole warp
+template <int COLS>
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 :: "r"(tc::smem_addr(slot)), "n"(COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+template <int COLS>
+__device__ __forceinline__ void tmem_free(uint32_t tmem) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(COLS) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(bar) : "memory");
+}
+
+// Copies the nine plane rows of a tile (staged row j = point x0 - 1 + j of its x-row, wrapped;
+// both channel halves) into an A buffer with 16-byte asynchronous copies, all threads: thread
+// tid takes half h = tid / 128 of staged row j = tid % 128 (and of row 128 + j for j < 2) of
+// every plane.  With the planar activation layout consecutive threads copy consecutive 16
+// bytes, so every 32-byte sector read is used whole.  Commits one copy group.
+__device__ __forceinline__ void stage_planes(uint32_t abuf, const __nv_bfloat16* in, long long n,
+                                             const long long (&qb)[9], int x0, int L, int n1) {
+    const int h = threadIdx.x >> 7;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int j = (threadIdx.x & (tc::M - 1)) + rep * tc::M;
+        if (j < L + 2) {
+            int x = x0 - 1 + j;
+            x = x < 0 ? x + n1 : (x >= n1 ? x - n1 : x);
+            const __nv_bfloat16* src = in + ((long long)h * n + x) * 8;
+            const uint32_t dst = abuf + h * tc::HALF + j * 16;
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                             :: "r"(dst + q * tc::PLANE), "l"(src + qb[q] * 8) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Layer 1: z1 = W1 * (sgn r / s) + b1, a1 = GELU(z1), as the GEMM D[128 x 16] = A B^T with
+// A[m][k] = (sgn r / s)(x_m + t_k) (taps k < 27, zero up to 32) and B[o][k] = W1[o][t_k]: two
+// MMAs of K = 16.  The nine plane rows of r are staged in FP32 (plain loads), each thread
+// builds half of its A row in BF16.  rnout: the input as rounded to BF16 (training).  One CTA
+// of 256 threads per tile; thread tid owns row m = tid % 128 and channels 8 (tid / 128) .. + 7.
+__global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, int lseg,
+                                                             const float* __restrict__ rin,
+                                                             const __nv_bfloat16* __restrict__ P,
+                                                             __nv_bfloat16* zout, __nv_bfloat16* aout,
+                                                             float* rnout, const double* s_dev, float sgn,
+                                                             double* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char* As = sm;
+    unsigned char* Bs = sm + tc::A_BYTES;
+    uint64_t* bar = (uint64_t*)(Bs + 2 * tc::B_TAP);
+    uint32_t* tslot = (uint32_t*)(bar + 1);
+    __shared__ float bias[NC];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = tid & (tc::M - 1), ch = tid >> 7;
+    for (int k = tid; k < tc::A_BYTES / 16; k += tc::THREADS)
+        reinterpret_cast<uint4*>(As)[k] = make_uint4(0, 0, 0, 0);
+    fill_b<1>(Bs, P, bias);
+    const uint32_t bar_a = tc::smem_addr(bar);
+    if (tid == 0) {
+        mbar_init(bar_a);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc<32>(tslot);
+    tc::fence_async_smem();
+    tc::fence_before();
     __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const Nb nb = neighbours(d, i);
-    float acc[NC];
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t a_base = tc::smem_addr(As), b_base = tc::smem_addr(Bs);
+    const double rms = *s_dev;
+    const float inv = rms > 0.0 ? sgn * (float)(1.0 / rms) : 0.f;   // 0 for a zero residual
+    const long long ntiles = (long long)d.n2 * d.n3 * nseg;
+    float* rs = reinterpret_cast<float*>(As + tc::L1_STAGE);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = (int)blockIdx.x; ok && tile < ntiles; tile += (int)gridDim.x) {
+        const int rowi = tile / nseg;
+        const int x0 = (tile - rowi * nseg) * lseg;
+        const int L = min(lseg, d.n1 - x0);
+        const int z = rowi / d.n2;
+        long long qb[9];
+        plane_bases(d, rowi - z * d.n2, z, qb);
+        if (tid < L + 2) {   // staged row j = tid, point x0 - 1 + j (wrapped)
+            int x = x0 - 1 + tid;
+            x = x < 0 ? x + d.n1 : (x >= d.n1 ? x - d.n1 : x);
+            float v[9];
 #pragma unroll
-    for (int o = 0; o < NC; ++o) acc[o] = W[NT * NC * NC + o];
-#pragma unroll 1
-    for (int t = 0; t < NT; ++t) {
-        float v[NC];
-        load16(a1 + nb.at(t) * NC, v);
-        const float4* Wt = reinterpret_cast<const float4*>(W + t * NC * NC);
+            for (int q = 0; q < 9; ++q) v[q] = __ldg(rin + qb[q] + x);
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+            for (int q = 0; q < 9; ++q) rs[q * tc::ROWS + tid] = v[q] * inv;
+        }
+        __syncthreads();
+        __nv_bfloat16 row[16];
 #pragma unroll
-            for (int q = 0; q < NC / 4; ++q) {
-                const float4 w = Wt[c * (NC / 4) + q];
-                acc[4 * q] = fmaf(w.x, v[c], acc[4 * q]);
-                acc[4 * q + 1] = fmaf(w.y, v[c], acc[4 * q + 1]);
-                acc[4 * q + 2] = fmaf(w.z, v[c], acc[4 * q + 2]);
-                acc[4 * q + 3] = fmaf(w.w, v[c], acc[4 * q + 3]);
+        for (int u = 0; u < 16; ++u) {
+            const int t = 16 * ch + u;
+            row[u] = __float2bfloat16(t < NT ? rs[(t / 3) * tc::ROWS + m + t % 3] : 0.f);
+        }
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb)
+            *(uint4*)(As + (2 * ch + kb) * tc::L1_KB + m * 16) = *reinterpret_cast<const uint4*>(row + 8 * kb);
+        if (rnout && ch == 0 && m < L)   // tap 13 is the point itself
+            rnout[(long long)rowi * d.n1 + x0 + m] = __bfloat162float(row[13]);
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                tc::mma(tmem, tc::desc(a_base + 2 * h * tc::L1_KB, tc::L1_KB, tc::A_SBO),
+                        tc::desc(b_base + h * tc::B_TAP, tc::B_LBO, tc::B_SBO), h > 0 ? 1u : 0u);
+            mma_commit(bar_a);
+        }
+        const bool seen = tc::mbar_wait(bar_a, phase);
+        phase ^= 1u;
+        ok = __syncthreads_and(seen) != 0;
+        tc::fence_after();
+        if (!ok) break;
+        float acc[8];
+        tc::ld8(tmem + ((uint32_t)((warp & 3) * 32) << 16) + 8 * ch, acc);
+        if (m < L) {
+            const long long i = (long long)rowi * d.n1 + x0 + m;
+            float zv[8], g[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) {
+                zv[o] = acc[o] + bias[8 * ch + o];
+                g[o] = gelu_f(zv[o]);
             }
+            if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
+            store8(aout + ((long long)ch * d.n + i) * 8, g);
+        }
+        tc::fence_before();
     }
-    float g[NC];
-#pragma unroll
-    for (int o = 0; o < NC; ++o) g[o] = gelu_f(acc[o]);
-    if (z2) store16(z2 + i * NC, acc);
-    store16(a2 + i * NC, g);
+    if (!ok) {
+        if (tid == 0) *err = 1.0;
+        tc::mbar_wait(bar_a, phase ^ 1u);   // let MMAs still in flight finish (bounded)
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tmem_free<32>(tmem);
 }
 
-// layer 3: y = scale (W3 * a2 + b3), scale = s (application) or 1 (training)
-__global__ void __launch_bounds__(256) k_net_l3(Dims d, const __nv_bfloat16* __restrict__ a2,
-                                                const __nv_bfloat16* __restrict__ P, const double* s_dev,
-                                                float* y) {
-    __shared__ __align__(16) float W[NT * NC + 1];   // [t][c], then b3
-    for (int k = threadIdx.x; k < NT * NC; k += blockDim.x)
-        W[k] = __bfloat162float(P[OW3 + (k % NC) * NT + k / NC]);
-    if (threadIdx.x == 0) W[NT * NC] = __bfloat162float(P[OB3]);
-    __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const Nb nb = neighbours(d, i);
-    float acc = W[NT * NC];
-#pragma unroll 3
-    for (int t = 0; t < NT; ++t) {
-        float v[NC];
-        load16(a2 + nb.at(t) * NC, v);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc = fmaf(W[t * NC + c], v[c], acc);
+// Layers 2 and 3 (see above).  LAYER 2: in = a1 -> z2 (optional), a2.  LAYER 3: in = a2 ->
+// y = scale (W3 * a2 + b3), scale = *s_dev (1 with s_dev null).  The next tile's plane rows are
+// copied into the other A buffer while the current tile's MMAs and epilogue run; one CTA of 256
+// threads per tile, persistent; err as for layer 1.
+template <int LAYER>
+__global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, int lseg,
+                                                            const __nv_bfloat16* __restrict__ in,
+                                                            const __nv_bfloat16* __restrict__ P,
+                                                            __nv_bfloat16* zout, __nv_bfloat16* aout,
+                                                            float* yout, const double* s_dev, double* err) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    unsigned char* As = sm;                              // two A buffers
+    unsigned char* Bs = sm + 2 * tc::A_BYTES;
+    uint64_t* bar = (uint64_t*)(Bs + tc::B_BYTES);       // MMA completion
+    uint32_t* tslot = (uint32_t*)(bar + 1);
+    __shared__ float bias[NC];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = tid & (tc::M - 1), ch = tid >> 7;
+    for (int k = tid; k < 2 * tc::A_BYTES / 16; k += tc::THREADS)   // finite values in unused rows
+        reinterpret_cast<uint4*>(As)[k] = make_uint4(0, 0, 0, 0);
+    fill_b<LAYER>(Bs, P, bias);
+    const uint32_t bar_m = tc::smem_addr(bar);
+    if (tid == 0) {
+        mbar_init(bar_m);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const float scale = s_dev ? (float)*s_dev : 1.f;
-    y[i] = scale * acc;
+    if (warp == 0) tmem_alloc<tc::ACC_COLS>(tslot);
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t a_base = tc::smem_addr(As), b_base = tc::smem_addr(Bs);
+    const float scale = (LAYER == 3 && s_dev) ? (float)*s_dev : 1.f;
+    const long long ntiles = (long long)d.n2 * d.n3 * nseg;
+    // tile -> x-row rowi = y + n2 z, segment start x0, length L (32-bit: the host keeps the
+    // tile count below 2^31)
+    auto geom = [&](int tile, int& rowi, int& x0, int& L) {
+        rowi = tile / nseg;
+        x0 = (tile - rowi * nseg) * lseg;
+        L = min(lseg, d.n1 - x0);
+    };
+    auto stage = [&](int tile, int b) {
+        int rowi, x0, L;
+        geom(tile, rowi, x0, L);
+        const int z = rowi / d.n2;
+        long long qb[9];
+        plane_bases(d, rowi - z * d.n2, z, qb);
+        stage_planes(a_base + b * tc::A_BYTES, in, d.n, qb, x0, L, d.n1);
+    };
+    if ((long long)blockIdx.x < ntiles) stage((int)blockIdx.x, 0);
+    uint32_t phase = 0;
+    bool ok = true;
+    int k = 0;
+    for (int tile = (int)blockIdx.x; tile < ntiles; tile += (int)gridDim.x, ++k) {
+        const int b = k & 1;
+        const long long next = (long long)tile + gridDim.x;
+        if (next < ntiles) {   // the other buffer's MMAs completed in the previous iteration
+            stage((int)next, b ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t abuf = a_base + b * tc::A_BYTES;
+            // tap t reads plane q = t / 3 shifted dx + 1 = t % 3 rows and accumulates into
+            // accumulator q (columns 16 q ..): nine independent chains of three MMAs, issued
+            // dx-major so that consecutive MMAs never share an accumulator
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx)
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const int t = 3 * q + dx;
+                    tc::mma(tmem + NC * q, tc::desc(abuf + q * tc::PLANE + dx * 16, tc::A_LBO, tc::A_SBO),
+                            tc::desc(b_base + t * tc::B_TAP, tc::B_LBO, tc::B_SBO), dx > 0 ? 1u : 0u);
+                }
+            mma_commit(bar_m);
+        }
+        const bool done = tc::mbar_wait(bar_m, phase);
+        ok = __syncthreads_and(done) != 0;
+        tc::fence_after();
+        if (!ok) break;
+        phase ^= 1u;
+        int rowi, x0, L;
+        geom(tile, rowi, x0, L);
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const long long i = (long long)rowi * d.n1 + x0 + m;
+        if (LAYER == 2) {
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            uint32_t part[9][8];   // the nine plane accumulators, loaded together
+#pragma unroll
+            for (int q = 0; q < 9; ++q) tc::ld8_nowait(taddr + NC * q + 8 * ch, part[q]);
+            tc::wait_ld();
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+#pragma unroll
+                for (int o = 0; o < 8; ++o) acc[o] += __uint_as_float(part[q][o]);
+            if (m < L) {
+                float zv[8], g[8];
+#pragma unroll
+                for (int o = 0; o < 8; ++o) {
+                    zv[o] = acc[o] + bias[8 * ch + o];
+                    g[o] = gelu_f(zv[o]);
+                }
+                if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
+                store8(aout + ((long long)ch * d.n + i) * 8, g);
+            }
+        } else if (ch == 0) {
+            uint32_t part[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) tc::ld1_nowait(taddr + NC * q, part[q]);
+            tc::wait_ld();
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v += __uint_as_float(part[q]);
+            if (m < L) yout[i] = scale * (v + bias[0]);
+        }
+        tc::fence_before();   // the next tile's MMAs overwrite the accumulators
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
+    if (!ok) {
+        if (tid == 0) *err = 1.0;
+        tc::mbar_wait(bar_m, phase);   // let MMAs still in flight finish (bounded)
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tmem_free<tc::ACC_COLS>(tmem);
 }
 
 // ---------------------------------------------------------------- backward
@@ -244,7 +583,7 @@ __global__ void __launch_bounds__(256) k_net_l3_bwd(Dims d, const float* __restr
         for (int c = 0; c < NC; ++c) acc[c] = fmaf(W[t * NC + c], g, acc[c]);
     }
     float z[NC];
-    load16(z2 + i * NC, z);
+    load16p(z2, d.n, i, z);
     float4* out = reinterpret_cast<float4*>(gz2 + i * NC);
 #pragma unroll
     for (int q = 0; q < NC / 4; ++q)
@@ -292,7 +631,7 @@ __global__ void __launch_bounds__(256) k_net_l2_bwd(Dims d, const float* __restr
         }
     }
     float z[NC];
-    load16(z1 + i * NC, z);
+    load16p(z1, d.n, i, z);
     float4* out = reinterpret_cast<float4*>(gz1 + i * NC);
 #pragma unroll
     for (int q = 0; q < NC / 4; ++q)
@@ -361,8 +700,8 @@ __global__ void __launch_bounds__(256) k_net_wgrad(Dims d, const float* __restri
             for (int k = tid; k < WT * NC; k += blockDim.x) {
                 const int p = k / NC, c = k % NC;
                 const long long j = s_idx[p];
-                s_a1[p][c] = j >= 0 ? __bfloat162float(a1[j * NC + c]) : 0.f;
-                s_a2[p][c] = j >= 0 ? __bfloat162float(a2[j * NC + c]) : 0.f;
+                s_a1[p][c] = j >= 0 ? getp(a1, d.n, j, c) : 0.f;
+                s_a2[p][c] = j >= 0 ? getp(a2, d.n, j, c) : 0.f;
             }
             for (int p = tid; p < WT; p += blockDim.x) s_rn[p] = s_idx[p] >= 0 ? rn[s_idx[p]] : 0.f;
             __syncthreads();
@@ -687,6 +1026,60 @@ struct OpNegLap32 {
 
 static inline unsigned pt_blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
+constexpr int SC_NET_ERR = SC_NET + 4;   // set by k_net_l2_tc when a wait gave up
+
+static void net_reset_error(of_grid* g) {
+    OF_CUDA(cudaMemsetAsync(g->s.scalars + SC_NET_ERR, 0, sizeof(double), g->stream));
+}
+static void net_check_error(of_grid* g) {
+    double e = 0.0;
+    fetch_scalars(g, SC_NET_ERR, 1, &e);
+    OF_REQUIRE(e == 0.0, OF_ETIMEOUT,
+               "tensor-core convolution: an MMA completion was not seen within %.1f s",
+               tc::WAIT_NS * 1e-9);
+}
+
+// The tensor-core layers: x-rows cut into segments of at most 128 points, persistent grids
+// (layer 1: four CTAs per SM; layers 2 and 3: two, each with two A buffers).
+static void conv_geometry(of_grid* g, int& nseg, int& lseg, long long& tiles) {
+    nseg = (g->d.n1 + tc::M - 1) / tc::M;
+    lseg = (g->d.n1 + nseg - 1) / nseg;
+    tiles = (long long)g->d.n2 * g->d.n3 * nseg;
+    OF_REQUIRE(tiles < (1LL << 31) - 4LL * num_sms(), OF_EINVAL,
+               "grid too large for the network kernels (%lld row segments)", tiles);
+}
+
+static void launch_conv1_tc(of_grid* g, const float* r, const __nv_bfloat16* P, __nv_bfloat16* z1,
+                            __nv_bfloat16* a1, float* rn, const double* rms, float sgn) {
+    static int configured_device = -1;
+    if (configured_device != g->device) {
+        OF_CUDA(cudaFuncSetAttribute(k_conv1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM1));
+        configured_device = g->device;
+    }
+    int nseg, lseg;
+    long long tiles;
+    conv_geometry(g, nseg, lseg, tiles);
+    const int grid = (int)std::max(1LL, std::min(tiles, 4LL * num_sms()));
+    launch_smem(k_conv1_tc, grid, tc::THREADS, tc::SMEM1, g->stream, g->d, nseg, lseg, r, P, z1, a1, rn,
+                rms, sgn, g->s.scalars + SC_NET_ERR);
+}
+
+template <int LAYER>
+static void launch_conv_tc(of_grid* g, const __nv_bfloat16* in, const __nv_bfloat16* P,
+                           __nv_bfloat16* zout, __nv_bfloat16* aout, float* y, const double* s_dev) {
+    static int configured_device = -1;
+    if (configured_device != g->device) {
+        OF_CUDA(cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+        configured_device = g->device;
+    }
+    int nseg, lseg;
+    long long tiles;
+    conv_geometry(g, nseg, lseg, tiles);
+    const int grid = (int)std::max(1LL, std::min(tiles, 2LL * num_sms()));
+    launch_smem(k_conv_tc<LAYER>, grid, tc::THREADS, tc::SMEM, g->stream, g->d, nseg, lseg, in, P, zout,
+                aout, y, s_dev, g->s.scalars + SC_NET_ERR);
+}
+
 // algorithmic bytes of one application: r read by the RMS pass and by layer 1, a1 and a2
 // (16 BF16 channels) written once and read once, z written
 static double net_bytes(long long n) { return (double)n * (4.0 + 4.0 + 4 * 32.0 + 4.0); }
@@ -698,12 +1091,10 @@ static void net_forward(of_grid* g, of_precond* P, const float* r, float* out, c
     ProfScope ps(g, PC_NET, net_bytes(n));
     const double* rms = g->s.scalars + SC_NET + 1;
     launch(k_rms32, vec_blocks(n), 256, g->stream, n, r, red_ctx(g, SC_NET));
-    launch(k_net_l1, pt_blocks(n), 256, g->stream, g->d, r, rms, sgn, (const __nv_bfloat16*)P->pbf,
-           training ? B.z1 : nullptr, B.a1, training ? B.rn : nullptr);
-    launch(k_net_l2, pt_blocks(n), 256, g->stream, g->d, (const __nv_bfloat16*)B.a1,
-           (const __nv_bfloat16*)P->pbf, training ? B.z2 : nullptr, B.a2);
-    launch(k_net_l3, pt_blocks(n), 256, g->stream, g->d, (const __nv_bfloat16*)B.a2,
-           (const __nv_bfloat16*)P->pbf, training ? nullptr : rms, out);
+    const __nv_bfloat16* W = P->pbf;
+    launch_conv1_tc(g, r, W, training ? B.z1 : nullptr, B.a1, training ? B.rn : nullptr, rms, sgn);
+    launch_conv_tc<2>(g, B.a1, W, training ? B.z2 : nullptr, B.a2, nullptr, nullptr);
+    launch_conv_tc<3>(g, B.a2, W, nullptr, nullptr, out, training ? nullptr : rms);
 }
 
 // loss sums (scalars 112, 113) and gradient accumulation (scaled) for one residual, taken
@@ -766,6 +1157,7 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
         ++sink->count;
     };
     launch(k_fcg_reset, 1, 1, g->stream, fs);
+    if (net) net_reset_error(g);
     if (sink && sink->count < sink->max_samples) take_sample(r);
     if (net) net_forward(g, P, r, z, B, false);
     launch(k_fcg_dots, nb, 256, g->stream, n, (const float*)r, (const float*)z, (int)net, theta, ring, 0,
@@ -801,6 +1193,7 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
             if (h.done != 0.0) break;
         }
     }
+    if (net) net_check_error(g);
     if (net_steps) {
         FState f;
         fetch_scalars(g, FS_OFF, sizeof(FState) / sizeof(double), (double*)&f);
@@ -876,8 +1269,9 @@ of_status of_precond_apply(of_grid* g, of_precond* P, const float* r, float* z) 
     try {
         require_device(g, P);
         NetBufs B = net_bufs(g, false);
+        net_reset_error(g);
         net_forward(g, P, r, z, B, false);
-        OF_CUDA(cudaStreamSynchronize(g->stream));
+        net_check_error(g);
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
@@ -893,7 +1287,9 @@ of_status of_precond_loss_grad(of_grid* g, of_precond* P, const float* r, double
         require_device(g, P);
         NetBufs B = net_bufs(g, true);
         OF_CUDA(cudaMemsetAsync(P->grad, 0, sizeof(float) * NPAR, g->stream));
+        net_reset_error(g);
         net_loss_grad(g, P, r, B, 1.f);
+        net_check_error(g);
         double s[2];
         fetch_scalars(g, SC_NET + 2, 2, s);
         if (loss) *loss = 0.5 * s[0] - s[1];
@@ -922,6 +1318,7 @@ of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int 
         NetBufs B = net_bufs(g, true);
         const long long n = g->d.n;
         double last = 0.0;
+        net_reset_error(g);
         for (int s = 0; s < steps; ++s) {
             const bool final_step = s == steps - 1;
             double lsum = 0.0;
@@ -943,7 +1340,7 @@ of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int 
                    b1, b2, c1, c2);
             if (final_step) last = lsum / batch;
         }
-        OF_CUDA(cudaStreamSynchronize(g->stream));
+        net_check_error(g);
         if (loss_out) *loss_out = last / (double)n;
         return OF_OK;
     } catch (const Error& e) {

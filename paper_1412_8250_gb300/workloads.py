@@ -185,3 +185,16 @@ def random_field(shape, seed=0, kind="white", dtype=np.float64):
             f += amp * np.cos(2 * np.pi * (k[0] * x + k[1] * y + k[2] * z) + ph)
         return f.astype(dtype)
     raise ValueError(kind)
+
+
+def initial_network(seed=0, channels=16, scale=0.3):
+    """Seeded initial parameters of the preconditioner network, flattened in the order of the C
+    ABI (W1[16][27], b1[16], W2[16][16][27], b2[16], W3[16][27], b3), float32: normal weights
+    with variance 2 / fan-in (1 / fan-in for the last layer), times `scale`; zero biases."""
+    rng = np.random.default_rng(seed)
+    c = channels
+    W1 = rng.normal(0, np.sqrt(2.0 / 27), size=(c, 1, 27))
+    W2 = rng.normal(0, np.sqrt(2.0 / (27 * c)), size=(c, c, 27))
+    W3 = rng.normal(0, np.sqrt(1.0 / (27 * c)), size=(1, c, 27))
+    parts = [scale * W1, np.zeros(c), scale * W2, np.zeros(c), scale * W3, np.zeros(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)

@@ -1,11 +1,11 @@
 """Learned preconditioner through the C ABI: network and gradients against the oracle network,
 training on the GPU, and what the trained network gains in the Poisson solve.
 
-Tolerances.  The kernels keep the weights and the activations z1, a1, z2, a2 in BF16
-(relative rounding <= 2^-9) and sum in FP32.  The oracle runs in FP64 on the same BF16-rounded
-weights.  Repeating the oracle with its activations rounded to BF16 gives, on these inputs,
-an RMS error of 0.30 % in the output, 0.01 % in the loss and <= 0.07 % in each weight
-gradient; the bars below are about five times those.  db3 = sum(A y - r) is close to zero, so
+Tolerances.  The kernels keep the weights, the scaled input r / s and the activations z1, a1,
+z2, a2 in BF16 (relative rounding <= 2^-9) and sum in FP32.  The oracle runs in FP64 on the same
+BF16-rounded weights.  Repeating the oracle with its input and activations rounded to BF16
+gives, on these inputs, an RMS error of 0.37 % in the output, 0.012 % in the loss and <= 0.1 %
+in each weight gradient; the bars below are four to five times those.  db3 = sum(A y - r) is close to zero, so
 its bar is absolute, relative to the size of the whole gradient.
 """
 import numpy as np
