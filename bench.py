@@ -47,7 +47,7 @@ def parse():
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-cell batched-vs-sequential Poisson comparison")
-    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf"],
+    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf", "net160"],
                    help="run only a bounded piece of the step (for profiler captures) and exit: "
                         "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil320 = "
                         "FP32/FP64 Laplacian sweeps on a 320^3 grid; scf = one ground state")
@@ -367,6 +367,19 @@ def kernel_case(args):
     import torch
     from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
     B.load()
+    if args.kernel_case == "net160":
+        # three applications of the preconditioner network on a 160^3 grid (seeded weights)
+        n = 160
+        h = B.of_grid_create((n, n, n), (0.2375 * n,) * 3, 6, torch.cuda.current_stream())
+        net = B.of_precond_create(W.initial_network(0))
+        r = torch.from_numpy(W.random_field((n, n, n), seed=1).astype(np.float32)).cuda()
+        z = torch.empty_like(r)
+        for _ in range(3):
+            B.of_precond_apply(h, net, r, z)
+        torch.cuda.synchronize()
+        B.of_precond_destroy(net)
+        B.of_grid_destroy(h)
+        return 0
     if args.kernel_case == "stencil320":
         n = 320
         h = B.of_grid_create((n, n, n), (0.2375 * n,) * 3, 6, torch.cuda.current_stream())
