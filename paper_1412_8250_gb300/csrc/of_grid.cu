@@ -184,7 +184,8 @@ const char* of_kernel_class_name(int cls) {
                                       "cg_stencil_f32", "cocg_stencil_f64", "cocg_stencil_f32",
                                       "krylov_update", "mg_smooth", "mg_transfer",
                                       "line_energy", "ions", "other", "pcg_iteration_pair_graph",
-                                      "cg_cocg_iteration_pair_graph", "precond_net"};
+                                      "cg_cocg_iteration_pair_graph", "precond_net",
+                                      "mg_cocg_iteration_pair_graph"};
     return (cls >= 0 && cls < PC_N) ? names[cls] : "";
 }
 

@@ -59,7 +59,7 @@ inline void launch_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t 
 // Sampled per-class kernel timing with CUDA events on the launching stream.
 enum ProfClass {
     PC_STENCIL_F64 = 0, PC_STENCIL_F32, PC_CG_F64, PC_CG_F32, PC_COCG_F64, PC_COCG_F32,
-    PC_UPDATE, PC_MG_SMOOTH, PC_MG_TRANSFER, PC_LINE, PC_ATOMS, PC_OTHER, PC_PCG_GRAPH, PC_KRYLOV_GRAPH, PC_NET, PC_N
+    PC_UPDATE, PC_MG_SMOOTH, PC_MG_TRANSFER, PC_LINE, PC_ATOMS, PC_OTHER, PC_PCG_GRAPH, PC_KRYLOV_GRAPH, PC_NET, PC_PCOCG_GRAPH, PC_N
 };
 
 // While a CUDA graph is being captured, ProfScope adds the algorithmic bytes of each captured

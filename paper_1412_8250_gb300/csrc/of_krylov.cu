@@ -60,6 +60,37 @@ __global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __re
     }
 }
 
+// Preconditioned COCG (complex symmetric A, real symmetric positive M): the bilinear form
+// rho_new = r^T z (no conjugation) ; beta = rho_new / rho (0 on the first call) ; rho = rho_new.
+__global__ void __launch_bounds__(256) k_pcocg_beta(long long n, const float2* __restrict__ r,
+                                                    const float2* __restrict__ z, bool first,
+                                                    KState* st, RedCtx rc) {
+    if (st->done != 0.0) return;
+    float pre = 0.f, pim = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 ri = r[i], zi = z[i];
+        pre = fmaf(ri.x, zi.x, fmaf(-ri.y, zi.y, pre));
+        pim = fmaf(ri.x, zi.y, fmaf(ri.y, zi.x, pim));
+    }
+    double acc[2] = {(double)pre, (double)pim};
+    if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        const double2 rho = make_double2(acc[0], acc[1]);
+        if (!(fabs(rho.x) + fabs(rho.y) > 0.0)) {
+            st->breakdown = 1.0;
+            st->done = 1.0;
+            return;
+        }
+        const double2 beta = first ? make_double2(0.0, 0.0)
+                                   : cdiv(rho, make_double2(st->rho_re, st->rho_im));
+        st->beta_re = beta.x;
+        st->beta_im = beta.y;
+        st->rho_re = rho.x;
+        st->rho_im = rho.y;
+        st->zshift = 0.0;
+    }
+}
+
 // ---------------------------------------------------------------- small vector kernels
 // sum of a[i] * (b ? b[i] : 1) over the grid into out[0]
 __global__ void __launch_bounds__(256) k_sum_product(long long n, const double* a, const double* b,
@@ -240,6 +271,30 @@ static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pou
     launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
 }
 
+static void pcocg_init_body(of_grid* g, float2* r, float2* z, KState* st, double sigma) {
+    const long long n = g->d.n;
+    mg_vcycle_shifted(g, r, z, &st->done, sigma);
+    ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
+    launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, true, st,
+           red_ctx(g, 0));
+}
+
+static void pcocg_step_body(of_grid* g, float2* x, float2* r, float2* pin, float2* pout, float2* Ap,
+                            float2* z, KState* st, float a, double2 Q, double sigma) {
+    const long long n = g->d.n;
+    OpKrylovA<float2> op{z, pin, pout, Ap, st, red_ctx(g, 0), a, Q};
+    launch_stencil<float2, 1>(g, g->w32, op);
+    {
+        ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float2) * (double)n);
+        launch(krylov_update<float2, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
+               red_ctx(g, 0));
+    }
+    mg_vcycle_shifted(g, r, z, &st->done, sigma);
+    ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
+    launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, false, st,
+           red_ctx(g, 0));
+}
+
 // One plain CG / COCG iteration: p_out = r + beta p_in with A p_out and p^T A p in one sweep,
 // then the update of x and r with the next beta.
 template <typename T>
@@ -304,6 +359,58 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
 }
 
 void destroy_graphs(void* p) { destroy_graphs_impl(p); }
+
+// COCG on the complex shifted operator A = a(-L) + Q in FP32, preconditioned by one V-cycle of
+// the real positive operator -L + sigma applied to real and imaginary parts (sigma = |Q| / a).
+// Pairs of iterations replay from cached CUDA graphs as for the Poisson PCG.
+static KState iterate_pcocg(of_grid* g, int st_off, float2* x, float2* r, float2* pa, float2* pb,
+                            float2* Ap, float2* z, float a, double2 Q, double sigma, int check_every) {
+    KState* st = kstate(g, st_off);
+    const long long n = g->d.n;
+    OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float2) * n, g->stream));
+    KState h;
+    if (std::getenv("OF_NO_GRAPHS") == nullptr) {
+        Graphs& G = graphs(g);
+        const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
+        const double consts[4] = {(double)a, Q.x, Q.y, sigma};
+        PcocgGraph* e = nullptr;
+        for (auto& c : G.pcocg)
+            if (!std::memcmp(c.key, key, sizeof(key)) && !std::memcmp(c.consts, consts, sizeof(consts))) e = &c;
+        if (!e) {
+            PcocgGraph c{};
+            std::memcpy(c.key, key, sizeof(key));
+            std::memcpy(c.consts, consts, sizeof(consts));
+            c.init = capture(g, [&] { pcocg_init_body(g, r, z, st, sigma); }, c.init_kernels, c.init_bytes);
+            c.pair = capture(g, [&] {
+                pcocg_step_body(g, x, r, pa, pb, Ap, z, st, a, Q, sigma);
+                pcocg_step_body(g, x, r, pb, pa, Ap, z, st, a, Q, sigma);
+            }, c.pair_kernels, c.pair_bytes);
+            G.pcocg.push_back(c);
+            e = &G.pcocg.back();
+        }
+        replay(g, e->init, e->init_kernels, e->init_bytes, PC_PCOCG_GRAPH);
+        const int pairs = std::max(1, check_every / 8);
+        for (;;) {
+            for (int k = 0; k < pairs; ++k) replay(g, e->pair, e->pair_kernels, e->pair_bytes, PC_PCOCG_GRAPH);
+            fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+            if (h.done != 0.0) break;
+        }
+        return h;
+    }
+    float2* p[2] = {pa, pb};
+    int ping = 0;
+    pcocg_init_body(g, r, z, st, sigma);
+    const int every = std::max(1, check_every / 4);
+    for (;;) {
+        for (int k = 0; k < every; ++k) {
+            pcocg_step_body(g, x, r, p[ping], p[1 - ping], Ap, z, st, a, Q, sigma);
+            ping ^= 1;
+        }
+        fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+        if (h.done != 0.0) break;
+    }
+    return h;
+}
 
 // Preconditioned CG (multigrid V-cycle) on A = -L in FP32.  Without profiling the iterations
 // run as replays of captured CUDA graphs; with profiling on, as individual launches so that
@@ -394,6 +501,15 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             OF_LAUNCH_CHECK();
             KState hi;
             bool pcg = false, fcg = false;
+            if constexpr (std::is_same<T32, float2>::value) {
+                // shifted systems: COCG preconditioned by the V-cycle of -L + |Q| / a
+                const double qabs = std::sqrt(Q.x * Q.x + Q.y * Q.y);
+                pcg = qabs > 0.0 && !o.no_multigrid && mg_available(g);
+                if (pcg)
+                    hi = iterate_pcocg(g, KS32, e32, r32, (float2*)ar.pa32, (float2*)ar.pb32,
+                                       (float2*)ar.Ap32, (float2*)ar.z32, (float)a, Q, qabs / a,
+                                       o.check_every);
+            }
             if constexpr (std::is_same<T32, float>::value) {
                 const bool poisson_op = a == 1.0 && Q.x == 0.0 && Q.y == 0.0;
                 fcg = poisson_op && o.precond != nullptr;
@@ -415,7 +531,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 status = OF_EBREAKDOWN;
                 set_error("Krylov solve (FP32 inner, %s): breakdown at the start of refinement pass "
                           "%d: inner |r|^2 %.3e, r^T M r %.3e, p^T A p %.3e, outer |r|^2 %.3e, tol2 %.3e",
-                          fcg ? "flexible CG" : pcg ? "multigrid PCG" : "CG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
+                          fcg ? "flexible CG" : pcg ? "multigrid-preconditioned CG/COCG" : "CG/COCG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
                           h.rr, h.tol2);
                 break;
             }

@@ -290,9 +290,19 @@ struct PlainGraph {
     double bytes;
 };
 
+// Graphs of the multigrid-preconditioned COCG (init + pair), keyed by buffers and constants.
+struct PcocgGraph {
+    const void* key[8];
+    double consts[4];   // a, Q (re, im), sigma
+    cudaGraphExec_t init, pair;
+    unsigned long long init_kernels, pair_kernels;
+    double init_bytes, pair_bytes;
+};
+
 struct Graphs {
     PcgGraphs pcg;
     std::vector<PlainGraph> plain;
+    std::vector<PcocgGraph> pcocg;
 };
 
 inline void destroy_graphs_impl(void* p) {
@@ -301,6 +311,10 @@ inline void destroy_graphs_impl(void* p) {
     if (G->pcg.init) cudaGraphExecDestroy(G->pcg.init);
     if (G->pcg.pair) cudaGraphExecDestroy(G->pcg.pair);
     for (auto& e : G->plain) cudaGraphExecDestroy(e.exec);
+    for (auto& e : G->pcocg) {
+        cudaGraphExecDestroy(e.init);
+        cudaGraphExecDestroy(e.pair);
+    }
     delete G;
 }
 

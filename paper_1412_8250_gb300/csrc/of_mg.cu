@@ -13,6 +13,7 @@
 // Every kernel reads the solver's stop flag and returns at once after convergence.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -28,16 +29,30 @@ struct MGLevel {
     double h[3];
     int N;
     Weights<float> W;
-    float invD;
-    float lmax, lmin;
-    float *x, *b, *r, *d0, *d1;
+    double diag;             // diagonal of -L_h on this level
+    double lmax, lmin;       // largest and smallest non-zero eigenvalue of -L_h
+    float *x, *b, *r, *d0, *d1;   // each sized for complex (float2) fields
 };
+
+// Level parameters for the operator A = -L_h + sigma (sigma >= 0): Jacobi scaling and the
+// extreme eigenvalues of D^{-1} A (the constant mode has eigenvalue sigma).
+struct Shifted {
+    float invD;
+    double lmax, lmin;
+};
+static Shifted shifted_level(const MGLevel& L, double sigma) {
+    const double D = L.diag + sigma;
+    Shifted s;
+    s.invD = (float)(1.0 / D);
+    s.lmax = (L.lmax + sigma) / D;
+    s.lmin = (sigma > 0.0 ? std::min(sigma, L.lmin + sigma) : L.lmin) / D;
+    return s;
+}
 
 struct MG {
     std::vector<MGLevel> lv;
     int deg = 2;
-    int deg_coarse = 16;
-    int first_small = 1;   // levels from here down run inside one thread block
+    int first_small = 1;   // levels from here down run inside one thread-block cluster
     bool ok = false;
 };
 
@@ -110,11 +125,11 @@ static bool build(of_grid* g, MG& m) {
         double diag, lmax, lmin;
         weights_for(N, h, L.W, diag);
         spectrum(N, h, d, diag, lmax, lmin);
-        L.invD = (float)(1.0 / diag);
-        L.lmax = (float)lmax;
-        L.lmin = (float)lmin;
+        L.diag = diag;
+        L.lmax = lmax * diag;
+        L.lmin = lmin * diag;
         lv.push_back(L);
-        total += 5 * (size_t)d.n;
+        total += 5 * (2 * (size_t)d.n + 64);
         const bool can = d.n1 % 2 == 0 && d.n2 % 2 == 0 && d.n3 % 2 == 0 && d.n1 >= 8 &&
                          d.n2 >= 8 && d.n3 >= 8;
         if (!can) break;
@@ -130,14 +145,11 @@ static bool build(of_grid* g, MG& m) {
         float** p[5] = {&L.x, &L.b, &L.r, &L.d0, &L.d1};
         for (int k = 0; k < 5; ++k) {
             *p[k] = base + off;
-            off += ((size_t)L.d.n + 63) / 64 * 64;
+            off += (2 * (size_t)L.d.n + 63) / 64 * 64;
         }
     }
     m.lv = lv;
     m.ok = true;
-    const MGLevel& C = m.lv.back();
-    const double kappa = C.lmax / std::max(C.lmin, 1e-12f);
-    m.deg_coarse = std::min(96, std::max(8, (int)std::ceil(2.0 * std::sqrt(kappa))));
     m.first_small = (int)m.lv.size() - 1;
     while (m.first_small > 1 && m.lv[m.first_small - 1].d.n <= MG_SMALL_POINTS) --m.first_small;
     return true;
@@ -152,46 +164,55 @@ bool mg_available(of_grid* g) {
 }
 
 // ---------------------------------------------------------------- kernels
-// One Chebyshev step on A = -L: x (+)= d ; r_out = r_in - A d ; d_out = a d + bD r_out
+// T = float (real fields) or float2 (complex fields, real and imaginary parts smoothed alike:
+// the operator is real).  A = -L_h + sigma.
+// One Chebyshev step: x (+)= d ; r_out = r_in - A d ; d_out = a d + bD r_out
+template <typename T>
 struct OpCheby {
     static constexpr int kClass = PC_MG_SMOOTH, kWords = 6;
-    const float* din;
+    const T* din;
     float dscale;
-    float* x;
+    T* x;
     bool x_init;
-    const float* rin;
-    float* rout;
-    float* dout;
-    float a, bD;
+    const T* rin;
+    T* rout;
+    T* dout;
+    float a, bD, sigma;
     const double* done;
     __device__ bool begin() { return *done == 0.0; }
-    __device__ float load(long long i) const { return din[i] * dscale; }
-    __device__ void store(long long i, float c, float lap) {
-        x[i] = x_init ? c : x[i] + c;
-        const float rn = rin[i] + lap;   // r - A d, A = -L
+    __device__ T load(long long i) const { return vmul(dscale, din[i]); }
+    __device__ void store(long long i, T c, T lap) {
+        x[i] = x_init ? c : vadd(x[i], c);
+        const T rn = vfma(-sigma, c, vadd(rin[i], lap));   // r - A d
         rout[i] = rn;
-        if (dout) dout[i] = a * c + bD * rn;
+        if (dout) dout[i] = vfma(a, c, vmul(bD, rn));
     }
     __device__ void end() {}
 };
 
 // r = b - A x
+template <typename T>
 struct OpResid32 {
     static constexpr int kClass = PC_MG_SMOOTH, kWords = 3;
-    const float* x;
-    const float* b;
-    float* r;
+    const T* x;
+    const T* b;
+    T* r;
+    float sigma;
     const double* done;
     __device__ bool begin() { return *done == 0.0; }
-    __device__ float load(long long i) const { return x[i]; }
-    __device__ void store(long long i, float, float lap) { r[i] = b[i] + lap; }
+    __device__ T load(long long i) const { return x[i]; }
+    __device__ void store(long long i, T c, T lap) { r[i] = vfma(-sigma, c, vadd(b[i], lap)); }
     __device__ void end() {}
 };
 
 __device__ __forceinline__ int wrapc(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+template <typename T> __device__ __forceinline__ T vzero();
+template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
 // coarse b = full weighting of fine r
-__global__ void k_restrict(Dims f, Dims c, const float* __restrict__ r, float* __restrict__ b,
+template <typename T>
+__global__ void k_restrict(Dims f, Dims c, const T* __restrict__ r, T* __restrict__ b,
                            const double* done) {
     if (*done != 0.0) return;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -199,7 +220,7 @@ __global__ void k_restrict(Dims f, Dims c, const float* __restrict__ r, float* _
     const int I = (int)(idx % c.n1);
     const int J = (int)((idx / c.n1) % c.n2);
     const int K = (int)(idx / ((long long)c.n1 * c.n2));
-    float s = 0.f;
+    T s = vzero<T>();
     const float w[3] = {0.25f, 0.5f, 0.25f};
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz) {
@@ -211,15 +232,31 @@ __global__ void k_restrict(Dims f, Dims c, const float* __restrict__ r, float* _
 #pragma unroll
             for (int dx = -1; dx <= 1; ++dx) {
                 const int x = wrapc(2 * I + dx, f.n1);
-                s += w[dz + 1] * w[dy + 1] * w[dx + 1] * r[row + x];
+                s = vfma(w[dz + 1] * w[dy + 1] * w[dx + 1], r[row + x], s);
             }
         }
     }
     b[idx] = s;
 }
 
+// trilinear interpolation of the coarse field e at fine point (i, j, k)
+template <typename T>
+__device__ __forceinline__ T interp(const T* e, Dims c, int i, int j, int k) {
+    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
+    const int I1 = (i & 1) ? wrapc(I0 + 1, c.n1) : I0;
+    const int J1 = (j & 1) ? wrapc(J0 + 1, c.n2) : J0;
+    const int K1 = (k & 1) ? wrapc(K0 + 1, c.n3) : K0;
+    // (1 - w) is the weight of the second node; for even indices both nodes coincide
+    const float wx = (i & 1) ? 0.5f : 1.0f, wy = (j & 1) ? 0.5f : 1.0f, wz = (k & 1) ? 0.5f : 1.0f;
+    auto at = [&](int I, int J, int K) { return e[((long long)K * c.n2 + J) * c.n1 + I]; };
+    auto lx = [&](int J, int K) { return vfma(wx, at(I0, J, K), vmul(1.f - wx, at(I1, J, K))); };
+    auto ly = [&](int K) { return vfma(wy, lx(J0, K), vmul(1.f - wy, lx(J1, K))); };
+    return vfma(wz, ly(K0), vmul(1.f - wz, ly(K1)));
+}
+
 // fine x += trilinear interpolation of coarse e
-__global__ void k_prolong_add(Dims f, Dims c, const float* __restrict__ e, float* __restrict__ x,
+template <typename T>
+__global__ void k_prolong_add(Dims f, Dims c, const T* __restrict__ e, T* __restrict__ x,
                               const double* done) {
     if (*done != 0.0) return;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -227,42 +264,34 @@ __global__ void k_prolong_add(Dims f, Dims c, const float* __restrict__ e, float
     const int i = (int)(idx % f.n1);
     const int j = (int)((idx / f.n1) % f.n2);
     const int k = (int)(idx / ((long long)f.n1 * f.n2));
-    const int I0 = i >> 1, J0 = j >> 1, K0 = k >> 1;
-    const int I1 = (i & 1) ? wrapc(I0 + 1, c.n1) : I0;
-    const int J1 = (j & 1) ? wrapc(J0 + 1, c.n2) : J0;
-    const int K1 = (k & 1) ? wrapc(K0 + 1, c.n3) : K0;
-    const float wx = (i & 1) ? 0.5f : 1.0f, wy = (j & 1) ? 0.5f : 1.0f, wz = (k & 1) ? 0.5f : 1.0f;
-    auto at = [&](int I, int J, int K) { return e[((long long)K * c.n2 + J) * c.n1 + I]; };
-    float s = wz * (wy * (wx * at(I0, J0, K0) + (1.f - wx) * at(I1, J0, K0)) +
-                    (1.f - wy) * (wx * at(I0, J1, K0) + (1.f - wx) * at(I1, J1, K0))) +
-              (1.f - wz) * (wy * (wx * at(I0, J0, K1) + (1.f - wx) * at(I1, J0, K1)) +
-                            (1.f - wy) * (wx * at(I0, J1, K1) + (1.f - wx) * at(I1, J1, K1)));
-    // (1 - w) is the weight of the second node; for even indices both nodes coincide
-    x[idx] += s;
+    x[idx] = vadd(x[idx], interp(e, c, i, j, k));
 }
 
-// ---- the small levels inside one thread block (second-order operator on all of them)
+// ---- the small levels inside one thread-block cluster (second-order operator on all of them)
 struct SmallLevels {
     int count;
     int deg;
     int deg_coarse;
     float ctheta, cdelta;
+    float sigma;
     Dims d[MG_MAX_LEVELS];
     float cx[MG_MAX_LEVELS], cy[MG_MAX_LEVELS], cz[MG_MAX_LEVELS], centre[MG_MAX_LEVELS];
     float invD[MG_MAX_LEVELS], theta[MG_MAX_LEVELS];
     float ca[MG_MAX_LEVELS][4], cb[MG_MAX_LEVELS][4];
-    float *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS], *dv[MG_MAX_LEVELS];
+    void *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS], *dv[MG_MAX_LEVELS];
 };
 
-// (L_h a)(i) for the 7-point operator of level l
-__device__ __forceinline__ float lap7(const SmallLevels& P, int l, const float* a, int i) {
+// -(A a)(i) = (L_h a)(i) - sigma a(i) for the 7-point operator of level l
+template <typename T>
+__device__ __forceinline__ T neg_op7(const SmallLevels& P, int l, const T* a, int i) {
     const Dims& d = P.d[l];
     const int ix = i % d.n1, iy = (i / d.n1) % d.n2, iz = i / (d.n1 * d.n2);
     const int sx = d.n1, sy = d.n1 * d.n2;
-    return P.centre[l] * a[i] +
-           P.cx[l] * (a[i - ix + wrapc(ix + 1, d.n1)] + a[i - ix + wrapc(ix - 1, d.n1)]) +
-           P.cy[l] * (a[i + (wrapc(iy + 1, d.n2) - iy) * sx] + a[i + (wrapc(iy - 1, d.n2) - iy) * sx]) +
-           P.cz[l] * (a[i + (wrapc(iz + 1, d.n3) - iz) * sy] + a[i + (wrapc(iz - 1, d.n3) - iz) * sy]);
+    T v = vmul(P.centre[l] - P.sigma, a[i]);
+    v = vfma(P.cx[l], vadd(a[i - ix + wrapc(ix + 1, d.n1)], a[i - ix + wrapc(ix - 1, d.n1)]), v);
+    v = vfma(P.cy[l], vadd(a[i + (wrapc(iy + 1, d.n2) - iy) * sx], a[i + (wrapc(iy - 1, d.n2) - iy) * sx]), v);
+    v = vfma(P.cz[l], vadd(a[i + (wrapc(iz + 1, d.n3) - iz) * sy], a[i + (wrapc(iz - 1, d.n3) - iz) * sy]), v);
+    return v;
 }
 
 // The small levels run on one thread-block cluster (MG_CLUSTER CTAs of 1024 threads, one per
@@ -274,100 +303,93 @@ __device__ __forceinline__ int cl_stride() { return gridDim.x * blockDim.x; }
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 
 // Chebyshev smoothing of level l (zero initial guess, or starting from x), whole cluster
+template <typename T>
 __device__ void blk_smooth(const SmallLevels& P, int l, bool zero) {
     const int n = (int)P.d[l].n;
-    float *x = P.x[l], *b = P.b[l], *r = P.r[l], *dv = P.dv[l];
+    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
     const float s0 = P.invD[l] / P.theta[l];
     if (zero) {
-        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = b[i] * s0;
+        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vmul(s0, b[i]);
     } else {
-        for (int i = cl_tid(); i < n; i += cl_stride()) r[i] = b[i] + lap7(P, l, x, i);
+        for (int i = cl_tid(); i < n; i += cl_stride()) r[i] = vadd(b[i], neg_op7(P, l, x, i));
         cl_sync();
-        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = r[i] * s0;
+        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vmul(s0, r[i]);
     }
     cl_sync();
     for (int k = 0; k < P.deg; ++k) {
         const bool first = zero && k == 0;
         for (int i = cl_tid(); i < n; i += cl_stride()) {
-            x[i] = first ? dv[i] : x[i] + dv[i];
-            r[i] = (first ? b[i] : r[i]) + lap7(P, l, dv, i);
+            x[i] = first ? dv[i] : vadd(x[i], dv[i]);
+            r[i] = vadd(first ? b[i] : r[i], neg_op7(P, l, dv, i));
         }
         cl_sync();
         if (k + 1 < P.deg) {
             for (int i = cl_tid(); i < n; i += cl_stride())
-                dv[i] = P.ca[l][k] * dv[i] + P.cb[l][k] * P.invD[l] * r[i];
+                dv[i] = vfma(P.ca[l][k], dv[i], vmul(P.cb[l][k] * P.invD[l], r[i]));
             cl_sync();
         }
     }
 }
 
+template <typename T>
 __global__ void __cluster_dims__(MG_CLUSTER, 1, 1) __launch_bounds__(1024)
 k_small_vcycle(SmallLevels P, const double* done) {
     if (*done != 0.0) return;
     const float w[3] = {0.25f, 0.5f, 0.25f};
     for (int l = 0; l + 1 < P.count; ++l) {
-        blk_smooth(P, l, true);
+        blk_smooth<T>(P, l, true);
         const Dims f = P.d[l], c = P.d[l + 1];
-        const float* r = P.r[l];
+        const T* r = (const T*)P.r[l];
+        T* bc = (T*)P.b[l + 1];
         for (int I = cl_tid(); I < (int)c.n; I += cl_stride()) {
             const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
-            float s = 0.f;
+            T s = vzero<T>();
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
                         const int fx = wrapc(2 * ci + dx, f.n1), fy = wrapc(2 * cj + dy, f.n2),
                                   fz = wrapc(2 * ck + dz, f.n3);
-                        s += w[dz + 1] * w[dy + 1] * w[dx + 1] * r[(fz * f.n2 + fy) * f.n1 + fx];
+                        s = vfma(w[dz + 1] * w[dy + 1] * w[dx + 1], r[(fz * f.n2 + fy) * f.n1 + fx], s);
                     }
-            P.b[l + 1][I] = s;
+            bc[I] = s;
         }
         cl_sync();
     }
-    {   // coarsest: Chebyshev over the whole non-zero spectrum from a zero guess
+    {   // coarsest: Chebyshev over the whole spectrum (non-zero part for sigma = 0) from zero
         const int l = P.count - 1;
         const int n = (int)P.d[l].n;
-        float *x = P.x[l], *b = P.b[l], *r = P.r[l], *dv = P.dv[l];
+        T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
         const float sigma1 = P.ctheta / P.cdelta;
         float rho = 1.f / sigma1;
         for (int i = cl_tid(); i < n; i += cl_stride()) {
-            x[i] = 0.f;
+            x[i] = vzero<T>();
             r[i] = b[i];
-            dv[i] = b[i] * P.invD[l] / P.ctheta;
+            dv[i] = vmul(P.invD[l] / P.ctheta, b[i]);
         }
         cl_sync();
         for (int s = 0; s < P.deg_coarse; ++s) {
             const float rn = 1.f / (2.f * sigma1 - rho);
             const float a = rn * rho, bb = 2.f * rn / P.cdelta;
             for (int i = cl_tid(); i < n; i += cl_stride()) {
-                x[i] += dv[i];
-                r[i] += lap7(P, l, dv, i);
+                x[i] = vadd(x[i], dv[i]);
+                r[i] = vadd(r[i], neg_op7(P, l, dv, i));
             }
             cl_sync();
-            for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = a * dv[i] + bb * P.invD[l] * r[i];
+            for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vfma(a, dv[i], vmul(bb * P.invD[l], r[i]));
             cl_sync();
             rho = rn;
         }
     }
     for (int l = P.count - 2; l >= 0; --l) {
         const Dims f = P.d[l], c = P.d[l + 1];
-        const float* e = P.x[l + 1];
-        float* x = P.x[l];
+        const T* e = (const T*)P.x[l + 1];
+        T* x = (T*)P.x[l];
         for (int i = cl_tid(); i < (int)f.n; i += cl_stride()) {
             const int fi = i % f.n1, fj = (i / f.n1) % f.n2, fk = i / (f.n1 * f.n2);
-            const int I0 = fi >> 1, J0 = fj >> 1, K0 = fk >> 1;
-            const int I1 = (fi & 1) ? wrapc(I0 + 1, c.n1) : I0;
-            const int J1 = (fj & 1) ? wrapc(J0 + 1, c.n2) : J0;
-            const int K1 = (fk & 1) ? wrapc(K0 + 1, c.n3) : K0;
-            const float wx = (fi & 1) ? 0.5f : 1.0f, wy = (fj & 1) ? 0.5f : 1.0f,
-                        wz = (fk & 1) ? 0.5f : 1.0f;
-            auto at = [&](int I, int J, int K) { return e[(K * c.n2 + J) * c.n1 + I]; };
-            x[i] += wz * (wy * (wx * at(I0, J0, K0) + (1.f - wx) * at(I1, J0, K0)) +
-                          (1.f - wy) * (wx * at(I0, J1, K0) + (1.f - wx) * at(I1, J1, K0))) +
-                    (1.f - wz) * (wy * (wx * at(I0, J0, K1) + (1.f - wx) * at(I1, J0, K1)) +
-                                  (1.f - wy) * (wx * at(I0, J1, K1) + (1.f - wx) * at(I1, J1, K1)));
+            x[i] = vadd(x[i], interp(e, c, fi, fj, fk));
         }
         cl_sync();
-        blk_smooth(P, l, false);
+        blk_smooth<T>(P, l, false);
     }
 }
 
@@ -389,65 +411,76 @@ static void cheby_coeffs(double lmin, double lmax, int deg, std::vector<float>& 
     }
 }
 
-static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const double* done) {
+template <typename T>
+static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const double* done, double sigma) {
+    constexpr int RY = std::is_same<T, float>::value ? 2 : 1;
+    const Shifted S = shifted_level(L, sigma);
     std::vector<float> a, b;
     double theta;
-    cheby_coeffs(0.15 * L.lmax, 1.05 * L.lmax, deg, a, b, theta);
-    if (!zero_guess) {
-        launch_stencil_dims<float, 2>(g, L.d, L.N, L.W, OpResid32{L.x, L.b, L.r, done});
-    }
-    float* din = zero_guess ? L.b : L.r;
-    float* dbuf[2] = {L.d0, L.d1};
+    cheby_coeffs(0.15 * S.lmax, 1.05 * S.lmax, deg, a, b, theta);
+    T *x = (T*)L.x, *lb = (T*)L.b, *r = (T*)L.r;
+    if (!zero_guess)
+        launch_stencil_dims<T, RY>(g, L.d, L.N, L.W, OpResid32<T>{x, lb, r, (float)sigma, done});
+    T* din = zero_guess ? lb : r;
+    T* dbuf[2] = {(T*)L.d0, (T*)L.d1};
     for (int k = 0; k < deg; ++k) {
-        OpCheby op;
+        OpCheby<T> op;
         op.din = (k == 0) ? din : dbuf[(k + 1) & 1];
-        op.dscale = (k == 0) ? (float)(L.invD / theta) : 1.f;
-        op.x = L.x;
+        op.dscale = (k == 0) ? (float)(S.invD / theta) : 1.f;
+        op.x = x;
         op.x_init = zero_guess && k == 0;
-        op.rin = (k == 0 && zero_guess) ? L.b : L.r;
-        op.rout = L.r;
+        op.rin = (k == 0 && zero_guess) ? lb : r;
+        op.rout = r;
         op.dout = (k + 1 < deg) ? dbuf[k & 1] : nullptr;
         op.a = a[k];
-        op.bD = b[k] * L.invD;
+        op.bD = b[k] * S.invD;
+        op.sigma = (float)sigma;
         op.done = done;
-        launch_stencil_dims<float, 2>(g, L.d, L.N, L.W, op);
+        launch_stencil_dims<T, RY>(g, L.d, L.N, L.W, op);
     }
 }
 
-// z = M^{-1} r (one V-cycle); r, z fine-level FP32 fields.  Levels above first_small are
-// swept by grid-wide launches, the rest by k_small_vcycle in one block.
-void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
+// z = M^{-1} r, one V-cycle for A = -L_h + sigma; r, z fine-level fields.  Levels above
+// first_small are swept by grid-wide launches, the rest by k_small_vcycle on one cluster.
+template <typename T>
+static void vcycle(of_grid* g, const T* r, T* z, const double* done, double sigma) {
     MG& m = *g->mg;
     const int nl = (int)m.lv.size();
     const int fs = m.first_small;
-    m.lv[0].b = const_cast<float*>(r);
-    m.lv[0].x = z;
+    float* saved_b = m.lv[0].b;
+    float* saved_x = m.lv[0].x;
+    m.lv[0].b = (float*)const_cast<T*>(r);
+    m.lv[0].x = (float*)z;
     for (int l = 0; l < fs; ++l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
-        smooth(g, L, m.deg, true, done);   // x_l = S b_l, r_l = b_l - A x_l
-        ProfScope ps(g, PC_MG_TRANSFER, sizeof(float) * (double)(L.d.n + C.d.n));
-        launch(k_restrict, (unsigned)((C.d.n + 255) / 256), 256, g->stream, L.d, C.d, L.r, C.b, done);
+        smooth<T>(g, L, m.deg, true, done, sigma);   // x_l = S b_l, r_l = b_l - A x_l
+        ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(L.d.n + C.d.n));
+        launch(k_restrict<T>, (unsigned)((C.d.n + 255) / 256), 256, g->stream, L.d, C.d,
+               (const T*)L.r, (T*)C.b, done);
     }
     {
         SmallLevels P{};
         P.count = nl - fs;
         P.deg = m.deg;
-        P.deg_coarse = m.deg_coarse;
-        const MGLevel& C = m.lv[nl - 1];
-        P.ctheta = 0.5f * (C.lmax + C.lmin);
-        P.cdelta = 0.5f * (C.lmax - C.lmin);
+        P.sigma = (float)sigma;
+        const Shifted SC = shifted_level(m.lv[nl - 1], sigma);
+        const double kappa = SC.lmax / std::max(SC.lmin, 1e-12);
+        P.deg_coarse = std::min(96, std::max(8, (int)std::ceil(2.0 * std::sqrt(kappa))));
+        P.ctheta = (float)(0.5 * (SC.lmax + SC.lmin));
+        P.cdelta = (float)(0.5 * (SC.lmax - SC.lmin));
         for (int k = 0; k < P.count; ++k) {
             const MGLevel& L = m.lv[fs + k];
+            const Shifted S = shifted_level(L, sigma);
             P.d[k] = L.d;
             P.cx[k] = L.W.w[0][1];
             P.cy[k] = L.W.w[1][1];
             P.cz[k] = L.W.w[2][1];
             P.centre[k] = L.W.centre;
-            P.invD[k] = L.invD;
+            P.invD[k] = S.invD;
             std::vector<float> a, b;
             double theta;
-            cheby_coeffs(0.15 * L.lmax, 1.05 * L.lmax, m.deg, a, b, theta);
+            cheby_coeffs(0.15 * S.lmax, 1.05 * S.lmax, m.deg, a, b, theta);
             P.theta[k] = (float)theta;
             for (int j = 0; j < m.deg && j < 4; ++j) {
                 P.ca[k][j] = a[j];
@@ -459,17 +492,28 @@ void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
             P.dv[k] = L.d0;
         }
         ProfScope ps(g, PC_MG_TRANSFER, 0.0);
-        launch(k_small_vcycle, MG_CLUSTER, 1024, g->stream, P, done);
+        launch(k_small_vcycle<T>, MG_CLUSTER, 1024, g->stream, P, done);
     }
     for (int l = fs - 1; l >= 0; --l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
         {
-            ProfScope ps(g, PC_MG_TRANSFER, sizeof(float) * (double)(2 * L.d.n + C.d.n));
-            launch(k_prolong_add, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d, C.x, L.x, done);
+            ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(2 * L.d.n + C.d.n));
+            launch(k_prolong_add<T>, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d,
+                   (const T*)C.x, (T*)L.x, done);
         }
-        smooth(g, L, m.deg, false, done);
+        smooth<T>(g, L, m.deg, false, done, sigma);
     }
+    m.lv[0].b = saved_b;
+    m.lv[0].x = saved_x;
+}
+
+void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
+    vcycle<float>(g, r, z, done, 0.0);
+}
+
+void mg_vcycle_shifted(of_grid* g, const float2* r, float2* z, const double* done, double sigma) {
+    vcycle<float2>(g, r, z, done, sigma);
 }
 
 }  // namespace of
