@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--compare-f64", action="store_true",
                    help="also time one plain FP64 CG ground state and report it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--config5", action="store_true",
+                   help="measure the 3999-atom 320^3 ground state instead of the benchmark step")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
@@ -361,6 +363,88 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def config5(args):
+    """The 3999-atom cell (10x10x10 FCC minus the centre site, +-0.1 bohr displacements, seed 5),
+    320^3 grid (32.8 M points): one ground state + forces in the mixed form, timed whole; the
+    plain FP64 CG form timed on bounded samples (the first outer iteration stopped after 2 and
+    after 4 NLCG steps, and one FP64 kernel map) and extrapolated with the mixed run's NLCG
+    and outer counts (both forms run the same algorithm).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    cell = W.al3999_cell()
+    stream = torch.cuda.current_stream()
+    h = B.of_grid_create(cell.n, cell.L, 6, stream)
+    sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+    fn = Fn.wt()
+
+    def opts(prec):
+        o = B.of_default_scf_opts()
+        o.precision = prec
+        o.fp_tol = 1e-6
+        o.anderson_m = 3
+        o.anderson_zeta = 1.0
+        o.nlcg_tol_rel = 1e-2
+        return o
+
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t = time.time()
+        res = B.of_scf_ground_state(h, sysd, fn, opts(B.OF_F32), u, phi)
+        F = B.of_forces(h, sysd, u, phi)
+        torch.cuda.synchronize()
+        t_mixed = time.time() - t
+        u_gs = u.clone()
+        samples = {}
+        for k in (2, 4):
+            o = opts(B.OF_F64)
+            o.fp_max_iter = 1
+            o.nlcg_max_iter = k
+            u.fill_(1.0)
+            phi.zero_()
+            torch.cuda.synchronize()
+            t = time.time()
+            B.of_scf_ground_state(h, sysd, fn, o, u, phi, allow=(B.OF_ENOCONV,))
+            torch.cuda.synchronize()
+            samples[k] = time.time() - t
+        ko = B.of_default_solve_opts()
+        vlr = torch.zeros_like(u)
+        kf2 = Fn.kf2(cell.n_electrons, cell.L[0] * cell.L[1] * cell.L[2])
+        torch.cuda.synchronize()
+        t = time.time()
+        B.of_lr_potential(h, fn, kf2, u_gs, vlr, opts=ko)
+        torch.cuda.synchronize()
+        kmap = time.time() - t
+    per_step = (samples[4] - samples[2]) / 2.0
+    est = samples[2] + per_step * (res.nlcg_iterations - 2) + kmap * (res.outer_iterations - 1)
+    stencil = stencil_rates(torch, B, h, cell.shape, reps=10)
+    line = {"metric": METRIC, "unit": UNIT, "higher_is_better": False, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": "3999-atom FCC Al-like cell (10x10x10 minus the centre site, "
+                                   "a=7.6 bohr, +-0.1 bohr displacements, seed 5), 320^3, "
+                                   "12th-order FD, WT-type kernel (sigma=1.2, r_c=10); ground "
+                                   "state + forces"},
+            "mixed_multigrid_s": t_mixed,
+            "plain_fp64_cg_s_estimate": est,
+            "plain_fp64_sample": {"first_outer_2_nlcg_steps_s": samples[2],
+                                  "first_outer_4_nlcg_steps_s": samples[4],
+                                  "per_nlcg_step_s": per_step, "fp64_kernel_map_s": kmap},
+            "result": {"energy_ha": res.energy, "energy_per_atom_ha": res.energy / cell.n_atoms,
+                       "outer_iterations": res.outer_iterations, "nlcg_steps": res.nlcg_iterations,
+                       "poisson_iterations": res.poisson_iterations,
+                       "kernel_iterations": res.kernel_iterations, "fp_error": res.fp_error,
+                       "max_force": float(np.abs(F).max()),
+                       "force_sum": [float(x) for x in F.sum(0)],
+                       "u_min": float(u_gs.min())},
+            "stencil_320": stencil, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    B.of_grid_destroy(h)
+    return 0
+
+
 def kernel_case(args):
     """Bounded pieces of the benchmark step, for profiler captures."""
     import numpy as np
@@ -416,6 +500,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.kernel_case:
         return kernel_case(args)
+    if args.config5:
+        return config5(args)
     import numpy as np
     import torch
     from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
