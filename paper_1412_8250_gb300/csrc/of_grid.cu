@@ -77,6 +77,9 @@ struct OpLap {
     T* y;
     __device__ bool begin() { return true; }
     __device__ T load(long long i) const { return __ldg(x + i); }
+    // two neighbours at an even index (FP32 fast path)
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ float2 load2(long long i) const { return __ldg(reinterpret_cast<const float2*>(x + i)); }
     __device__ void store(long long i, T, T lap) { y[i] = lap; }
     __device__ void end() {}
 };

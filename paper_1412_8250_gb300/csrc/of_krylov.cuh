@@ -166,6 +166,13 @@ struct OpKrylovA {
     __device__ T load(long long i) const {
         return vadd(vadd(r[i], cs_mul(shift, one<T>())), cs_mul(beta, pin[i]));
     }
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ float2 load2(long long i) const {
+        const float2 rv = *reinterpret_cast<const float2*>(r + i);
+        const float2 pv = *reinterpret_cast<const float2*>(pin + i);
+        const float s = (float)shift.x, b = (float)beta.x;
+        return make_float2(fmaf(b, pv.x, rv.x + s), fmaf(b, pv.y, rv.y + s));
+    }
     __device__ void store(long long i, T c, T lap) {
         pout[i] = c;
         const T av = apply_A(c, lap, a, Q);

@@ -181,6 +181,11 @@ struct OpCheby {
     const double* done;
     __device__ bool begin() { return *done == 0.0; }
     __device__ T load(long long i) const { return vmul(dscale, din[i]); }
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ float2 load2(long long i) const {
+        const float2 v = *reinterpret_cast<const float2*>(din + i);
+        return make_float2(dscale * v.x, dscale * v.y);
+    }
     __device__ void store(long long i, T c, T lap) {
         x[i] = x_init ? c : vadd(x[i], c);
         const T rn = vfma(-sigma, c, vadd(rin[i], lap));   // r - A d
@@ -201,6 +206,8 @@ struct OpResid32 {
     const double* done;
     __device__ bool begin() { return *done == 0.0; }
     __device__ T load(long long i) const { return x[i]; }
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ float2 load2(long long i) const { return *reinterpret_cast<const float2*>(x + i); }
     __device__ void store(long long i, T c, T lap) { r[i] = vfma(-sigma, c, vadd(b[i], lap)); }
     __device__ void end() {}
 };

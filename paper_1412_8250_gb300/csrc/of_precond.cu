@@ -813,6 +813,7 @@ struct OpFcgA {
         return true;
     }
     __device__ float load(long long i) const { return p[i]; }
+    __device__ float2 load2(long long i) const { return *reinterpret_cast<const float2*>(p + i); }
     __device__ void store(long long i, float c, float lap) {
         Ap[i] = -lap;
         acc[0] = fmaf(c, -lap, acc[0]);

@@ -9,6 +9,9 @@
 // block.  Symmetric taps are paired: w_p (f(i+p) + f(i-p)).
 #pragma once
 
+#include <type_traits>
+#include <utility>
+
 #include "of_internal.cuh"
 
 namespace of {
@@ -177,6 +180,217 @@ __device__ __forceinline__ void stencil_tile(const Dims& d, const Weights<typena
     }
 }
 
+// ---------------------------------------------------------------- FP32 fast path
+// For FP32 fields with an even n1: a block of 16 x (32 / RY) threads owns a 32 x 32 tile of the
+// x-y plane, each thread two x-neighbouring points (one float2) in RY adjacent rows, whose y
+// taps share one column of staged values.  Every two-element chunk of the
+// staged tile (with its periodic halo) starts at an even x and so is contiguous in global
+// memory even where the halo wraps, so the tile moves as 64-bit loads and stores.  The z
+// neighbours sit in a register queue of float2 rotated by compile-time index (the z loop is
+// unrolled by 2N + 1), the z and y taps use packed FP32x2 arithmetic, the x taps scalar FP32.
+constexpr int S2_BX = 16;    // threads in x (two points each)
+constexpr int S2_TY = 32;    // rows per tile
+
+template <class Op, class = void>
+struct HasLoad2 { static constexpr bool value = false; };
+template <class Op>
+struct HasLoad2<Op, decltype((void)std::declval<const Op&>().load2(0LL), void())> {
+    static constexpr bool value = true;
+};
+template <class Op>
+__device__ __forceinline__ float2 op_load2(const Op& op, long long i) {
+    if constexpr (HasLoad2<Op>::value) return op.load2(i);
+    else return make_float2(op.load(i), op.load(i + 1));
+}
+
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+// packed FP32x2: a + b, and w (both lanes) * s + c
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long w, unsigned long long s,
+                                                   unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(w), "l"(s), "l"(c));
+    return r;
+}
+
+template <int N, int RY, class Op>
+__device__ __forceinline__ void stencil2_tile(const Dims& d, const Weights<float>& W, int cz, int bx,
+                                              int by, int bz, Op& op) {
+    constexpr int BY = S2_TY / RY;            // threads in y
+    constexpr int THREADS = S2_BX * BY;
+    constexpr int HX = (N + 1) & ~1;          // x halo, rounded up to even
+    constexpr int TX = 2 * S2_BX;             // 32 points in x
+    constexpr int SX = TX + 2 * HX;
+    constexpr int SY = S2_TY + 2 * N;
+    constexpr int C2 = SX / 2;                // two-element chunks per staged row
+    constexpr int CH = C2 * SY;
+    constexpr int PER = (CH + THREADS - 1) / THREADS;
+    constexpr int Q = 2 * N + 1;
+    __shared__ __align__(16) float tile[2][SY * SX];
+    __shared__ int xi2[C2];
+    __shared__ int yi[SY];
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + S2_BX * ty;
+    const int x0 = bx * TX, y0 = by * S2_TY, z0 = bz * cz;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    for (int t = tid; t < C2; t += THREADS) xi2[t] = wrap_index(x0 - HX + 2 * t, n1);
+    for (int t = tid; t < SY; t += THREADS) yi[t] = wrap_index(y0 - N + t, n2);
+    __syncthreads();
+
+    // this thread's points: x, x + 1 in rows y0 + RY ty + r, r < RY
+    const int x = x0 + 2 * tx;
+    const long long plane = (long long)n1 * n2;
+    long long rowoff[RY];
+    bool act[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const int yl = RY * ty + r;
+        rowoff[r] = (long long)yi[yl + N] * n1 + (x < n1 ? x : 0);
+        act[r] = x < n1 && y0 + yl < n2;      // n1 even: x + 1 < n1 as well
+    }
+    long long goff[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int e = tid + k * THREADS;
+        const int sy = e / C2, c2 = e - (e / C2) * C2;
+        goff[k] = e < CH ? (long long)yi[sy] * n1 + xi2[c2] : 0;
+    }
+    unsigned long long wz2[N + 1], wy2[N + 1];
+#pragma unroll
+    for (int p = 0; p <= N; ++p) {
+        wz2[p] = pk2(make_float2(W.w[2][p], W.w[2][p]));
+        wy2[p] = pk2(make_float2(W.w[1][p], W.w[1][p]));
+    }
+    const unsigned long long centre2 = pk2(make_float2(W.centre, W.centre));
+
+    unsigned long long q[RY][Q];
+    float2 pre[PER];
+    float2 qn[RY];
+    const int zend = min(z0 + cz, n3);
+    if (z0 >= n3) return;
+#pragma unroll
+    for (int j = 0; j < 2 * N; ++j) {
+        const long long zo = (long long)wrap_index(z0 - N + j, n3) * plane;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) q[r][j] = pk2(op_load2(op, zo + rowoff[r]));
+    }
+    {
+        const long long zo = (long long)z0 * plane;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int e = tid + k * THREADS;
+            if (e < CH) *reinterpret_cast<float2*>(&tile[0][2 * e]) = op_load2(op, zo + goff[k]);
+        }
+        const long long z1 = (long long)wrap_index(z0 + 1, n3) * plane;
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (tid + k * THREADS < CH) pre[k] = op_load2(op, z1 + goff[k]);
+        const long long zq = (long long)wrap_index(z0 + N, n3) * plane;
+#pragma unroll
+        for (int r = 0; r < RY; ++r) qn[r] = op_load2(op, zq + rowoff[r]);
+    }
+    __syncthreads();
+    const int ly0 = RY * ty + N, lx = HX + 2 * tx;
+    // running offsets of planes z + 2 and z + 1 + N, wrapped by one subtraction (both start
+    // inside [0, n3) and advance by one plane per step)
+    const long long wrapoff = (long long)n3 * plane;
+    long long off_pre = (long long)wrap_index(z0 + 2, n3) * plane;
+    long long off_q = (long long)wrap_index(z0 + 1 + N, n3) * plane;
+    for (int zb = z0; zb < zend; zb += Q) {
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            const int z = zb + k;
+            if (z >= zend) break;
+            const int par = (z - z0) & 1;
+            float* cur = tile[par];
+            float* nxt = tile[par ^ 1];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) q[r][(2 * N + k) % Q] = pk2(qn[r]);
+            if (z + 1 < zend) {
+#pragma unroll
+                for (int kk = 0; kk < PER; ++kk) {
+                    const int e = tid + kk * THREADS;
+                    if (e < CH) *reinterpret_cast<float2*>(&nxt[2 * e]) = pre[kk];
+                }
+#pragma unroll
+                for (int kk = 0; kk < PER; ++kk)
+                    if (tid + kk * THREADS < CH) pre[kk] = op_load2(op, off_pre + goff[kk]);
+#pragma unroll
+                for (int r = 0; r < RY; ++r) qn[r] = op_load2(op, off_q + rowoff[r]);
+            }
+            off_pre += plane;
+            if (off_pre >= wrapoff) off_pre -= wrapoff;
+            off_q += plane;
+            if (off_q >= wrapoff) off_q -= wrapoff;
+            // z taps and centre
+            unsigned long long acc[RY];
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                acc[r] = fma2(centre2, q[r][(N + k) % Q], 0ull);
+#pragma unroll
+                for (int p = 1; p <= N; ++p)
+                    acc[r] = fma2(wz2[p], add2(q[r][(N + p + k) % Q], q[r][(N - p + k) % Q]), acc[r]);
+            }
+            // y taps: rows ly0 - N .. ly0 + RY - 1 + N of this column, each read once
+            unsigned long long col[RY + 2 * N];
+#pragma unroll
+            for (int j = 0; j < RY + 2 * N; ++j)
+                col[j] = pk2(*reinterpret_cast<const float2*>(&cur[(ly0 - N + j) * SX + lx]));
+#pragma unroll
+            for (int r = 0; r < RY; ++r)
+#pragma unroll
+                for (int p = 1; p <= N; ++p)
+                    acc[r] = fma2(wy2[p], add2(col[N + r + p], col[N + r - p]), acc[r]);
+            // x taps, scalar, row by row
+#pragma unroll
+            for (int r = 0; r < RY; ++r) {
+                float v[2 * HX + 2];   // row ly0 + r, points lx - HX .. lx + 1 + HX
+#pragma unroll
+                for (int m = 0; m <= HX; ++m) {
+                    const float2 t2 = *reinterpret_cast<const float2*>(&cur[(ly0 + r) * SX + lx - HX + 2 * m]);
+                    v[2 * m] = t2.x;
+                    v[2 * m + 1] = t2.y;
+                }
+                float2 a = upk2(acc[r]);
+#pragma unroll
+                for (int p = 1; p <= N; ++p) {
+                    a.x = fmaf(W.w[0][p], v[HX + p] + v[HX - p], a.x);
+                    a.y = fmaf(W.w[0][p], v[HX + 1 + p] + v[HX + 1 - p], a.y);
+                }
+                if (act[r]) {
+                    const float2 c = upk2(q[r][(N + k) % Q]);
+                    const long long i = (long long)z * plane + rowoff[r];
+                    op.store(i, c.x, a.x);
+                    op.store(i + 1, c.y, a.y);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int N, int RY, class Op>
+__global__ void __launch_bounds__(S2_BX * (S2_TY / RY), 2)
+stencil2_kernel(Dims d, Weights<float> W, int cz, Op op) {
+    if (!op.begin()) return;
+    stencil2_tile<N, RY, Op>(d, W, cz, blockIdx.x, blockIdx.y, blockIdx.z, op);
+    op.end();
+}
+
 template <typename T, int N, int RY, class Op>
 __global__ void __launch_bounds__(ST_THREADS)
 stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
@@ -229,6 +443,29 @@ void launch_stencil_dims(of_grid* g, const Dims& d, int N,
                                          : (sizeof(typename Real<T>::type) == 8 ? PC_STENCIL_F64 : PC_STENCIL_F32);
     ProfScope ps(g, cls, (double)OpInfo<Op>::words * sizeof(T) * (double)d.n);
     cudaStream_t stream = g->stream;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 fast path on large grids: below ~128^3 points its 32 x 32 tiles leave too few
+        // blocks to fill the GPU, and for the 7-point operator of the coarse multigrid levels
+        // the smaller tiles of the general kernel are faster
+        if (d.n1 % 2 == 0 && N == 6 && d.n >= (1LL << 21)) {
+            const int bx = (d.n1 + 2 * S2_BX - 1) / (2 * S2_BX);
+            const int by = (d.n2 + S2_TY - 1) / S2_TY;
+            const long long tiles = (long long)bx * by;
+            // one wave of two blocks per SM: as many z chunks as fit, at least 8 planes each
+            const long long chunks = std::max(1LL, (2LL * num_sms()) / tiles);
+            int cz = (int)((d.n3 + chunks - 1) / chunks);
+            cz = std::max(cz, std::min(8, d.n3));
+            constexpr int RY2 = 2;
+            const dim3 grid2(bx, by, (d.n3 + cz - 1) / cz);
+            const dim3 block2(S2_BX, S2_TY / RY2, 1);
+            switch (N) {
+                case 1: launch(stencil2_kernel<1, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
+                case 3: launch(stencil2_kernel<3, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
+                case 6: launch(stencil2_kernel<6, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
+                default: break;
+            }
+        }
+    }
     switch (N) {
         case 1: launch(stencil_kernel<T, 1, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
         case 3: launch(stencil_kernel<T, 3, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
