@@ -277,6 +277,7 @@ __global__ void k_prolong_add(Dims f, Dims c, const T* __restrict__ e, T* __rest
 // ---- the small levels inside one thread-block cluster (second-order operator on all of them)
 struct SmallLevels {
     int count;
+    int solo;     // levels solo .. count - 1 run on the cluster's first CTA alone
     int deg;
     int deg_coarse;
     float ctheta, cdelta;
@@ -308,33 +309,108 @@ constexpr int MG_CLUSTER = 8;
 __device__ __forceinline__ int cl_tid() { return blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int cl_stride() { return gridDim.x * blockDim.x; }
 __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+// Levels of at most MG_SOLO_POINTS run on the first CTA alone with block barriers (a cluster
+// barrier costs about a microsecond, several times the work of a sweep of such a level).
+constexpr int MG_SOLO_POINTS = 4096;
+template <bool SOLO> __device__ __forceinline__ int lv_tid() { return SOLO ? (int)threadIdx.x : cl_tid(); }
+template <bool SOLO> __device__ __forceinline__ int lv_stride() { return SOLO ? (int)blockDim.x : cl_stride(); }
+template <bool SOLO> __device__ __forceinline__ void lv_sync() {
+    if (SOLO) __syncthreads();
+    else cl_sync();
+}
 
-// Chebyshev smoothing of level l (zero initial guess, or starting from x), whole cluster
-template <typename T>
+// Chebyshev smoothing of level l (zero initial guess, or starting from x): the whole cluster,
+// or the first CTA alone (SOLO)
+template <typename T, bool SOLO>
 __device__ void blk_smooth(const SmallLevels& P, int l, bool zero) {
     const int n = (int)P.d[l].n;
     T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
     const float s0 = P.invD[l] / P.theta[l];
+    const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
     if (zero) {
-        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vmul(s0, b[i]);
+        for (int i = t0; i < n; i += ts) dv[i] = vmul(s0, b[i]);
     } else {
-        for (int i = cl_tid(); i < n; i += cl_stride()) r[i] = vadd(b[i], neg_op7(P, l, x, i));
-        cl_sync();
-        for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vmul(s0, r[i]);
+        for (int i = t0; i < n; i += ts) r[i] = vadd(b[i], neg_op7(P, l, x, i));
+        lv_sync<SOLO>();
+        for (int i = t0; i < n; i += ts) dv[i] = vmul(s0, r[i]);
     }
-    cl_sync();
+    lv_sync<SOLO>();
     for (int k = 0; k < P.deg; ++k) {
         const bool first = zero && k == 0;
-        for (int i = cl_tid(); i < n; i += cl_stride()) {
+        for (int i = t0; i < n; i += ts) {
             x[i] = first ? dv[i] : vadd(x[i], dv[i]);
             r[i] = vadd(first ? b[i] : r[i], neg_op7(P, l, dv, i));
         }
-        cl_sync();
+        lv_sync<SOLO>();
         if (k + 1 < P.deg) {
-            for (int i = cl_tid(); i < n; i += cl_stride())
+            for (int i = t0; i < n; i += ts)
                 dv[i] = vfma(P.ca[l][k], dv[i], vmul(P.cb[l][k] * P.invD[l], r[i]));
-            cl_sync();
+            lv_sync<SOLO>();
         }
+    }
+}
+
+// coarse b[l + 1] = full weighting of r[l]
+template <typename T, bool SOLO>
+__device__ void blk_restrict(const SmallLevels& P, int l) {
+    const float w[3] = {0.25f, 0.5f, 0.25f};
+    const Dims f = P.d[l], c = P.d[l + 1];
+    const T* r = (const T*)P.r[l];
+    T* bc = (T*)P.b[l + 1];
+    for (int I = lv_tid<SOLO>(); I < (int)c.n; I += lv_stride<SOLO>()) {
+        const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
+        T s = vzero<T>();
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int fx = wrapc(2 * ci + dx, f.n1), fy = wrapc(2 * cj + dy, f.n2),
+                              fz = wrapc(2 * ck + dz, f.n3);
+                    s = vfma(w[dz + 1] * w[dy + 1] * w[dx + 1], r[(fz * f.n2 + fy) * f.n1 + fx], s);
+                }
+        bc[I] = s;
+    }
+    lv_sync<SOLO>();
+}
+
+// x[l] += interpolation of x[l + 1]
+template <typename T, bool SOLO>
+__device__ void blk_prolong(const SmallLevels& P, int l) {
+    const Dims f = P.d[l], c = P.d[l + 1];
+    const T* e = (const T*)P.x[l + 1];
+    T* x = (T*)P.x[l];
+    for (int i = lv_tid<SOLO>(); i < (int)f.n; i += lv_stride<SOLO>()) {
+        const int fi = i % f.n1, fj = (i / f.n1) % f.n2, fk = i / (f.n1 * f.n2);
+        x[i] = vadd(x[i], interp(e, c, fi, fj, fk));
+    }
+    lv_sync<SOLO>();
+}
+
+// coarsest level: Chebyshev over the whole spectrum (non-zero part for sigma = 0) from zero
+template <typename T, bool SOLO>
+__device__ void blk_coarse(const SmallLevels& P) {
+    const int l = P.count - 1;
+    const int n = (int)P.d[l].n;
+    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
+    const float sigma1 = P.ctheta / P.cdelta;
+    float rho = 1.f / sigma1;
+    const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
+    for (int i = t0; i < n; i += ts) {
+        x[i] = vzero<T>();
+        r[i] = b[i];
+        dv[i] = vmul(P.invD[l] / P.ctheta, b[i]);
+    }
+    lv_sync<SOLO>();
+    for (int s = 0; s < P.deg_coarse; ++s) {
+        const float rn = 1.f / (2.f * sigma1 - rho);
+        const float a = rn * rho, bb = 2.f * rn / P.cdelta;
+        for (int i = t0; i < n; i += ts) {
+            x[i] = vadd(x[i], dv[i]);
+            r[i] = vadd(r[i], neg_op7(P, l, dv, i));
+        }
+        lv_sync<SOLO>();
+        for (int i = t0; i < n; i += ts) dv[i] = vfma(a, dv[i], vmul(bb * P.invD[l], r[i]));
+        lv_sync<SOLO>();
+        rho = rn;
     }
 }
 
@@ -342,61 +418,30 @@ template <typename T>
 __global__ void __cluster_dims__(MG_CLUSTER, 1, 1) __launch_bounds__(1024)
 k_small_vcycle(SmallLevels P, const double* done) {
     if (*done != 0.0) return;
-    const float w[3] = {0.25f, 0.5f, 0.25f};
+    const bool lead = blockIdx.x == 0;
+    // every cluster barrier below is reached by all CTAs: the solo parts contain none
     for (int l = 0; l + 1 < P.count; ++l) {
-        blk_smooth<T>(P, l, true);
-        const Dims f = P.d[l], c = P.d[l + 1];
-        const T* r = (const T*)P.r[l];
-        T* bc = (T*)P.b[l + 1];
-        for (int I = cl_tid(); I < (int)c.n; I += cl_stride()) {
-            const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
-            T s = vzero<T>();
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int fx = wrapc(2 * ci + dx, f.n1), fy = wrapc(2 * cj + dy, f.n2),
-                                  fz = wrapc(2 * ck + dz, f.n3);
-                        s = vfma(w[dz + 1] * w[dy + 1] * w[dx + 1], r[(fz * f.n2 + fy) * f.n1 + fx], s);
-                    }
-            bc[I] = s;
-        }
-        cl_sync();
-    }
-    {   // coarsest: Chebyshev over the whole spectrum (non-zero part for sigma = 0) from zero
-        const int l = P.count - 1;
-        const int n = (int)P.d[l].n;
-        T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
-        const float sigma1 = P.ctheta / P.cdelta;
-        float rho = 1.f / sigma1;
-        for (int i = cl_tid(); i < n; i += cl_stride()) {
-            x[i] = vzero<T>();
-            r[i] = b[i];
-            dv[i] = vmul(P.invD[l] / P.ctheta, b[i]);
-        }
-        cl_sync();
-        for (int s = 0; s < P.deg_coarse; ++s) {
-            const float rn = 1.f / (2.f * sigma1 - rho);
-            const float a = rn * rho, bb = 2.f * rn / P.cdelta;
-            for (int i = cl_tid(); i < n; i += cl_stride()) {
-                x[i] = vadd(x[i], dv[i]);
-                r[i] = vadd(r[i], neg_op7(P, l, dv, i));
-            }
-            cl_sync();
-            for (int i = cl_tid(); i < n; i += cl_stride()) dv[i] = vfma(a, dv[i], vmul(bb * P.invD[l], r[i]));
-            cl_sync();
-            rho = rn;
+        if (l < P.solo) {
+            blk_smooth<T, false>(P, l, true);
+            blk_restrict<T, false>(P, l);
+        } else if (lead) {
+            blk_smooth<T, true>(P, l, true);
+            blk_restrict<T, true>(P, l);
         }
     }
+    if (P.count - 1 < P.solo) blk_coarse<T, false>(P);
+    else if (lead) blk_coarse<T, true>(P);
     for (int l = P.count - 2; l >= 0; --l) {
-        const Dims f = P.d[l], c = P.d[l + 1];
-        const T* e = (const T*)P.x[l + 1];
-        T* x = (T*)P.x[l];
-        for (int i = cl_tid(); i < (int)f.n; i += cl_stride()) {
-            const int fi = i % f.n1, fj = (i / f.n1) % f.n2, fk = i / (f.n1 * f.n2);
-            x[i] = vadd(x[i], interp(e, c, fi, fj, fk));
+        if (l >= P.solo) {
+            if (lead) {
+                blk_prolong<T, true>(P, l);
+                blk_smooth<T, true>(P, l, false);
+            }
+        } else {
+            if (l + 1 >= P.solo) cl_sync();   // the first CTA has finished the solo levels
+            blk_prolong<T, false>(P, l);
+            blk_smooth<T, false>(P, l, false);
         }
-        cl_sync();
-        blk_smooth<T>(P, l, false);
     }
 }
 
@@ -469,6 +514,8 @@ static void vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
     {
         SmallLevels P{};
         P.count = nl - fs;
+        P.solo = P.count;
+        while (P.solo > 0 && m.lv[fs + P.solo - 1].d.n <= MG_SOLO_POINTS) --P.solo;
         P.deg = m.deg;
         P.sigma = (float)sigma;
         const Shifted SC = shifted_level(m.lv[nl - 1], sigma);

