@@ -44,20 +44,8 @@ __global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __re
         pr += ri;
     }
     double acc[3] = {(double)prz, (double)pz, (double)pr};
-    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
-        const double zbar = acc[1] / (double)n;
-        const double rho = acc[0] - zbar * acc[2];
-        if (!(rho > 0.0)) {   // M^{-1} must be positive definite on r
-            st->breakdown = 1.0;
-            st->done = 1.0;
-            return;
-        }
-        st->beta_re = first ? 0.0 : rho / st->rho_re;
-        st->beta_im = 0.0;
-        st->rho_re = rho;
-        st->rho_im = 0.0;
-        st->zshift = zbar;
-    }
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0)
+        pcg_finish(st, acc, n, first);
 }
 
 // Preconditioned COCG (complex symmetric A, real symmetric positive M): the bilinear form
@@ -74,21 +62,8 @@ __global__ void __launch_bounds__(256) k_pcocg_beta(long long n, const float2* _
         pim = fmaf(ri.x, zi.y, fmaf(ri.y, zi.x, pim));
     }
     double acc[2] = {(double)pre, (double)pim};
-    if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
-        const double2 rho = make_double2(acc[0], acc[1]);
-        if (!(fabs(rho.x) + fabs(rho.y) > 0.0)) {
-            st->breakdown = 1.0;
-            st->done = 1.0;
-            return;
-        }
-        const double2 beta = first ? make_double2(0.0, 0.0)
-                                   : cdiv(rho, make_double2(st->rho_re, st->rho_im));
-        st->beta_re = beta.x;
-        st->beta_im = beta.y;
-        st->rho_re = rho.x;
-        st->rho_im = rho.y;
-        st->zshift = 0.0;
-    }
+    if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0)
+        pcocg_finish(st, acc, first);
 }
 
 // ---------------------------------------------------------------- small vector kernels
@@ -251,7 +226,7 @@ KrylovOpts krylov_opts(const of_solve_opts* o) {
 
 static void pcg_init_body(of_grid* g, float* r, float* z, KState* st) {
     const long long n = g->d.n;
-    mg_vcycle(g, r, z, &st->done);
+    if (mg_vcycle_beta(g, r, z, st, true)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
     launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, true, st, red_ctx(g, 0));
 }
@@ -266,14 +241,14 @@ static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pou
         launch(krylov_update<float, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
                red_ctx(g, 0));
     }
-    mg_vcycle(g, r, z, &st->done);
+    if (mg_vcycle_beta(g, r, z, st, false)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
     launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
 }
 
 static void pcocg_init_body(of_grid* g, float2* r, float2* z, KState* st, double sigma) {
     const long long n = g->d.n;
-    mg_vcycle_shifted(g, r, z, &st->done, sigma);
+    if (mg_vcycle_shifted_beta(g, r, z, st, true, sigma)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
     launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, true, st,
            red_ctx(g, 0));
@@ -289,7 +264,7 @@ static void pcocg_step_body(of_grid* g, float2* x, float2* r, float2* pin, float
         launch(krylov_update<float2, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
                red_ctx(g, 0));
     }
-    mg_vcycle_shifted(g, r, z, &st->done, sigma);
+    if (mg_vcycle_shifted_beta(g, r, z, st, false, sigma)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
     launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, false, st,
            red_ctx(g, 0));
@@ -496,24 +471,35 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             KState* s32 = kstate(g, KS32);
             T32* r32 = (T32*)ar.r32;
             T32* e32 = (T32*)ar.e32;
-            launch(k_demote<T64, T32>, vec_blocks(n), 256, g->stream, 
-                n, r, r32, e32, o.inner_tol, st, s32, o.max_iter - total_iters, red_ctx(g, 0));
+            // which inner solver: flexible CG with the network, multigrid-preconditioned CG /
+            // COCG, or plain CG / COCG
+            bool pcg = false, fcg = false;
+            const double qabs = std::sqrt(Q.x * Q.x + Q.y * Q.y);
+            if constexpr (std::is_same<T32, float2>::value) {
+                pcg = qabs > 0.0 && !o.no_multigrid && mg_available(g);
+            } else {
+                const bool poisson_op = a == 1.0 && Q.x == 0.0 && Q.y == 0.0;
+                fcg = poisson_op && o.precond != nullptr;
+                pcg = poisson_op && !fcg && !o.no_multigrid && mg_available(g);
+            }
+            // A multigrid-preconditioned pass normally needs a few dozen iterations; one that
+            // has not converged after MG_PASS_CAP has stalled in FP32, and the next pass
+            // restarts the recurrence from the true FP64 residual.
+            constexpr int MG_PASS_CAP = 100;
+            const int pass_max = pcg ? std::min(MG_PASS_CAP, o.max_iter - total_iters)
+                                     : o.max_iter - total_iters;
+            launch(k_demote<T64, T32>, vec_blocks(n), 256, g->stream,
+                n, r, r32, e32, o.inner_tol, st, s32, pass_max, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
             KState hi;
-            bool pcg = false, fcg = false;
             if constexpr (std::is_same<T32, float2>::value) {
                 // shifted systems: COCG preconditioned by the V-cycle of -L + |Q| / a
-                const double qabs = std::sqrt(Q.x * Q.x + Q.y * Q.y);
-                pcg = qabs > 0.0 && !o.no_multigrid && mg_available(g);
                 if (pcg)
                     hi = iterate_pcocg(g, KS32, e32, r32, (float2*)ar.pa32, (float2*)ar.pb32,
                                        (float2*)ar.Ap32, (float2*)ar.z32, (float)a, Q, qabs / a,
                                        o.check_every);
             }
             if constexpr (std::is_same<T32, float>::value) {
-                const bool poisson_op = a == 1.0 && Q.x == 0.0 && Q.y == 0.0;
-                fcg = poisson_op && o.precond != nullptr;
-                pcg = poisson_op && !fcg && !o.no_multigrid && mg_available(g);
                 if (fcg)
                     hi = iterate_fcg(g, o.precond, o.theta, KS32, e32, r32, (float*)ar.pa32,
                                      (float*)ar.z32, o.check_every, nullptr, &net_steps);

@@ -249,6 +249,45 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
 
 inline int vec_blocks(long long n) { return red_blocks(n, 256 * 4); }
 
+// Preconditioned-CG scalars from the grid-reduced sums s = (r^T z, sum z, sum r) (projected:
+// z is used with its mean removed): rho = r^T (z - zbar), beta = rho / rho_old (0 first).
+__device__ __forceinline__ void pcg_finish(KState* st, const double (&s)[3], long long n, bool first) {
+    const double zbar = s[1] / (double)n;
+    const double rho = s[0] - zbar * s[2];
+    if (!(rho > 0.0)) {   // M^{-1} must be positive definite on r
+        st->breakdown = 1.0;
+        st->done = 1.0;
+        return;
+    }
+    st->beta_re = first ? 0.0 : rho / st->rho_re;
+    st->beta_im = 0.0;
+    st->rho_re = rho;
+    st->rho_im = 0.0;
+    st->zshift = zbar;
+}
+// Preconditioned COCG: rho = r^T z (bilinear, complex), beta = rho / rho_old (0 first).
+__device__ __forceinline__ void pcocg_finish(KState* st, const double (&s)[2], bool first) {
+    const double2 rho = make_double2(s[0], s[1]);
+    if (!(fabs(rho.x) + fabs(rho.y) > 0.0)) {
+        st->breakdown = 1.0;
+        st->done = 1.0;
+        return;
+    }
+    const double2 beta = first ? make_double2(0.0, 0.0) : cdiv(rho, make_double2(st->rho_re, st->rho_im));
+    st->beta_re = beta.x;
+    st->beta_im = beta.y;
+    st->rho_re = rho.x;
+    st->rho_im = rho.y;
+    st->zshift = 0.0;
+}
+
+// One V-cycle z = M^{-1} r (of_mg.cu) whose last smoothing sweep also forms the
+// preconditioned-CG scalars (pcg_finish / pcocg_finish) on state st.  Returns false when the
+// hierarchy has no grid-wide level to fuse into; the caller then reduces separately.
+bool mg_vcycle_beta(of_grid* g, const float* r, float* z, KState* st, bool first);
+bool mg_vcycle_shifted_beta(of_grid* g, const float2* r, float2* z, KState* st, bool first,
+                            double sigma);
+
 
 // Arena of Krylov vectors: FP64 (r, pa, pb, Ap, b) and FP32 (r, pa, pb, Ap, e), complex-sized.
 struct Arena {

@@ -18,7 +18,7 @@
 
 #include <cooperative_groups.h>
 
-#include "of_stencil.cuh"
+#include "of_krylov.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -179,7 +179,18 @@ struct OpCheby {
     T* dout;
     float a, bD, sigma;
     const double* done;
-    __device__ bool begin() { return *done == 0.0; }
+    // last sweep of a V-cycle inside preconditioned CG / COCG (rk non-null): also reduce
+    // r^T z, sum z, sum r (real) or the complex r^T z, z = the updated x, and finish beta
+    const T* rk = nullptr;
+    KState* st = nullptr;
+    RedCtx rc{};
+    bool first = false;
+    long long n = 0;
+    float acc[3];
+    __device__ bool begin() {
+        acc[0] = acc[1] = acc[2] = 0.f;
+        return *done == 0.0;
+    }
     __device__ T load(long long i) const { return vmul(dscale, din[i]); }
     template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
     __device__ float2 load2(long long i) const {
@@ -187,12 +198,42 @@ struct OpCheby {
         return make_float2(dscale * v.x, dscale * v.y);
     }
     __device__ void store(long long i, T c, T lap) {
-        x[i] = x_init ? c : vadd(x[i], c);
+        const T xn = x_init ? c : vadd(x[i], c);
+        x[i] = xn;
         const T rn = vfma(-sigma, c, vadd(rin[i], lap));   // r - A d
         rout[i] = rn;
         if (dout) dout[i] = vfma(a, c, vmul(bD, rn));
+        if (rk) accumulate(rk[i], xn);
     }
-    __device__ void end() {}
+    __device__ void accumulate(float r, float z) {
+        acc[0] = fmaf(r, z, acc[0]);
+        acc[1] += z;
+        acc[2] += r;
+    }
+    __device__ void accumulate(float2 r, float2 z) {
+        acc[0] = fmaf(r.x, z.x, fmaf(-r.y, z.y, acc[0]));
+        acc[1] = fmaf(r.x, z.y, fmaf(r.y, z.x, acc[1]));
+    }
+    __device__ void end() {
+        if (!rk) return;
+        if constexpr (std::is_same<T, float>::value) {
+            double s[3] = {(double)acc[0], (double)acc[1], (double)acc[2]};
+            if (grid_reduce<3>(s, rc.partials, rc.counter, st->red) && threadIdx.x == 0 && threadIdx.y == 0)
+                pcg_finish(st, s, n, first);
+        } else {
+            double s[2] = {(double)acc[0], (double)acc[1]};
+            if (grid_reduce<2>(s, rc.partials, rc.counter, st->red) && threadIdx.x == 0 && threadIdx.y == 0)
+                pcocg_finish(st, s, first);
+        }
+    }
+};
+
+// the CG scalars fused into a V-cycle's last sweep: (KState, first call, residual)
+template <typename T>
+struct BetaFuse {
+    KState* st;
+    bool first;
+    const T* r;
 };
 
 // r = b - A x
@@ -464,7 +505,8 @@ static void cheby_coeffs(double lmin, double lmax, int deg, std::vector<float>& 
 }
 
 template <typename T>
-static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const double* done, double sigma) {
+static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const double* done, double sigma,
+                   const BetaFuse<T>* fuse = nullptr) {
     constexpr int RY = std::is_same<T, float>::value ? 2 : 1;
     const Shifted S = shifted_level(L, sigma);
     std::vector<float> a, b;
@@ -488,6 +530,13 @@ static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const doubl
         op.bD = b[k] * S.invD;
         op.sigma = (float)sigma;
         op.done = done;
+        if (fuse && k + 1 == deg) {
+            op.rk = fuse->r;
+            op.st = fuse->st;
+            op.rc = red_ctx(g, 0);
+            op.first = fuse->first;
+            op.n = L.d.n;
+        }
         launch_stencil_dims<T, RY>(g, L.d, L.N, L.W, op);
     }
 }
@@ -495,7 +544,8 @@ static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const doubl
 // z = M^{-1} r, one V-cycle for A = -L_h + sigma; r, z fine-level fields.  Levels above
 // first_small are swept by grid-wide launches, the rest by k_small_vcycle on one cluster.
 template <typename T>
-static void vcycle(of_grid* g, const T* r, T* z, const double* done, double sigma) {
+static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigma,
+                   const BetaFuse<T>* fuse = nullptr) {
     MG& m = *g->mg;
     const int nl = (int)m.lv.size();
     const int fs = m.first_small;
@@ -556,10 +606,11 @@ static void vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
             launch(k_prolong_add<T>, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d,
                    (const T*)C.x, (T*)L.x, done);
         }
-        smooth<T>(g, L, m.deg, false, done, sigma);
+        smooth<T>(g, L, m.deg, false, done, sigma, l == 0 ? fuse : nullptr);
     }
     m.lv[0].b = saved_b;
     m.lv[0].x = saved_x;
+    return fs >= 1 && m.deg >= 1;   // the last sweep was level 0's, and carried the fusion
 }
 
 void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
@@ -568,6 +619,16 @@ void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
 
 void mg_vcycle_shifted(of_grid* g, const float2* r, float2* z, const double* done, double sigma) {
     vcycle<float2>(g, r, z, done, sigma);
+}
+
+bool mg_vcycle_beta(of_grid* g, const float* r, float* z, KState* st, bool first) {
+    const BetaFuse<float> f{st, first, r};
+    return vcycle<float>(g, r, z, &st->done, 0.0, &f);
+}
+
+bool mg_vcycle_shifted_beta(of_grid* g, const float2* r, float2* z, KState* st, bool first, double sigma) {
+    const BetaFuse<float2> f{st, first, r};
+    return vcycle<float2>(g, r, z, &st->done, sigma, &f);
 }
 
 }  // namespace of
