@@ -497,8 +497,13 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
             OF_LAUNCH_CHECK();
             fetch_scalars(g, SC_RD, 4, m);
         }
-        poisson_into(g, u, v.d, v.B, po, st);
-        poisson_into(g, v.d, v.d, v.C, po, st);
+        // phi_ud and phi_dd only shape the line energy E(s) (the Hartree moments) and the
+        // starting point of the re-solve below, which sets phi for the gradient and the energy
+        // to the full tolerance; 1e-8 resolves E(s) far below the step's energy change
+        KrylovOpts pl = po;
+        pl.tol = std::max(po.tol, 1e-8);
+        poisson_into(g, u, v.d, v.B, pl, st);
+        poisson_into(g, v.d, v.d, v.C, pl, st);
         launch_stencil<double, 2>(g, g->w64, OpLapDot{v.d, u, v.Ld, red_ctx(g, SC_DLD)});
         launch(k_line_moments, nb, 256, g->stream, n, u, v.d, fn.mu != 0.0 ? V : nullptr, phi, v.D,
                                                   v.B, v.C, v.b, red_ctx(g, SC_MD));
@@ -535,7 +540,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         launch(k_step, nb, 256, g->stream, n, u, v.d, phi, v.D, v.B, v.C, s, c);
         launch(k_density_plus, nb, 256, g->stream, n, u, v.b, v.rho);
         OF_LAUNCH_CHECK();
-        poisson_into(g, v.rho, nullptr, phi, po, st);   // polish (warm start is nearly exact)
+        poisson_into(g, v.rho, nullptr, phi, po, st);   // re-solve (warm start is nearly exact)
         std::swap(v.r, v.rp);
         std::swap(v.d, v.dp);
         rr_prev = rr;
