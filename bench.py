@@ -49,7 +49,7 @@ def parse():
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-cell batched-vs-sequential Poisson comparison")
-    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf", "net160"],
+    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf", "net160", "scf96_short"],
                    help="run only a bounded piece of the step (for profiler captures) and exit: "
                         "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil320 = "
                         "FP32/FP64 Laplacian sweeps on a 320^3 grid; scf = one ground state")
@@ -476,6 +476,18 @@ def kernel_case(args):
         B.of_grid_destroy(h)
         return 0
     cell, h, sysd, fn, o = make_case(torch, B, Fn, W, args.precision)
+    if args.kernel_case == "scf96_short":
+        # the benchmark's ground state cut short (2 outer iterations of at most 10 NLCG steps):
+        # every kernel class of the step, in a launch count a profiler can list
+        o.fp_max_iter = 2
+        o.nlcg_max_iter = 10
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(u)
+        B.of_scf_ground_state(h, sysd, fn, o, u, phi, allow=(B.OF_ENOCONV,))
+        B.of_forces(h, sysd, u, phi)
+        torch.cuda.synchronize()
+        B.of_grid_destroy(h)
+        return 0
     if args.kernel_case == "poisson96":
         rho = torch.from_numpy(W.random_field(cell.shape, seed=3, kind="smooth")).cuda()
         so = B.of_default_solve_opts()
