@@ -78,6 +78,35 @@ def test_laplacian_fp32(n, L, N):
         assert np.max(np.abs(host(yd) - ref)) <= 8 * 2**-24 * wsum * np.max(np.abs(x))
 
 
+# grids of at least 2^21 points with even n1 take the FP32 fast-path sweep (float2 points, two
+# rows per thread, 32 x 32 tiles); these sizes leave partial tiles in x and y
+LARGE_CASES = [((136, 140, 120), (32.3, 33.25, 28.5)), ((160, 128, 104), (38.0, 30.4, 24.7))]
+
+
+@pytest.mark.parametrize("n,L", LARGE_CASES)
+def test_laplacian_fp32_large_grids(n, L):
+    with G(n, L, 6) as g:
+        x = W.random_field(g.shape, seed=9).astype(np.float32)
+        xd = dev(x, torch.float32)
+        yd = torch.empty_like(xd)
+        B.of_laplacian_apply(g.h, B.OF_F32, xd, yd)
+        ref = O.laplacian(x.astype(np.float64), g.grid)
+        wsum = sum(np.abs(O.fd_laplacian_weights(6, hd)).sum() * 2 for hd in g.grid.h)
+        assert np.max(np.abs(host(yd) - ref)) <= 8 * 2**-24 * wsum * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("n,L", LARGE_CASES[:1])
+def test_poisson_mixed_large_grid(n, L):
+    # the mixed solve's FP32 Krylov and V-cycle sweeps run on the fast path at this size
+    with G(n, L) as g:
+        rho = W.random_field(g.shape, seed=3, kind="smooth") + 0.1 * W.random_field(g.shape, seed=4)
+        ref = O.poisson_solve(rho, g.grid)
+        phi = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        info = B.of_poisson_solve(g.h, dev(rho), phi, _opts(B.OF_F32, 1e-13))
+        assert info.rel_residual <= 1e-13
+        assert np.max(np.abs(host(phi) - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
 def test_laplacian_symbol_on_device():
     with G((24, 18, 30), (7.6, 6.0, 9.0), 6) as g:
         sig = O.laplacian_symbol(g.grid)
