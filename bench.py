@@ -173,9 +173,10 @@ def stencil_rates(torch, B, h, shape, reps=30):
 def batched_compare(torch, B, W, reps=2):
     """64 uneven cells (reps 2..4 per axis, 64-128 points per axis, half with a vacancy, seed 3):
     the Poisson problem of each cell's initial density (uniform electrons plus its Gaussian
-    nuclear charge), solved to relative residual 1e-10 by (a) one batched call, (b) the
-    single-grid solver cell by cell with the same plain FP32 CG + FP64 refinement, (c) cell by
-    cell with the multigrid-preconditioned CG."""
+    nuclear charge), solved to relative residual 1e-10 by (a) one batched call of grouped
+    launches (plain FP32 CG + FP64 refinement), (b) one batched call in the multigrid form
+    (per-cell multigrid PCG over concurrent streams), (c) the single-grid solver cell by cell
+    with the same plain CG, (d) cell by cell with the multigrid-preconditioned CG."""
     cells = W.batched_cells()
     stream = torch.cuda.current_stream()
     grids, rhos, phis = [], [], []
@@ -205,11 +206,19 @@ def batched_compare(torch, B, W, reps=2):
             p.zero_()
             B.of_poisson_solve(g, r, p, opts)
 
+    def run_batched_mg():
+        for p in phis:
+            p.zero_()
+        return B.of_poisson_solve_batched(grids, rhos, phis, om)
+
     out = {}
     run_batched()   # tunes the blocking, captures the graph
+    run_batched_mg()
     run_seq(o)
     run_seq(om)
-    for name, fn in [("batched_plain_cg_s", run_batched), ("sequential_plain_cg_s", lambda: run_seq(o)),
+    for name, fn in [("batched_plain_cg_s", run_batched),
+                     ("batched_multigrid_concurrent_s", run_batched_mg),
+                     ("sequential_plain_cg_s", lambda: run_seq(o)),
                      ("sequential_multigrid_pcg_s", lambda: run_seq(om))]:
         ts = []
         for _ in range(reps):

@@ -177,11 +177,17 @@ of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1, double L2,
 
 /* Poisson solves (as of_poisson_solve) of ncells independent cells at once: grids[c] with
  * rho[c] and phi[c] (device double*, in = guess, out = mean-free solution).  All grids must
- * share the stream and the finite-difference order.  Every Krylov phase of all cells is one
- * grouped launch and the lockstep FP32 CG iterations (FP64 refinement as in the OF_F32
- * mode, no multigrid) are replayed from one CUDA graph; the z extent of the stencil blocks is
- * chosen per set of grid shapes by timing candidates on the first call.  infos (optional)
- * receives one record per cell.  Synchronises the stream. */
+ * share the stream and the finite-difference order.  Two forms:
+ *  - opts->no_multigrid = 1 (or OF_F64): every Krylov phase of all cells is one grouped launch
+ *    and the lockstep FP32 CG iterations (FP64 refinement as in the OF_F32 mode) are replayed
+ *    from one CUDA graph; the z extent of the stencil blocks is chosen per set of grid shapes
+ *    by timing candidates on the first call.
+ *  - OF_F32 with multigrid (the default no_multigrid = 0, every cell coarsenable): each cell
+ *    runs the multigrid-preconditioned solve of of_poisson_solve, the cells spread over up to 8
+ *    internal streams driven by host threads so that their kernels overlap; the call orders
+ *    them after the work queued on the shared stream and the shared stream after them.  The
+ *    grids must not be used by other threads meanwhile.
+ * infos (optional) receives one record per cell.  Synchronises the stream. */
 of_status of_poisson_solve_batched(int ncells, of_grid* const* grids, const double* const* rho,
                                    double* const* phi, const of_solve_opts* opts,
                                    of_solve_info* infos);

@@ -1,6 +1,7 @@
-"""GPU parity of the batched Poisson solver (grouped launches over uneven cells, one CUDA
-graph for the lockstep CG) against the oracle's exact discrete solutions, and against the
-single-grid solver run cell by cell."""
+"""GPU parity of the batched Poisson solver against the oracle's exact discrete solutions, and
+against the single-grid solver run cell by cell, in both forms: grouped launches over uneven
+cells with one CUDA graph for the lockstep plain CG (no_multigrid), and the per-cell multigrid
+solves spread over concurrent streams (the default)."""
 import numpy as np
 import pytest
 
@@ -24,7 +25,8 @@ def _opts(tol, multigrid=True):
     return o
 
 
-def test_batched_poisson_matches_oracle_and_single_grid():
+@pytest.mark.parametrize("multigrid", [False, True], ids=["grouped_cg", "concurrent_multigrid"])
+def test_batched_poisson_matches_oracle_and_single_grid(multigrid):
     stream = torch.cuda.current_stream()
     grids, rhos, phis, refs = [], [], [], []
     try:
@@ -36,7 +38,7 @@ def test_batched_poisson_matches_oracle_and_single_grid():
             rhos.append(torch.from_numpy(rho).cuda())
             phis.append(torch.zeros(grid.shape, dtype=torch.float64, device="cuda"))
             refs.append(O.poisson_solve(rho, grid))
-        infos = B.of_poisson_solve_batched(grids, rhos, phis, _opts(1e-12))
+        infos = B.of_poisson_solve_batched(grids, rhos, phis, _opts(1e-12, multigrid))
         for k in range(len(SHAPES)):
             got = phis[k].cpu().numpy()
             assert infos[k].rel_residual <= 1e-12, k
@@ -47,10 +49,10 @@ def test_batched_poisson_matches_oracle_and_single_grid():
                 one = torch.zeros_like(phis[k])
                 B.of_poisson_solve(grids[k], rhos[k], one, _opts(1e-12, mg))
                 assert np.max(np.abs(one.cpu().numpy() - got)) <= 2e-9 * np.max(np.abs(refs[k]))
-        # second call reuses the tuned blocking and the captured graph
+        # second call reuses the tuned blocking and the captured graphs
         for p in phis:
             p.zero_()
-        B.of_poisson_solve_batched(grids, rhos, phis, _opts(1e-12))
+        B.of_poisson_solve_batched(grids, rhos, phis, _opts(1e-12, multigrid))
         for k in range(len(SHAPES)):
             assert np.max(np.abs(phis[k].cpu().numpy() - refs[k])) <= 1e-9 * np.max(np.abs(refs[k]))
     finally:
