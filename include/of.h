@@ -219,6 +219,16 @@ of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functio
                               const of_scf_opts* opts, double* u, double* phi,
                               of_scf_result* res);
 
+/* Ground states of ncells independent cells at once (same functional and options): grids[c]
+ * (distinct handles, one shared stream), systems[c], u[c], phi[c] as in of_scf_ground_state,
+ * one result per cell in results[c].  The cells run on up to 8 internal streams driven by host
+ * threads, so that their kernels overlap; the call orders them after the work queued on the
+ * shared stream and the shared stream after them, and synchronises it.  Returns the first
+ * failing cell's status (OF_ENOCONV for a cell that did not converge, results still written). */
+of_status of_scf_ground_state_batched(int ncells, of_grid* const* grids, const of_system* systems,
+                                      const of_functional* fn, const of_scf_opts* opts,
+                                      double* const* u, double* const* phi, of_scf_result* results);
+
 /* Hellmann-Feynman forces of Eq. Force:Nuclei with the overlap correction f^c of App. B:
  * F[3*J + c] (host) for ion J, component c.  phi: device, the ground-state potential.
  * u is accepted for the interface of the paper's statement and not read. */

@@ -85,6 +85,9 @@ _SIGNATURES = {
     "of_scf_ground_state": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional),
                                  C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
+    "of_scf_ground_state_batched": (_I, [_I, C.POINTER(_P), C.POINTER(of_system),
+                                         C.POINTER(of_functional), C.POINTER(of_scf_opts),
+                                         C.POINTER(_P), C.POINTER(_P), C.POINTER(of_scf_result)]),
     "of_last_error": (C.c_char_p, []),
     "of_poisson_solve_noalloc": (_I, [_I, _I, _I, _D, _D, _D, _I, _P, _P, _P,
                                       C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
@@ -259,6 +262,19 @@ def of_scf_ground_state(h, sys, fn, opts, u, phi, allow=()):
                                     _ptr(phi), C.byref(res))
     _check(st, "of_scf_ground_state", allow)
     return res
+
+
+def of_scf_ground_state_batched(grids, systems, fn, opts, us, phis, allow=()):
+    """Ground states of several cells in one call (see include/of.h); returns their results."""
+    nc = len(grids)
+    G = (_P * nc)(*[g.value if isinstance(g, _P) else g for g in grids])
+    S = (of_system * nc)(*systems)
+    U = (_P * nc)(*[_ptr(x) for x in us])
+    Ph = (_P * nc)(*[_ptr(x) for x in phis])
+    res = (of_scf_result * nc)()
+    st = load().of_scf_ground_state_batched(nc, G, S, C.byref(fn), C.byref(opts), U, Ph, res)
+    _check(st, "of_scf_ground_state_batched", allow)
+    return list(res)
 
 
 def of_forces(h, sys, u, phi):

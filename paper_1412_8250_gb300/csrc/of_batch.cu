@@ -11,12 +11,11 @@
 #include <cstdint>
 #include <cstdlib>
 #include <map>
-#include <string>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
 #include "of_krylov.cuh"
+#include "of_pool.cuh"
 
 namespace of {
 
@@ -533,74 +532,13 @@ using namespace of;
 
 namespace of {
 // Multigrid form of the batched solve: the multigrid-preconditioned solver is host-driven per
-// cell and, on cells of this size, latency bound, so the cells run on a pool of worker
-// streams, one host thread each, and their kernels overlap on the GPU.  Each worker stream
-// first waits for the work already queued on the cells' shared stream; the shared stream
-// then waits for every worker.  A cell's graphs, workspace and scalars are its own, so cells
-// never share state.
+// cell and, on cells of this size, latency bound, so the cells run on the stream pool and
+// their kernels overlap on the GPU.
 static of_status poisson_concurrent(int ncells, of_grid* const* grids, const double* const* rho,
                                     double* const* phi, const KrylovOpts& o, of_solve_info* infos) {
-    of_grid* g0 = grids[0];
-    const cudaStream_t shared = g0->stream;
-    const int T = std::min(ncells, 8);
-    std::vector<cudaStream_t> wstream(T, nullptr);
-    std::vector<cudaEvent_t> wdone(T, nullptr);
-    cudaEvent_t start = nullptr;
-    std::vector<of_status> status(ncells, OF_OK);
-    std::vector<std::string> message(ncells);
-    auto cleanup = [&]() {
-        for (int t = 0; t < T; ++t) {
-            if (wstream[t]) cudaStreamDestroy(wstream[t]);
-            if (wdone[t]) cudaEventDestroy(wdone[t]);
-        }
-        if (start) cudaEventDestroy(start);
-    };
-    try {
-        OF_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-        OF_CUDA(cudaEventRecord(start, shared));
-        for (int t = 0; t < T; ++t) {
-            OF_CUDA(cudaStreamCreateWithFlags(&wstream[t], cudaStreamNonBlocking));
-            OF_CUDA(cudaEventCreateWithFlags(&wdone[t], cudaEventDisableTiming));
-            OF_CUDA(cudaStreamWaitEvent(wstream[t], start, 0));
-        }
-    } catch (const Error& e) {
-        cleanup();
-        return e.code;
-    }
-    auto work = [&](int t) {
-        cudaSetDevice(g0->device);
-        for (int c = t; c < ncells; c += T) {
-            of_grid* g = grids[c];
-            g->stream = wstream[t];
-            try {
-                status[c] = poisson(g, rho[c], phi[c], o, infos ? &infos[c] : nullptr);
-            } catch (const Error& e) {
-                status[c] = e.code;
-            } catch (...) {
-                status[c] = OF_ECUDA;
-            }
-            if (status[c] != OF_OK) message[c] = of_last_error();
-            g->stream = shared;
-        }
-        cudaEventRecord(wdone[t], wstream[t]);
-    };
-    std::vector<std::thread> pool;
-    for (int t = 0; t < T; ++t) pool.emplace_back(work, t);
-    for (auto& th : pool) th.join();
-    of_status worst = OF_OK;
-    try {
-        for (int t = 0; t < T; ++t) OF_CUDA(cudaStreamWaitEvent(shared, wdone[t], 0));
-        OF_CUDA(cudaStreamSynchronize(shared));
-    } catch (const Error& e) {
-        worst = e.code;
-    }
-    cleanup();
-    for (int c = 0; c < ncells && worst == OF_OK; ++c)
-        if (status[c] != OF_OK) {
-            worst = status[c];
-            set_error("batched solve, cell %d: %s", c, message[c].c_str());
-        }
-    return worst;
+    return run_on_stream_pool(ncells, grids, [&](int c) {
+        return poisson(grids[c], rho[c], phi[c], o, infos ? &infos[c] : nullptr);
+    });
 }
 }  // namespace of
 

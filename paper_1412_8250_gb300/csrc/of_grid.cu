@@ -1,4 +1,5 @@
 // Grid handle, workspace, error reporting and the plain Laplacian entry point.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 #include <cmath>
@@ -20,15 +21,16 @@ void set_error(const char* fmt, ...) {
 }
 
 int num_sms() {
-    static int cached = 0;
-    if (!cached) {
+    static std::atomic<int> cached{0};
+    int v = cached.load(std::memory_order_relaxed);
+    if (!v) {
         int dev = 0;
         cudaGetDevice(&dev);
-        int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached = v > 0 ? v : 1;
+        v = v > 0 ? v : 1;
+        cached.store(v, std::memory_order_relaxed);
     }
-    return cached;
+    return v;
 }
 
 void* ws(of_grid* g, int slot, size_t bytes) {

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "of_functional.cuh"
+#include "of_pool.cuh"
 #include "of_stencil.cuh"
 
 namespace of {
@@ -837,6 +838,39 @@ of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const
         const double s = lr_potential_impl(g, fn, kf2, u, vlr, W, krylov_opts(opts), st, info);
         if (t_lr) *t_lr = 0.5 * OF_CF * s * g->dV;
         return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+of_status of_scf_ground_state_batched(int ncells, of_grid* const* grids, const of_system* systems,
+                                      const of_functional* fn, const of_scf_opts* opts,
+                                      double* const* u, double* const* phi, of_scf_result* results) {
+    if (ncells < 1 || !grids || !systems || !fn || !u || !phi || !results) {
+        set_error("of_scf_ground_state_batched: bad argument");
+        return OF_EINVAL;
+    }
+    try {
+        for (int c = 0; c < ncells; ++c) {
+            OF_REQUIRE(grids[c] && u[c] && phi[c], OF_EINVAL,
+                       "of_scf_ground_state_batched: null grid or field for cell %d", c);
+            OF_REQUIRE(grids[c]->stream == grids[0]->stream && grids[c]->device == grids[0]->device,
+                       OF_EINVAL, "of_scf_ground_state_batched: cell %d differs in stream or device", c);
+            for (int k = 0; k < c; ++k)
+                OF_REQUIRE(grids[k] != grids[c], OF_EINVAL,
+                           "of_scf_ground_state_batched: cells %d and %d share a grid handle", k, c);
+        }
+        of_scf_opts o;
+        if (opts) o = *opts; else of_default_scf_opts(&o);
+        return run_on_stream_pool(ncells, grids, [&](int c) -> of_status {
+            scf(grids[c], &systems[c], fn, &o, u[c], phi[c], &results[c]);
+            if (!results[c].converged) {
+                set_error("ground state not converged: nlcg residual %.3e, fixed-point error %.3e",
+                          results[c].nlcg_residual, results[c].fp_error);
+                return OF_ENOCONV;
+            }
+            return OF_OK;
+        });
     } catch (const Error& e) {
         return e.code;
     }

@@ -103,3 +103,33 @@ def test_wt_108_atoms_full_size_properties():
     assert np.max(np.abs(F.sum(0))) < 1e-4
     # the ground state lies below the uniform-density energy reached before any update
     assert res.energy < 0
+
+
+def test_batched_ground_states_match_single_cell_calls():
+    # three different cells in one call (stream pool): each equals its own single-cell ground
+    # state, and the first equals the oracle's
+    cells = [W.al4_displaced_cell(points_per_cell=16), W.al4_cell(points_per_cell=16),
+             W.small_cell(n=(16, 20, 18), L=(7.6, 9.5, 8.55), seed=3)]
+    stream = torch.cuda.current_stream()
+    grids = [B.of_grid_create(c.n, c.L, 6, stream) for c in cells]
+    try:
+        systems = [B.make_system(c.R, c.Z, c.sigma, c.rc) for c in cells]
+        o = B.of_default_scf_opts()
+        o.precision = B.OF_F32
+        us = [torch.ones(c.shape, dtype=torch.float64, device="cuda") for c in cells]
+        phis = [torch.zeros_like(x) for x in us]
+        results = B.of_scf_ground_state_batched(grids, systems, Fn.tfw(), o, us, phis)
+        for k, c in enumerate(cells):
+            assert results[k].converged, k
+            u1 = torch.ones(c.shape, dtype=torch.float64, device="cuda")
+            p1 = torch.zeros_like(u1)
+            one = B.of_scf_ground_state(grids[k], systems[k], Fn.tfw(), o, u1, p1)
+            assert abs(results[k].energy - one.energy) / c.n_atoms <= 1e-8, k
+            assert torch.max(torch.abs(us[k] - u1)).item() <= 1e-5 * torch.max(u1).item(), k
+        grid = O.Grid(cells[0].n, cells[0].L, 6)
+        ref = O.scf_ground_state(grid, cells[0].R, cells[0].Z, cells[0].sigma, cells[0].rc,
+                                 O.tfw_functional(), nlcg_tol=1e-7)
+        assert abs(results[0].energy - ref.energy) / cells[0].n_atoms <= E_TOL
+    finally:
+        for g in grids:
+            B.of_grid_destroy(g)
