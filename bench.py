@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--compare-f64", action="store_true",
                    help="also time one plain FP64 CG ground state and report it")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--config3", action="store_true",
+                   help="batched ground states of the first --cells cells of the 64-cell set")
+    p.add_argument("--cells", type=int, default=16)
     p.add_argument("--config5", action="store_true",
                    help="measure the 3999-atom 320^3 ground state instead of the benchmark step")
     p.add_argument("--no-learned", action="store_true",
@@ -470,6 +473,71 @@ def whole_job_value(step_ms, steps, world, device="cuda"):
     return total_ms, total_ms / 1e3 / (steps * world)
 
 
+def config3(args):
+    """Ground states + forces of the first --cells cells of the 64-cell set (reps 2..4 per axis,
+    64-128 points per axis, half with a vacancy, +-0.1 bohr, seed 3; WT-type kernel, the
+    benchmark's options): one batched call (cells on a pool of streams) against the same ground
+    states one after another.  Prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    cells = W.batched_cells()[:args.cells]
+    stream = torch.cuda.current_stream()
+    grids = [B.of_grid_create(c.n, c.L, 6, stream) for c in cells]
+    systems = [B.make_system(c.R, c.Z, c.sigma, c.rc) for c in cells]
+    _, h0, _, _, o = make_case(torch, B, Fn, W, "mixed")
+    B.of_grid_destroy(h0)
+    fn = Fn.wt()
+    us = [torch.ones(c.shape, dtype=torch.float64, device="cuda") for c in cells]
+    phis = [torch.zeros_like(x) for x in us]
+
+    def batched():
+        for x, p in zip(us, phis):
+            x.fill_(1.0)
+            p.zero_()
+        r = B.of_scf_ground_state_batched(grids, systems, fn, o, us, phis)
+        for g, s, x, p in zip(grids, systems, us, phis):
+            B.of_forces(g, s, x, p)
+        return r
+
+    def sequential():
+        out = []
+        for g, s, x, p in zip(grids, systems, us, phis):
+            x.fill_(1.0)
+            p.zero_()
+            out.append(B.of_scf_ground_state(g, s, fn, o, x, p))
+            B.of_forces(g, s, x, p)
+        return out
+
+    batched()   # warm-up: workspaces, multigrid hierarchies, graphs
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t = time.time()
+        rb = batched()
+        torch.cuda.synchronize()
+        tb = time.time() - t
+        t = time.time()
+        rs = sequential()
+        torch.cuda.synchronize()
+        ts = time.time() - t
+    de = max(abs(a.energy - b.energy) / c.n_atoms for a, b, c in zip(rb, rs, cells))
+    line = {"metric": "s per batch of ground states + forces", "unit": "s", "higher_is_better": False,
+            "data": "synthetic",
+            "config": {"workload": f"first {len(cells)} cells of the 64-cell set (seed 3), "
+                                   "WT-type kernel, ground state + forces each",
+                       "points": int(sum(c.n_points for c in cells)),
+                       "atoms": int(sum(c.n_atoms for c in cells))},
+            "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+            "max_energy_difference_ha_per_atom": de,
+            "energies_per_atom_ha": [r.energy / c.n_atoms for r, c in zip(rb, cells)],
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    for g in grids:
+        B.of_grid_destroy(g)
+    return 0
+
+
 def kernel_case(args):
     """Bounded pieces of the benchmark step, for profiler captures."""
     import numpy as np
@@ -539,6 +607,8 @@ def main():
         return kernel_case(args)
     if args.config5:
         return config5(args)
+    if args.config3:
+        return config3(args)
     import numpy as np
     import torch
     from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
