@@ -52,10 +52,11 @@ def parse():
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-cell batched-vs-sequential Poisson comparison")
-    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil320", "scf", "net160", "scf96_short"],
+    p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil96", "stencil320", "scf", "net160", "scf96_short"],
                    help="run only a bounded piece of the step (for profiler captures) and exit: "
-                        "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil320 = "
-                        "FP32/FP64 Laplacian sweeps on a 320^3 grid; scf = one ground state")
+                        "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil96 / "
+                        "stencil320 = FP32/FP64 Laplacian sweeps on a 96^3 / 320^3 grid; scf = one "
+                        "ground state")
     return p.parse_args()
 
 
@@ -151,25 +152,41 @@ def run_step(B, h, sysd, fn, o, u, phi, u0):
     return res, F
 
 
-def stencil_rates(torch, B, h, shape, reps=30):
+def stencil_rates(torch, B, shape, L, reps=30):
+    """Device time of one of_laplacian_apply sweep (FP32 and FP64) on this grid: `reps` sweeps
+    captured in one CUDA graph on a grid handle of their own, replayed between CUDA events
+    (host launch overhead excluded; consecutive sweeps keep the fields in L2)."""
     out = {}
-    for dt, tdt, name in [(B.OF_F32, torch.float32, "f32"), (B.OF_F64, torch.float64, "f64")]:
-        x = torch.rand(shape, dtype=tdt, device="cuda")
-        y = torch.empty_like(x)
-        for _ in range(5):
-            B.of_laplacian_apply(h, dt, x, y)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.Stream()
+    h = B.of_grid_create(shape, L, 6, s)
+    try:
+        for dt, tdt, name in [(B.OF_F32, torch.float32, "f32"), (B.OF_F64, torch.float64, "f64")]:
+            x = torch.rand(shape, dtype=tdt, device="cuda")
+            y = torch.empty_like(x)
+            torch.cuda.synchronize()
+            for _ in range(5):
+                B.of_laplacian_apply(h, dt, x, y)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+                for _ in range(reps):
+                    B.of_laplacian_apply(h, dt, x, y)
+            graph.replay()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            graph.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            n = x.numel()
+            out[name] = {"gpts": n / (ms * 1e-3) / 1e9, "ms": ms,
+                         "gbs": 2 * n * x.element_size() / (ms * 1e-3) / 1e9}
+            del graph
+    finally:
         torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            B.of_laplacian_apply(h, dt, x, y)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        n = x.numel()
-        out[name] = {"gpts": n / (ms * 1e-3) / 1e9, "ms": ms,
-                     "gbs": 2 * n * x.element_size() / (ms * 1e-3) / 1e9}
+        B.of_grid_destroy(h)
     return out
 
 
@@ -434,7 +451,7 @@ def config5(args):
         kmap = time.time() - t
     per_step = (samples[4] - samples[2]) / 2.0
     est = samples[2] + per_step * (res.nlcg_iterations - 2) + kmap * (res.outer_iterations - 1)
-    stencil = stencil_rates(torch, B, h, cell.shape, reps=10)
+    stencil = stencil_rates(torch, B, cell.shape, cell.L, reps=10)
     line = {"metric": METRIC, "unit": UNIT, "higher_is_better": False, "dtype": "f64+f32",
             "data": "synthetic",
             "config": {"workload": "3999-atom FCC Al-like cell (10x10x10 minus the centre site, "
@@ -557,8 +574,8 @@ def kernel_case(args):
         B.of_precond_destroy(net)
         B.of_grid_destroy(h)
         return 0
-    if args.kernel_case == "stencil320":
-        n = 320
+    if args.kernel_case in ("stencil96", "stencil320"):
+        n = 96 if args.kernel_case == "stencil96" else 320
         h = B.of_grid_create((n, n, n), (0.2375 * n,) * 3, 6, torch.cuda.current_stream())
         for dt, tdt in [(B.OF_F32, torch.float32), (B.OF_F64, torch.float64)]:
             x = torch.rand((n, n, n), dtype=tdt, device="cuda")
@@ -671,7 +688,7 @@ def main():
     h2d = u_host.numel() * 8
     d2h = 2 * out_u.numel() * 8 + F_e2e.size * 8
 
-    stencil = stencil_rates(torch, B, h, cell.shape)
+    stencil = stencil_rates(torch, B, cell.shape, cell.L)
     batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
     learned = None if (args.no_learned or rank != 0) else learned_compare(torch, B, W)
     compare = None

@@ -40,6 +40,14 @@ typedef enum {
     OF_F32 = 1           /* FP32 sweeps; in solvers: FP32 inner Krylov + FP64 refinement */
 } of_dtype;
 
+/* Line search of the NLCG step (App. C).  OF_LINE_BRENT: Brent's method on the energy, as in
+ * the paper (Sec. 3.3).  OF_LINE_SLOPE (default): the root of dE/ds by a safeguarded secant,
+ * E and dE/ds from one pass over the grid; the same minimiser in about a third of the passes. */
+typedef enum {
+    OF_LINE_BRENT = 0,
+    OF_LINE_SLOPE = 1
+} of_line_search;
+
 typedef struct of_grid of_grid;
 typedef struct of_precond of_precond;   /* learned preconditioner (of_precond_create) */
 
@@ -107,10 +115,12 @@ typedef struct {
     of_solve_opts poisson;  /* defaults: tol 1e-10 */
     of_solve_opts kernel;   /* defaults: tol 1e-10 */
     int verbose;            /* 1: one line per outer iteration on stderr */
-    double line_tol;        /* Brent tolerance, relative in the step length; default 1e-3 */
+    double line_tol;        /* line-search tolerance, relative in the step length (for
+                               OF_LINE_SLOPE: |dE/ds| <= line_tol |dE/ds(0)|); default 1e-3 */
     double nlcg_tol_rel;    /* > 0: inexact inner solves, outer step k stops its NLCG at
                                max(nlcg_tol, nlcg_tol_rel * fixed-point error of step k-1);
                                0 (default): every inner solve to nlcg_tol */
+    int line_search;        /* of_line_search; default OF_LINE_SLOPE */
 } of_scf_opts;
 
 typedef struct {

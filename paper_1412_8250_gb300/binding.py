@@ -16,6 +16,7 @@ from . import build_lib
 
 OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ENOCONV, OF_EBREAKDOWN, OF_ETIMEOUT = range(7)
 OF_F64, OF_F32 = 0, 1
+OF_LINE_BRENT, OF_LINE_SLOPE = 0, 1
 STATUS_NAMES = {0: "OF_OK", 1: "OF_EINVAL", 2: "OF_ENOMEM", 3: "OF_ECUDA", 4: "OF_ENOCONV",
                 5: "OF_EBREAKDOWN", 6: "OF_ETIMEOUT"}
 
@@ -47,7 +48,8 @@ class of_scf_opts(C.Structure):
                 ("nlcg_restart", C.c_int), ("fp_tol", C.c_double), ("fp_max_iter", C.c_int),
                 ("anderson_m", C.c_int), ("anderson_zeta", C.c_double),
                 ("precision", C.c_int), ("poisson", of_solve_opts), ("kernel", of_solve_opts),
-                ("verbose", C.c_int), ("line_tol", C.c_double), ("nlcg_tol_rel", C.c_double)]
+                ("verbose", C.c_int), ("line_tol", C.c_double), ("nlcg_tol_rel", C.c_double),
+                ("line_search", C.c_int)]
 
 
 class of_scf_result(C.Structure):

@@ -37,6 +37,15 @@ __device__ __forceinline__ double sqrt_newton(double x) {
     return x * y;
 }
 
+// 1/x by Newton's method y <- y (2 - x y), written as e = 1 - x y, y <- y + y e, from a
+// single-precision seed (two FP64 steps: 1e-7 -> 1e-14 -> rounding); x a normal float.
+__device__ __forceinline__ double rcp_newton(double x) {
+    double y = (double)__frcp_rn((float)x);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) y = fma(y, fma(-x, y, 1.0), y);
+    return y;
+}
+
 // e = eps_xc(rho) * rho and v = V_xc(rho) for the exchange (Slater) and PZ correlation.
 __device__ __forceinline__ void lda_xc(double rho, double& e, double& v) {
     const double r = fmax(rho, OF_RHO_FLOOR);
@@ -87,6 +96,31 @@ __device__ __forceinline__ double tf_xc_energy(double rho) {
         ec = PZ_A1 * lr + PZ_BB1 + PZ_C1 * rs * lr + PZ_D1 * rs;
     }
     return etf + (-0.75 * OF_CX * c + ec) * r;
+}
+
+// Energy density and its derivative along the line (slope line search): e = C_F rho^{5/3} +
+// eps_xc(rho) rho as in tf_xc_energy, v = dE/drho = V_TF + V_xc, one reciprocal cube root and
+// one Newton reciprocal of the Perdew-Zunger denominator shared by both.
+__device__ __forceinline__ void tf_xc_energy_slope(double rho, double& e, double& v) {
+    const double r = fmax(rho, OF_RHO_FLOOR);
+    const double t = inv_cbrt(r);
+    const double c = r * t * t;                     // rho^{1/3}
+    const double tf = rho > 0.0 ? OF_CF * c * c : 0.0;   // C_F rho^{2/3}
+    const double rs = OF_RS0 * t;
+    double ec, vc;
+    if (rs >= 1.0) {
+        const double sq = sqrt_newton(rs);
+        const double inv = rcp_newton(1.0 + PZ_B1 * sq + PZ_B2 * rs);
+        ec = PZ_G1 * inv;
+        vc = (PZ_G1 + (7.0 / 6.0) * PZ_G1 * PZ_B1 * sq + (4.0 / 3.0) * PZ_G1 * PZ_B2 * rs) * inv * inv;
+    } else {
+        const double lr = log(rs);
+        ec = PZ_A1 * lr + PZ_BB1 + PZ_C1 * rs * lr + PZ_D1 * rs;
+        vc = (PZ_A1 + (2.0 / 3.0) * PZ_C1 * rs) * lr + (PZ_BB1 - PZ_A1 / 3.0) +
+             (1.0 / 3.0) * (2.0 * PZ_D1 - PZ_C1) * rs;
+    }
+    e = tf * rho + (-0.75 * OF_CX * c + ec) * r;
+    v = (5.0 / 3.0) * tf - OF_CX * c + vc;
 }
 
 }  // namespace of

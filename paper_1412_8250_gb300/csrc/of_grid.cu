@@ -83,6 +83,8 @@ struct OpLap {
     template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
     __device__ float2 load2(long long i) const { return __ldg(reinterpret_cast<const float2*>(x + i)); }
     __device__ void store(long long i, T, T lap) { y[i] = lap; }
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ void store2(long long i, float2, float2 lap) { *reinterpret_cast<float2*>(y + i) = lap; }
     __device__ void end() {}
 };
 

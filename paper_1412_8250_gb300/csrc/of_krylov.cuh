@@ -181,6 +181,18 @@ struct OpKrylovA {
         accp[0] += s.x;
         accp[1] += s.y;
     }
+    // points i, i + 1 of a real field (i even): the same as two store calls
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ void store2(long long i, float2 c, float2 lap) {
+        *reinterpret_cast<float2*>(pout + i) = c;
+        const float a0 = apply_A(c.x, lap.x, a, Q), a1 = apply_A(c.y, lap.y, a, Q);
+        *reinterpret_cast<float2*>(Ap + i) = make_float2(a0, a1);
+        const auto s0 = bilf(c.x, a0), s1 = bilf(c.y, a1);
+        accp[0] += s0.x;
+        accp[1] += s0.y;
+        accp[0] += s1.x;
+        accp[1] += s1.y;
+    }
     __device__ void end() {
         double acc[2] = {(double)accp[0], (double)accp[1]};
         if (grid_reduce<2>(acc, rc.partials, rc.counter, st->red) &&

@@ -205,6 +205,27 @@ struct OpCheby {
         if (dout) dout[i] = vfma(a, c, vmul(bD, rn));
         if (rk) accumulate(rk[i], xn);
     }
+    // points i, i + 1 of a real field (i even): the same as two store calls
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ void store2(long long i, float2 c, float2 lap) {
+        float2 xn = c;
+        if (!x_init) {
+            const float2 xo = *reinterpret_cast<const float2*>(x + i);
+            xn = make_float2(xo.x + c.x, xo.y + c.y);
+        }
+        *reinterpret_cast<float2*>(x + i) = xn;
+        const float2 ri = *reinterpret_cast<const float2*>(rin + i);
+        const float2 rn = make_float2(fmaf(-sigma, c.x, ri.x + lap.x), fmaf(-sigma, c.y, ri.y + lap.y));
+        *reinterpret_cast<float2*>(rout + i) = rn;
+        if (dout)
+            *reinterpret_cast<float2*>(dout + i) =
+                make_float2(fmaf(a, c.x, bD * rn.x), fmaf(a, c.y, bD * rn.y));
+        if (rk) {
+            const float2 rr = *reinterpret_cast<const float2*>(rk + i);
+            accumulate(rr.x, xn.x);
+            accumulate(rr.y, xn.y);
+        }
+    }
     __device__ void accumulate(float r, float z) {
         acc[0] = fmaf(r, z, acc[0]);
         acc[1] += z;
@@ -250,6 +271,12 @@ struct OpResid32 {
     template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
     __device__ float2 load2(long long i) const { return *reinterpret_cast<const float2*>(x + i); }
     __device__ void store(long long i, T c, T lap) { r[i] = vfma(-sigma, c, vadd(b[i], lap)); }
+    template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
+    __device__ void store2(long long i, float2 c, float2 lap) {
+        const float2 bv = *reinterpret_cast<const float2*>(b + i);
+        *reinterpret_cast<float2*>(r + i) =
+            make_float2(fmaf(-sigma, c.x, bv.x + lap.x), fmaf(-sigma, c.y, bv.y + lap.y));
+    }
     __device__ void end() {}
 };
 

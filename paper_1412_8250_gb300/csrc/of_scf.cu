@@ -32,6 +32,7 @@ enum {
     SC_DLD = 8, SC_ULD = 9,
     SC_MD = 10,        // 13 line-search moments
     SC_LINE = 25,
+    SC_SLOPE = 96,     // 3 sums of the slope line search
     SC_EN = 26,        // 4 energy sums
     SC_TLR = 30,
     SC_FP = 32,        // |f|^2, |Vhat|^2
@@ -200,6 +201,25 @@ __global__ void __launch_bounds__(256) k_line_energy(long long n, const double* 
         acc[0] += tf_xc_energy(c2 * w * w);
     }
     grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// With w = u + s d and rho = c2 w^2: sums of e(rho), v(rho) w^2 and v(rho) w d, e the TF + xc
+// energy density and v = de/drho.  The line derivative of the TF + xc energy follows from them.
+__global__ void __launch_bounds__(256) k_line_energy_slope(long long n, const double* u,
+                                                           const double* d, double s, double c2,
+                                                           RedCtx rc) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double di = d[i];
+        const double w = fma(s, di, u[i]);
+        double e, v;
+        tf_xc_energy_slope(c2 * w * w, e, v);
+        const double vw = v * w;
+        acc[0] += e;
+        acc[1] += vw * w;
+        acc[2] += vw * di;
+    }
+    grid_reduce<3>(acc, rc.partials, rc.counter, rc.out);
 }
 
 // u <- c (u + s d) ; phi <- c^2 (phi - D + 2 s B + s^2 C) + D
@@ -423,6 +443,61 @@ static double line_minimum(F&& f, double s_try, double tol, int& evals) {
     return brent_minimise(f, a, b, c, fb, tol, 100, evals);
 }
 
+// Minimises E along s >= 0 from E' alone (E and E' come from one pass; only the slope is used,
+// since near convergence E changes along the line by less than its rounding).  g0 = E'(0) < 0.
+// The trial step s_try is extended while E' stays negative (secant extrapolation of E',
+// between 1.5x and 8x per extension); inside the bracket the root of E' is found by the secant
+// method with the Illinois modification.  Stops when |E'| <= tol |g0| (for E' linear in s, a
+// relative error tol in the step) or the bracket is narrower than tol times its right end.
+// Returns 0 when no step with E' < 0 beyond s = 0 is found.
+template <class F>
+static double line_minimum_slope(F&& f, double g0, double s_try, double tol, int& evals) {
+    if (!(g0 < 0.0)) return 0.0;
+    const double gtol = -tol * g0;
+    double a = 0.0, ga = g0;
+    double b = std::fabs(s_try) > 0.0 ? std::fabs(s_try) : 1e-2, gb;
+    double e;
+    f(b, e, gb);
+    ++evals;
+    for (int k = 0; gb < 0.0; ++k) {   // still descending at b: extend
+        if (-gb <= gtol) return b;
+        if (k == 60) return b;
+        double next = 8.0 * b;
+        if (gb > ga) next = std::min(8.0 * b, std::max(1.5 * b, b - gb * (b - a) / (gb - ga)));
+        a = b;
+        ga = gb;
+        b = next;
+        f(b, e, gb);
+        ++evals;
+    }
+    if (gb <= gtol) return b;
+    // bracket: E'(a) < 0 <= E'(b)
+    double Ga = ga, Gb = gb;   // end values of the secant, halved by the Illinois rule
+    int kept = 0;              // +1: a was kept by the last step, -1: b was
+    for (int it = 0; it < 40; ++it) {
+        double m = a - Ga * (b - a) / (Gb - Ga);
+        if (!(m > a && m < b)) m = 0.5 * (a + b);
+        double gm;
+        f(m, e, gm);
+        ++evals;
+        if (std::fabs(gm) <= gtol) return m;
+        if (gm < 0.0) {
+            a = m;
+            Ga = gm;
+            if (kept == -1) Gb *= 0.5;
+            kept = -1;
+        } else {
+            b = m;
+            Gb = gm;
+            if (kept == 1) Ga *= 0.5;
+            kept = 1;
+        }
+        if (b - a <= tol * b) return 0.5 * (a + b);
+        if (a == 0.0 && b <= 1e-9 * std::fabs(s_try)) return 0.0;   // E' > 0 right of 0
+    }
+    return a;
+}
+
 // Device vectors used by the ground-state driver.
 struct ScfVecs {
     double *Hu, *Lu, *r, *rp, *d, *dp, *B, *C, *Ld, *b, *D, *rho, *V, *Vhat;
@@ -454,7 +529,7 @@ static void poisson_into(of_grid* g, const double* a, const double* b, double* p
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
 static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
                  const double* V, double tol, int max_iter, int n_restart, double line_tol,
-                 const KrylovOpts& po, ScfStats& st) {
+                 int line_search, const KrylovOpts& po, ScfStats& st) {
     const long long n = g->d.n;
     const double dV = g->dV;
     const int nb = vb(n);
@@ -541,15 +616,45 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
             const double hart = 0.5 * c2 * c2 * quart + c2 * (N0 + 2.0 * s * N1 + s * s * N2) + 0.5 * bD;
             return tfxc + vw + vl + hart;
         };
+        // E and dE/ds together (slope line search): the TF + xc sums of k_line_energy_slope
+        // and the derivatives of the closed-form vW, kernel and Hartree terms
+        auto energy_slope = [&](double s, double& E, double& G) {
+            const double q = uu + 2.0 * s * ud + s * s * dd;
+            const double c2 = Ne / q;
+            const double c2p = -c2 * (2.0 * ud + 2.0 * s * dd) / q;
+            ProfScope ps(g, PC_LINE, 2.0 * sizeof(double) * (double)n);
+            launch(k_line_energy_slope, nb, 256, g->stream, n, u, v.d, s, c2, red_ctx(g, SC_SLOPE));
+            OF_LAUNCH_CHECK();
+            double t[3];
+            fetch_scalars(g, SC_SLOPE, 3, t);
+            const double tfxc = t[0] * dV, tfxc_p = (c2p * t[1] + 2.0 * c2 * t[2]) * dV;
+            const double P = uLu_ + 2.0 * s * uLd + s * s * dLd, Pp = 2.0 * uLd + 2.0 * s * dLd;
+            const double R = Vq0 + 2.0 * s * Vq1 + s * s * Vq2, Rp = 2.0 * Vq1 + 2.0 * s * Vq2;
+            const double quart = M00 + 4.0 * s * M01 + 2.0 * s * s * M02 + 4.0 * s * s * M11 +
+                                 4.0 * s * s * s * M12 + s * s * s * s * M22;
+            const double quart_p = 4.0 * M01 + 4.0 * s * M02 + 8.0 * s * M11 +
+                                   12.0 * s * s * M12 + 4.0 * s * s * s * M22;
+            const double Nq = N0 + 2.0 * s * N1 + s * s * N2, Nq_p = 2.0 * N1 + 2.0 * s * N2;
+            E = tfxc - 0.5 * fn.lam * c2 * P + fn.mu * c2 * R + 0.5 * c2 * c2 * quart + c2 * Nq + 0.5 * bD;
+            G = tfxc_p - 0.5 * fn.lam * (c2p * P + c2 * Pp) + fn.mu * (c2p * R + c2 * Rp) +
+                c2 * c2p * quart + 0.5 * c2 * c2 * quart_p + c2p * Nq + c2 * Nq_p;
+        };
+        const double g0 = -m[0] * dV;   // dE/ds at s = 0 on the normalised path: -<r, d>
+        auto search = [&]() {
+            int evals = 0;
+            const double s = line_search == OF_LINE_BRENT
+                                 ? line_minimum(energy, s_prev, line_tol, evals)
+                                 : line_minimum_slope(energy_slope, g0, s_prev, line_tol, evals);
+            st.line += evals;
+            return s;
+        };
         const double tol_line = std::min(1e-8, 1e-2 * st.last_residual);
         prepare_line(tol_line);
-        int evals = 0;
-        double s = line_minimum(energy, s_prev, line_tol, evals);
+        double s = search();
         if (s == 0.0 && tol_line > po.tol) {   // retry with exact line energies
             prepare_line(po.tol);
-            s = line_minimum(energy, s_prev, line_tol, evals);
+            s = search();
         }
-        st.line += evals;
         if (s == 0.0) break;   // energy flat to rounding along d: stagnated
         const double c = std::sqrt(Ne / (uu + 2.0 * s * ud + s * s * dd));
         launch(k_step, nb, 256, g->stream, n, u, v.d, phi, v.D, v.B, v.C, s, c);
@@ -727,7 +832,8 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
                                  ? std::max(o->nlcg_tol, o->nlcg_tol_rel * prev_err)
                                  : o->nlcg_tol;
         inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, tol_k, o->nlcg_max_iter,
-                        std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3, po, st);
+                        std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3,
+                        o->line_search, po, st);
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
         // inexact kernel map while the fixed point is far off: the shifted solves stop at
@@ -818,6 +924,7 @@ void of_default_scf_opts(of_scf_opts* o) {
     of_default_solve_opts(&o->kernel);
     o->verbose = 0;
     o->line_tol = 1e-3;
+    o->line_search = OF_LINE_SLOPE;
 }
 
 of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double* u,

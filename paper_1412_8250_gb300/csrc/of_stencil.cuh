@@ -383,6 +383,208 @@ __device__ __forceinline__ void stencil2_tile(const Dims& d, const Weights<float
     }
 }
 
+// ---------------------------------------------------------------- FP32 brick kernel
+// For FP32 fields (real, or complex as float2) on grids too small for long z runs (below 2^21
+// points): a block of 16 x 8 threads owns a brick of 16 units x 8 rows x BZ planes, a unit
+// being two x-neighbouring real points or one complex point, one float2 either way.  The brick
+// and its periodic halo (N planes below and above, N rows, at least N points each side in x)
+// are staged once into shared memory in 16-byte chunks, which stay contiguous across the
+// periodic wrap (real n1 a multiple of 4, complex n1 even); each thread then holds the column
+// of its unit through all BZ + 2N planes in registers for the z taps and reads its y and x
+// taps from shared memory.  Every block is independent: no z-queue prologue and one barrier
+// between staging and arithmetic, so that a 96^3 grid gives 432 (real) or 864 (complex)
+// blocks with all staging loads in flight at once.
+constexpr int B3_UX = 16;    // units (float2) per row of a brick = threads in x
+constexpr int B3_BY = 8;     // rows per brick = threads in y
+constexpr int B3_THREADS = B3_UX * B3_BY;
+
+template <class Op, class = void>
+struct HasStore2 { static constexpr bool value = false; };
+template <class Op>
+struct HasStore2<Op, decltype((void)std::declval<Op&>().store2(0LL, float2{}, float2{}), void())> {
+    static constexpr bool value = true;
+};
+// two x-neighbouring real points i, i + 1 (i even)
+template <class Op>
+__device__ __forceinline__ void op_store2(Op& op, long long i, float2 c, float2 lap) {
+    if constexpr (HasStore2<Op>::value) {
+        op.store2(i, c, lap);
+    } else {
+        op.store(i, c.x, lap.x);
+        op.store(i + 1, c.y, lap.y);
+    }
+}
+
+// 16 bytes of the differentiated field from float offset f (a multiple of 4) of the grid
+template <typename T, class Op>
+__device__ __forceinline__ float4 brick_load4(const Op& op, long long f) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float2 a = op_load2(op, f), b = op_load2(op, f + 2);
+        return make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        const float2 a = op.load(f >> 1), b = op.load((f >> 1) + 1);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+template <typename T, int N, int BZ, class Op>
+__device__ __forceinline__ void brick_tile(const Dims& d, const Weights<float>& W, Op& op) {
+    constexpr bool CPLX = std::is_same<T, float2>::value;
+    constexpr int HXF = CPLX ? ((2 * N + 3) & ~3) : ((N + 3) & ~3);   // halo floats per side
+    constexpr int HXC = HXF / 4;              // halo chunks per side
+    constexpr int RW = 32 + 2 * HXF;          // floats per staged row of a central plane
+    constexpr int ROWS = B3_BY + 2 * N;       // staged rows of a central plane
+    constexpr int CPL = ROWS * RW;            // floats per central plane
+    constexpr int ZP = BZ + 2 * N;            // planes of a unit's column
+    constexpr int ZPL = B3_BY * 32;           // floats per z-halo plane (core rows only)
+    constexpr int SLOTS = ROWS * 8 + B3_BY * 2 * HXC;   // chunks per central plane
+    constexpr int SPT = (SLOTS + B3_THREADS - 1) / B3_THREADS;
+    static_assert(B3_THREADS % 64 == 0, "z-halo staging assumes 64 chunks per plane");
+    extern __shared__ float4 brick_smem[];    // central planes, then the z-halo planes
+    float* cen = reinterpret_cast<float*>(brick_smem);
+    float* zh = cen + BZ * CPL;
+    __shared__ long long zoff[ZP];            // float offset of staged plane z0 - N + t
+    __shared__ long long yoff[ROWS];          // float offset of staged row y0 - N + t in a plane
+    __shared__ int xoff[RW / 4];              // float offset of staged chunk t in a row
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + B3_UX * ty;
+    const int n1 = d.n1, n2 = d.n2, n3 = d.n3;
+    const int RF = CPLX ? 2 * n1 : n1;        // floats per grid row
+    const long long PF = (long long)RF * n2;  // floats per grid plane
+    const int x0f = blockIdx.x * 32, y0 = blockIdx.y * B3_BY, z0 = blockIdx.z * BZ;
+    for (int t = tid; t < ZP; t += B3_THREADS) zoff[t] = (long long)wrap_index(z0 - N + t, n3) * PF;
+    for (int t = tid; t < ROWS; t += B3_THREADS) yoff[t] = (long long)wrap_index(y0 - N + t, n2) * RF;
+    for (int t = tid; t < RW / 4; t += B3_THREADS) xoff[t] = wrap_index(x0f - HXF + 4 * t, RF);
+    __syncthreads();
+
+    // central planes: each thread's chunk slots (row, chunk) are the same in every plane
+#pragma unroll
+    for (int m = 0; m < SPT; ++m) {
+        const int sl = tid + m * B3_THREADS;
+        if (sl < SLOTS) {
+            int row, cc;
+            if (sl < ROWS * 8) {
+                row = sl >> 3;
+                cc = HXC + (sl & 7);
+            } else {
+                const int s2 = sl - ROWS * 8;
+                const int h = s2 % (2 * HXC);
+                row = N + s2 / (2 * HXC);
+                cc = h < HXC ? h : h + 8;
+            }
+            const long long go = yoff[row] + xoff[cc];
+            float* so = cen + row * RW + 4 * cc;
+            float4 v[BZ];
+#pragma unroll
+            for (int k = 0; k < BZ; ++k) v[k] = brick_load4<T>(op, zoff[N + k] + go);
+#pragma unroll
+            for (int k = 0; k < BZ; ++k) *reinterpret_cast<float4*>(so + k * CPL) = v[k];
+        }
+    }
+    {   // z-halo planes j < N (z0 - N + j) and j >= N (z0 + BZ + j - N): core rows only
+        const int sl = tid & 63, j0 = tid >> 6;
+        const int row = sl >> 3, cc = HXC + (sl & 7);
+        const long long go = yoff[N + row] + xoff[cc];
+        float* so = zh + row * 32 + 4 * (sl & 7);
+        constexpr int JP = B3_THREADS / 64;
+        constexpr int NJ = (2 * N + JP - 1) / JP;
+        float4 v[NJ];
+#pragma unroll
+        for (int m = 0; m < NJ; ++m) {
+            const int j = j0 + m * JP;
+            if (j < 2 * N) v[m] = brick_load4<T>(op, zoff[j < N ? j : j + BZ] + go);
+        }
+#pragma unroll
+        for (int m = 0; m < NJ; ++m) {
+            const int j = j0 + m * JP;
+            if (j < 2 * N) *reinterpret_cast<float4*>(so + j * ZPL) = v[m];
+        }
+    }
+    __syncthreads();
+
+    // this thread's unit: floats 2 tx, 2 tx + 1 of row ty; its column through the ZP planes
+    const int uo = 2 * tx;
+    unsigned long long col[ZP];
+#pragma unroll
+    for (int j = 0; j < ZP; ++j) {
+        const float* src = j < N ? zh + j * ZPL + ty * 32 + uo
+                         : j < N + BZ ? cen + (j - N) * CPL + (ty + N) * RW + HXF + uo
+                                      : zh + (j - BZ) * ZPL + ty * 32 + uo;
+        col[j] = pk2(*reinterpret_cast<const float2*>(src));
+    }
+    unsigned long long wz2[N + 1], wy2[N + 1], wx2[N + 1];
+#pragma unroll
+    for (int p = 0; p <= N; ++p) {
+        wz2[p] = pk2(make_float2(W.w[2][p], W.w[2][p]));
+        wy2[p] = pk2(make_float2(W.w[1][p], W.w[1][p]));
+        wx2[p] = pk2(make_float2(W.w[0][p], W.w[0][p]));
+    }
+    const unsigned long long centre2 = pk2(make_float2(W.centre, W.centre));
+    const int y = y0 + ty;
+    const int xu = (x0f >> 1) + tx;           // complex: point index; real: x / 2
+    const bool act = y < n2 && (CPLX ? xu < n1 : 2 * xu < n1);
+    const long long rowi = (long long)y * n1 + (CPLX ? xu : 2 * xu);   // grid index in units of T
+#pragma unroll
+    for (int k = 0; k < BZ; ++k) {
+        const int z = z0 + k;
+        if (z >= n3) break;
+        unsigned long long acc = fma2(centre2, col[N + k], 0ull);
+#pragma unroll
+        for (int p = 1; p <= N; ++p) acc = fma2(wz2[p], add2(col[N + k + p], col[N + k - p]), acc);
+        const float* b = cen + k * CPL + (ty + N) * RW + HXF + uo;
+#pragma unroll
+        for (int p = 1; p <= N; ++p)
+            acc = fma2(wy2[p], add2(pk2(*reinterpret_cast<const float2*>(b + p * RW)),
+                                    pk2(*reinterpret_cast<const float2*>(b - p * RW))), acc);
+        if constexpr (CPLX) {
+#pragma unroll
+            for (int p = 1; p <= N; ++p)
+                acc = fma2(wx2[p], add2(pk2(*reinterpret_cast<const float2*>(b + 2 * p)),
+                                        pk2(*reinterpret_cast<const float2*>(b - 2 * p))), acc);
+        } else {
+            constexpr int HX = (N + 1) & ~1;  // row floats uo - HX .. uo + 1 + HX, in pairs
+            float v[2 * HX + 2];
+#pragma unroll
+            for (int m = 0; m <= HX; ++m) {
+                const float2 t2 = *reinterpret_cast<const float2*>(b - HX + 2 * m);
+                v[2 * m] = t2.x;
+                v[2 * m + 1] = t2.y;
+            }
+            float2 a = upk2(acc);
+#pragma unroll
+            for (int p = 1; p <= N; ++p) {
+                a.x = fmaf(W.w[0][p], v[HX + p] + v[HX - p], a.x);
+                a.y = fmaf(W.w[0][p], v[HX + 1 + p] + v[HX + 1 - p], a.y);
+            }
+            acc = pk2(a);
+        }
+        if (act) {
+            const long long i = (long long)z * n2 * n1 + rowi;
+            if constexpr (CPLX) op.store(i, upk2(col[N + k]), upk2(acc));
+            else op_store2(op, i, upk2(col[N + k]), upk2(acc));
+        }
+    }
+}
+
+// dynamic shared memory of brick_tile: BZ central planes and 2N z-halo planes
+template <typename T, int N, int BZ>
+constexpr size_t brick_smem_bytes() {
+    constexpr bool CPLX = std::is_same<T, float2>::value;
+    constexpr int HXF = CPLX ? ((2 * N + 3) & ~3) : ((N + 3) & ~3);
+    return sizeof(float) * ((size_t)BZ * (B3_BY + 2 * N) * (32 + 2 * HXF) + (size_t)2 * N * B3_BY * 32);
+}
+
+template <typename T, int N, int BZ, class Op>
+__global__ void __launch_bounds__(B3_THREADS, 4) brick_kernel(Dims d, Weights<float> W, Op op) {
+    if (!op.begin()) return;
+    brick_tile<T, N, BZ, Op>(d, W, op);
+    op.end();
+}
+
+// planes per brick: 8 for the order-12 operator, 2 for the 7-point one (coarse levels, where
+// a deeper brick leaves too few blocks)
+template <int N> struct BrickDepth { static constexpr int value = N >= 3 ? 8 : 2; };
+
 template <int N, int RY, class Op>
 __global__ void __launch_bounds__(S2_BX * (S2_TY / RY), 2)
 stencil2_kernel(Dims d, Weights<float> W, int cz, Op op) {
@@ -434,6 +636,21 @@ struct OpInfo<Op, decltype((void)Op::kClass, void())> {
     static constexpr int words = Op::kWords;
 };
 
+template <typename T, int N, class Op>
+void launch_brick(of_grid* g, dim3 grid, dim3 block, const Dims& d, const Weights<float>& W, Op op) {
+    constexpr int BZ = BrickDepth<N>::value;
+    constexpr size_t smem = brick_smem_bytes<T, N, BZ>();
+    if constexpr (smem > 48 * 1024) {   // above the default limit: raise it once per thread
+        static thread_local int configured_device = -1;
+        if (configured_device != g->device) {
+            OF_CUDA(cudaFuncSetAttribute(brick_kernel<T, N, BZ, Op>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            configured_device = g->device;
+        }
+    }
+    launch_smem(brick_kernel<T, N, BZ, Op>, grid, block, smem, g->stream, d, W, op);
+}
+
 template <typename T, int RY, class Op>
 void launch_stencil_dims(of_grid* g, const Dims& d, int N,
                          const Weights<typename Real<T>::type>& W, Op op) {
@@ -443,6 +660,22 @@ void launch_stencil_dims(of_grid* g, const Dims& d, int N,
                                          : (sizeof(typename Real<T>::type) == 8 ? PC_STENCIL_F64 : PC_STENCIL_F32);
     ProfScope ps(g, cls, (double)OpInfo<Op>::words * sizeof(T) * (double)d.n);
     cudaStream_t stream = g->stream;
+    if constexpr (std::is_same<T, float>::value || std::is_same<T, float2>::value) {
+        // FP32 brick kernel on small grids (order 12 and the 7-point coarse operator)
+        constexpr bool CPLX = std::is_same<T, float2>::value;
+        const long long RF = CPLX ? 2LL * d.n1 : d.n1;
+        if (d.n < (1LL << 21) && (N == 6 || N == 1) && RF % 4 == 0) {
+            const int bz = N == 6 ? BrickDepth<6>::value : BrickDepth<1>::value;
+            const dim3 g3((unsigned)((RF + 31) / 32), (unsigned)((d.n2 + B3_BY - 1) / B3_BY),
+                          (unsigned)((d.n3 + bz - 1) / bz));
+            if ((long long)g3.x * g3.y * g3.z <= OF_MAX_RED_BLOCKS) {
+                const dim3 b3(B3_UX, B3_BY, 1);
+                if (N == 6) launch_brick<T, 6, Op>(g, g3, b3, d, W, op);
+                else launch_brick<T, 1, Op>(g, g3, b3, d, W, op);
+                return;
+            }
+        }
+    }
     if constexpr (std::is_same<T, float>::value) {
         // FP32 fast path on large grids: below ~128^3 points its 32 x 32 tiles leave too few
         // blocks to fill the GPU, and for the 7-point operator of the coarse multigrid levels

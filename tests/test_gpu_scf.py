@@ -91,6 +91,27 @@ def test_wt_small_cell_against_golden(prec, inexact):
     assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
 
 
+def test_line_searches_reach_the_same_ground_state():
+    # Brent on the energy (the paper's line search) and the slope search (root of dE/ds from
+    # the same line model) stop the NLCG at the same minimiser; the slope search needs fewer
+    # passes per NLCG step.  A wrong term in dE/ds would move its root off the energy minimum
+    # and fail the golden bars or stall the NLCG.
+    rec = _golden()["al4_wt"]
+    cell = _cell_from(rec)
+    out = {}
+    for line in (B.OF_LINE_BRENT, B.OF_LINE_SLOPE):
+        res, F, u, phi = _run(cell, Fn.wt(), B.OF_F32, line_search=line, anderson_m=3,
+                              anderson_zeta=1.0)
+        assert res.converged, (line, res.fp_error, res.nlcg_residual)
+        assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
+        assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
+        out[line] = res
+    rb, rs = out[B.OF_LINE_BRENT], out[B.OF_LINE_SLOPE]
+    assert abs(rb.energy - rs.energy) / cell.n_atoms <= 1e-8
+    per_step = {k: r.line_evaluations / max(1, r.nlcg_iterations) for k, r in out.items()}
+    assert per_step[B.OF_LINE_SLOPE] < 0.6 * per_step[B.OF_LINE_BRENT], per_step
+
+
 def test_wt_108_atoms_full_size_properties():
     cell = W.al108_cell()
     res, F, u, phi = _run(cell, Fn.wt(), B.OF_F32, fp_tol=1e-6)
