@@ -47,6 +47,35 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
     OF_CUDA(cudaGetLastError());
 }
 
+// Programmatic dependent launch, for the kernels of the solver loops: the next kernel of the
+// stream may be scheduled while this one runs, and every kernel launched this way starts with
+// pdl_enter(), which waits until the previous kernel of the stream has completed and its
+// writes are visible, then lets the next kernel start launching.  Nothing a kernel reads from
+// global memory is touched before pdl_enter().  The launch and block scheduling of each
+// kernel overlap the previous one's tail instead of following it.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    OF_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+    __atomic_add_fetch(&g_launch_count, 1ull, __ATOMIC_RELAXED);
+}
+
+// First statement of every kernel launched with launch_pdl (a no-op under a plain launch).
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Same, with `smem` bytes of dynamic shared memory (the caller raises the kernel's limit).
 template <typename... KArgs, typename... Args>
 inline void launch_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

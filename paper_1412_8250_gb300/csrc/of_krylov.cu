@@ -34,6 +34,7 @@ namespace of {
 __global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __restrict__ r,
                                                   const float* __restrict__ z, bool first,
                                                   KState* st, RedCtx rc) {
+    pdl_enter();
     if (st->done != 0.0) return;
     float prz = 0.f, pz = 0.f, pr = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(256) k_pcg_beta(long long n, const float* __re
 __global__ void __launch_bounds__(256) k_pcocg_beta(long long n, const float2* __restrict__ r,
                                                     const float2* __restrict__ z, bool first,
                                                     KState* st, RedCtx rc) {
+    pdl_enter();
     if (st->done != 0.0) return;
     float pre = 0.f, pim = 0.f;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -228,7 +230,7 @@ static void pcg_init_body(of_grid* g, float* r, float* z, KState* st) {
     const long long n = g->d.n;
     if (mg_vcycle_beta(g, r, z, st, true)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
-    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, true, st, red_ctx(g, 0));
+    launch_pdl(k_pcg_beta, vec_blocks(n), 256, 0, g->stream, n, r, z, true, st, red_ctx(g, 0));
 }
 
 static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pout, float* Ap,
@@ -238,20 +240,19 @@ static void pcg_step_body(of_grid* g, float* x, float* r, float* pin, float* pou
     launch_stencil<float, 2>(g, g->w32, op);
     {
         ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float) * (double)n);
-        launch(krylov_update<float, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
-               red_ctx(g, 0));
+        launch_krylov_update<float, true>(g, n, x, r, pout, Ap, st, red_ctx(g, 0), vec_blocks(n));
     }
     if (mg_vcycle_beta(g, r, z, st, false)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float) * (double)n);
-    launch(k_pcg_beta, vec_blocks(n), 256, g->stream, n, r, z, false, st, red_ctx(g, 0));
+    launch_pdl(k_pcg_beta, vec_blocks(n), 256, 0, g->stream, n, r, z, false, st, red_ctx(g, 0));
 }
 
 static void pcocg_init_body(of_grid* g, float2* r, float2* z, KState* st, double sigma) {
     const long long n = g->d.n;
     if (mg_vcycle_shifted_beta(g, r, z, st, true, sigma)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
-    launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, true, st,
-           red_ctx(g, 0));
+    launch_pdl(k_pcocg_beta, vec_blocks(n), 256, 0, g->stream, n, (const float2*)r, (const float2*)z,
+               true, st, red_ctx(g, 0));
 }
 
 static void pcocg_step_body(of_grid* g, float2* x, float2* r, float2* pin, float2* pout, float2* Ap,
@@ -261,13 +262,12 @@ static void pcocg_step_body(of_grid* g, float2* x, float2* r, float2* pin, float
     launch_stencil<float2, 1>(g, g->w32, op);
     {
         ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(float2) * (double)n);
-        launch(krylov_update<float2, true>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st,
-               red_ctx(g, 0));
+        launch_krylov_update<float2, true>(g, n, x, r, pout, Ap, st, red_ctx(g, 0), vec_blocks(n));
     }
     if (mg_vcycle_shifted_beta(g, r, z, st, false, sigma)) return;
     ProfScope ps(g, PC_UPDATE, 2.0 * sizeof(float2) * (double)n);
-    launch(k_pcocg_beta, vec_blocks(n), 256, g->stream, n, (const float2*)r, (const float2*)z, false, st,
-           red_ctx(g, 0));
+    launch_pdl(k_pcocg_beta, vec_blocks(n), 256, 0, g->stream, n, (const float2*)r, (const float2*)z,
+               false, st, red_ctx(g, 0));
 }
 
 // One plain CG / COCG iteration: p_out = r + beta p_in with A p_out and p^T A p in one sweep,
@@ -280,7 +280,7 @@ static void krylov_step(of_grid* g, KState* st, T* x, T* r, T* pin, T* pout, T* 
     OpKrylovA<T> op{r, pin, pout, Ap, st, red_ctx(g, 0), a, Q};
     launch_stencil<T, RY>(g, W, op);
     ProfScope ps(g, PC_UPDATE, 6.0 * sizeof(T) * (double)n);
-    launch(krylov_update<T>, vec_blocks(n), 256, g->stream, n, x, r, pout, Ap, st, red_ctx(g, 0));
+    launch_krylov_update<T, false>(g, n, x, r, pout, Ap, st, red_ctx(g, 0), vec_blocks(n));
 }
 
 // Runs Krylov iterations on state `st` until its done flag is set.  Returns host copy.  Pairs

@@ -214,12 +214,37 @@ struct OpKrylovA {
     }
 };
 
+// The scalars of a Krylov update from its grid-reduced sums acc = (|r|^2, r^T r): iteration
+// count, convergence, beta (plain CG / COCG; the preconditioned forms take beta from r^T z).
+template <bool PRECOND>
+__device__ __forceinline__ void krylov_update_finish(const double (&acc)[3], KState* st) {
+    const double2 rho_new = make_double2(acc[1], acc[2]);
+    const double2 rho_old = make_double2(st->rho_re, st->rho_im);
+    st->rr = acc[0];
+    st->iters += 1.0;
+    if (acc[0] <= st->tol2 || st->iters >= st->maxit) {
+        st->done = 1.0;
+    } else if (PRECOND) {
+        return;   // beta follows from r^T z once the preconditioner has run
+    } else if (!(fabs(rho_old.x) + fabs(rho_old.y) > 0.0)) {
+        st->breakdown = 1.0;
+        st->done = 1.0;
+    } else {
+        const double2 be = cdiv(rho_new, rho_old);
+        st->beta_re = be.x;
+        st->beta_im = be.y;
+    }
+    st->rho_re = rho_new.x;
+    st->rho_im = rho_new.y;
+}
+
 // x += alpha p ; r -= alpha Ap ; reduces |r|^2 and r^T r ; sets beta, iteration count, done.
 template <typename T, bool PRECOND = false>
 __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict__ x,
                                                      T* __restrict__ r, const T* __restrict__ p,
                                                      const T* __restrict__ Ap, KState* st,
                                                      RedCtx rc) {
+    pdl_enter();
     if (st->done != 0.0) return;
     const double2 al = make_double2(st->alpha_re, st->alpha_im);
     typename AccT<typename KT<T>::R>::type a0 = 0, a1 = 0, a2 = 0;
@@ -236,28 +261,66 @@ __global__ void __launch_bounds__(256) krylov_update(long long n, T* __restrict_
         }
     }
     double acc[3] = {(double)a0, (double)a1, (double)a2};
-    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
-        const double2 rho_new = make_double2(acc[1], acc[2]);
-        const double2 rho_old = make_double2(st->rho_re, st->rho_im);
-        st->rr = acc[0];
-        st->iters += 1.0;
-        if (acc[0] <= st->tol2 || st->iters >= st->maxit) {
-            st->done = 1.0;
-        } else if (PRECOND) {
-            return;   // beta follows from r^T z once the preconditioner has run
-        } else if (!(fabs(rho_old.x) + fabs(rho_old.y) > 0.0)) {
-            st->breakdown = 1.0;
-            st->done = 1.0;
-        } else {
-            const double2 be = cdiv(rho_new, rho_old);
-            st->beta_re = be.x;
-            st->beta_im = be.y;
-        }
-        st->rho_re = rho_new.x;
-        st->rho_im = rho_new.y;
-    }
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0)
+        krylov_update_finish<PRECOND>(acc, st);
 }
 
+// The same for FP32 fields (real, or complex as float2) moved as 16-byte vectors: nv = the
+// number of float4 (n * sizeof(T) / 16), all four arrays 16-byte aligned.
+template <typename T, bool PRECOND = false>
+__global__ void __launch_bounds__(256) krylov_update_v4(long long nv, float4* __restrict__ x,
+                                                        float4* __restrict__ r,
+                                                        const float4* __restrict__ p,
+                                                        const float4* __restrict__ Ap, KState* st,
+                                                        RedCtx rc) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "FP32 fields only");
+    constexpr int K = 16 / sizeof(T);
+    pdl_enter();
+    if (st->done != 0.0) return;
+    const double2 al = make_double2(st->alpha_re, st->alpha_im);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+         v += (long long)gridDim.x * blockDim.x) {
+        float4 xv = x[v], rv4 = r[v];
+        const float4 pv = p[v], av = Ap[v];
+        T* xe = reinterpret_cast<T*>(&xv);
+        T* re = reinterpret_cast<T*>(&rv4);
+        const T* pe = reinterpret_cast<const T*>(&pv);
+        const T* ae = reinterpret_cast<const T*>(&av);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            xe[k] = vadd(xe[k], cs_mul(al, pe[k]));
+            const T rk = vsub(re[k], cs_mul(al, ae[k]));
+            re[k] = rk;
+            a0 += hn2f(rk);
+            if (!PRECOND) {
+                const auto s = bilf(rk, rk);
+                a1 += s.x;
+                a2 += s.y;
+            }
+        }
+        x[v] = xv;
+        r[v] = rv4;
+    }
+    double acc[3] = {(double)a0, (double)a1, (double)a2};
+    if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0)
+        krylov_update_finish<PRECOND>(acc, st);
+}
+
+// Launches the Krylov update, as 16-byte vectors where the FP32 fields allow it.
+template <typename T, bool PRECOND>
+inline void launch_krylov_update(of_grid* g, long long n, T* x, T* r, const T* p, const T* Ap,
+                                 KState* st, RedCtx rc, int blocks) {
+    if constexpr (sizeof(typename KT<T>::R) == 4) {
+        const bool aligned = (((uintptr_t)x | (uintptr_t)r | (uintptr_t)p | (uintptr_t)Ap) & 15) == 0;
+        if (aligned && (n * (long long)sizeof(T)) % 16 == 0) {
+            launch_pdl(krylov_update_v4<T, PRECOND>, blocks, 256, 0, g->stream, n * (long long)sizeof(T) / 16,
+                   (float4*)x, (float4*)r, (const float4*)p, (const float4*)Ap, st, rc);
+            return;
+        }
+    }
+    launch_pdl(krylov_update<T, PRECOND>, blocks, 256, 0, g->stream, n, x, r, p, Ap, st, rc);
+}
 
 inline int vec_blocks(long long n) { return red_blocks(n, 256 * 4); }
 

@@ -289,6 +289,7 @@ template <> __device__ __forceinline__ float2 vzero<float2>() { return make_floa
 template <typename T>
 __global__ void k_restrict(Dims f, Dims c, const T* __restrict__ r, T* __restrict__ b,
                            const double* done) {
+    pdl_enter();
     if (*done != 0.0) return;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= c.n) return;
@@ -333,6 +334,7 @@ __device__ __forceinline__ T interp(const T* e, Dims c, int i, int j, int k) {
 template <typename T>
 __global__ void k_prolong_add(Dims f, Dims c, const T* __restrict__ e, T* __restrict__ x,
                               const double* done) {
+    pdl_enter();
     if (*done != 0.0) return;
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= f.n) return;
@@ -354,7 +356,8 @@ struct SmallLevels {
     float cx[MG_MAX_LEVELS], cy[MG_MAX_LEVELS], cz[MG_MAX_LEVELS], centre[MG_MAX_LEVELS];
     float invD[MG_MAX_LEVELS], theta[MG_MAX_LEVELS];
     float ca[MG_MAX_LEVELS][4], cb[MG_MAX_LEVELS][4];
-    void *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS], *dv[MG_MAX_LEVELS];
+    void *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS];
+    void *dv[MG_MAX_LEVELS], *dw[MG_MAX_LEVELS];   // the Chebyshev direction, double-buffered
 };
 
 // -(A a)(i) = (L_h a)(i) - sigma a(i) for the 7-point operator of level l
@@ -388,43 +391,57 @@ template <bool SOLO> __device__ __forceinline__ void lv_sync() {
 }
 
 // Chebyshev smoothing of level l (zero initial guess, or starting from x): the whole cluster,
-// or the first CTA alone (SOLO)
+// or the first CTA alone (SOLO).  One barrier per step: step k reads the direction d_k at the
+// neighbours and writes x, r and d_{k+1} of its own points, d_{k+1} into the other buffer.
+// With a zero guess, d_0 = D^{-1} b / theta is already in dv (written by the restriction) when
+// d0_ready, else formed here.
 template <typename T, bool SOLO>
-__device__ void blk_smooth(const SmallLevels& P, int l, bool zero) {
+__device__ void blk_smooth(const SmallLevels& P, int l, bool zero, bool d0_ready) {
     const int n = (int)P.d[l].n;
-    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
+    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l];
+    T* dbuf[2] = {(T*)P.dv[l], (T*)P.dw[l]};
     const float s0 = P.invD[l] / P.theta[l];
     const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
     if (zero) {
-        for (int i = t0; i < n; i += ts) dv[i] = vmul(s0, b[i]);
-    } else {
-        for (int i = t0; i < n; i += ts) r[i] = vadd(b[i], neg_op7(P, l, x, i));
-        lv_sync<SOLO>();
-        for (int i = t0; i < n; i += ts) dv[i] = vmul(s0, r[i]);
-    }
-    lv_sync<SOLO>();
-    for (int k = 0; k < P.deg; ++k) {
-        const bool first = zero && k == 0;
-        for (int i = t0; i < n; i += ts) {
-            x[i] = first ? dv[i] : vadd(x[i], dv[i]);
-            r[i] = vadd(first ? b[i] : r[i], neg_op7(P, l, dv, i));
-        }
-        lv_sync<SOLO>();
-        if (k + 1 < P.deg) {
-            for (int i = t0; i < n; i += ts)
-                dv[i] = vfma(P.ca[l][k], dv[i], vmul(P.cb[l][k] * P.invD[l], r[i]));
+        if (!d0_ready) {
+            for (int i = t0; i < n; i += ts) dbuf[0][i] = vmul(s0, b[i]);
             lv_sync<SOLO>();
         }
+    } else {
+        for (int i = t0; i < n; i += ts) {
+            const T rv = vadd(b[i], neg_op7(P, l, x, i));
+            r[i] = rv;
+            dbuf[0][i] = vmul(s0, rv);
+        }
+        lv_sync<SOLO>();
+    }
+    for (int k = 0; k < P.deg; ++k) {
+        const bool first = zero && k == 0;
+        const T* dc = dbuf[k & 1];
+        T* dn = dbuf[(k + 1) & 1];
+        const bool more = k + 1 < P.deg;
+        const float ca = more ? P.ca[l][k] : 0.f, cb = more ? P.cb[l][k] * P.invD[l] : 0.f;
+        for (int i = t0; i < n; i += ts) {
+            const T di = dc[i];
+            x[i] = first ? di : vadd(x[i], di);
+            const T rv = vadd(first ? b[i] : r[i], neg_op7(P, l, dc, i));
+            r[i] = rv;
+            if (more) dn[i] = vfma(ca, di, vmul(cb, rv));
+        }
+        lv_sync<SOLO>();
     }
 }
 
-// coarse b[l + 1] = full weighting of r[l]
+// coarse b[l + 1] = full weighting of r[l], and the first Chebyshev direction of level l + 1
+// (its smoother's, or the coarse solve's) from it
 template <typename T, bool SOLO>
 __device__ void blk_restrict(const SmallLevels& P, int l) {
     const float w[3] = {0.25f, 0.5f, 0.25f};
     const Dims f = P.d[l], c = P.d[l + 1];
     const T* r = (const T*)P.r[l];
     T* bc = (T*)P.b[l + 1];
+    T* dc = (T*)P.dv[l + 1];
+    const float s0 = P.invD[l + 1] / (l + 2 == P.count ? P.ctheta : P.theta[l + 1]);
     for (int I = lv_tid<SOLO>(); I < (int)c.n; I += lv_stride<SOLO>()) {
         const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
         T s = vzero<T>();
@@ -436,6 +453,7 @@ __device__ void blk_restrict(const SmallLevels& P, int l) {
                     s = vfma(w[dz + 1] * w[dy + 1] * w[dx + 1], r[(fz * f.n2 + fy) * f.n1 + fx], s);
                 }
         bc[I] = s;
+        dc[I] = vmul(s0, s);
     }
     lv_sync<SOLO>();
 }
@@ -453,30 +471,34 @@ __device__ void blk_prolong(const SmallLevels& P, int l) {
     lv_sync<SOLO>();
 }
 
-// coarsest level: Chebyshev over the whole spectrum (non-zero part for sigma = 0) from zero
+// coarsest level: Chebyshev over the whole spectrum (non-zero part for sigma = 0) from zero;
+// the first direction D^{-1} b / theta comes from the restriction when d0_ready.  One barrier
+// per step, as in blk_smooth.
 template <typename T, bool SOLO>
-__device__ void blk_coarse(const SmallLevels& P) {
+__device__ void blk_coarse(const SmallLevels& P, bool d0_ready) {
     const int l = P.count - 1;
     const int n = (int)P.d[l].n;
-    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l], *dv = (T*)P.dv[l];
+    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l];
+    T* dbuf[2] = {(T*)P.dv[l], (T*)P.dw[l]};
     const float sigma1 = P.ctheta / P.cdelta;
     float rho = 1.f / sigma1;
     const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
-    for (int i = t0; i < n; i += ts) {
-        x[i] = vzero<T>();
-        r[i] = b[i];
-        dv[i] = vmul(P.invD[l] / P.ctheta, b[i]);
+    if (!d0_ready) {
+        for (int i = t0; i < n; i += ts) dbuf[0][i] = vmul(P.invD[l] / P.ctheta, b[i]);
+        lv_sync<SOLO>();
     }
-    lv_sync<SOLO>();
     for (int s = 0; s < P.deg_coarse; ++s) {
         const float rn = 1.f / (2.f * sigma1 - rho);
-        const float a = rn * rho, bb = 2.f * rn / P.cdelta;
+        const float a = rn * rho, bb = 2.f * rn / P.cdelta * P.invD[l];
+        const T* dc = dbuf[s & 1];
+        T* dn = dbuf[(s + 1) & 1];
         for (int i = t0; i < n; i += ts) {
-            x[i] = vadd(x[i], dv[i]);
-            r[i] = vadd(r[i], neg_op7(P, l, dv, i));
+            const T di = dc[i];
+            x[i] = s == 0 ? di : vadd(x[i], di);
+            const T rv = vadd(s == 0 ? b[i] : r[i], neg_op7(P, l, dc, i));
+            r[i] = rv;
+            dn[i] = vfma(a, di, vmul(bb, rv));
         }
-        lv_sync<SOLO>();
-        for (int i = t0; i < n; i += ts) dv[i] = vfma(a, dv[i], vmul(bb * P.invD[l], r[i]));
         lv_sync<SOLO>();
         rho = rn;
     }
@@ -485,30 +507,31 @@ __device__ void blk_coarse(const SmallLevels& P) {
 template <typename T>
 __global__ void __cluster_dims__(MG_CLUSTER, 1, 1) __launch_bounds__(1024)
 k_small_vcycle(SmallLevels P, const double* done) {
+    pdl_enter();
     if (*done != 0.0) return;
     const bool lead = blockIdx.x == 0;
     // every cluster barrier below is reached by all CTAs: the solo parts contain none
     for (int l = 0; l + 1 < P.count; ++l) {
         if (l < P.solo) {
-            blk_smooth<T, false>(P, l, true);
+            blk_smooth<T, false>(P, l, true, l > 0);
             blk_restrict<T, false>(P, l);
         } else if (lead) {
-            blk_smooth<T, true>(P, l, true);
+            blk_smooth<T, true>(P, l, true, l > 0);
             blk_restrict<T, true>(P, l);
         }
     }
-    if (P.count - 1 < P.solo) blk_coarse<T, false>(P);
-    else if (lead) blk_coarse<T, true>(P);
+    if (P.count - 1 < P.solo) blk_coarse<T, false>(P, P.count > 1);
+    else if (lead) blk_coarse<T, true>(P, P.count > 1);
     for (int l = P.count - 2; l >= 0; --l) {
         if (l >= P.solo) {
             if (lead) {
                 blk_prolong<T, true>(P, l);
-                blk_smooth<T, true>(P, l, false);
+                blk_smooth<T, true>(P, l, false, false);
             }
         } else {
             if (l + 1 >= P.solo) cl_sync();   // the first CTA has finished the solo levels
             blk_prolong<T, false>(P, l);
-            blk_smooth<T, false>(P, l, false);
+            blk_smooth<T, false>(P, l, false, false);
         }
     }
 }
@@ -585,8 +608,8 @@ static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
         MGLevel& C = m.lv[l + 1];
         smooth<T>(g, L, m.deg, true, done, sigma);   // x_l = S b_l, r_l = b_l - A x_l
         ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(L.d.n + C.d.n));
-        launch(k_restrict<T>, (unsigned)((C.d.n + 255) / 256), 256, g->stream, L.d, C.d,
-               (const T*)L.r, (T*)C.b, done);
+        launch_pdl(k_restrict<T>, (unsigned)((C.d.n + 255) / 256), 256, 0, g->stream, L.d, C.d,
+                   (const T*)L.r, (T*)C.b, done);
     }
     {
         SmallLevels P{};
@@ -621,17 +644,18 @@ static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
             P.b[k] = L.b;
             P.r[k] = L.r;
             P.dv[k] = L.d0;
+            P.dw[k] = L.d1;
         }
         ProfScope ps(g, PC_MG_TRANSFER, 0.0);
-        launch(k_small_vcycle<T>, MG_CLUSTER, 1024, g->stream, P, done);
+        launch_pdl(k_small_vcycle<T>, MG_CLUSTER, 1024, 0, g->stream, P, done);
     }
     for (int l = fs - 1; l >= 0; --l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
         {
             ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(2 * L.d.n + C.d.n));
-            launch(k_prolong_add<T>, (unsigned)((L.d.n + 255) / 256), 256, g->stream, L.d, C.d,
-                   (const T*)C.x, (T*)L.x, done);
+            launch_pdl(k_prolong_add<T>, (unsigned)((L.d.n + 255) / 256), 256, 0, g->stream, L.d,
+                       C.d, (const T*)C.x, (T*)L.x, done);
         }
         smooth<T>(g, L, m.deg, false, done, sigma, l == 0 ? fuse : nullptr);
     }

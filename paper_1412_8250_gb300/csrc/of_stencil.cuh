@@ -576,6 +576,7 @@ constexpr size_t brick_smem_bytes() {
 
 template <typename T, int N, int BZ, class Op>
 __global__ void __launch_bounds__(B3_THREADS, 4) brick_kernel(Dims d, Weights<float> W, Op op) {
+    pdl_enter();
     if (!op.begin()) return;
     brick_tile<T, N, BZ, Op>(d, W, op);
     op.end();
@@ -588,6 +589,7 @@ template <int N> struct BrickDepth { static constexpr int value = N >= 3 ? 8 : 2
 template <int N, int RY, class Op>
 __global__ void __launch_bounds__(S2_BX * (S2_TY / RY), 2)
 stencil2_kernel(Dims d, Weights<float> W, int cz, Op op) {
+    pdl_enter();
     if (!op.begin()) return;
     stencil2_tile<N, RY, Op>(d, W, cz, blockIdx.x, blockIdx.y, blockIdx.z, op);
     op.end();
@@ -596,6 +598,7 @@ stencil2_kernel(Dims d, Weights<float> W, int cz, Op op) {
 template <typename T, int N, int RY, class Op>
 __global__ void __launch_bounds__(ST_THREADS)
 stencil_kernel(Dims d, Weights<typename Real<T>::type> W, int cz, Op op) {
+    pdl_enter();
     if (!op.begin()) return;
     stencil_tile<T, N, RY, Op>(d, W, cz, blockIdx.x, blockIdx.y, blockIdx.z, op);
     op.end();
@@ -648,7 +651,7 @@ void launch_brick(of_grid* g, dim3 grid, dim3 block, const Dims& d, const Weight
             configured_device = g->device;
         }
     }
-    launch_smem(brick_kernel<T, N, BZ, Op>, grid, block, smem, g->stream, d, W, op);
+    launch_pdl(brick_kernel<T, N, BZ, Op>, grid, block, smem, g->stream, d, W, op);
 }
 
 template <typename T, int RY, class Op>
@@ -692,17 +695,17 @@ void launch_stencil_dims(of_grid* g, const Dims& d, int N,
             const dim3 grid2(bx, by, (d.n3 + cz - 1) / cz);
             const dim3 block2(S2_BX, S2_TY / RY2, 1);
             switch (N) {
-                case 1: launch(stencil2_kernel<1, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
-                case 3: launch(stencil2_kernel<3, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
-                case 6: launch(stencil2_kernel<6, RY2, Op>, grid2, block2, stream, d, W, cz, op); return;
+                case 1: launch_pdl(stencil2_kernel<1, RY2, Op>, grid2, block2, 0, stream, d, W, cz, op); return;
+                case 3: launch_pdl(stencil2_kernel<3, RY2, Op>, grid2, block2, 0, stream, d, W, cz, op); return;
+                case 6: launch_pdl(stencil2_kernel<6, RY2, Op>, grid2, block2, 0, stream, d, W, cz, op); return;
                 default: break;
             }
         }
     }
     switch (N) {
-        case 1: launch(stencil_kernel<T, 1, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
-        case 3: launch(stencil_kernel<T, 3, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
-        case 6: launch(stencil_kernel<T, 6, RY, Op>, sl.grid, block, stream, d, W, sl.cz, op); break;
+        case 1: launch_pdl(stencil_kernel<T, 1, RY, Op>, sl.grid, block, 0, stream, d, W, sl.cz, op); break;
+        case 3: launch_pdl(stencil_kernel<T, 3, RY, Op>, sl.grid, block, 0, stream, d, W, sl.cz, op); break;
+        case 6: launch_pdl(stencil_kernel<T, 6, RY, Op>, sl.grid, block, 0, stream, d, W, sl.cz, op); break;
         default: OF_REQUIRE(false, OF_EINVAL, "unsupported finite-difference half order %d", N);
     }
 }
