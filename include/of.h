@@ -291,7 +291,9 @@ const char* of_last_error(void);
  * stream with CUDA events (0 stops timing, counting continues); resets the statistics.
  * of_profile_read: synchronises the stream, fills up to max records (one per kernel class
  * seen) and returns their number, -1 on error.  bytes_per_launch is the algorithmic traffic
- * of one launch (fields read plus written, no halo re-reads). */
+ * of one launch (fields read plus written, no halo re-reads), averaged over the timed
+ * launches: a graph launch of a whole preconditioned pass (classes "mg_pcg_pass_graph",
+ * "mg_cocg_pass_graph") counts the iterations it ran. */
 typedef struct {
     int kernel_class;
     long long launches;

@@ -156,6 +156,7 @@ of_status of_grid_destroy(of_grid* g) {
     if (g->mg) mg_destroy(g->mg);
     if (g->graphs) destroy_graphs(g->graphs);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    if (g->cap_stream2) cudaStreamDestroy(g->cap_stream2);
     if (g->prof) {
         for (auto& r : g->prof->recs) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
         for (auto e : g->prof->pool) cudaEventDestroy(e);
@@ -190,9 +191,9 @@ const char* of_kernel_class_name(int cls) {
     static const char* names[PC_N] = {"stencil_f64", "stencil_f32", "cg_stencil_f64",
                                       "cg_stencil_f32", "cocg_stencil_f64", "cocg_stencil_f32",
                                       "krylov_update", "mg_smooth", "mg_transfer",
-                                      "line_energy", "ions", "other", "pcg_iteration_pair_graph",
+                                      "line_energy", "ions", "other", "mg_pcg_pass_graph",
                                       "cg_cocg_iteration_pair_graph", "precond_net",
-                                      "mg_cocg_iteration_pair_graph"};
+                                      "mg_cocg_pass_graph"};
     return (cls >= 0 && cls < PC_N) ? names[cls] : "";
 }
 
@@ -222,7 +223,7 @@ int of_profile_read(of_grid* g, of_kernel_stat* out, int max) {
             OF_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
             p.timed[r.cls] += 1;
             p.ms[r.cls] += ms;
-            p.bytes[r.cls] = r.bytes;
+            p.bytes[r.cls] += r.bytes;
             p.pool.push_back(r.e0);
             p.pool.push_back(r.e1);
         }
@@ -235,7 +236,7 @@ int of_profile_read(of_grid* g, of_kernel_stat* out, int max) {
             out[k].timed = p.timed[c];
             out[k].total_ms = p.ms[c];
             out[k].mean_ms = p.timed[c] ? p.ms[c] / p.timed[c] : 0.0;
-            out[k].bytes_per_launch = p.bytes[c];
+            out[k].bytes_per_launch = p.timed[c] ? p.bytes[c] / p.timed[c] : 0.0;
             ++k;
         }
         return k;

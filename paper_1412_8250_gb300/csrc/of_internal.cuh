@@ -47,12 +47,10 @@ inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t
     OF_CUDA(cudaGetLastError());
 }
 
-// Programmatic dependent launch, for the kernels of the solver loops: the next kernel of the
-// stream may be scheduled while this one runs, and every kernel launched this way starts with
-// pdl_enter(), which waits until the previous kernel of the stream has completed and its
-// writes are visible, then lets the next kernel start launching.  Nothing a kernel reads from
-// global memory is touched before pdl_enter().  The launch and block scheduling of each
-// kernel overlap the previous one's tail instead of following it.
+// Programmatic dependent launch, for the kernels of the solver loops: every kernel launched
+// this way starts with pdl_enter(), which waits until the previous kernel of the stream has
+// completed and its writes are visible; nothing a kernel reads from global memory is touched
+// before it.  The launch of each kernel is prepared while the previous one runs.
 template <typename... KArgs, typename... Args>
 inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t stream, Args&&... args) {
@@ -71,10 +69,10 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // First statement of every kernel launched with launch_pdl (a no-op under a plain launch).
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// No early trigger: the next kernel's blocks are released when this grid completes (released
+// at the start, they sat resident beside this grid's blocks and slowed a 96^3 sweep from 5.8 to
+// 8.1 us).
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Same, with `smem` bytes of dynamic shared memory (the caller raises the kernel's limit).
 template <typename... KArgs, typename... Args>
@@ -108,6 +106,15 @@ struct Prof {
     double bytes[PC_N] = {};
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
+    // sets the bytes of the latest timed launch of class cls not yet read (graph launches whose
+    // traffic is known only after a later host read)
+    void amend_last(int cls, double b) {
+        for (auto it = recs.rbegin(); it != recs.rend(); ++it)
+            if (it->cls == cls) {
+                it->bytes = b;
+                return;
+            }
+    }
     cudaEvent_t get() {
         if (pool.empty()) {
             cudaEvent_t e;
@@ -176,6 +183,7 @@ struct of_grid {
     of::MG* mg = nullptr;            // multigrid hierarchy (built on first use)
     of::Prof* prof = nullptr;        // kernel timing (of_profile_enable)
     cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
+    cudaStream_t cap_stream2 = nullptr;  // second capture stream (bodies of conditional nodes)
     void* graphs = nullptr;              // cached CUDA graphs (of_krylov.cu)
 };
 
@@ -186,6 +194,7 @@ struct ProfScope {
     double bytes;
     cudaStream_t s;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bool ended = false;
     ProfScope(of_grid* g, int cls_, double bytes_) : cls(cls_), bytes(bytes_), s(g->stream) {
         if (g_capturing) {
             g_capture_bytes += bytes;
@@ -200,9 +209,17 @@ struct ProfScope {
         }
         p->seen[cls]++;
     }
+    // ends the timed interval here (the record, with `bytes` as set by then, is kept at scope
+    // exit): for a launch whose traffic is known only after a later host read
+    void end_timing() {
+        if (e0 && !ended) {
+            cudaEventRecord(e1, s);
+            ended = true;
+        }
+    }
     ~ProfScope() {
         if (e0) {
-            cudaEventRecord(e1, s);
+            if (!ended) cudaEventRecord(e1, s);
             p->recs.push_back(ProfRec{cls, e0, e1, bytes});
         }
     }

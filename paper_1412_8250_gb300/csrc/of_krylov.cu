@@ -335,11 +335,61 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
 
 void destroy_graphs(void* p) { destroy_graphs_impl(p); }
 
+__global__ void k_loop_continue(cudaGraphConditionalHandle h, const KState* st) {
+    pdl_enter();
+    cudaGraphSetConditional(h, st->done == 0.0 ? 1u : 0u);
+}
+
+// A launched loop graph (capture_loop) whose state has not been read back yet: its kernel
+// count and algorithmic bytes follow from the iterations it ran, once the host has them.
+struct PendingLoop {
+    int cls = -1;
+    bool sampled = false;   // the launch was timed: its profile record gets the bytes
+    unsigned long long init_kernels = 0, pair_kernels = 0;
+    double init_bytes = 0.0, pair_bytes = 0.0;
+    void account(of_grid* g, double iters) const {
+        if (cls < 0) return;
+        const double pairs = std::max(1.0, std::ceil(iters / 2.0));
+        __atomic_add_fetch(&g_launch_count, init_kernels + (unsigned long long)pairs * pair_kernels,
+                           __ATOMIC_RELAXED);
+        if (sampled && g->prof) g->prof->amend_last(cls, init_bytes + pairs * pair_bytes);
+    }
+};
+
+// Launches a loop graph.  pending == nullptr: reads the solver state back (one
+// synchronisation) and returns it; else returns at once (done = -1) and the caller reads the
+// state later and calls pending->account.
+static KState replay_loop(of_grid* g, cudaGraphExec_t exec, int st_off, int cls,
+                          unsigned long long init_kernels, double init_bytes,
+                          unsigned long long pair_kernels, double pair_bytes, PendingLoop* pending) {
+    PendingLoop pl;
+    pl.cls = cls;
+    pl.init_kernels = init_kernels;
+    pl.pair_kernels = pair_kernels;
+    pl.init_bytes = init_bytes;
+    pl.pair_bytes = pair_bytes;
+    {
+        ProfScope ps(g, cls, 0.0);
+        OF_CUDA(cudaGraphLaunch(exec, g->stream));
+        pl.sampled = ps.e0 != nullptr;
+    }
+    KState h{};
+    if (pending) {
+        *pending = pl;
+        h.done = -1.0;
+        return h;
+    }
+    fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
+    pl.account(g, h.iters);
+    return h;
+}
+
 // COCG on the complex shifted operator A = a(-L) + Q in FP32, preconditioned by one V-cycle of
 // the real positive operator -L + sigma applied to real and imaginary parts (sigma = |Q| / a).
 // Pairs of iterations replay from cached CUDA graphs as for the Poisson PCG.
 static KState iterate_pcocg(of_grid* g, int st_off, float2* x, float2* r, float2* pa, float2* pb,
-                            float2* Ap, float2* z, float a, double2 Q, double sigma, int check_every) {
+                            float2* Ap, float2* z, float a, double2 Q, double sigma, int check_every,
+                            PendingLoop* pending = nullptr) {
     KState* st = kstate(g, st_off);
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float2) * n, g->stream));
@@ -355,22 +405,18 @@ static KState iterate_pcocg(of_grid* g, int st_off, float2* x, float2* r, float2
             PcocgGraph c{};
             std::memcpy(c.key, key, sizeof(key));
             std::memcpy(c.consts, consts, sizeof(consts));
-            c.init = capture(g, [&] { pcocg_init_body(g, r, z, st, sigma); }, c.init_kernels, c.init_bytes);
-            c.pair = capture(g, [&] {
-                pcocg_step_body(g, x, r, pa, pb, Ap, z, st, a, Q, sigma);
-                pcocg_step_body(g, x, r, pb, pa, Ap, z, st, a, Q, sigma);
-            }, c.pair_kernels, c.pair_bytes);
+            c.loop = capture_loop(
+                g, st, [&] { pcocg_init_body(g, r, z, st, sigma); },
+                [&] {
+                    pcocg_step_body(g, x, r, pa, pb, Ap, z, st, a, Q, sigma);
+                    pcocg_step_body(g, x, r, pb, pa, Ap, z, st, a, Q, sigma);
+                },
+                c.init_kernels, c.init_bytes, c.pair_kernels, c.pair_bytes);
             G.pcocg.push_back(c);
             e = &G.pcocg.back();
         }
-        replay(g, e->init, e->init_kernels, e->init_bytes, PC_PCOCG_GRAPH);
-        const int pairs = std::max(1, check_every / 8);
-        for (;;) {
-            for (int k = 0; k < pairs; ++k) replay(g, e->pair, e->pair_kernels, e->pair_bytes, PC_PCOCG_GRAPH);
-            fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
-            if (h.done != 0.0) break;
-        }
-        return h;
+        return replay_loop(g, e->loop, st_off, PC_PCOCG_GRAPH, e->init_kernels, e->init_bytes,
+                           e->pair_kernels, e->pair_bytes, pending);
     }
     float2* p[2] = {pa, pb};
     int ping = 0;
@@ -391,7 +437,7 @@ static KState iterate_pcocg(of_grid* g, int st_off, float2* x, float2* r, float2
 // run as replays of captured CUDA graphs; with profiling on, as individual launches so that
 // every kernel class can be timed.
 static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa, float* pb,
-                          float* Ap, float* z, int check_every) {
+                          float* Ap, float* z, int check_every, PendingLoop* pending = nullptr) {
     KState* st = kstate(g, st_off);
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float) * n, g->stream));
@@ -400,25 +446,20 @@ static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa,
     if (use_graphs) {
         PcgGraphs& G = graphs(g).pcg;
         const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
-        if (!G.pair || std::memcmp(key, G.key, sizeof(key)) != 0) {
-            if (G.init) cudaGraphExecDestroy(G.init);
-            if (G.pair) cudaGraphExecDestroy(G.pair);
-            G.init = G.pair = nullptr;
-            G.init = capture(g, [&] { pcg_init_body(g, r, z, st); }, G.init_kernels, G.init_bytes);
-            G.pair = capture(g, [&] {
-                pcg_step_body(g, x, r, pa, pb, Ap, z, st);
-                pcg_step_body(g, x, r, pb, pa, Ap, z, st);
-            }, G.pair_kernels, G.pair_bytes);
+        if (!G.loop || std::memcmp(key, G.key, sizeof(key)) != 0) {
+            if (G.loop) cudaGraphExecDestroy(G.loop);
+            G.loop = nullptr;
+            G.loop = capture_loop(
+                g, st, [&] { pcg_init_body(g, r, z, st); },
+                [&] {
+                    pcg_step_body(g, x, r, pa, pb, Ap, z, st);
+                    pcg_step_body(g, x, r, pb, pa, Ap, z, st);
+                },
+                G.init_kernels, G.init_bytes, G.pair_kernels, G.pair_bytes);
             std::memcpy(G.key, key, sizeof(key));
         }
-        replay(g, G.init, G.init_kernels, G.init_bytes);
-        const int pairs = std::max(1, check_every / 8);
-        for (;;) {
-            for (int k = 0; k < pairs; ++k) replay(g, G.pair, G.pair_kernels, G.pair_bytes);
-            fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);
-            if (h.done != 0.0) break;
-        }
-        return h;
+        return replay_loop(g, G.loop, st_off, PC_PCG_GRAPH, G.init_kernels, G.init_bytes,
+                           G.pair_kernels, G.pair_bytes, pending);
     }
     float* p[2] = {pa, pb};
     int ping = 0;
@@ -467,6 +508,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     }
     while (bb > 0.0 && h.rr > h.tol2) {
         if (total_iters >= o.max_iter || refinements > 200) { status = OF_ENOCONV; break; }
+        bool residual_done = false;   // this pass read the true residual back already
         if (o.precision == OF_F32) {
             KState* s32 = kstate(g, KS32);
             T32* r32 = (T32*)ar.r32;
@@ -492,12 +534,13 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 n, r, r32, e32, o.inner_tol, st, s32, pass_max, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
             KState hi;
+            PendingLoop pending;   // a loop graph whose state is read with the outer residual
             if constexpr (std::is_same<T32, float2>::value) {
                 // shifted systems: COCG preconditioned by the V-cycle of -L + |Q| / a
                 if (pcg)
                     hi = iterate_pcocg(g, KS32, e32, r32, (float2*)ar.pa32, (float2*)ar.pb32,
                                        (float2*)ar.Ap32, (float2*)ar.z32, (float)a, Q, qabs / a,
-                                       o.check_every);
+                                       o.check_every, &pending);
             }
             if constexpr (std::is_same<T32, float>::value) {
                 if (fcg)
@@ -505,14 +548,26 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                                      (float*)ar.z32, o.check_every, nullptr, &net_steps);
                 else if (pcg)
                     hi = iterate_pcg(g, KS32, e32, r32, (float*)ar.pa32, (float*)ar.pb32,
-                                     (float*)ar.Ap32, (float*)ar.z32, o.check_every);
+                                     (float*)ar.Ap32, (float*)ar.z32, o.check_every, &pending);
             }
             if (!pcg && !fcg)
                 hi = iterate<T32>(g, KS32, e32, r32, (T32*)ar.pa32, (T32*)ar.pb32,
                                   (T32*)ar.Ap32, (float)a, Q, g->w32, o.check_every);
-            total_iters += (int)hi.iters;
             launch(k_promote_add<T64, T32>, vec_blocks(n), 256, g->stream, n, x, (const T32*)e32, (const KState*)s32);
             OF_LAUNCH_CHECK();
+            if (hi.done == -1.0) {
+                // one read-back for both states: the inner pass and the true residual after it
+                // (a pass that broke down at its start has a zero correction)
+                residual<T64>(g, KS64, x, b, r, a, Q);
+                static_assert(KS32 > KS64, "KState layout");
+                double both[KS32 - KS64 + KSTATE_DOUBLES];
+                fetch_scalars(g, KS64, KS32 - KS64 + KSTATE_DOUBLES, both);
+                std::memcpy(&h, both, sizeof(KState));
+                std::memcpy(&hi, both + (KS32 - KS64), sizeof(KState));
+                pending.account(g, hi.iters);
+                residual_done = true;
+            }
+            total_iters += (int)hi.iters;
             if (hi.breakdown != 0.0 && hi.iters == 0) {
                 status = OF_EBREAKDOWN;
                 set_error("Krylov solve (FP32 inner, %s): breakdown at the start of refinement pass "
@@ -532,9 +587,11 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 break;
             }
         }
-        residual<T64>(g, KS64, x, b, r, a, Q);   // true residual; restarts the recurrence
+        if (!residual_done) {
+            residual<T64>(g, KS64, x, b, r, a, Q);   // true residual; restarts the recurrence
+            fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
+        }
         ++refinements;
-        fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
     }
     if (info) {
         info->iterations += total_iters;

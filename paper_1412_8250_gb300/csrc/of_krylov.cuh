@@ -400,6 +400,7 @@ struct PcgGraphs {
     cudaGraphExec_t init = nullptr, pair = nullptr;
     unsigned long long init_kernels = 0, pair_kernels = 0;
     double init_bytes = 0.0, pair_bytes = 0.0;
+    cudaGraphExec_t loop = nullptr;   // init, then pair while not done (device-side loop)
 };
 
 // Graphs of two plain CG / COCG iterations, keyed by buffers and operator constants.
@@ -418,6 +419,7 @@ struct PcocgGraph {
     cudaGraphExec_t init, pair;
     unsigned long long init_kernels, pair_kernels;
     double init_bytes, pair_bytes;
+    cudaGraphExec_t loop;   // init, then pair while not done (device-side loop)
 };
 
 struct Graphs {
@@ -431,10 +433,13 @@ inline void destroy_graphs_impl(void* p) {
     if (!G) return;
     if (G->pcg.init) cudaGraphExecDestroy(G->pcg.init);
     if (G->pcg.pair) cudaGraphExecDestroy(G->pcg.pair);
-    for (auto& e : G->plain) cudaGraphExecDestroy(e.exec);
+    if (G->pcg.loop) cudaGraphExecDestroy(G->pcg.loop);
+    for (auto& e : G->plain)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
     for (auto& e : G->pcocg) {
-        cudaGraphExecDestroy(e.init);
-        cudaGraphExecDestroy(e.pair);
+        if (e.init) cudaGraphExecDestroy(e.init);
+        if (e.pair) cudaGraphExecDestroy(e.pair);
+        if (e.loop) cudaGraphExecDestroy(e.loop);
     }
     delete G;
 }
@@ -477,6 +482,91 @@ inline cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kern
     __atomic_sub_fetch(&g_launch_count, kernels, __ATOMIC_RELAXED);   // captured, not launched
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    OF_CUDA(e);
+    return exec;
+}
+
+// Sets the condition of the enclosing WHILE node: repeat while the solver state is not done.
+__global__ void k_loop_continue(cudaGraphConditionalHandle h, const KState* st);
+
+// One executable graph for a whole preconditioned pass: `init` once, then `pair` (two
+// iterations) under a conditional WHILE node whose body ends with k_loop_continue, so that the
+// iterations repeat on the device until the state's done flag is set (convergence, breakdown or
+// the iteration cap, all set by the kernels).  One host launch and one host synchronisation per
+// pass instead of one per pair.
+template <class Init, class Pair>
+inline cudaGraphExec_t capture_loop(of_grid* g, KState* st, Init&& init, Pair&& pair,
+                                    unsigned long long& init_kernels, double& init_bytes,
+                                    unsigned long long& pair_kernels, double& pair_bytes) {
+    if (!g->cap_stream) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    if (!g->cap_stream2) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream2, cudaStreamNonBlocking));
+    cudaStream_t saved = g->stream;
+    Prof* saved_prof = g->prof;
+    g->prof = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool main_open = false, body_open = false;
+    auto restore = [&]() {
+        g_capturing = false;
+        g->stream = saved;
+        g->prof = saved_prof;
+    };
+    try {
+        unsigned long long c0 = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
+        g->stream = g->cap_stream;
+        OF_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+        main_open = true;
+        g_capturing = true;
+        g_capture_bytes = 0.0;
+        init();
+        init_bytes = g_capture_bytes;
+        init_kernels = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED) - c0;
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        OF_CUDA(cudaStreamGetCaptureInfo(g->cap_stream, &cs, nullptr, &graph, &deps, nullptr, &ndeps));
+        cudaGraphConditionalHandle handle;
+        OF_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        OF_CUDA(cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &cp));
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        c0 = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
+        g->stream = g->cap_stream2;
+        OF_CUDA(cudaStreamBeginCaptureToGraph(g->stream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+        body_open = true;
+        g_capture_bytes = 0.0;
+        pair();
+        launch_pdl(k_loop_continue, 1, 1, 0, g->stream, handle, (const KState*)st);
+        pair_bytes = g_capture_bytes;
+        pair_kernels = __atomic_load_n(&g_launch_count, __ATOMIC_RELAXED) - c0;
+        body_open = false;
+        OF_CUDA(cudaStreamEndCapture(g->stream, nullptr));
+        g->stream = g->cap_stream;
+        OF_CUDA(cudaStreamUpdateCaptureDependencies(g->stream, &node, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies));
+        main_open = false;
+        OF_CUDA(cudaStreamEndCapture(g->stream, &graph));
+    } catch (...) {
+        if (body_open) cudaStreamEndCapture(g->cap_stream2, nullptr);
+        if (main_open) {
+            cudaGraph_t partial = nullptr;
+            cudaStreamEndCapture(g->cap_stream, &partial);
+            if (partial) cudaGraphDestroy(partial);
+        }
+        restore();
+        throw;
+    }
+    restore();
+    // captured, not launched
+    __atomic_sub_fetch(&g_launch_count, init_kernels + pair_kernels, __ATOMIC_RELAXED);
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     OF_CUDA(e);
     return exec;

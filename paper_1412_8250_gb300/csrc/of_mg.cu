@@ -285,17 +285,21 @@ template <typename T> __device__ __forceinline__ T vzero();
 template <> __device__ __forceinline__ float vzero<float>() { return 0.f; }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 
+// grid of 32 x 8 thread blocks over the points of a level, one block row per plane
+static inline dim3 grid3(const Dims& d) {
+    return dim3((unsigned)((d.n1 + 31) / 32), (unsigned)((d.n2 + 7) / 8), (unsigned)d.n3);
+}
+
 // coarse b = full weighting of fine r
 template <typename T>
 __global__ void k_restrict(Dims f, Dims c, const T* __restrict__ r, T* __restrict__ b,
                            const double* done) {
     pdl_enter();
     if (*done != 0.0) return;
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= c.n) return;
-    const int I = (int)(idx % c.n1);
-    const int J = (int)((idx / c.n1) % c.n2);
-    const int K = (int)(idx / ((long long)c.n1 * c.n2));
+    // 3-D launch (x_blocks, y_blocks, c.n3) of 32 x 8 threads: no index division
+    const int I = blockIdx.x * 32 + threadIdx.x, J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+    if (I >= c.n1 || J >= c.n2) return;
+    const long long idx = ((long long)K * c.n2 + J) * c.n1 + I;
     T s = vzero<T>();
     const float w[3] = {0.25f, 0.5f, 0.25f};
 #pragma unroll
@@ -336,11 +340,10 @@ __global__ void k_prolong_add(Dims f, Dims c, const T* __restrict__ e, T* __rest
                               const double* done) {
     pdl_enter();
     if (*done != 0.0) return;
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= f.n) return;
-    const int i = (int)(idx % f.n1);
-    const int j = (int)((idx / f.n1) % f.n2);
-    const int k = (int)(idx / ((long long)f.n1 * f.n2));
+    // 3-D launch (x_blocks, y_blocks, f.n3) of 32 x 8 threads: no index division
+    const int i = blockIdx.x * 32 + threadIdx.x, j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (i >= f.n1 || j >= f.n2) return;
+    const long long idx = ((long long)k * f.n2 + j) * f.n1 + i;
     x[idx] = vadd(x[idx], interp(e, c, i, j, k));
 }
 
@@ -358,7 +361,22 @@ struct SmallLevels {
     float ca[MG_MAX_LEVELS][4], cb[MG_MAX_LEVELS][4];
     void *x[MG_MAX_LEVELS], *b[MG_MAX_LEVELS], *r[MG_MAX_LEVELS];
     void *dv[MG_MAX_LEVELS], *dw[MG_MAX_LEVELS];   // the Chebyshev direction, double-buffered
+    int soff[MG_MAX_LEVELS];   // solo levels: element offset of their arrays in shared memory
 };
+
+// The five arrays of level l: x, b, r and the two direction buffers (k = 0..4).  Solo levels
+// keep them in the first CTA's shared memory (five consecutive runs of n_l elements from
+// soff[l]), the others in global memory.
+template <typename T, bool SOLO>
+__device__ __forceinline__ T* lv_arr(const SmallLevels& P, int l, int k) {
+    if constexpr (SOLO) {
+        extern __shared__ float4 mg_solo_smem[];
+        return reinterpret_cast<T*>(mg_solo_smem) + P.soff[l] + (long long)k * P.d[l].n;
+    } else {
+        void* p = k == 0 ? P.x[l] : k == 1 ? P.b[l] : k == 2 ? P.r[l] : k == 3 ? P.dv[l] : P.dw[l];
+        return reinterpret_cast<T*>(p);
+    }
+}
 
 // -(A a)(i) = (L_h a)(i) - sigma a(i) for the 7-point operator of level l
 template <typename T>
@@ -398,8 +416,8 @@ template <bool SOLO> __device__ __forceinline__ void lv_sync() {
 template <typename T, bool SOLO>
 __device__ void blk_smooth(const SmallLevels& P, int l, bool zero, bool d0_ready) {
     const int n = (int)P.d[l].n;
-    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l];
-    T* dbuf[2] = {(T*)P.dv[l], (T*)P.dw[l]};
+    T *x = lv_arr<T, SOLO>(P, l, 0), *b = lv_arr<T, SOLO>(P, l, 1), *r = lv_arr<T, SOLO>(P, l, 2);
+    T* dbuf[2] = {lv_arr<T, SOLO>(P, l, 3), lv_arr<T, SOLO>(P, l, 4)};
     const float s0 = P.invD[l] / P.theta[l];
     const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
     if (zero) {
@@ -438,9 +456,9 @@ template <typename T, bool SOLO>
 __device__ void blk_restrict(const SmallLevels& P, int l) {
     const float w[3] = {0.25f, 0.5f, 0.25f};
     const Dims f = P.d[l], c = P.d[l + 1];
-    const T* r = (const T*)P.r[l];
-    T* bc = (T*)P.b[l + 1];
-    T* dc = (T*)P.dv[l + 1];
+    const T* r = lv_arr<T, SOLO>(P, l, 2);
+    T* bc = lv_arr<T, SOLO>(P, l + 1, 1);
+    T* dc = lv_arr<T, SOLO>(P, l + 1, 3);
     const float s0 = P.invD[l + 1] / (l + 2 == P.count ? P.ctheta : P.theta[l + 1]);
     for (int I = lv_tid<SOLO>(); I < (int)c.n; I += lv_stride<SOLO>()) {
         const int ci = I % c.n1, cj = (I / c.n1) % c.n2, ck = I / (c.n1 * c.n2);
@@ -462,8 +480,8 @@ __device__ void blk_restrict(const SmallLevels& P, int l) {
 template <typename T, bool SOLO>
 __device__ void blk_prolong(const SmallLevels& P, int l) {
     const Dims f = P.d[l], c = P.d[l + 1];
-    const T* e = (const T*)P.x[l + 1];
-    T* x = (T*)P.x[l];
+    const T* e = lv_arr<T, SOLO>(P, l + 1, 0);
+    T* x = lv_arr<T, SOLO>(P, l, 0);
     for (int i = lv_tid<SOLO>(); i < (int)f.n; i += lv_stride<SOLO>()) {
         const int fi = i % f.n1, fj = (i / f.n1) % f.n2, fk = i / (f.n1 * f.n2);
         x[i] = vadd(x[i], interp(e, c, fi, fj, fk));
@@ -478,8 +496,8 @@ template <typename T, bool SOLO>
 __device__ void blk_coarse(const SmallLevels& P, bool d0_ready) {
     const int l = P.count - 1;
     const int n = (int)P.d[l].n;
-    T *x = (T*)P.x[l], *b = (T*)P.b[l], *r = (T*)P.r[l];
-    T* dbuf[2] = {(T*)P.dv[l], (T*)P.dw[l]};
+    T *x = lv_arr<T, SOLO>(P, l, 0), *b = lv_arr<T, SOLO>(P, l, 1), *r = lv_arr<T, SOLO>(P, l, 2);
+    T* dbuf[2] = {lv_arr<T, SOLO>(P, l, 3), lv_arr<T, SOLO>(P, l, 4)};
     const float sigma1 = P.ctheta / P.cdelta;
     float rho = 1.f / sigma1;
     const int t0 = lv_tid<SOLO>(), ts = lv_stride<SOLO>();
@@ -504,35 +522,52 @@ __device__ void blk_coarse(const SmallLevels& P, bool d0_ready) {
     }
 }
 
+// Levels solo .. count - 1 on the first CTA alone, in its shared memory: b of the first solo
+// level (and its first direction, when the cluster's restriction formed it) come in from
+// global memory, its x goes back out for the cluster's prolongation.
+template <typename T>
+__device__ void solo_part(const SmallLevels& P) {
+    const int s0 = P.solo;
+    const int n0 = (int)P.d[s0].n;
+    const T* gb = (const T*)P.b[s0];
+    const T* gd = (const T*)P.dv[s0];
+    T* sb = lv_arr<T, true>(P, s0, 1);
+    T* sd = lv_arr<T, true>(P, s0, 3);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+        sb[i] = gb[i];
+        if (s0 > 0) sd[i] = gd[i];
+    }
+    __syncthreads();
+    for (int l = s0; l + 1 < P.count; ++l) {
+        blk_smooth<T, true>(P, l, true, l > 0);
+        blk_restrict<T, true>(P, l);
+    }
+    blk_coarse<T, true>(P, P.count > 1);
+    for (int l = P.count - 2; l >= s0; --l) {
+        blk_prolong<T, true>(P, l);
+        blk_smooth<T, true>(P, l, false, false);
+    }
+    const T* sx = lv_arr<T, true>(P, s0, 0);
+    T* gx = (T*)P.x[s0];
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) gx[i] = sx[i];
+}
+
 template <typename T>
 __global__ void __cluster_dims__(MG_CLUSTER, 1, 1) __launch_bounds__(1024)
 k_small_vcycle(SmallLevels P, const double* done) {
     pdl_enter();
     if (*done != 0.0) return;
-    const bool lead = blockIdx.x == 0;
-    // every cluster barrier below is reached by all CTAs: the solo parts contain none
-    for (int l = 0; l + 1 < P.count; ++l) {
-        if (l < P.solo) {
-            blk_smooth<T, false>(P, l, true, l > 0);
-            blk_restrict<T, false>(P, l);
-        } else if (lead) {
-            blk_smooth<T, true>(P, l, true, l > 0);
-            blk_restrict<T, true>(P, l);
-        }
+    // every cluster barrier below is reached by all CTAs: the solo part contains none
+    for (int l = 0; l < P.solo && l + 1 < P.count; ++l) {
+        blk_smooth<T, false>(P, l, true, l > 0);
+        blk_restrict<T, false>(P, l);
     }
-    if (P.count - 1 < P.solo) blk_coarse<T, false>(P, P.count > 1);
-    else if (lead) blk_coarse<T, true>(P, P.count > 1);
-    for (int l = P.count - 2; l >= 0; --l) {
-        if (l >= P.solo) {
-            if (lead) {
-                blk_prolong<T, true>(P, l);
-                blk_smooth<T, true>(P, l, false, false);
-            }
-        } else {
-            if (l + 1 >= P.solo) cl_sync();   // the first CTA has finished the solo levels
-            blk_prolong<T, false>(P, l);
-            blk_smooth<T, false>(P, l, false, false);
-        }
+    if (P.solo >= P.count) blk_coarse<T, false>(P, P.count > 1);
+    else if (blockIdx.x == 0) solo_part<T>(P);
+    for (int l = min(P.solo, P.count - 1) - 1; l >= 0; --l) {
+        if (l + 1 == P.solo) cl_sync();   // the first CTA has finished the solo levels
+        blk_prolong<T, false>(P, l);
+        blk_smooth<T, false>(P, l, false, false);
     }
 }
 
@@ -608,7 +643,7 @@ static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
         MGLevel& C = m.lv[l + 1];
         smooth<T>(g, L, m.deg, true, done, sigma);   // x_l = S b_l, r_l = b_l - A x_l
         ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(L.d.n + C.d.n));
-        launch_pdl(k_restrict<T>, (unsigned)((C.d.n + 255) / 256), 256, 0, g->stream, L.d, C.d,
+        launch_pdl(k_restrict<T>, grid3(C.d), dim3(32, 8), 0, g->stream, L.d, C.d,
                    (const T*)L.r, (T*)C.b, done);
     }
     {
@@ -646,16 +681,34 @@ static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
             P.dv[k] = L.d0;
             P.dw[k] = L.d1;
         }
+        // shared memory of the solo levels: five arrays each
+        size_t elems = 0;
+        for (int k = P.solo; k < P.count; ++k) {
+            P.soff[k] = (int)elems;
+            elems += 5 * (size_t)P.d[k].n;
+        }
+        const size_t smem = (elems * sizeof(T) + 15) / 16 * 16;
+        OF_REQUIRE(smem <= 227 * 1024, OF_EINVAL, "multigrid: %zu bytes of small levels exceed shared memory", smem);
+        if (smem > 48 * 1024) {   // above the default limit: raise it (per host thread and device)
+            static thread_local int configured_device = -1;
+            static thread_local size_t configured = 0;
+            if (configured_device != g->device || configured < smem) {
+                OF_CUDA(cudaFuncSetAttribute(k_small_vcycle<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024));
+                configured_device = g->device;
+                configured = 227 * 1024;
+            }
+        }
         ProfScope ps(g, PC_MG_TRANSFER, 0.0);
-        launch_pdl(k_small_vcycle<T>, MG_CLUSTER, 1024, 0, g->stream, P, done);
+        launch_pdl(k_small_vcycle<T>, MG_CLUSTER, 1024, smem, g->stream, P, done);
     }
     for (int l = fs - 1; l >= 0; --l) {
         MGLevel& L = m.lv[l];
         MGLevel& C = m.lv[l + 1];
         {
             ProfScope ps(g, PC_MG_TRANSFER, sizeof(T) * (double)(2 * L.d.n + C.d.n));
-            launch_pdl(k_prolong_add<T>, (unsigned)((L.d.n + 255) / 256), 256, 0, g->stream, L.d,
-                       C.d, (const T*)C.x, (T*)L.x, done);
+            launch_pdl(k_prolong_add<T>, grid3(L.d), dim3(32, 8), 0, g->stream, L.d, C.d,
+                       (const T*)C.x, (T*)L.x, done);
         }
         smooth<T>(g, L, m.deg, false, done, sigma, l == 0 ? fuse : nullptr);
     }
