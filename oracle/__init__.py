@@ -23,8 +23,9 @@ from .pseudo import (pseudocharge, self_energy, repulsive_correction,
                      repulsive_correction_forces, gaussian_b, gaussian_V, atom_box)
 from .functional import (C_F, tf_energy_density, tf_potential, xc_energy_density,
                          eps_xc, v_xc, PZ)
-from .kernel import (WGC_TABLE, wt_functional, Functional, tfw_functional, kernel_solve,
-                     lr_potential, kf2_of)
+from .kernel import (WGC_TABLE, wt_functional, wgc_functional, Functional, tfw_functional,
+                     kernel_solve, lr_potential, lr_potential_wgc, kernel_class, c_mnpq,
+                     rho_bar_of, kf2_of)
 from .scf import (hamiltonian_apply, inner_energy, nlcg, anderson_update, scf_ground_state,
                   ground_state_energy, ScfResult)
 from .forces import forces
