@@ -29,5 +29,6 @@ from .kernel import (WGC_TABLE, wt_functional, wgc_functional, Functional, tfw_f
 from .scf import (hamiltonian_apply, inner_energy, nlcg, anderson_update, scf_ground_state,
                   ground_state_energy, ScfResult)
 from .forces import forces
+from .relax import relax, RelaxResult
 
 __all__ = [n for n in dir() if not n.startswith("_")]
