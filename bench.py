@@ -48,6 +48,12 @@ def parse():
     p.add_argument("--cells", type=int, default=16)
     p.add_argument("--config5", action="store_true",
                    help="measure the 3999-atom 320^3 ground state instead of the benchmark step")
+    p.add_argument("--wgc", action="store_true",
+                   help="measure the 108-atom 96^3 ground state with the full WGC functional "
+                        "(second-order kernel expansion) instead of the benchmark step")
+    p.add_argument("--relax", action="store_true",
+                   help="measure a geometry relaxation of the 108-atom 96^3 cell instead of the "
+                        "benchmark step")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
@@ -394,6 +400,100 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def wgc(args):
+    """The 108-atom 96^3 cell with the full WGC functional (L = 2: K_00, K_10 = K_01,
+    K_20 = K_02, K_11 of App. A; 16 potentials, 32 shifted solves per kernel map): one ground
+    state + forces in the mixed form, timed whole after one untimed ground state; and one
+    kernel map V[u] (mixed, tolerance 1e-10) on the GPU against the oracle's map of the same u
+    (FFT-exact solves on the host cores).  Prints one JSON line."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    cell, h, sysd, _, o = make_case(torch, B, Fn, W, "mixed")
+    fn = Fn.wgc()
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    times = []
+    with ClockSampler(0) as clk:
+        for k in range(2):
+            u.fill_(1.0)
+            phi.zero_()
+            torch.cuda.synchronize()
+            t = time.time()
+            res = B.of_scf_ground_state(h, sysd, fn, o, u, phi)
+            F = B.of_forces(h, sysd, u, phi)
+            torch.cuda.synchronize()
+            times.append(time.time() - t)
+        # one kernel map at the ground state, GPU against the oracle
+        kf2 = Fn.kf2(cell.n_electrons, cell.L[0] * cell.L[1] * cell.L[2])
+        ko = B.of_default_solve_opts()
+        ko.precision = B.OF_F32
+        vlr = torch.empty_like(u)
+        torch.cuda.synchronize()
+        t = time.time()
+        T_gpu, info = B.of_lr_potential(h, fn, kf2, u, vlr, opts=ko)
+        torch.cuda.synchronize()
+        t_map_gpu = time.time() - t
+    grid = O.Grid(cell.n, cell.L, 6)
+    t = time.time()
+    V_ref, T_ref, _ = O.lr_potential_wgc(u.cpu().numpy(), grid, O.wgc_functional(), kf2)
+    t_map_oracle = time.time() - t
+    v_err = float(np.max(np.abs(vlr.cpu().numpy() - V_ref)) / np.max(np.abs(V_ref)))
+    line = {"metric": "s per WGC ground state + forces (second-order kernel, 32 shifted solves per map)",
+            "value": times[-1], "unit": "s/ground-state", "higher_is_better": False,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("WT-type kernel functional", "full WGC functional (L = 2)")},
+            "result": {"energy_per_atom_ha": res.energy / cell.n_atoms, "e_lr_per_atom_ha": res.e_lr / cell.n_atoms,
+                       "outer_iterations": res.outer_iterations, "nlcg_steps": res.nlcg_iterations,
+                       "poisson_iterations": res.poisson_iterations,
+                       "kernel_iterations": res.kernel_iterations, "fp_error": res.fp_error,
+                       "max_force": float(np.abs(F).max())},
+            "kernel_map": {"gpu_s": t_map_gpu, "gpu_iterations": info.iterations},
+            "cpu_baseline": {"value": t_map_oracle, "unit": "s/kernel map", "cores": 1, "kind": "oracle",
+                             "sample": "one second-order kernel map V[u] at the GPU ground state, oracle "
+                                       "(numpy FP64, FFT-exact solves)",
+                             "gpu_vs_oracle": {"T_lr_rel_diff": abs(T_gpu - T_ref) / abs(T_ref),
+                                               "V_lr_max_rel_diff": v_err}},
+            "times_s": times, "clocks": clk.summary()}
+    B.of_grid_destroy(h)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def relax_case(args):
+    """Geometry relaxation (Sec. 3.3) of the 108-atom 96^3 cell from its +-0.1 bohr displaced
+    positions, WT-type functional, mixed form, to max |F| < 1e-3 Ha/bohr: every line-search
+    point a ground state warm-started from the previous one, plus its forces.  Timed whole;
+    prints one JSON line."""
+    import numpy as np
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    cell, h, sysd, fn, o = make_case(torch, B, Fn, W, "mixed")
+    ro = B.of_default_relax_opts()
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t = time.time()
+        R, F, res = B.of_relax(h, sysd, fn, o, ro, u, phi, allow=(B.OF_ENOCONV,))
+        torch.cuda.synchronize()
+        wall = time.time() - t
+    line = {"metric": "s per geometry relaxation (NLCG + secant on the forces, max |F| < 1e-3 Ha/bohr)",
+            "value": wall, "unit": "s/relaxation", "higher_is_better": False, "dtype": "f64+f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD.replace("ground state + forces", "geometry relaxation")},
+            "result": {"converged": bool(res.converged), "steps": res.steps, "ground_states": res.evaluations,
+                       "s_per_ground_state": wall / max(1, res.evaluations),
+                       "energy_per_atom_ha": res.energy / cell.n_atoms, "max_force": res.max_force,
+                       "max_displacement_bohr": float(np.abs(R - cell.R).max())},
+            "clocks": clk.summary()}
+    B.of_grid_destroy(h)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config5(args):
     """The 3999-atom cell (10x10x10 FCC minus the centre site, +-0.1 bohr displacements, seed 5),
     320^3 grid (32.8 M points): one ground state + forces in the mixed form, timed whole; the
@@ -622,6 +722,10 @@ def main():
         return reference_arm(args, rank, world)
     if args.kernel_case:
         return kernel_case(args)
+    if args.wgc:
+        return wgc(args)
+    if args.relax:
+        return relax_case(args)
     if args.config5:
         return config5(args)
     if args.config3:

@@ -89,10 +89,13 @@ typedef struct {
     double rc;
 } of_system;
 
-/* Kinetic functional T_TF + lambda T_vW + mu T_LR (Eq. KineticEnergyComponents).  For the
- * kernel term (mu != 0) only the density-independent m = n = 0 term of Eq.
- * LR:KineticEnergy:Linearized is used, with exponents alpha, beta and n_terms rational
- * terms (P_r, Q_r) of the fitted kernel (Sec. 3.1, App. A), interleaved re/im. */
+/* Kinetic functional T_TF + lambda T_vW + mu T_LR (Eq. KineticEnergyComponents).  The
+ * kernel term (mu != 0) is Eq. LR:KineticEnergy:Linearized with exponents alpha, beta and
+ * n_terms rational terms per kernel K_mn (Sec. 3.1, App. A; coefficients interleaved re/im,
+ * terms (0,1), (2,3), ... complex-conjugate pairs).  L = 0: the density-independent
+ * m = n = 0 term only (P, Q fit K_00).  L = 2 (WGC): the second-order expansion about
+ * rho_bar = N_e / Omega, every (m, n) with m + n <= 2: K_00 (P, Q), K_10 = K_01 (P10, Q10),
+ * K_20 = K_02 (P20, Q20), K_11 (P11, Q11). */
 typedef struct {
     double lambda;
     double mu;
@@ -101,6 +104,10 @@ typedef struct {
     int n_terms;
     double P[16];
     double Q[16];
+    int L;
+    double P10[16], Q10[16];
+    double P20[16], Q20[16];
+    double P11[16], Q11[16];
 } of_functional;
 
 typedef struct {
@@ -211,12 +218,16 @@ of_status of_pseudocharge(of_grid* g, const of_system* sys, double* b, double* e
 of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double* u,
                                const double* phi, const double* vlr, double* hu);
 
-/* The kernel map V[u] of Eq. MVF (m = n = 0 term, Eq. VLinearResponse:local): builds
- * f = -(1/kf2) L_h u^{2e} for e = alpha, beta, solves the n_terms shifted systems of each
- * (conjugate pairs solved once), writes V_LR (device double*) and T_LR (host double, may be
- * NULL).  n_terms must be even, terms (0,1), (2,3), ... complex-conjugate pairs.  W_ws:
- * device workspace and warm start of n_terms complex fields (one per pair and exponent);
- * NULL uses the handle's own workspace with a zero start. */
+/* The kernel map V[u] of Eq. MVF (Eq. VLinearResponse:local and the T_LR expression after
+ * it).  L = 0: builds f = -(1/kf2) L_h u^{2e} for e = alpha, beta and solves the n_terms
+ * shifted systems of each (conjugate pairs solved once).  L = 2: the 16 potentials K_mn *
+ * u^{2(k+e)} the second-order sum needs (k <= 2; the right-hand side is the density power
+ * itself for (m, n) != (0, 0)), n_terms / 2 shifted solves each, then the sum over m, n, p, q
+ * with C_mnpq of Sec. 2.  Writes V_LR (device double*) and T_LR (host double, may be NULL).
+ * n_terms must be even.  W_ws: device workspace and warm start of
+ * of_lr_workspace_fields(fn) complex fields; NULL uses the handle's own workspace with a
+ * zero start. */
+int of_lr_workspace_fields(const of_functional* fn);
 of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const double* u,
                           double* vlr, double* t_lr, double* W_ws, const of_solve_opts* opts,
                           of_solve_info* info);
@@ -228,6 +239,40 @@ of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const
 of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functional* fn,
                               const of_scf_opts* opts, double* u, double* phi,
                               of_scf_result* res);
+
+/* Geometry relaxation (Sec. 3.3): non-linear CG on the nuclear positions with the
+ * Polak-Ribiere update (restart at beta < 0 or when the direction is not downhill) and a
+ * secant line search on E'(s) = -F(R + s d) . d, started from E'(0) and a trial step that moves
+ * the farthest atom by step0 bohr, stopped at |E'(s)| <= line_tol |E'(0)| or after max_line
+ * points (the last point is accepted).  Every evaluation is a ground state
+ * (of_scf_ground_state with scf, warm-started from the previous evaluation's u) and its forces
+ * (of_forces).  Stops when max_J |F_J| < ftol. */
+typedef struct {
+    double ftol;       /* Ha/bohr; default 1e-3 */
+    int max_steps;     /* default 40 */
+    double step0;      /* bohr; default 0.05 */
+    double line_tol;   /* default 0.1 */
+    int max_line;      /* secant points per step; default 4 */
+} of_relax_opts;
+
+typedef struct {
+    double energy;      /* ground-state energy at the final positions */
+    double max_force;   /* max_J |F_J| there */
+    int steps;          /* NLCG steps taken */
+    int evaluations;    /* ground states (each with forces) computed */
+    int converged;      /* max_force < ftol */
+} of_relax_result;
+
+void of_default_relax_opts(of_relax_opts* o);
+
+/* sys: the starting geometry (host).  u, phi: device double* as in of_scf_ground_state (u in:
+ * initial guess, out: the ground state at the final positions).  R_out (host, 3 n_atoms):
+ * final positions; F_out (host, 3 n_atoms, may be NULL): final forces.  OF_ENOCONV when
+ * max_steps is reached first (R_out, F_out and res still describe the last geometry), or when a
+ * ground state does not converge. */
+of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
+                   const of_scf_opts* scf_opts, const of_relax_opts* opts, double* u, double* phi,
+                   double* R_out, double* F_out, of_relax_result* res);
 
 /* Ground states of ncells independent cells at once (same functional and options): grids[c]
  * (distinct handles, one shared stream), systems[c], u[c], phi[c] as in of_scf_ground_state,

@@ -3,7 +3,8 @@ equilibrium positions of the nuclei by non-linear conjugate gradients with the P
 update and a secant line search, Shewchuk's formulation).
 
 Oracle (test infrastructure only).  Each force evaluation is a full ground state
-(scf_ground_state, warm-started from the previous density) followed by forces().
+(scf_ground_state, warm-started from the density of the previous evaluation) followed by
+forces().
 
 Readings (the paper names the method only):
   * objective E(R), gradient -F(R); the search direction starts along F, then
@@ -68,8 +69,10 @@ def relax(grid: Grid, R0, Z, sigma, rc, fn: Functional, ftol=1e-3, max_steps=40,
             g0 = -float(np.sum(F * F))
         s_a, g_a = 0.0, g0
         s = step0 / np.abs(d).max()
+        u_warm = res.u
         for j in range(max_line):
-            res_s, F_s = evaluate(R + s * d, res.u)
+            res_s, F_s = evaluate(R + s * d, u_warm)
+            u_warm = res_s.u
             evals += 1
             g = -float(np.sum(F_s * d))
             if abs(g) <= line_tol * abs(g0) or j + 1 == max_line:

@@ -40,7 +40,10 @@ class of_system(C.Structure):
 class of_functional(C.Structure):
     _fields_ = [("lambda_", C.c_double), ("mu", C.c_double), ("alpha", C.c_double),
                 ("beta", C.c_double), ("n_terms", C.c_int), ("P", C.c_double * 16),
-                ("Q", C.c_double * 16)]
+                ("Q", C.c_double * 16), ("L", C.c_int),
+                ("P10", C.c_double * 16), ("Q10", C.c_double * 16),
+                ("P20", C.c_double * 16), ("Q20", C.c_double * 16),
+                ("P11", C.c_double * 16), ("Q11", C.c_double * 16)]
 
 
 class of_scf_opts(C.Structure):
@@ -60,6 +63,16 @@ class of_scf_result(C.Structure):
                 ("nlcg_iterations", C.c_int), ("poisson_iterations", C.c_int),
                 ("kernel_iterations", C.c_int), ("line_evaluations", C.c_int),
                 ("converged", C.c_int)]
+
+
+class of_relax_opts(C.Structure):
+    _fields_ = [("ftol", C.c_double), ("max_steps", C.c_int), ("step0", C.c_double),
+                ("line_tol", C.c_double), ("max_line", C.c_int)]
+
+
+class of_relax_result(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_force", C.c_double), ("steps", C.c_int),
+                ("evaluations", C.c_int), ("converged", C.c_int)]
 
 
 class of_kernel_stat(C.Structure):
@@ -84,6 +97,11 @@ _SIGNATURES = {
     "of_hamiltonian_apply": (_I, [_P, C.POINTER(of_functional), _P, _P, _P, _P]),
     "of_lr_potential": (_I, [_P, C.POINTER(of_functional), _D, _P, _P, C.POINTER(_D), _P,
                              C.POINTER(of_solve_opts), C.POINTER(of_solve_info)]),
+    "of_lr_workspace_fields": (_I, [C.POINTER(of_functional)]),
+    "of_default_relax_opts": (None, [C.POINTER(of_relax_opts)]),
+    "of_relax": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional), C.POINTER(of_scf_opts),
+                      C.POINTER(of_relax_opts), _P, _P, C.POINTER(_D), C.POINTER(_D),
+                      C.POINTER(of_relax_result)]),
     "of_scf_ground_state": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional),
                                  C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
@@ -228,13 +246,24 @@ def make_system(R, Z, sigma, rc):
     return s
 
 
-def make_functional(lam, mu, alpha=0.0, beta=0.0, P=(), Q=()):
+def make_functional(lam, mu, alpha=0.0, beta=0.0, P=(), Q=(), L=0, K=None):
+    """of_functional record.  P, Q: the K_00 terms; L = 2 with K = {"10": (P, Q), "20": ...,
+    "11": ...}: the density-dependent classes (same number of terms each)."""
     f = of_functional()
     f.lambda_, f.mu, f.alpha, f.beta = float(lam), float(mu), float(alpha), float(beta)
     f.n_terms = len(P)
-    for k, (p, q) in enumerate(zip(P, Q)):
-        f.P[2 * k], f.P[2 * k + 1] = complex(p).real, complex(p).imag
-        f.Q[2 * k], f.Q[2 * k + 1] = complex(q).real, complex(q).imag
+    f.L = int(L)
+
+    def fill(dstP, dstQ, P, Q):
+        for k, (p, q) in enumerate(zip(P, Q)):
+            dstP[2 * k], dstP[2 * k + 1] = complex(p).real, complex(p).imag
+            dstQ[2 * k], dstQ[2 * k + 1] = complex(q).real, complex(q).imag
+
+    fill(f.P, f.Q, P, Q)
+    for c, (Pc, Qc) in (K or {}).items():
+        if len(Pc) != len(P):
+            raise ValueError(f"class {c}: {len(Pc)} terms, K_00 has {len(P)}")
+        fill(getattr(f, "P" + c), getattr(f, "Q" + c), Pc, Qc)
     return f
 
 
@@ -247,6 +276,30 @@ def of_pseudocharge(h, sys, b):
 def of_hamiltonian_apply(h, fn, u, phi, vlr, hu):
     return _check(load().of_hamiltonian_apply(h, C.byref(fn), _ptr(u), _ptr(phi), _ptr(vlr),
                                               _ptr(hu)), "of_hamiltonian_apply")
+
+
+def of_default_relax_opts():
+    o = of_relax_opts()
+    load().of_default_relax_opts(C.byref(o))
+    return o
+
+
+def of_relax(h, sys, fn, scf_opts, relax_opts, u, phi, allow=()):
+    """Relaxes the geometry of sys; returns (R (n, 3), F (n, 3), of_relax_result)."""
+    n = sys.n_atoms
+    R = (C.c_double * (3 * n))()
+    F = (C.c_double * (3 * n))()
+    res = of_relax_result()
+    st = load().of_relax(h, C.byref(sys), C.byref(fn), C.byref(scf_opts) if scf_opts else None,
+                         C.byref(relax_opts) if relax_opts else None, _ptr(u), _ptr(phi), R, F,
+                         C.byref(res))
+    if st != OF_OK and st not in allow:
+        _check(st, "of_relax")
+    return (np.array(R[:]).reshape(n, 3), np.array(F[:]).reshape(n, 3), res)
+
+
+def of_lr_workspace_fields(fn):
+    return int(load().of_lr_workspace_fields(C.byref(fn)))
 
 
 def of_lr_potential(h, fn, kf2, u, vlr, W=None, opts=None):

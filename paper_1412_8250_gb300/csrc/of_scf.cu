@@ -252,6 +252,66 @@ __global__ void k_powers(long long n, const double* u, double two_a, double two_
     }
 }
 
+// The density powers of the second-order kernel term: g[j] = u^{2(j + alpha)} and
+// g[3 + j] = u^{2(j + beta)}, j = 0..2 (u raised to the floor)
+__global__ void k_powers6(long long n, const double* u, double two_a, double two_b, double* g) {
+    GRID_LOOP(i, n) {
+        const double uf = fmax(u[i], OF_U_FLOOR);
+        const double rho = uf * uf;
+        const double a = pow(uf, two_a), b = pow(uf, two_b);
+        g[i] = a;
+        g[n + i] = a * rho;
+        g[2 * n + i] = a * rho * rho;
+        g[3 * n + i] = b;
+        g[4 * n + i] = b * rho;
+        g[5 * n + i] = b * rho * rho;
+    }
+}
+
+// Second-order (L = 2) kernel term, summed over potentials: the potential p is
+// V_p = sum over its conjugate pairs of 2 Re W[p][k]; with g the six density powers,
+//   V_LR = (C_F / rho) sum_p V_p sum_j cv[p][j] g_j,   sum of sum_p V_p sum_j ct[p][j] g_j,
+// cv and ct holding C_mnpq (times m - p + alpha or n - q + beta for cv) of the terms that
+// pair potential p with power j.
+constexpr int LR_MAX_POT = 16;
+struct LrSum {
+    int npot, npairs;
+    const double2* W[LR_MAX_POT][4];
+    double cv[LR_MAX_POT][6];
+    double ct[LR_MAX_POT][6];
+};
+__global__ void __launch_bounds__(256) k_lr_assemble2(long long n, const double* u, const double* g,
+                                                      LrSum S, double* vlr, RedCtx rc) {
+    double acc[1] = {0.0};
+    GRID_LOOP(i, n) {
+        double gj[6];
+#pragma unroll
+        for (int j = 0; j < 6; ++j) gj[j] = g[j * n + i];
+        double vl = 0.0, te = 0.0;
+#pragma unroll
+        for (int p = 0; p < LR_MAX_POT; ++p) {
+            if (p < S.npot) {
+                double V = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < S.npairs) V += 2.0 * S.W[p][k][i].x;
+                double a = 0.0, b = 0.0;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    a = fma(S.cv[p][j], gj[j], a);
+                    b = fma(S.ct[p][j], gj[j], b);
+                }
+                vl = fma(a, V, vl);
+                te = fma(b, V, te);
+            }
+        }
+        const double uf = fmax(u[i], OF_U_FLOOR);
+        vlr[i] = OF_CF * vl / (uf * uf);
+        acc[0] += te;
+    }
+    grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
 // V_LR = C_F [alpha u^{2(alpha-1)} V_beta + beta u^{2(beta-1)} V_alpha], V_e = sum over
 // conjugate pairs of 2 Re W ; sum of u^{2 alpha} V_beta + u^{2 beta} V_alpha.
 struct PairPtrs {
@@ -670,7 +730,106 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
     return converged;
 }
 
-// Kernel map V[u] (Eq. MVF, m = n = 0 term): V_LR into vlr, returns T_LR / C_F / dV sum.
+// Complex fields of the kernel map's warm starts: one per potential and conjugate pair.
+static int lr_ws_fields(const of_functional* fn) {
+    return (fn->L == 2 ? 16 : 2) * (fn->n_terms / 2);
+}
+
+static void require_conjugate_pairs(const double* P, const double* Q, int n_terms, const char* what) {
+    for (int k = 0; k < n_terms; k += 2)
+        OF_REQUIRE(P[2 * k] == P[2 * k + 2] && P[2 * k + 1] == -P[2 * k + 3] &&
+                       Q[2 * k] == Q[2 * k + 2] && Q[2 * k + 1] == -Q[2 * k + 3],
+                   OF_EINVAL, "%s: kernel coefficients %d and %d are not complex conjugates", what, k,
+                   k + 1);
+}
+
+static void add_info(of_solve_info* out, const of_solve_info& a) {
+    if (!out) return;
+    out->iterations += a.iterations;
+    out->refinements += a.refinements;
+    out->rel_residual = std::max(out->rel_residual, a.rel_residual);
+}
+
+// Second-order kernel map (L = 2): the 16 potentials K_mn * u^{2(k+e)} that Eq.
+// VLinearResponse:local needs, each the sum of n_terms / 2 shifted solves (one per conjugate
+// pair), then V_LR and the T_LR sum from them.  Returns the sum s with T_LR = C_F dV s / 2.
+static double lr_potential_l2(of_grid* g, const of_functional* fn, double kf2, const double* u,
+                              double* vlr, double* Wws, const KrylovOpts& ko, ScfStats& st,
+                              of_solve_info* info_out) {
+    const long long n = g->d.n;
+    const int nb = vb(n);
+    const int npairs = fn->n_terms / 2;
+    const double* PC[4] = {fn->P, fn->P10, fn->P20, fn->P11};
+    const double* QC[4] = {fn->Q, fn->Q10, fn->Q20, fn->Q11};
+    const char* names[4] = {"K_00", "K_10", "K_20", "K_11"};
+    for (int c = 0; c < 4; ++c) require_conjugate_pairs(PC[c], QC[c], fn->n_terms, names[c]);
+    // class of K_mn (K_mn = K_nm): 00, 10, 20, 11
+    auto cls = [](int m, int n_) { return m + n_ == 0 ? 0 : (m == 1 && n_ == 1) ? 3 : m + n_; };
+    const double kF = 0.5 * std::sqrt(kf2);
+    const double rho_bar = kF * kF * kF / (3.0 * M_PI * M_PI);
+    auto fact = [](int k) { return k == 2 ? 2.0 : 1.0; };
+    auto binom = [](int m, int p) { return (m == 2 && p == 1) ? 2.0 : 1.0; };
+    // the potentials: (class, exponent 0 = alpha / 1 = beta, k), and the coefficient tables
+    int pot_of[4][2][3];
+    for (auto& a : pot_of) for (auto& b : a) for (int& c : b) c = -1;
+    int pot_cls[LR_MAX_POT], pot_e[LR_MAX_POT], pot_k[LR_MAX_POT];
+    LrSum S{};
+    S.npairs = npairs;
+    auto pot = [&](int c, int e, int k) {
+        if (pot_of[c][e][k] < 0) {
+            OF_REQUIRE(S.npot < LR_MAX_POT, OF_EINVAL, "kernel map: too many potentials");
+            pot_of[c][e][k] = S.npot;
+            pot_cls[S.npot] = c;
+            pot_e[S.npot] = e;
+            pot_k[S.npot] = k;
+            ++S.npot;
+        }
+        return pot_of[c][e][k];
+    };
+    for (int m = 0; m <= 2; ++m)
+        for (int nn = 0; m + nn <= 2; ++nn)
+            for (int p = 0; p <= m; ++p)
+                for (int q = 0; q <= nn; ++q) {
+                    // C_mnpq = (-1)^{p+q} / (m! n!) binom(m,p) binom(n,q) rho_bar^{p+q-m-n} (Sec. 2)
+                    const double C = ((p + q) % 2 ? -1.0 : 1.0) / (fact(m) * fact(nn)) * binom(m, p) *
+                                     binom(nn, q) * std::pow(rho_bar, (double)(p + q - m - nn));
+                    const int c = cls(m, nn), ka = m - p, kb = nn - q;
+                    const int pb = pot(c, 1, kb), pa = pot(c, 0, ka);
+                    // u^{2(m-p+alpha)} V_{mnq beta} and u^{2(n-q+beta)} V_{mnp alpha}
+                    S.cv[pb][ka] += C * (ka + fn->alpha);
+                    S.ct[pb][ka] += C;
+                    S.cv[pa][3 + kb] += C * (kb + fn->beta);
+                    S.ct[pa][3 + kb] += C;
+                }
+    double* scratch = (double*)ws(g, WS_LR, sizeof(double) * 8 * (size_t)n);
+    double* gp = scratch;            // six density powers
+    double* f00 = scratch + 6 * n;   // -(1/kf2) L_h u^{2 alpha}, -(1/kf2) L_h u^{2 beta}
+    launch(k_powers6, nb, 256, g->stream, n, u, 2.0 * fn->alpha, 2.0 * fn->beta, gp);
+    OF_LAUNCH_CHECK();
+    launch_stencil<double, 2>(g, g->w64, OpScaledLap{gp, f00, -1.0 / kf2});
+    launch_stencil<double, 2>(g, g->w64, OpScaledLap{gp + 3 * n, f00 + n, -1.0 / kf2});
+    for (int p = 0; p < S.npot; ++p) {
+        const int c = pot_cls[p], e = pot_e[p], k = pot_k[p];
+        // right-hand side: the density power itself, or -(1/kf2) L_h of it for K_00 (Sec. 3.1)
+        const double* f = c == 0 ? f00 + (size_t)e * n : gp + (size_t)(3 * e + k) * n;
+        for (int r = 0; r < npairs; ++r) {
+            const double2 P = make_double2(PC[c][4 * r], PC[c][4 * r + 1]);
+            const double2 Q = make_double2(QC[c][4 * r], QC[c][4 * r + 1]);
+            double2* W = (double2*)Wws + (size_t)(p * npairs + r) * n;
+            of_solve_info si{};
+            const of_status s1 = shifted(g, f, P, Q, kf2, W, ko, &si);
+            if (s1 != OF_OK && s1 != OF_ENOCONV) throw Error{s1};
+            st.kernel += si.iterations;
+            add_info(info_out, si);
+            S.W[p][r] = W;
+        }
+    }
+    launch(k_lr_assemble2, nb, 256, g->stream, n, u, (const double*)gp, S, vlr, red_ctx(g, SC_TLR));
+    OF_LAUNCH_CHECK();
+    return sc(g, SC_TLR);
+}
+
+// Kernel map V[u] (Eq. MVF): V_LR into vlr, returns the sum s with T_LR = C_F dV s / 2.
 static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2, const double* u,
                                 double* vlr, double* Wws, const KrylovOpts& ko, ScfStats& st,
                                 of_solve_info* info_out) {
@@ -678,11 +837,9 @@ static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2,
     const int nb = vb(n);
     OF_REQUIRE(fn->n_terms >= 2 && fn->n_terms <= 8 && fn->n_terms % 2 == 0, OF_EINVAL,
                "kernel term needs 2..8 coefficients in conjugate pairs (got %d)", fn->n_terms);
-    for (int k = 0; k < fn->n_terms; k += 2) {
-        OF_REQUIRE(fn->P[2 * k] == fn->P[2 * k + 2] && fn->P[2 * k + 1] == -fn->P[2 * k + 3] &&
-                       fn->Q[2 * k] == fn->Q[2 * k + 2] && fn->Q[2 * k + 1] == -fn->Q[2 * k + 3],
-                   OF_EINVAL, "kernel coefficients %d and %d are not complex conjugates", k, k + 1);
-    }
+    OF_REQUIRE(fn->L == 0 || fn->L == 2, OF_EINVAL, "kernel expansion order L = %d (0 or 2)", fn->L);
+    if (fn->L == 2) return lr_potential_l2(g, fn, kf2, u, vlr, Wws, ko, st, info_out);
+    require_conjugate_pairs(fn->P, fn->Q, fn->n_terms, "K_00");
     const int npairs = fn->n_terms / 2;
     double* scratch = (double*)ws(g, WS_LR, sizeof(double) * 4 * (size_t)n);
     double *ga = scratch, *gb = scratch + n, *fa = scratch + 2 * n, *fb = scratch + 3 * n;
@@ -809,16 +966,15 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
     double* Wws = nullptr;
     double *Shist = nullptr, *Yhist = nullptr, *Vprev = nullptr, *fcur = nullptr, *fprev = nullptr;
     if (lr) {
-        const int npairs = fn->n_terms / 2;
         // Anderson history (S, Y), V_{k-1}, f_k, f_{k-1}, then the kernel-solve warm starts
-        double* hist = (double*)ws(g, WS_AND, sizeof(double) * (size_t)n * (2 * m + 3 + 4 * npairs));
+        double* hist = (double*)ws(g, WS_AND, sizeof(double) * (size_t)n * (2 * m + 3 + 2 * lr_ws_fields(fn)));
         Shist = hist;
         Yhist = hist + (size_t)m * n;
         Vprev = hist + (size_t)2 * m * n;
         fcur = Vprev + n;
         fprev = fcur + n;
-        Wws = fprev + n;   // 2 * npairs complex fields = 4 * npairs doubles per point
-        OF_CUDA(cudaMemsetAsync(Wws, 0, sizeof(double) * n * 4 * npairs, g->stream));
+        Wws = fprev + n;   // lr_ws_fields complex fields
+        OF_CUDA(cudaMemsetAsync(Wws, 0, sizeof(double2) * n * lr_ws_fields(fn), g->stream));
     }
 
     double t_lr_sum = 0.0;
@@ -943,6 +1099,8 @@ of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double
     }
 }
 
+int of_lr_workspace_fields(const of_functional* fn) { return fn ? lr_ws_fields(fn) : 0; }
+
 of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const double* u,
                           double* vlr, double* t_lr, double* W_ws, const of_solve_opts* opts,
                           of_solve_info* info) {
@@ -951,7 +1109,7 @@ of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const
         if (info) std::memset(info, 0, sizeof(*info));
         double* W = W_ws;
         if (!W) {
-            const size_t bytes = sizeof(double2) * (size_t)fn->n_terms * g->d.n;
+            const size_t bytes = sizeof(double2) * (size_t)lr_ws_fields(fn) * g->d.n;
             W = (double*)ws(g, WS_AND, bytes);
             OF_CUDA(cudaMemsetAsync(W, 0, bytes, g->stream));
         }
@@ -992,6 +1150,103 @@ of_status of_scf_ground_state_batched(int ncells, of_grid* const* grids, const o
             }
             return OF_OK;
         });
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+void of_default_relax_opts(of_relax_opts* o) {
+    if (!o) return;
+    o->ftol = 1e-3;
+    o->max_steps = 40;
+    o->step0 = 0.05;
+    o->line_tol = 0.1;
+    o->max_line = 4;
+}
+
+of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
+                   const of_scf_opts* scf_opts, const of_relax_opts* opts, double* u, double* phi,
+                   double* R_out, double* F_out, of_relax_result* res) {
+    if (!g || !sys || !sys->R || sys->n_atoms < 1 || !fn || !u || !phi || !R_out || !res) {
+        set_error("of_relax: null argument");
+        return OF_EINVAL;
+    }
+    try {
+        of_scf_opts so;
+        if (scf_opts) so = *scf_opts; else of_default_scf_opts(&so);
+        of_relax_opts ro;
+        if (opts) ro = *opts; else of_default_relax_opts(&ro);
+        OF_REQUIRE(ro.ftol > 0 && ro.step0 > 0 && ro.max_line >= 1 && ro.max_steps >= 0, OF_EINVAL,
+                   "of_relax: bad options");
+        std::memset(res, 0, sizeof(*res));
+        const size_t m3 = 3 * (size_t)sys->n_atoms;
+        std::vector<double> R(sys->R, sys->R + m3), F(m3), Fp(m3), d(m3), Rs(m3), Fs(m3);
+        of_system sx = *sys;
+        of_scf_result gs{};
+        auto dot = [&](const std::vector<double>& a, const std::vector<double>& b) {
+            double s = 0.0;
+            for (size_t i = 0; i < m3; ++i) s += a[i] * b[i];
+            return s;
+        };
+        auto maxabs = [&](const std::vector<double>& a) {
+            double s = 0.0;
+            for (double v : a) s = std::max(s, std::fabs(v));
+            return s;
+        };
+        // ground state (warm-started from u) and forces at positions Rx
+        auto evaluate = [&](const std::vector<double>& Rx, std::vector<double>& Fx) {
+            sx.R = Rx.data();
+            scf(g, &sx, fn, &so, u, phi, &gs);
+            ++res->evaluations;
+            OF_REQUIRE(gs.converged, OF_ENOCONV,
+                       "of_relax: ground state %d not converged (nlcg residual %.3e, fixed-point error %.3e)",
+                       res->evaluations, gs.nlcg_residual, gs.fp_error);
+            forces(g, &sx, phi, Fx.data());
+        };
+        evaluate(R, F);
+        d = F;
+        bool have_prev = false;
+        while (res->steps < ro.max_steps && maxabs(F) >= ro.ftol) {
+            if (have_prev) {   // Polak-Ribiere, restarted at beta < 0
+                double num = 0.0;
+                for (size_t i = 0; i < m3; ++i) num += F[i] * (F[i] - Fp[i]);
+                const double beta = std::max(0.0, num / dot(Fp, Fp));
+                for (size_t i = 0; i < m3; ++i) d[i] = F[i] + beta * d[i];
+            }
+            double g0 = -dot(F, d);   // E'(0) along d
+            if (!(g0 < 0.0)) {        // not downhill: restart along F
+                d = F;
+                g0 = -dot(F, F);
+            }
+            double sa = 0.0, ga = g0, s = ro.step0 / maxabs(d);
+            for (int j = 0; j < ro.max_line; ++j) {
+                for (size_t i = 0; i < m3; ++i) Rs[i] = R[i] + s * d[i];
+                evaluate(Rs, Fs);
+                const double gv = -dot(Fs, d);
+                if (std::fabs(gv) <= ro.line_tol * std::fabs(g0) || j + 1 == ro.max_line) break;
+                // secant root of E'(s) through the last two points; without positive curvature
+                // seen yet, a longer step
+                const double sn = gv > ga ? s - gv * (s - sa) / (gv - ga) : 2.0 * s;
+                sa = s;
+                ga = gv;
+                s = sn;
+            }
+            Fp = F;
+            R = Rs;
+            F = Fs;
+            have_prev = true;
+            ++res->steps;
+        }
+        res->energy = gs.energy;
+        res->max_force = maxabs(F);
+        res->converged = res->max_force < ro.ftol;
+        std::copy(R.begin(), R.end(), R_out);
+        if (F_out) std::copy(F.begin(), F.end(), F_out);
+        if (!res->converged) {
+            set_error("of_relax: max force %.3e after %d steps", res->max_force, res->steps);
+            return OF_ENOCONV;
+        }
+        return OF_OK;
     } catch (const Error& e) {
         return e.code;
     }

@@ -258,6 +258,24 @@ def test_lr_potential(prec):
         assert abs(T - Tref) <= 1e-9 * abs(Tref)
 
 
+@pytest.mark.parametrize("prec", [B.OF_F64, B.OF_F32])
+def test_lr_potential_second_order_wgc(prec):
+    # L = 2: 16 potentials (32 shifted solves) and the sum over m, n, p, q against the oracle
+    cell = W.al4_lr_cell(points_per_cell=20)
+    with G(cell.n, cell.L) as g:
+        u = W.random_field(g.shape, seed=6, kind="smooth")
+        u *= np.sqrt(cell.n_electrons / (g.grid.dV * np.sum(u * u)))
+        kf2 = Fn.kf2(cell.n_electrons, g.grid.volume)
+        fn = Fn.wgc()
+        assert B.of_lr_workspace_fields(fn) == 32 and B.of_lr_workspace_fields(Fn.wt()) == 4
+        v = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        T, info = B.of_lr_potential(g.h, fn, kf2, dev(u), v, opts=_opts(prec, 1e-12))
+        Vref, Tref, _ = O.lr_potential_wgc(u, g.grid, O.wgc_functional(), kf2)
+        assert np.max(np.abs(host(v) - Vref)) <= 1e-9 * np.max(np.abs(Vref))
+        assert abs(T - Tref) <= 1e-9 * abs(Tref)
+        assert info.iterations > 0
+
+
 @pytest.mark.parametrize("cell", [W.al4_displaced_cell(), W.al108_cell()], ids=["al4d", "al108"])
 def test_forces_for_given_potential(cell):
     with G(cell.n, cell.L) as g:

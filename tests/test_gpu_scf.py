@@ -91,6 +91,51 @@ def test_wt_small_cell_against_golden(prec, inexact):
     assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
 
 
+@pytest.mark.parametrize("prec", [B.OF_F64, B.OF_F32])
+def test_wgc_second_order_kernel_small_cell_live_oracle(prec):
+    # full WGC (L = 2, every class of App. A) on the soft-ion 4-atom cell at 16^3
+    cell = W.al4_lr_cell(points_per_cell=16)
+    grid = O.Grid(cell.n, cell.L, 6)
+    ref = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.wgc_functional(),
+                             nlcg_tol=1e-8, fp_tol=1e-7, anderson_m=3, zeta=1.0)
+    Fref = O.forces(ref.phi, cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    res, F, u, phi = _run(cell, Fn.wgc(), prec, nlcg_tol=1e-8, anderson_m=3, anderson_zeta=1.0)
+    assert res.converged, (res.fp_error, res.nlcg_residual)
+    assert abs(res.energy - ref.energy) / cell.n_atoms <= E_TOL
+    assert abs(res.e_lr - ref.terms["lr"]) / cell.n_atoms <= 1e-5
+    assert np.max(np.abs(F - Fref)) <= F_TOL
+
+
+@pytest.mark.parametrize("prec", [B.OF_F64, B.OF_F32])
+def test_relaxation_matches_oracle(prec):
+    # geometry relaxation (Sec. 3.3): one atom of the 4-atom TFW cell moved by 0.25 bohr, both
+    # sides relaxed to max |F| < 1e-5 with the same NLCG / secant steps
+    from oracle.relax import relax
+    cell = W.al4_cell(points_per_cell=12)
+    R0 = cell.R.copy()
+    R0[0, 0] += 0.25
+    grid = O.Grid(cell.n, cell.L, 6)
+    ref = relax(grid, R0, cell.Z, cell.sigma, cell.rc, O.tfw_functional(), ftol=1e-5, nlcg_tol=1e-9)
+    h = B.of_grid_create(cell.n, cell.L, 6, torch.cuda.current_stream())
+    try:
+        so = B.of_default_scf_opts()
+        so.precision = prec
+        so.nlcg_tol = 1e-9
+        ro = B.of_default_relax_opts()
+        ro.ftol = 1e-5
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(u)
+        R, F, res = B.of_relax(h, B.make_system(R0, cell.Z, cell.sigma, cell.rc), Fn.tfw(), so, ro,
+                               u, phi)
+    finally:
+        B.of_grid_destroy(h)
+    assert res.converged and res.max_force < 1e-5 and np.abs(F).max() == res.max_force
+    assert res.steps == ref.steps and res.evaluations == ref.evaluations
+    assert abs(res.energy - ref.energy) / cell.n_atoms <= E_TOL
+    assert np.abs((R - R[0]) - (ref.R - ref.R[0])).max() < 2e-4
+    assert np.abs(R - ref.R).max() < 1e-3
+
+
 def test_line_searches_reach_the_same_ground_state():
     # Brent on the energy (the paper's line search) and the slope search (root of dE/ds from
     # the same line model) stop the NLCG at the same minimiser; the slope search needs fewer
