@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--relax", action="store_true",
                    help="measure a geometry relaxation of the 108-atom 96^3 cell instead of the "
                         "benchmark step")
+    p.add_argument("--mixing-study", action="store_true",
+                   help="fixed point on V_LR vs on u, Anderson m and zeta, on the 108-atom cell")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
@@ -494,6 +496,41 @@ def relax_case(args):
     return 0
 
 
+def mixing_study(args):
+    """Sec. 5.3 as a benchmark: the 108-atom 96^3 ground state (WT-type, mixed form) with the
+    outer fixed point on V_LR (the method) and on u (Table MixComparison's alternative), each
+    with Anderson history m and mixing parameter zeta in {(3, 1.0), (3, 0.5), (7, 0.3)}: outer
+    iterations, NLCG steps, seconds, energy.  Prints one JSON line."""
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    cell, h, sysd, fn, o = make_case(torch, B, Fn, W, "mixed")
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    runs = []
+    with ClockSampler(0) as clk:
+        for fpm, name in ((B.OF_FP_VLR, "V_LR"), (B.OF_FP_U, "u")):
+            for m, zeta in ((3, 1.0), (3, 0.5), (7, 0.3)):
+                o.fixed_point, o.anderson_m, o.anderson_zeta = fpm, m, zeta
+                u.fill_(1.0)
+                phi.zero_()
+                torch.cuda.synchronize()
+                t = time.time()
+                res = B.of_scf_ground_state(h, sysd, fn, o, u, phi, allow=(B.OF_ENOCONV,))
+                torch.cuda.synchronize()
+                runs.append({"fixed_point": name, "m": m, "zeta": zeta, "s": time.time() - t,
+                             "converged": bool(res.converged), "outer": res.outer_iterations,
+                             "nlcg_steps": res.nlcg_iterations, "fp_error": res.fp_error,
+                             "energy_per_atom_ha": res.energy / cell.n_atoms})
+    line = {"metric": "outer iterations and s per ground state: fixed point on V_LR vs on u, Anderson m / zeta",
+            "unit": "s/ground-state", "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace(", ground state + forces", ", ground state")},
+            "runs": runs, "clocks": clk.summary()}
+    B.of_grid_destroy(h)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def config5(args):
     """The 3999-atom cell (10x10x10 FCC minus the centre site, +-0.1 bohr displacements, seed 5),
     320^3 grid (32.8 M points): one ground state + forces in the mixed form, timed whole; the
@@ -726,6 +763,8 @@ def main():
         return wgc(args)
     if args.relax:
         return relax_case(args)
+    if args.mixing_study:
+        return mixing_study(args)
     if args.config5:
         return config5(args)
     if args.config3:

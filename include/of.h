@@ -48,6 +48,12 @@ typedef enum {
     OF_LINE_SLOPE = 1
 } of_line_search;
 
+/* Variable of the outer fixed point with Anderson mixing (App. D). */
+typedef enum {
+    OF_FP_VLR = 0,
+    OF_FP_U = 1
+} of_fixed_point;
+
 typedef struct of_grid of_grid;
 typedef struct of_precond of_precond;   /* learned preconditioner (of_precond_create) */
 
@@ -128,6 +134,8 @@ typedef struct {
                                max(nlcg_tol, nlcg_tol_rel * fixed-point error of step k-1);
                                0 (default): every inner solve to nlcg_tol */
     int line_search;        /* of_line_search; default OF_LINE_SLOPE */
+    int fixed_point;        /* OF_FP_VLR (default, Sec. 3.3.1): mix V_LR; OF_FP_U: mix u, the
+                               alternative of Sec. 5.3 (Table MixComparison) */
 } of_scf_opts;
 
 typedef struct {

@@ -209,9 +209,16 @@ def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c
 
 def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_tol=1e-7,
                      fp_tol=1e-7, max_outer=50, anderson_m=7, zeta=0.3, n_restart=50,
-                     max_nlcg=5000):
+                     max_nlcg=5000, fixed_point="V"):
     """Fixed point V_LR = V[U(V_LR)] (Eqs. FixedPoint:Map1, MVF) with Anderson mixing
-    (App. D); V_LR,0 = 0.  Returns the ground state and its energy."""
+    (App. D); V_LR,0 = 0.  Returns the ground state and its energy.
+
+    fixed_point="u": the alternative the paper compares in Sec. 5.3 (Table MixComparison), the
+    fixed point u = U(V[u]) with Anderson mixing of u (renormalised to N_e before each map),
+    error ||U(V[u_k]) - u_k|| / ||U(V[u_k])||, the energy taken at u = U(V[u_k])."""
+    if fixed_point == "u" and fn.mu != 0.0:
+        return _scf_ground_state_u(grid, R, Z, sigma, rc, fn, u0, nlcg_tol, fp_tol, max_outer,
+                                   anderson_m, zeta, n_restart, max_nlcg)
     Ne = float(np.sum(Z))
     b = pseudocharge(R, Z, sigma, rc, grid)
     phi_b = poisson_solve(b, grid)
@@ -238,4 +245,33 @@ def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_
         V = anderson_update(V_hist, f_hist, zeta, anderson_m)
     E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c)
     return ScfResult(u=u, phi=phi, V_LR=V, energy=E, terms=terms, outer_iterations=len(its),
+                     nlcg_iterations=its, fp_errors=errs)
+
+
+def _scf_ground_state_u(grid, R, Z, sigma, rc, fn, u0, nlcg_tol, fp_tol, max_outer, anderson_m,
+                        zeta, n_restart, max_nlcg):
+    Ne = float(np.sum(Z))
+    b = pseudocharge(R, Z, sigma, rc, grid)
+    phi_b = poisson_solve(b, grid)
+    E_self = self_energy(R, Z, sigma, rc, grid)
+    E_c = repulsive_correction(R, Z, sigma, grid.L)
+    kf2 = kf2_of(Ne, grid.volume)
+    x = np.full(grid.shape, sqrt(Ne / grid.volume)) if u0 is None else u0.copy()
+    x_hist, f_hist, errs, its = [], [], [], []
+    for k in range(max_outer):
+        x = x * sqrt(Ne / inner(x, x, grid))
+        V, _, _, _ = lr_potential(x, grid, fn, kf2)
+        u, phi, info = nlcg(x, V, b, phi_b, grid, fn, Ne, tol=nlcg_tol, max_iter=max_nlcg,
+                            n_restart=n_restart)
+        its.append(info.iterations)
+        f = u - x
+        errs.append(float(np.linalg.norm(f) / np.linalg.norm(u)))
+        x_hist.append(x)
+        f_hist.append(f)
+        if errs[-1] < fp_tol:
+            break
+        x = anderson_update(x_hist, f_hist, zeta, anderson_m)
+    V_u, T_LR, _, _ = lr_potential(u, grid, fn, kf2)
+    E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c)
+    return ScfResult(u=u, phi=phi, V_LR=V_u, energy=E, terms=terms, outer_iterations=len(its),
                      nlcg_iterations=its, fp_errors=errs)

@@ -982,23 +982,45 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
     double err = 0.0;
     bool inner_ok = true;
     double prev_err = 1.0;
+    // fixed point on u instead of V_LR (Sec. 5.3, Table MixComparison): the mixed iterate is
+    // u_k (kept in v.Vhat), the map u_k -> U(V[u_k])
+    const bool fp_u = lr && o->fixed_point == OF_FP_U;
+    double* xk = fp_u ? v.Vhat : v.V;   // the iterate Anderson mixes
     for (int k = 0; k < std::max(1, o->fp_max_iter); ++k) {
         // inexact inner solves while the outer iteration is far from its fixed point
         const double tol_k = (lr && o->nlcg_tol_rel > 0.0)
                                  ? std::max(o->nlcg_tol, o->nlcg_tol_rel * prev_err)
                                  : o->nlcg_tol;
+        // the kernel map's tolerance: 1e-3 of the previous fixed-point error, at most 1e-6
+        KrylovOpts kk = ko;
+        kk.tol = std::max(ko.tol, std::min(1e-6, 1e-3 * prev_err));
+        if (fp_u) {
+            // u_k normalised to N_e (mixing does not keep the norm), V = V[u_k], u_k kept
+            launch(k_sum_product, nb, 256, g->stream, n, u, u, red_ctx(g, SC_UU));
+            OF_LAUNCH_CHECK();
+            const double uu = sc(g, SC_UU) * dV;
+            OF_REQUIRE(uu > 0 && std::isfinite(uu), OF_EBREAKDOWN, "fixed point on u: iterate has norm %g", uu);
+            launch(k_scale, nb, 256, g->stream, n, u, std::sqrt(Ne / uu));
+            OF_LAUNCH_CHECK();
+            t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.V, Wws, kk, st, nullptr);
+            OF_CUDA(cudaMemcpyAsync(xk, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+        }
         inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, tol_k, o->nlcg_max_iter,
                         std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3,
                         o->line_search, po, st);
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
-        // inexact kernel map while the fixed point is far off: the shifted solves stop at
-        // 1e-3 of the previous fixed-point error (at most 1e-6, never below the requested
-        // tolerance); the converged map is evaluated to ~1e-9
-        KrylovOpts kk = ko;
-        kk.tol = std::max(ko.tol, std::min(1e-6, 1e-3 * prev_err));
-        t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, kk, st, nullptr);
-        launch(k_fp_residual, nb, 256, g->stream, n, v.Vhat, v.V, fcur, red_ctx(g, SC_FP));
+        if (fp_u) {
+            // f = U(V[u_k]) - u_k
+            launch(k_fp_residual, nb, 256, g->stream, n, (const double*)u, (const double*)xk, fcur,
+                   red_ctx(g, SC_FP));
+        } else {
+            // inexact kernel map while the fixed point is far off (the shifted solves stop at
+            // 1e-3 of the previous fixed-point error, at most 1e-6, never below the requested
+            // tolerance); the converged map is evaluated to ~1e-9.  f = V[u_k] - V_k
+            t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, kk, st, nullptr);
+            launch(k_fp_residual, nb, 256, g->stream, n, v.Vhat, v.V, fcur, red_ctx(g, SC_FP));
+        }
         OF_LAUNCH_CHECK();
         double nf[2];
         fetch_scalars(g, SC_FP, 2, nf);
@@ -1009,16 +1031,16 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
                     k, err, st.nlcg, st.poisson, st.kernel);
         if (err < o->fp_tol && tol_k <= o->nlcg_tol) break;
         if (k + 1 >= o->fp_max_iter) break;
-        // history: S = V_k - V_{k-1}, Y = f_k - f_{k-1}
+        // history: S = x_k - x_{k-1}, Y = f_k - f_{k-1} (x = V_LR, or u)
         if (k > 0 && m > 0) {
             const int slot = hist_head;
-            launch(k_diff, nb, 256, g->stream, n, v.V, Vprev, Shist + (size_t)slot * n);
+            launch(k_diff, nb, 256, g->stream, n, xk, Vprev, Shist + (size_t)slot * n);
             launch(k_diff, nb, 256, g->stream, n, fcur, fprev, Yhist + (size_t)slot * n);
             OF_LAUNCH_CHECK();
             hist_head = (hist_head + 1) % m;
             hist_count = std::min(hist_count + 1, m);
         }
-        OF_CUDA(cudaMemcpyAsync(Vprev, v.V, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+        OF_CUDA(cudaMemcpyAsync(Vprev, xk, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
         OF_CUDA(cudaMemcpyAsync(fprev, fcur, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
         HistPtrs H{};
         int j = hist_count;
@@ -1045,9 +1067,12 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         }
         H.m = j;
         for (int a = 0; a < j; ++a) H.g[a] = gamma[a];
-        launch(k_anderson_update, nb, 256, g->stream, n, v.V, fcur, o->anderson_zeta, H);
+        launch(k_anderson_update, nb, 256, g->stream, n, xk, fcur, o->anderson_zeta, H);
         OF_LAUNCH_CHECK();
+        if (fp_u) OF_CUDA(cudaMemcpyAsync(u, xk, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
     }
+    // u-mixing ends on u = U(V[u_k]); its own T_LR for the energy
+    if (fp_u) t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, ko, st, nullptr);
     energy_terms(g, fn, u, v.b, phi, t_lr_sum, e_self, e_c, res);
     res->fp_error = err;
     res->nlcg_residual = st.last_residual;

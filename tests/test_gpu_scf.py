@@ -136,6 +136,18 @@ def test_relaxation_matches_oracle(prec):
     assert np.abs(R - ref.R).max() < 1e-3
 
 
+def test_fixed_point_on_u_matches_golden():
+    # the alternative fixed point of Sec. 5.3 (Anderson mixing of u instead of V_LR) reaches
+    # the same ground state
+    rec = _golden()["al4_wt"]
+    cell = _cell_from(rec)
+    res, F, u, phi = _run(cell, Fn.wt(), B.OF_F32, anderson_m=3, anderson_zeta=1.0,
+                          fixed_point=B.OF_FP_U)
+    assert res.converged, (res.fp_error, res.nlcg_residual)
+    assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
+    assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
+
+
 def test_line_searches_reach_the_same_ground_state():
     # Brent on the energy (the paper's line search) and the slope search (root of dE/ds from
     # the same line model) stop the NLCG at the same minimiser; the slope search needs fewer

@@ -156,3 +156,18 @@ def test_fixed_point_ground_state_wt_small():
     eta = inner(res.u, Hu, grid) / cell.n_electrons
     r = Hu - eta * res.u
     assert sqrt(inner(r, r, grid) / cell.n_electrons) < 1e-5
+
+
+@pytest.mark.slow
+def test_fixed_point_on_u_reaches_the_same_ground_state():
+    # Sec. 5.3 compares Anderson mixing of V_LR (the method) with mixing of u; both fixed
+    # points are the ground state of the full functional, so the energies agree
+    cell = W.al4_lr_cell(points_per_cell=12)
+    grid = O.Grid(cell.n, cell.L, 6)
+    kw = dict(nlcg_tol=1e-8, fp_tol=1e-7, anderson_m=3, zeta=1.0)
+    rv = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.wt_functional(), **kw)
+    ru = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.wt_functional(),
+                            fixed_point="u", **kw)
+    assert ru.fp_errors[-1] < 1e-7 and rv.fp_errors[-1] < 1e-7
+    assert abs(ru.energy - rv.energy) / cell.n_atoms < 1e-9
+    assert np.max(np.abs(ru.u - rv.u)) < 1e-5 * np.max(rv.u)
