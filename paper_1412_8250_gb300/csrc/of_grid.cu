@@ -153,6 +153,10 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
 
 of_status of_grid_destroy(of_grid* g) {
     if (!g) return OF_OK;
+    if (g->twin) of_grid_destroy(g->twin);
+    if (g->twin_stream) cudaStreamDestroy(g->twin_stream);
+    if (g->twin_in) cudaEventDestroy(g->twin_in);
+    if (g->twin_out) cudaEventDestroy(g->twin_out);
     if (g->mg) mg_destroy(g->mg);
     if (g->graphs) destroy_graphs(g->graphs);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
@@ -200,6 +204,10 @@ const char* of_kernel_class_name(int cls) {
 of_status of_profile_enable(of_grid* g, int sample_every) {
     if (!g || sample_every < 0) { set_error("of_profile_enable: bad argument"); return OF_EINVAL; }
     try {
+        if (g->twin) {
+            const of_status st = of_profile_enable(g->twin, sample_every);
+            if (st != OF_OK) return st;
+        }
         if (!g->prof) g->prof = new Prof();
         Prof& p = *g->prof;
         OF_CUDA(cudaStreamSynchronize(g->stream));
@@ -216,27 +224,40 @@ of_status of_profile_enable(of_grid* g, int sample_every) {
 int of_profile_read(of_grid* g, of_kernel_stat* out, int max) {
     if (!g || !g->prof) return 0;
     try {
-        Prof& p = *g->prof;
+        // the timed launches of this handle and of its twin (whose solves ran beside it)
+        Prof* ps[2] = {g->prof, g->twin ? g->twin->prof : nullptr};
         OF_CUDA(cudaStreamSynchronize(g->stream));
-        for (auto& r : p.recs) {
-            float ms = 0.f;
-            OF_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
-            p.timed[r.cls] += 1;
-            p.ms[r.cls] += ms;
-            p.bytes[r.cls] += r.bytes;
-            p.pool.push_back(r.e0);
-            p.pool.push_back(r.e1);
+        for (Prof* pp : ps) {
+            if (!pp) continue;
+            for (auto& r : pp->recs) {
+                float ms = 0.f;
+                OF_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+                pp->timed[r.cls] += 1;
+                pp->ms[r.cls] += ms;
+                pp->bytes[r.cls] += r.bytes;
+                pp->pool.push_back(r.e0);
+                pp->pool.push_back(r.e1);
+            }
+            pp->recs.clear();
         }
-        p.recs.clear();
         int k = 0;
         for (int c = 0; c < PC_N && k < max; ++c) {
-            if (p.seen[c] == 0) continue;
+            long long seen = 0, timed = 0;
+            double ms = 0.0, bytes = 0.0;
+            for (Prof* pp : ps) {
+                if (!pp) continue;
+                seen += pp->seen[c];
+                timed += pp->timed[c];
+                ms += pp->ms[c];
+                bytes += pp->bytes[c];
+            }
+            if (seen == 0) continue;
             out[k].kernel_class = c;
-            out[k].launches = p.seen[c];
-            out[k].timed = p.timed[c];
-            out[k].total_ms = p.ms[c];
-            out[k].mean_ms = p.timed[c] ? p.ms[c] / p.timed[c] : 0.0;
-            out[k].bytes_per_launch = p.timed[c] ? p.bytes[c] / p.timed[c] : 0.0;
+            out[k].launches = seen;
+            out[k].timed = timed;
+            out[k].total_ms = ms;
+            out[k].mean_ms = timed ? ms / timed : 0.0;
+            out[k].bytes_per_launch = timed ? bytes / timed : 0.0;
             ++k;
         }
         return k;

@@ -184,6 +184,11 @@ struct of_grid {
     of::Prof* prof = nullptr;        // kernel timing (of_profile_enable)
     cudaStream_t cap_stream = nullptr;   // private stream for CUDA-graph capture
     cudaStream_t cap_stream2 = nullptr;  // second capture stream (bodies of conditional nodes)
+    // a second handle on the same grid (own workspace, graphs, stream) for a solve that runs
+    // concurrently with one on this handle; created on first use
+    of_grid* twin = nullptr;
+    cudaStream_t twin_stream = nullptr;
+    cudaEvent_t twin_in = nullptr, twin_out = nullptr;
     void* graphs = nullptr;              // cached CUDA graphs (of_krylov.cu)
 };
 
