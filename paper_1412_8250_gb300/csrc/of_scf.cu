@@ -606,29 +606,22 @@ static of_grid* twin_of(of_grid* g) {
     return g->twin;
 }
 
-// Two Poisson solves of products at once: phi1 for rho = a1 b1 on g's stream, phi2 for
-// rho = a2 b2 on the twin handle's stream, driven by a second host thread.  Both are
-// latency-bound at the benchmark's sizes, so they overlap on the GPU.  The twin's stream
-// starts after the work queued on g's stream, which waits for the twin's solve before it goes
-// on.
-static void poisson_pair(of_grid* g, const double* a1, const double* b1, double* phi1,
-                         const double* a2, const double* b2, double* phi2, const KrylovOpts& o,
-                         ScfStats& st) {
-    if (o.precond) {   // a learned preconditioner's buffers serve one solve at a time
-        poisson_into(g, a1, b1, phi1, o, st);
-        poisson_into(g, a2, b2, phi2, o, st);
-        return;
-    }
+// Two independent pieces of work at once: first(g) on g's stream in this thread, second(t) on
+// the twin handle t (its own stream and workspace) in a second host thread.  Both are
+// latency-bound solves at the benchmark's sizes, so they overlap on the GPU.  The twin's
+// stream starts after the work queued on g's stream, which waits for the twin before it goes
+// on.  An error of either side is rethrown after both have finished.
+template <class First, class Second>
+static void run_pair(of_grid* g, First&& first, Second&& second) {
     of_grid* t = twin_of(g);
     OF_CUDA(cudaEventRecord(g->twin_in, g->stream));
     OF_CUDA(cudaStreamWaitEvent(t->stream, g->twin_in, 0));
-    ScfStats st2;
     of_status err2 = OF_OK;
     std::string msg2;
     std::thread worker([&]() {
         cudaSetDevice(g->device);
         try {
-            poisson_into(t, a2, b2, phi2, o, st2);
+            second(t);
         } catch (const Error& e) {
             err2 = e.code;
             msg2 = of_last_error();
@@ -638,19 +631,42 @@ static void poisson_pair(of_grid* g, const double* a1, const double* b1, double*
     });
     of_status err1 = OF_OK;
     try {
-        poisson_into(g, a1, b1, phi1, o, st);
+        first(g);
     } catch (const Error& e) {
         err1 = e.code;
     }
     worker.join();
     OF_CUDA(cudaEventRecord(g->twin_out, t->stream));
     OF_CUDA(cudaStreamWaitEvent(g->stream, g->twin_out, 0));
-    st.poisson += st2.poisson;
     if (err1 != OF_OK) throw Error{err1};
     if (err2 != OF_OK) {
         set_error("%s", msg2.c_str());
         throw Error{err2};
     }
+}
+
+// The two line-energy Poisson solves of products, phi1 for rho = a1 b1 and phi2 for
+// rho = a2 b2, at once (run_pair); pre(g) is queued on g's stream ahead of the first solve, so
+// that it overlaps the second.
+template <class Pre>
+static void poisson_pair(of_grid* g, const double* a1, const double* b1, double* phi1,
+                         const double* a2, const double* b2, double* phi2, const KrylovOpts& o,
+                         ScfStats& st, Pre&& pre) {
+    if (o.precond) {   // a learned preconditioner's buffers serve one solve at a time; its
+                       // flexible CG reduces into more scalar slots, so pre goes last
+        poisson_into(g, a1, b1, phi1, o, st);
+        poisson_into(g, a2, b2, phi2, o, st);
+        pre(g);
+        return;
+    }
+    ScfStats st2;
+    run_pair(g,
+             [&](of_grid* h) {
+                 pre(h);
+                 poisson_into(h, a1, b1, phi1, o, st);
+             },
+             [&](of_grid* h) { poisson_into(h, a2, b2, phi2, o, st2); });
+    st.poisson += st2.poisson;
 }
 
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
@@ -711,8 +727,10 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         auto prepare_line = [&](double tol_line) {
             KrylovOpts pl = po;
             pl.tol = std::max(po.tol, tol_line);
-            poisson_pair(g, u, v.d, v.B, v.d, v.d, v.C, pl, st);
-            launch_stencil<double, 2>(g, g->w64, OpLapDot{v.d, u, v.Ld, red_ctx(g, SC_DLD)});
+            // L d with d^T L d and u^T L d (slots untouched by the solves) beside the twin's solve
+            poisson_pair(g, u, v.d, v.B, v.d, v.d, v.C, pl, st, [&](of_grid* h) {
+                launch_stencil<double, 2>(h, h->w64, OpLapDot{v.d, u, v.Ld, red_ctx(h, SC_DLD)});
+            });
             launch(k_line_moments, nb, 256, g->stream, n, u, v.d, fn.mu != 0.0 ? V : nullptr, phi,
                    v.D, v.B, v.C, v.b, red_ctx(g, SC_MD));
             OF_LAUNCH_CHECK();
@@ -874,20 +892,31 @@ static double lr_potential_l2(of_grid* g, const of_functional* fn, double kf2, c
     OF_LAUNCH_CHECK();
     launch_stencil<double, 2>(g, g->w64, OpScaledLap{gp, f00, -1.0 / kf2});
     launch_stencil<double, 2>(g, g->w64, OpScaledLap{gp + 3 * n, f00 + n, -1.0 / kf2});
-    for (int p = 0; p < S.npot; ++p) {
+    // the solves, one per potential and conjugate pair, two at a time (run_pair)
+    const int njobs = S.npot * npairs;
+    auto solve = [&](of_grid* h, int job, of_solve_info& si) {
+        const int p = job / npairs, r = job % npairs;
         const int c = pot_cls[p], e = pot_e[p], k = pot_k[p];
         // right-hand side: the density power itself, or -(1/kf2) L_h of it for K_00 (Sec. 3.1)
         const double* f = c == 0 ? f00 + (size_t)e * n : gp + (size_t)(3 * e + k) * n;
-        for (int r = 0; r < npairs; ++r) {
-            const double2 P = make_double2(PC[c][4 * r], PC[c][4 * r + 1]);
-            const double2 Q = make_double2(QC[c][4 * r], QC[c][4 * r + 1]);
-            double2* W = (double2*)Wws + (size_t)(p * npairs + r) * n;
-            of_solve_info si{};
-            const of_status s1 = shifted(g, f, P, Q, kf2, W, ko, &si);
-            if (s1 != OF_OK && s1 != OF_ENOCONV) throw Error{s1};
-            st.kernel += si.iterations;
-            add_info(info_out, si);
-            S.W[p][r] = W;
+        const double2 P = make_double2(PC[c][4 * r], PC[c][4 * r + 1]);
+        const double2 Q = make_double2(QC[c][4 * r], QC[c][4 * r + 1]);
+        double2* W = (double2*)Wws + (size_t)job * n;
+        S.W[p][r] = W;
+        return shifted(h, f, P, Q, kf2, W, ko, &si);
+    };
+    for (int job = 0; job < njobs; job += 2) {
+        of_solve_info si[2] = {};
+        of_status sj[2] = {OF_OK, OF_OK};
+        if (job + 1 < njobs)
+            run_pair(g, [&](of_grid* h) { sj[0] = solve(h, job, si[0]); },
+                     [&](of_grid* h) { sj[1] = solve(h, job + 1, si[1]); });
+        else
+            sj[0] = solve(g, job, si[0]);
+        for (int q = 0; q < 2; ++q) {
+            if (sj[q] != OF_OK && sj[q] != OF_ENOCONV) throw Error{sj[q]};
+            st.kernel += si[q].iterations;
+            add_info(info_out, si[q]);
         }
     }
     launch(k_lr_assemble2, nb, 256, g->stream, n, u, (const double*)gp, S, vlr, red_ctx(g, SC_TLR));
@@ -922,8 +951,10 @@ static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2,
         double2* Wa = (double2*)Wws + (size_t)(2 * k) * n;       // from u^{2 alpha}
         double2* Wb = (double2*)Wws + (size_t)(2 * k + 1) * n;   // from u^{2 beta}
         of_solve_info ia{}, ib{};
-        of_status s1 = shifted(g, fa, P, Q, kf2, Wa, ko, &ia);
-        of_status s2 = shifted(g, fb, P, Q, kf2, Wb, ko, &ib);
+        of_status s1 = OF_OK, s2 = OF_OK;
+        // the two exponents' solves at once, the second on the twin handle
+        run_pair(g, [&](of_grid* h) { s1 = shifted(h, fa, P, Q, kf2, Wa, ko, &ia); },
+                 [&](of_grid* h) { s2 = shifted(h, fb, P, Q, kf2, Wb, ko, &ib); });
         if (s1 != OF_OK && s1 != OF_ENOCONV) throw Error{s1};
         if (s2 != OF_OK && s2 != OF_ENOCONV) throw Error{s2};
         st.kernel += ia.iterations + ib.iterations;
