@@ -48,6 +48,12 @@ typedef enum {
     OF_LINE_SLOPE = 1
 } of_line_search;
 
+/* Discrete form of the reported vW energy (of_scf_opts.vw_energy). */
+typedef enum {
+    OF_VW_LAPLACIAN = 0,
+    OF_VW_GRADIENT = 1
+} of_vw_energy;
+
 /* Variable of the outer fixed point with Anderson mixing (App. D). */
 typedef enum {
     OF_FP_VLR = 0,
@@ -136,6 +142,10 @@ typedef struct {
     int line_search;        /* of_line_search; default OF_LINE_SLOPE */
     int fixed_point;        /* OF_FP_VLR (default, Sec. 3.3.1): mix V_LR; OF_FP_U: mix u, the
                                alternative of Sec. 5.3 (Table MixComparison) */
+    int vw_energy;          /* reported vW energy: OF_VW_LAPLACIAN (default) -(lambda/2) <u, L_h u>,
+                               whose gradient is the Hamiltonian's; OF_VW_GRADIENT (lambda/2)
+                               int |grad_h u|^2 with the order-2N gradient (Eq.
+                               gradient:approximate).  The minimisation is the same. */
 } of_scf_opts;
 
 typedef struct {

@@ -29,7 +29,7 @@ from math import pi, sqrt
 import numpy as np
 from scipy.optimize import brent
 
-from .fd import Grid, laplacian, integrate, poisson_solve
+from .fd import Grid, gradient, laplacian, integrate, poisson_solve
 from .functional import tf_energy_density, tf_potential, xc_energy_density, v_xc
 from .kernel import Functional, lr_potential, kf2_of
 from .pseudo import pseudocharge, self_energy, repulsive_correction
@@ -191,13 +191,20 @@ class ScfResult:
     fp_errors: list
 
 
-def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c):
+def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c,
+                        vw_energy="laplacian"):
     """Eq. GroundStateEnergy: TF + lam vW + mu T_LR + xc + 1/2 int (u^2 + b) phi
-    - 1/2 sum_J int b_J V_J + E_c^*."""
+    - 1/2 sum_J int b_J V_J + E_c^*.  The vW term is -(lam/2) int u L_h u (the discrete form
+    whose gradient is the Hamiltonian, R7) or, with vw_energy="gradient", (lam/2) int |grad_h u|^2
+    with the order-2N gradient of Eq. gradient:approximate (Eq. vW:KineticEnergy as printed)."""
     rho = u * u
+    if vw_energy == "gradient":
+        vw = integrate(0.5 * fn.lam * np.sum(gradient(u, grid) ** 2, axis=0), grid)
+    else:
+        vw = integrate(-0.5 * fn.lam * u * laplacian(u, grid), grid)
     t = dict(
         tf=integrate(tf_energy_density(rho), grid),
-        vw=integrate(-0.5 * fn.lam * u * laplacian(u, grid), grid),
+        vw=vw,
         lr=fn.mu * T_LR,
         xc=integrate(xc_energy_density(rho), grid),
         es=integrate(0.5 * (rho + b) * phi, grid),
@@ -209,7 +216,7 @@ def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c
 
 def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_tol=1e-7,
                      fp_tol=1e-7, max_outer=50, anderson_m=7, zeta=0.3, n_restart=50,
-                     max_nlcg=5000, fixed_point="V"):
+                     max_nlcg=5000, fixed_point="V", vw_energy="laplacian"):
     """Fixed point V_LR = V[U(V_LR)] (Eqs. FixedPoint:Map1, MVF) with Anderson mixing
     (App. D); V_LR,0 = 0.  Returns the ground state and its energy.
 
@@ -218,7 +225,7 @@ def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_
     error ||U(V[u_k]) - u_k|| / ||U(V[u_k])||, the energy taken at u = U(V[u_k])."""
     if fixed_point == "u" and fn.mu != 0.0:
         return _scf_ground_state_u(grid, R, Z, sigma, rc, fn, u0, nlcg_tol, fp_tol, max_outer,
-                                   anderson_m, zeta, n_restart, max_nlcg)
+                                   anderson_m, zeta, n_restart, max_nlcg, vw_energy)
     Ne = float(np.sum(Z))
     b = pseudocharge(R, Z, sigma, rc, grid)
     phi_b = poisson_solve(b, grid)
@@ -243,13 +250,13 @@ def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_
         if errs[-1] < fp_tol:
             break
         V = anderson_update(V_hist, f_hist, zeta, anderson_m)
-    E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c)
+    E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c, vw_energy)
     return ScfResult(u=u, phi=phi, V_LR=V, energy=E, terms=terms, outer_iterations=len(its),
                      nlcg_iterations=its, fp_errors=errs)
 
 
 def _scf_ground_state_u(grid, R, Z, sigma, rc, fn, u0, nlcg_tol, fp_tol, max_outer, anderson_m,
-                        zeta, n_restart, max_nlcg):
+                        zeta, n_restart, max_nlcg, vw_energy):
     Ne = float(np.sum(Z))
     b = pseudocharge(R, Z, sigma, rc, grid)
     phi_b = poisson_solve(b, grid)
@@ -272,6 +279,6 @@ def _scf_ground_state_u(grid, R, Z, sigma, rc, fn, u0, nlcg_tol, fp_tol, max_out
             break
         x = anderson_update(x_hist, f_hist, zeta, anderson_m)
     V_u, T_LR, _, _ = lr_potential(u, grid, fn, kf2)
-    E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c)
+    E, terms = ground_state_energy(u, phi, b, grid, fn, T_LR, E_self, E_c, vw_energy)
     return ScfResult(u=u, phi=phi, V_LR=V_u, energy=E, terms=terms, outer_iterations=len(its),
                      nlcg_iterations=its, fp_errors=errs)

@@ -18,6 +18,7 @@ OF_OK, OF_EINVAL, OF_ENOMEM, OF_ECUDA, OF_ENOCONV, OF_EBREAKDOWN, OF_ETIMEOUT = 
 OF_F64, OF_F32 = 0, 1
 OF_LINE_BRENT, OF_LINE_SLOPE = 0, 1
 OF_FP_VLR, OF_FP_U = 0, 1
+OF_VW_LAPLACIAN, OF_VW_GRADIENT = 0, 1
 STATUS_NAMES = {0: "OF_OK", 1: "OF_EINVAL", 2: "OF_ENOMEM", 3: "OF_ECUDA", 4: "OF_ENOCONV",
                 5: "OF_EBREAKDOWN", 6: "OF_ETIMEOUT"}
 
@@ -53,7 +54,7 @@ class of_scf_opts(C.Structure):
                 ("anderson_m", C.c_int), ("anderson_zeta", C.c_double),
                 ("precision", C.c_int), ("poisson", of_solve_opts), ("kernel", of_solve_opts),
                 ("verbose", C.c_int), ("line_tol", C.c_double), ("nlcg_tol_rel", C.c_double),
-                ("line_search", C.c_int), ("fixed_point", C.c_int)]
+                ("line_search", C.c_int), ("fixed_point", C.c_int), ("vw_energy", C.c_int)]
 
 
 class of_scf_result(C.Structure):

@@ -35,6 +35,7 @@ enum {
     SC_MD = 10,        // 13 line-search moments
     SC_LINE = 25,
     SC_SLOPE = 96,     // 3 sums of the slope line search
+    SC_GRADSQ = 100,   // sum of |grad_h u|^2
     SC_EN = 26,        // 4 energy sums
     SC_TLR = 30,
     SC_FP = 32,        // |f|^2, |Vhat|^2
@@ -1015,15 +1016,62 @@ static void launch_gram(of_grid* g, int m, long long n, const HistPtrs& H, const
     OF_LAUNCH_CHECK();
 }
 
+// Order-2N FD gradient weights of Eq. gradient:approximate per axis:
+// w~_p = (-1)^{p+1} (N!)^2 / (h p (N-p)! (N+p)!), p = 1..N
+struct GradWeights {
+    double w[3][OF_MAX_N + 1];
+    int N;
+};
+
+// sum over the grid of |grad_h u|^2, periodic wrap of every index
+__global__ void __launch_bounds__(256) k_grad_sq(Dims d, GradWeights G, const double* u, RedCtx rc) {
+    double acc[1] = {0.0};
+    const long long sz = (long long)d.n1 * d.n2;
+    GRID_LOOP(idx, d.n) {
+        const int i = (int)(idx % d.n1), j = (int)((idx / d.n1) % d.n2), k = (int)(idx / sz);
+        const long long row = (long long)k * sz + (long long)j * d.n1;
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int p = 1; p <= G.N; ++p) {
+            gx += G.w[0][p] * (u[row + wrap_index(i + p, d.n1)] - u[row + wrap_index(i - p, d.n1)]);
+            gy += G.w[1][p] * (u[(long long)k * sz + (long long)wrap_index(j + p, d.n2) * d.n1 + i] -
+                               u[(long long)k * sz + (long long)wrap_index(j - p, d.n2) * d.n1 + i]);
+            gz += G.w[2][p] * (u[(long long)wrap_index(k + p, d.n3) * sz + (long long)j * d.n1 + i] -
+                               u[(long long)wrap_index(k - p, d.n3) * sz + (long long)j * d.n1 + i]);
+        }
+        acc[0] += gx * gx + gy * gy + gz * gz;
+    }
+    grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+}
+
+static double grad_sq_sum(of_grid* g, const double* u) {
+    GradWeights G{};
+    G.N = g->N;
+    double fN = 1.0;
+    for (int q = 2; q <= g->N; ++q) fN *= q;
+    for (int a = 0; a < 3; ++a)
+        for (int p = 1; p <= g->N; ++p) {
+            double den = g->h[a] * p;
+            for (int q = 2; q <= g->N - p; ++q) den *= q;   // (N-p)!
+            double num = fN * fN;
+            for (int q = 2; q <= g->N + p; ++q) num /= q;   // / (N+p)!
+            G.w[a][p] = ((p + 1) % 2 ? -1.0 : 1.0) * num / den;
+        }
+    launch(k_grad_sq, vb(g->d.n), 256, g->stream, g->d, G, u, red_ctx(g, SC_GRADSQ));
+    OF_LAUNCH_CHECK();
+    return sc(g, SC_GRADSQ);
+}
+
 static void energy_terms(of_grid* g, const of_functional* fn, const double* u, const double* b,
                          const double* phi, double t_lr_sum, double e_self, double e_c,
-                         of_scf_result* res) {
+                         int vw_energy, of_scf_result* res) {
     launch_stencil<double, 2>(g, g->w64, OpEnergy{u, b, phi, red_ctx(g, SC_EN)});
     double e[4];
     fetch_scalars(g, SC_EN, 4, e);
     const double dV = g->dV;
     res->e_tf = e[0] * dV;   // e[0] already carries C_F
-    res->e_vw = -0.5 * fn->lambda * e[1] * dV;
+    // vW: -(lam/2) <u, L_h u> (its gradient is the Hamiltonian's), or (lam/2) int |grad_h u|^2
+    res->e_vw = vw_energy == OF_VW_GRADIENT ? 0.5 * fn->lambda * grad_sq_sum(g, u) * dV
+                                            : -0.5 * fn->lambda * e[1] * dV;
     res->e_xc = e[2] * dV;
     res->e_es = 0.5 * e[3] * dV;
     res->e_lr = fn->mu != 0.0 ? fn->mu * 0.5 * OF_CF * t_lr_sum * dV : 0.0;
@@ -1170,7 +1218,7 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
     }
     // u-mixing ends on u = U(V[u_k]); its own T_LR for the energy
     if (fp_u) t_lr_sum = lr_potential_impl(g, fn, kf2, u, v.Vhat, Wws, ko, st, nullptr);
-    energy_terms(g, fn, u, v.b, phi, t_lr_sum, e_self, e_c, res);
+    energy_terms(g, fn, u, v.b, phi, t_lr_sum, e_self, e_c, o->vw_energy, res);
     res->fp_error = err;
     res->nlcg_residual = st.last_residual;
     res->nlcg_iterations = st.nlcg;

@@ -148,6 +148,23 @@ def test_fixed_point_on_u_matches_golden():
     assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
 
 
+def test_vw_energy_gradient_form():
+    # the vW energy reported as (lam/2) int |grad_h u|^2 (Eq. gradient:approximate) instead of
+    # -(lam/2) <u, L_h u>: same ground state, the term equals the oracle's gradient form of the
+    # same u, and the two forms differ only by the discretisation error
+    rec = _golden()["al4_tfw"]
+    cell = _cell_from(rec)
+    res_l, _, u_l, _ = _run(cell, Fn.tfw(), B.OF_F64)
+    res_g, _, u_g, phi_g = _run(cell, Fn.tfw(), B.OF_F64, vw_energy=B.OF_VW_GRADIENT)
+    grid = O.Grid(cell.n, cell.L, 6)
+    zero = np.zeros(grid.shape)
+    _, t = O.ground_state_energy(u_g, zero, zero, grid, O.tfw_functional(), 0.0, 0.0, 0.0,
+                                 vw_energy="gradient")
+    assert abs(res_g.e_vw - t["vw"]) <= 1e-11 * abs(t["vw"])
+    assert abs(res_g.e_tf - res_l.e_tf) <= 1e-9 * abs(res_l.e_tf)
+    assert abs(res_g.e_vw - res_l.e_vw) <= 1e-3 * abs(res_l.e_vw)
+
+
 def test_line_searches_reach_the_same_ground_state():
     # Brent on the energy (the paper's line search) and the slope search (root of dE/ds from
     # the same line model) stop the NLCG at the same minimiser; the slope search needs fewer

@@ -171,3 +171,30 @@ def test_fixed_point_on_u_reaches_the_same_ground_state():
     assert ru.fp_errors[-1] < 1e-7 and rv.fp_errors[-1] < 1e-7
     assert abs(ru.energy - rv.energy) / cell.n_atoms < 1e-9
     assert np.max(np.abs(ru.u - rv.u)) < 1e-5 * np.max(rv.u)
+
+
+def test_vw_energy_gradient_form_plane_wave_and_limit():
+    # (lam/2) int |grad_h u|^2 for u = cos(2 pi m x / L): each mode contributes its FD symbol
+    # squared, (sum_p 2 w~_p sin(2 pi m p / n))^2 / 2 per unit volume (Eq. gradient:approximate)
+    grid = O.Grid((16, 12, 10), (7.6, 6.0, 5.5), 6)
+    z, y, x = np.meshgrid(np.arange(10), np.arange(12), np.arange(16), indexing="ij")
+    m = 3
+    u = np.cos(2 * pi * m * x / 16)
+    fn = O.tfw_functional()
+    zero = np.zeros(grid.shape)
+    _, tg = O.ground_state_energy(u, zero, zero, grid, fn, 0.0, 0.0, 0.0, vw_energy="gradient")
+    w = O.fd_gradient_weights(6, grid.h[0])
+    sym = sum(2 * w[p] * np.sin(2 * pi * m * p / 16) for p in range(1, 7))
+    ref = 0.5 * fn.lam * sym ** 2 * 0.5 * grid.volume
+    assert abs(tg["vw"] - ref) <= 1e-12 * ref
+    # for a smooth field the two discrete forms differ by the discretisation error only: the
+    # gap closes at the order of the scheme when the same field is sampled twice as finely
+    gaps = []
+    for n in (16, 32):
+        u = W.random_field((n, n, n), seed=3, kind="smooth")
+        g2 = O.Grid((n, n, n), (7.6, 7.6, 7.6), 6)
+        zero = np.zeros(g2.shape)
+        _, tl = O.ground_state_energy(u, zero, zero, g2, fn, 0.0, 0.0, 0.0)
+        _, tg = O.ground_state_energy(u, zero, zero, g2, fn, 0.0, 0.0, 0.0, vw_energy="gradient")
+        gaps.append(abs(tg["vw"] - tl["vw"]) / abs(tl["vw"]))
+    assert gaps[0] < 1e-3 and gaps[1] < gaps[0] / 100, gaps
