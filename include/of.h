@@ -99,6 +99,10 @@ typedef struct {
     const double* Z;
     double sigma;
     double rc;
+    int b_from_potential;   /* 0: b_J sampled from its closed form; 1: b_J = -(1/4 pi) L_h V_J,
+                               the paper's construction from the potential (Sec. 4), V_J sampled
+                               on each ion's box widened by N points (the self energy with it;
+                               forces keep the closed-form gradient of b_J) */
 } of_system;
 
 /* Kinetic functional T_TF + lambda T_vW + mu T_LR (Eq. KineticEnergyComponents).  The

@@ -65,6 +65,44 @@ def pseudocharge(R, Z, sigma, rc, grid: Grid) -> np.ndarray:
     return b
 
 
+def pseudocharge_fd(R, Z, sigma, rc, grid: Grid):
+    """The paper's construction b_J^{(i,j,k)} = -(1/4pi) (L_h V_J)^{(i,j,k)} (the nuclear charge
+    of Sec. 4, from the pseudopotential by the same order-2N Laplacian as the rest), at the grid
+    points within r_c of each image of ion J; V_J is sampled on the ion's box widened by N
+    points each way so that every stencil tap is a sample.  Returns (b, e_self) with
+    e_self = -(1/2) sum_J int b_J V_J over the same points."""
+    from .fd import fd_laplacian_weights
+    N = grid.N
+    h = grid.h
+    n1, n2, n3 = grid.n
+    b = np.zeros(grid.shape)
+    e = 0.0
+    W = [fd_laplacian_weights(N, h[d]) for d in range(3)]
+    for J in range(len(Z)):
+        lo = [ceil((R[J][d] - rc) / h[d]) for d in range(3)]
+        hi = [floor((R[J][d] + rc) / h[d]) for d in range(3)]
+        ax = [np.arange(lo[d] - N, hi[d] + N + 1) * h[d] - R[J][d] for d in range(3)]
+        DZ, DY, DX = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        V = gaussian_V(np.sqrt(DX**2 + DY**2 + DZ**2), Z[J], sigma)
+        core = tuple(slice(N, -N) for _ in range(3))
+        lap = np.zeros(V[core].shape)
+        for d, axis in ((0, 2), (1, 1), (2, 0)):      # x is the last numpy axis
+            for p in range(0, N + 1):
+                sp = [slice(N, -N)] * 3
+                sm = [slice(N, -N)] * 3
+                m = V.shape[axis]
+                sp[axis] = slice(N + p, m - N + p)
+                sm[axis] = slice(N - p, m - N - p)
+                lap += W[d][p] * (V[tuple(sp)] + V[tuple(sm)])
+        r = np.sqrt(DX[core]**2 + DY[core]**2 + DZ[core]**2)
+        bj = np.where(r <= rc, -lap / (4.0 * pi), 0.0)
+        K, Jj, I = np.meshgrid(np.arange(lo[2], hi[2] + 1), np.arange(lo[1], hi[1] + 1),
+                               np.arange(lo[0], hi[0] + 1), indexing="ij")
+        np.add.at(b, (K % n3, Jj % n2, I % n1), bj)
+        e += grid.dV * np.sum(bj * V[core])
+    return b, -0.5 * e
+
+
 def self_energy(R, Z, sigma, rc, grid: Grid) -> float:
     """Self-energy term -(1/2) sum_J int b_J V_J of Eq. LocalReformulationElectrostaticEnergy,
     each integral taken by the grid quadrature over the ion's support."""

@@ -36,7 +36,8 @@ class of_solve_info(C.Structure):
 
 class of_system(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("R", C.POINTER(C.c_double)),
-                ("Z", C.POINTER(C.c_double)), ("sigma", C.c_double), ("rc", C.c_double)]
+                ("Z", C.POINTER(C.c_double)), ("sigma", C.c_double), ("rc", C.c_double),
+                ("b_from_potential", C.c_int)]
 
 
 class of_functional(C.Structure):
@@ -238,12 +239,12 @@ def of_kernel_solve(h, f, P, Q, kf2, W, opts=None, allow=()):
     return info
 
 
-def make_system(R, Z, sigma, rc):
+def make_system(R, Z, sigma, rc, b_from_potential=False):
     """of_system from numpy arrays (kept alive on the returned object)."""
     R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
     Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
     s = of_system(int(Z.size), R.ctypes.data_as(C.POINTER(_D)), Z.ctypes.data_as(C.POINTER(_D)),
-                  float(sigma), float(rc))
+                  float(sigma), float(rc), int(bool(b_from_potential)))
     s._keep = (R, Z)
     return s
 

@@ -212,7 +212,102 @@ __global__ void k_overlap(int M, const AtomBox* boxes, double L1, double L2, dou
     fc[3 * I + 2] = f2;
 }
 
+// ---- b_J = -(1/4pi) L_h V_J (the paper's construction from the potential, Sec. 4)
+// V_J sampled on the ion's ball box widened by N points each way: box point (i, j, k), with
+// i = 0 .. n[0] - 1 standing for grid index lo[0] - N + i (unwrapped)
+struct WideBox {
+    int lo[3];   // unwrapped grid index of the ball box's first point
+    int n[3];    // widened box extents (ball box + 2N)
+    double R[3];
+    double Z;
+};
+
+__global__ void k_sample_V(WideBox B, int N, double h1, double h2, double h3, Gauss q, double* V) {
+    const long long nb = (long long)B.n[0] * B.n[1] * B.n[2];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nb;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % B.n[0]), j = (int)((t / B.n[0]) % B.n[1]),
+                  k = (int)(t / ((long long)B.n[0] * B.n[1]));
+        const double dx = (B.lo[0] - N + i) * h1 - B.R[0], dy = (B.lo[1] - N + j) * h2 - B.R[1],
+                     dz = (B.lo[2] - N + k) * h3 - B.R[2];
+        V[t] = gauss_V(sqrt(dx * dx + dy * dy + dz * dz), B.Z, q);
+    }
+}
+
+// For the ball points of the box: b_J = -(1/4pi) (L_h V_J) from the samples (every tap inside
+// the widened box), scattered into b (atomic: boxes overlap); sums b_J V_J for the self energy
+template <int N>
+__global__ void __launch_bounds__(256) k_box_lap(WideBox B, Dims d, double h1, double h2, double h3,
+                                                 Weights<double> Wt, double rc, const double* V,
+                                                 double* b, RedCtx rc_out) {
+    double acc[1] = {0.0};
+    const int m0 = B.n[0] - 2 * N, m1 = B.n[1] - 2 * N, m2 = B.n[2] - 2 * N;
+    const long long nin = (long long)m0 * m1 * m2;
+    const long long sy = B.n[0], sz = (long long)B.n[0] * B.n[1];
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nin;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % m0), j = (int)((t / m0) % m1), k = (int)(t / ((long long)m0 * m1));
+        const int gi = B.lo[0] + i, gj = B.lo[1] + j, gk = B.lo[2] + k;
+        const double dx = gi * h1 - B.R[0], dy = gj * h2 - B.R[1], dz = gk * h3 - B.R[2];
+        if (dx * dx + dy * dy + dz * dz > rc * rc) continue;
+        const long long c = (i + N) + (j + N) * sy + (k + N) * sz;
+        double lap = Wt.centre * V[c];
+        for (int p = 1; p <= N; ++p)
+            lap += Wt.w[0][p] * (V[c + p] + V[c - p]) + Wt.w[1][p] * (V[c + p * sy] + V[c - p * sy]) +
+                   Wt.w[2][p] * (V[c + p * sz] + V[c - p * sz]);
+        const double bj = -lap / (4.0 * M_PI);
+        const long long idx = wrap_index(gi, d.n1) +
+                              (long long)d.n1 * (wrap_index(gj, d.n2) + (long long)d.n2 * wrap_index(gk, d.n3));
+        atomicAdd(b + idx, bj);
+        acc[0] += bj * V[c];
+    }
+    grid_reduce<1>(acc, rc_out.partials, rc_out.counter, rc_out.out);
+}
+
+static void pseudocharge_fd(of_grid* g, const of_system* sys, double* b, double* e_self) {
+    AtomSet a = upload_atoms(g, sys);
+    Gauss q = gauss(sys);
+    const int N = g->N;
+    size_t max_box = 0;
+    std::vector<WideBox> boxes(a.n_atoms);
+    for (int J = 0; J < a.n_atoms; ++J) {
+        WideBox& w = boxes[J];
+        for (int c = 0; c < 3; ++c) {
+            w.lo[c] = a.h[J].lo[c];
+            w.n[c] = a.h[J].len[c] + 2 * N;
+            w.R[c] = a.h[J].R[c];
+        }
+        w.Z = a.h[J].Z;
+        max_box = std::max(max_box, (size_t)w.n[0] * w.n[1] * w.n[2]);
+    }
+    double* V = (double*)ws(g, WS_ATOMBOX, sizeof(double) * max_box);
+    double* per_atom = (double*)ws(g, WS_S15, sizeof(double) * ((size_t)a.n_atoms + 8));
+    OF_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * g->d.n, g->stream));
+    for (int J = 0; J < a.n_atoms; ++J) {   // one ion at a time through the shared box buffer
+        const WideBox& w = boxes[J];
+        const long long nb = (long long)w.n[0] * w.n[1] * w.n[2];
+        launch(k_sample_V, red_blocks(nb, 1024), 256, g->stream, w, N, g->h[0], g->h[1], g->h[2], q, V);
+        const long long nin = (long long)a.h[J].len[0] * a.h[J].len[1] * a.h[J].len[2];
+        RedCtx rc{g->s.partials, g->s.counter, per_atom + J};
+        const unsigned nbl = (unsigned)red_blocks(nin, 1024);
+        switch (N) {
+            case 1: launch(k_box_lap<1>, nbl, 256, g->stream, w, g->d, g->h[0], g->h[1], g->h[2], g->w64, sys->rc, (const double*)V, b, rc); break;
+            case 3: launch(k_box_lap<3>, nbl, 256, g->stream, w, g->d, g->h[0], g->h[1], g->h[2], g->w64, sys->rc, (const double*)V, b, rc); break;
+            default: launch(k_box_lap<6>, nbl, 256, g->stream, w, g->d, g->h[0], g->h[1], g->h[2], g->w64, sys->rc, (const double*)V, b, rc); break;
+        }
+        OF_LAUNCH_CHECK();
+    }
+    if (e_self) {
+        launch(k_sum_product, 1, 256, g->stream, (long long)a.n_atoms, (const double*)per_atom,
+               (const double*)nullptr, red_ctx(g, 119));
+        OF_LAUNCH_CHECK();
+        fetch_scalars(g, 119, 1, e_self);
+        *e_self *= -0.5 * g->dV;
+    }
+}
+
 static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, double* e_self) {
+    if (sys && sys->b_from_potential) return pseudocharge_fd(g, sys, b, e_self);
     AtomSet a = upload_atoms(g, sys);
     Gauss q = gauss(sys);
     const size_t nparts = (size_t)a.n_atoms * a.max_planes;

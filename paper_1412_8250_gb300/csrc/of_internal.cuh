@@ -242,6 +242,7 @@ enum Slot {
     WS_LR,       // kernel-solve warm starts
     WS_AND,      // Anderson history
     WS_ATOM,     // per-atom device data
+    WS_ATOMBOX,  // one ion's widened box (pseudocharge from the potential)
     WS_MG,       // multigrid hierarchy
     WS_NSLOTS
 };

@@ -229,6 +229,20 @@ def test_pseudocharge_and_self_energy(cell):
         assert abs(e - eref) <= 1e-12 * abs(eref)
 
 
+@pytest.mark.parametrize("cell", [W.al4_displaced_cell(points_per_cell=24), W.al4_lr_cell(points_per_cell=20)],
+                         ids=["al4d", "al4lr"])
+def test_pseudocharge_from_the_potential(cell):
+    # b_J = -(1/4pi) L_h V_J on each ion's widened box (Sec. 4), against the oracle's
+    from oracle.pseudo import pseudocharge_fd
+    with G(cell.n, cell.L) as g:
+        sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc, b_from_potential=True)
+        b = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+        e = B.of_pseudocharge(g.h, sysd, b)
+        ref, eref = pseudocharge_fd(cell.R, cell.Z, cell.sigma, cell.rc, g.grid)
+        assert np.max(np.abs(host(b) - ref)) <= 1e-12 * np.max(np.abs(ref))
+        assert abs(e - eref) <= 1e-12 * abs(eref)
+
+
 @pytest.mark.parametrize("which", ["tfw", "wt"])
 def test_hamiltonian_apply(which):
     with G((24, 28, 20), (7.6, 8.0, 6.5)) as g:

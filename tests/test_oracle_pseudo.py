@@ -92,3 +92,21 @@ def test_repulsive_correction_forces_finite_difference():
             fd = -(O.repulsive_correction(Rp, c.Z, c.sigma, c.L) - O.repulsive_correction(Rm, c.Z, c.sigma, c.L)) / (2 * d)
             assert abs(fd - F[J, a]) < 1e-7 + 1e-5 * abs(F[J, a])
     assert np.max(np.abs(F.sum(0))) < 1e-10
+
+
+def test_pseudocharge_from_the_potential_converges_to_the_gaussian():
+    # b_J = -(1/4pi) L_h V_J (the paper's construction from the potential, Sec. 4) against the
+    # closed-form Gaussian charge it discretises: the gap closes at the order of the scheme,
+    # the ions stay neutral, and the self energy converges with it
+    from oracle.pseudo import pseudocharge_fd
+    errs = []
+    for ppc in (24, 32):
+        cell = W.al4_cell(points_per_cell=ppc)
+        g = O.Grid(cell.n, cell.L, 6)
+        bfd, es_fd = pseudocharge_fd(cell.R, cell.Z, cell.sigma, cell.rc, g)
+        ba = O.pseudocharge(cell.R, cell.Z, cell.sigma, cell.rc, g)
+        errs.append(np.abs(bfd - ba).max() / np.abs(ba).max())
+        assert abs(bfd.sum() * g.dV + cell.Z.sum()) <= 1e-9 * cell.Z.sum()
+        es = O.self_energy(cell.R, cell.Z, cell.sigma, cell.rc, g)
+        assert abs(es_fd - es) <= 1e-4 * abs(es)
+    assert errs[1] < 1e-6 and errs[1] < errs[0] * (24 / 32) ** 8, errs
