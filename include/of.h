@@ -296,6 +296,38 @@ of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
                    const of_scf_opts* scf_opts, const of_relax_opts* opts, double* u, double* phi,
                    double* R_out, double* F_out, of_relax_result* res);
 
+/* Vacancy formation energy (Sec. 5.6):
+ *   E_vf = E(M-1, 1, (M-1)/M Omega) - ((M-1)/M) E(M, 0, Omega),
+ * E(M, n, Omega) the energy of a periodic cell of volume Omega with M occupied sites and n
+ * vacancies.  The vacancy cell keeps the volume per atom: its sides and the remaining ion
+ * positions are the perfect cell's scaled by ((M-1)/M)^(1/3) about the origin. */
+typedef struct {
+    double e_perfect;       /* E(M, 0, Omega), Ha */
+    double e_unrelaxed;     /* E(M-1, 1, (M-1)/M Omega) at the scaled sites, Ha */
+    double e_relaxed;       /* the same after relaxing the vacancy cell's ions (= e_unrelaxed
+                               without relaxation), Ha */
+    double evf_unrelaxed;   /* e_unrelaxed - (M-1)/M e_perfect, Ha */
+    double evf_relaxed;     /* e_relaxed - (M-1)/M e_perfect, Ha */
+    double max_force;       /* max_J |F_J| of the vacancy cell at its final positions */
+    int relax_steps;        /* NLCG steps of the relaxation (0 without) */
+    int evaluations;        /* ground states of the vacancy cell */
+} of_vacancy_result;
+
+/* perfect: handle of the perfect cell (sides L); vacancy: a distinct handle with the same grid
+ * points, order, stream and device and sides ((M-1)/M)^(1/3) L (to 1e-12 relative; OF_EINVAL
+ * otherwise).  sys: the perfect cell's ions (host); site: the index of the ion removed.
+ * relax_opts: NULL for the unrelaxed energy only, else the vacancy cell's ions are relaxed at
+ * fixed volume as in of_relax.  u_perfect, phi_perfect, u_vacancy, phi_vacancy: device double*
+ * fields of the two grids as in of_scf_ground_state (u in: guess, out: ground state).  R_out
+ * (host, 3 (M-1), may be NULL): the vacancy cell's final positions.  The two cells' ground
+ * states run at once on internal streams; the call synchronises the shared stream.  OF_ENOCONV
+ * when a ground state or the relaxation does not converge (res still written). */
+of_status of_vacancy_formation(of_grid* perfect, of_grid* vacancy, const of_system* sys, int site,
+                               const of_functional* fn, const of_scf_opts* scf_opts,
+                               const of_relax_opts* relax_opts, double* u_perfect,
+                               double* phi_perfect, double* u_vacancy, double* phi_vacancy,
+                               double* R_out, of_vacancy_result* res);
+
 /* Ground states of ncells independent cells at once (same functional and options): grids[c]
  * (distinct handles, one shared stream), systems[c], u[c], phi[c] as in of_scf_ground_state,
  * one result per cell in results[c].  The cells run on up to 8 internal streams driven by host

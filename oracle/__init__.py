@@ -30,5 +30,6 @@ from .scf import (hamiltonian_apply, inner_energy, nlcg, anderson_update, scf_gr
                   ground_state_energy, ScfResult)
 from .forces import forces
 from .relax import relax, RelaxResult
+from .vacancy import vacancy_cell, vacancy_formation, VacancyResult
 
 __all__ = [n for n in dir() if not n.startswith("_")]

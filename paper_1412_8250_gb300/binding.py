@@ -78,6 +78,13 @@ class of_relax_result(C.Structure):
                 ("evaluations", C.c_int), ("converged", C.c_int)]
 
 
+class of_vacancy_result(C.Structure):
+    _fields_ = [("e_perfect", C.c_double), ("e_unrelaxed", C.c_double),
+                ("e_relaxed", C.c_double), ("evf_unrelaxed", C.c_double),
+                ("evf_relaxed", C.c_double), ("max_force", C.c_double),
+                ("relax_steps", C.c_int), ("evaluations", C.c_int)]
+
+
 class of_kernel_stat(C.Structure):
     _fields_ = [("kernel_class", C.c_int), ("launches", C.c_longlong), ("timed", C.c_longlong),
                 ("total_ms", C.c_double), ("mean_ms", C.c_double),
@@ -105,6 +112,9 @@ _SIGNATURES = {
     "of_relax": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional), C.POINTER(of_scf_opts),
                       C.POINTER(of_relax_opts), _P, _P, C.POINTER(_D), C.POINTER(_D),
                       C.POINTER(of_relax_result)]),
+    "of_vacancy_formation": (_I, [_P, _P, C.POINTER(of_system), _I, C.POINTER(of_functional),
+                                  C.POINTER(of_scf_opts), C.POINTER(of_relax_opts), _P, _P, _P,
+                                  _P, C.POINTER(_D), C.POINTER(of_vacancy_result)]),
     "of_scf_ground_state": (_I, [_P, C.POINTER(of_system), C.POINTER(of_functional),
                                  C.POINTER(of_scf_opts), _P, _P, C.POINTER(of_scf_result)]),
     "of_forces": (_I, [_P, C.POINTER(of_system), _P, _P, C.POINTER(_D)]),
@@ -299,6 +309,30 @@ def of_relax(h, sys, fn, scf_opts, relax_opts, u, phi, allow=()):
     if st != OF_OK and st not in allow:
         _check(st, "of_relax")
     return (np.array(R[:]).reshape(n, 3), np.array(F[:]).reshape(n, 3), res)
+
+
+def vacancy_cell_lengths(L, n_atoms):
+    """Sides of the vacancy cell of a perfect cell with sides L and n_atoms ions: L scaled by
+    ((M - 1)/M)^(1/3), the volume per atom kept (Sec. 5.6)."""
+    s = ((n_atoms - 1) / n_atoms) ** (1.0 / 3.0)
+    return tuple(s * float(x) for x in L)
+
+
+def of_vacancy_formation(hp, hv, sys, site, fn, scf_opts, relax_opts, u_perfect, phi_perfect,
+                         u_vacancy, phi_vacancy, allow=()):
+    """Vacancy formation energy; returns (R of the vacancy cell (M - 1, 3), of_vacancy_result).
+    relax_opts None: unrelaxed only."""
+    m = sys.n_atoms - 1
+    R = (C.c_double * (3 * max(m, 1)))()
+    res = of_vacancy_result()
+    st = load().of_vacancy_formation(hp, hv, C.byref(sys), int(site), C.byref(fn),
+                                     C.byref(scf_opts) if scf_opts else None,
+                                     C.byref(relax_opts) if relax_opts else None,
+                                     _ptr(u_perfect), _ptr(phi_perfect), _ptr(u_vacancy),
+                                     _ptr(phi_vacancy), R, C.byref(res))
+    if st != OF_OK and st not in allow:
+        _check(st, "of_vacancy_formation")
+    return np.array(R[:3 * m]).reshape(m, 3), res
 
 
 def of_lr_workspace_fields(fn):

@@ -1334,20 +1334,15 @@ void of_default_relax_opts(of_relax_opts* o) {
     o->max_line = 4;
 }
 
-of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
-                   const of_scf_opts* scf_opts, const of_relax_opts* opts, double* u, double* phi,
-                   double* R_out, double* F_out, of_relax_result* res) {
-    if (!g || !sys || !sys->R || sys->n_atoms < 1 || !fn || !u || !phi || !R_out || !res) {
-        set_error("of_relax: null argument");
-        return OF_EINVAL;
-    }
-    try {
-        of_scf_opts so;
-        if (scf_opts) so = *scf_opts; else of_default_scf_opts(&so);
-        of_relax_opts ro;
-        if (opts) ro = *opts; else of_default_relax_opts(&ro);
-        OF_REQUIRE(ro.ftol > 0 && ro.step0 > 0 && ro.max_line >= 1 && ro.max_steps >= 0, OF_EINVAL,
-                   "of_relax: bad options");
+// Geometry relaxation (Sec. 3.3): NLCG on the positions of sys's ions (Polak-Ribiere, restarted
+// at beta < 0 or an uphill direction) with a secant line search on E'(s) = -F . d.  Every
+// evaluation is a ground state warm-started from u, then the forces.  R_out (host, 3 n_atoms):
+// final positions; F_out (may be null): final forces; e_first (may be null): the ground-state
+// energy at the starting positions.  Throws Error; res->converged tells whether max |F| < ftol.
+static void relax_impl(of_grid* g, const of_system* sys, const of_functional* fn,
+                       const of_scf_opts& so, const of_relax_opts& ro, double* u, double* phi,
+                       double* R_out, double* F_out, of_relax_result* res, double* e_first) {
+    {
         std::memset(res, 0, sizeof(*res));
         const size_t m3 = 3 * (size_t)sys->n_atoms;
         std::vector<double> R(sys->R, sys->R + m3), F(m3), Fp(m3), d(m3), Rs(m3), Fs(m3);
@@ -1374,6 +1369,7 @@ of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
             forces(g, &sx, phi, Fx.data());
         };
         evaluate(R, F);
+        if (e_first) *e_first = gs.energy;
         d = F;
         bool have_prev = false;
         while (res->steps < ro.max_steps && maxabs(F) >= ro.ftol) {
@@ -1412,11 +1408,126 @@ of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
         res->converged = res->max_force < ro.ftol;
         std::copy(R.begin(), R.end(), R_out);
         if (F_out) std::copy(F.begin(), F.end(), F_out);
+    }
+}
+
+static void check_relax_opts(const of_relax_opts& ro, const char* where) {
+    OF_REQUIRE(ro.ftol > 0 && ro.step0 > 0 && ro.max_line >= 1 && ro.max_steps >= 0, OF_EINVAL,
+               "%s: bad relaxation options", where);
+}
+
+of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
+                   const of_scf_opts* scf_opts, const of_relax_opts* opts, double* u, double* phi,
+                   double* R_out, double* F_out, of_relax_result* res) {
+    if (!g || !sys || !sys->R || sys->n_atoms < 1 || !fn || !u || !phi || !R_out || !res) {
+        set_error("of_relax: null argument");
+        return OF_EINVAL;
+    }
+    try {
+        of_scf_opts so;
+        if (scf_opts) so = *scf_opts; else of_default_scf_opts(&so);
+        of_relax_opts ro;
+        if (opts) ro = *opts; else of_default_relax_opts(&ro);
+        check_relax_opts(ro, "of_relax");
+        relax_impl(g, sys, fn, so, ro, u, phi, R_out, F_out, res, nullptr);
         if (!res->converged) {
             set_error("of_relax: max force %.3e after %d steps", res->max_force, res->steps);
             return OF_ENOCONV;
         }
         return OF_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}
+
+// Vacancy formation energy (Sec. 5.6): E_vf = E(M-1, 1, (M-1)/M Omega) - ((M-1)/M) E(M, 0, Omega).
+// The vacancy cell keeps the volume per atom: its sides and the remaining positions are the
+// perfect cell's scaled by ((M-1)/M)^{1/3} about the origin, on the same number of grid points.
+// The two cells' ground states run at once on the stream pool; the vacancy cell's relaxation
+// (optional) follows its own ground state.
+of_status of_vacancy_formation(of_grid* perfect, of_grid* vacancy, const of_system* sys, int site,
+                               const of_functional* fn, const of_scf_opts* scf_opts,
+                               const of_relax_opts* relax_opts, double* u_perfect,
+                               double* phi_perfect, double* u_vacancy, double* phi_vacancy,
+                               double* R_out, of_vacancy_result* res) {
+    if (!perfect || !vacancy || !sys || !sys->R || !sys->Z || !fn || !u_perfect || !phi_perfect ||
+        !u_vacancy || !phi_vacancy || !res) {
+        set_error("of_vacancy_formation: null argument");
+        return OF_EINVAL;
+    }
+    try {
+        const int M = sys->n_atoms;
+        OF_REQUIRE(M >= 2 && site >= 0 && site < M, OF_EINVAL,
+                   "of_vacancy_formation: site %d of a cell with %d ions", site, M);
+        OF_REQUIRE(perfect != vacancy, OF_EINVAL, "of_vacancy_formation: the two cells share a grid handle");
+        OF_REQUIRE(perfect->d.n1 == vacancy->d.n1 && perfect->d.n2 == vacancy->d.n2 &&
+                       perfect->d.n3 == vacancy->d.n3 && perfect->N == vacancy->N,
+                   OF_EINVAL, "of_vacancy_formation: the vacancy grid must have the perfect grid's "
+                   "points (%d x %d x %d) and order", perfect->d.n1, perfect->d.n2, perfect->d.n3);
+        OF_REQUIRE(perfect->stream == vacancy->stream && perfect->device == vacancy->device, OF_EINVAL,
+                   "of_vacancy_formation: the two handles differ in stream or device");
+        const double scale = std::cbrt((double)(M - 1) / (double)M);
+        for (int a = 0; a < 3; ++a)
+            OF_REQUIRE(std::fabs(vacancy->L[a] - scale * perfect->L[a]) <= 1e-12 * perfect->L[a],
+                       OF_EINVAL, "of_vacancy_formation: vacancy cell side %d is %.15g, expected "
+                       "((M-1)/M)^(1/3) x %.15g = %.15g", a, vacancy->L[a], perfect->L[a],
+                       scale * perfect->L[a]);
+        of_scf_opts so;
+        if (scf_opts) so = *scf_opts; else of_default_scf_opts(&so);
+        of_relax_opts ro;
+        if (relax_opts) {
+            ro = *relax_opts;
+            check_relax_opts(ro, "of_vacancy_formation");
+        }
+        std::memset(res, 0, sizeof(*res));
+        std::vector<double> Rv, Zv;
+        for (int J = 0; J < M; ++J) {
+            if (J == site) continue;
+            for (int c = 0; c < 3; ++c) Rv.push_back(scale * sys->R[3 * J + c]);
+            Zv.push_back(sys->Z[J]);
+        }
+        of_system vs = *sys;
+        vs.n_atoms = M - 1;
+        vs.R = Rv.data();
+        vs.Z = Zv.data();
+        std::vector<double> Rfin(Rv), Ffin(Rv.size());
+        of_scf_result rp{};
+        of_grid* grids[2] = {perfect, vacancy};
+        const of_status st = run_on_stream_pool(2, grids, [&](int c) -> of_status {
+            if (c == 0) {
+                scf(perfect, sys, fn, &so, u_perfect, phi_perfect, &rp);
+                OF_REQUIRE(rp.converged, OF_ENOCONV, "perfect cell: ground state not converged "
+                           "(nlcg residual %.3e, fixed-point error %.3e)", rp.nlcg_residual, rp.fp_error);
+                return OF_OK;
+            }
+            if (relax_opts) {
+                of_relax_result rr{};
+                relax_impl(vacancy, &vs, fn, so, ro, u_vacancy, phi_vacancy, Rfin.data(), Ffin.data(),
+                           &rr, &res->e_unrelaxed);
+                res->e_relaxed = rr.energy;
+                res->max_force = rr.max_force;
+                res->relax_steps = rr.steps;
+                res->evaluations = rr.evaluations;
+                OF_REQUIRE(rr.converged, OF_ENOCONV, "vacancy cell: max force %.3e after %d "
+                           "relaxation steps", rr.max_force, rr.steps);
+            } else {
+                of_scf_result rv{};
+                scf(vacancy, &vs, fn, &so, u_vacancy, phi_vacancy, &rv);
+                OF_REQUIRE(rv.converged, OF_ENOCONV, "vacancy cell: ground state not converged "
+                           "(nlcg residual %.3e, fixed-point error %.3e)", rv.nlcg_residual, rv.fp_error);
+                forces(vacancy, &vs, phi_vacancy, Ffin.data());
+                res->e_unrelaxed = res->e_relaxed = rv.energy;
+                for (double f : Ffin) res->max_force = std::max(res->max_force, std::fabs(f));
+                res->evaluations = 1;
+            }
+            return OF_OK;
+        });
+        const double frac = (double)(M - 1) / (double)M;
+        res->e_perfect = rp.energy;
+        res->evf_unrelaxed = res->e_unrelaxed - frac * rp.energy;
+        res->evf_relaxed = res->e_relaxed - frac * rp.energy;
+        if (R_out) std::copy(Rfin.begin(), Rfin.end(), R_out);
+        return st;
     } catch (const Error& e) {
         return e.code;
     }

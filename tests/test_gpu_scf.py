@@ -136,6 +136,69 @@ def test_relaxation_matches_oracle(prec):
     assert np.abs(R - ref.R).max() < 1e-3
 
 
+@pytest.mark.parametrize("relaxed", [False, True])
+def test_vacancy_formation_matches_oracle(relaxed):
+    # Sec. 5.6: E_vf = E(M-1, 1, (M-1)/M Omega) - ((M-1)/M) E(M, 0, Omega) for the 8-atom TFW cell
+    # (2x1x1 FCC, 12 points per cell edge) with site 0 removed, unrelaxed and relaxed at fixed
+    # volume, against the oracle's workflow
+    from oracle.vacancy import vacancy_formation
+    cell = W.fcc_supercell((2, 1, 1), points_per_cell=12)
+    grid = O.Grid(cell.n, cell.L, 6)
+    ref = vacancy_formation(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.tfw_functional(), 0,
+                            relaxed=relaxed, relax_kw=dict(ftol=1e-4), nlcg_tol=1e-9)
+    stream = torch.cuda.current_stream()
+    hp = B.of_grid_create(cell.n, cell.L, 6, stream)
+    hv = B.of_grid_create(cell.n, B.vacancy_cell_lengths(cell.L, cell.n_atoms), 6, stream)
+    try:
+        so = B.of_default_scf_opts()
+        so.precision = B.OF_F32
+        so.nlcg_tol = 1e-9
+        ro = None
+        if relaxed:
+            ro = B.of_default_relax_opts()
+            ro.ftol = 1e-4
+        up = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        uv = torch.ones_like(up)
+        pp, pv = torch.zeros_like(up), torch.zeros_like(up)
+        R, res = B.of_vacancy_formation(hp, hv, B.make_system(cell.R, cell.Z, cell.sigma, cell.rc),
+                                        0, Fn.tfw(), so, ro, up, pp, uv, pv)
+    finally:
+        B.of_grid_destroy(hp)
+        B.of_grid_destroy(hv)
+    M = cell.n_atoms
+    assert abs(res.e_perfect - ref.e_perfect) / M <= E_TOL
+    assert abs(res.e_unrelaxed - ref.e_unrelaxed) / (M - 1) <= E_TOL
+    assert abs(res.evf_unrelaxed - ref.evf_unrelaxed) <= 2 * M * E_TOL
+    assert abs(res.evf_relaxed - ref.evf_relaxed) <= 2 * M * E_TOL
+    if relaxed:
+        assert res.relax_steps == ref.relax_steps and res.evaluations == ref.evaluations
+        assert res.max_force < 1e-4 and res.evf_relaxed < res.evf_unrelaxed
+        assert np.abs(R - ref.R_vacancy).max() < 1e-3
+    else:
+        assert res.evf_relaxed == res.evf_unrelaxed and res.relax_steps == 0
+        assert np.abs(R - O.vacancy_cell(grid, cell.R, cell.Z, 0)[1]).max() <= 1e-13
+
+
+def test_vacancy_formation_rejects_a_cell_of_the_wrong_size():
+    cell = W.al4_cell(points_per_cell=12)
+    stream = torch.cuda.current_stream()
+    hp = B.of_grid_create(cell.n, cell.L, 6, stream)
+    hv = B.of_grid_create(cell.n, cell.L, 6, stream)   # not scaled to the volume per atom
+    try:
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+        with pytest.raises(B.OfError) as e:
+            B.of_vacancy_formation(hp, hv, sysd, 0, Fn.tfw(), None, None, u, u.clone(), u.clone(),
+                                   u.clone())
+        assert e.value.status == B.OF_EINVAL
+        with pytest.raises(B.OfError):
+            B.of_vacancy_formation(hp, hv, sysd, 4, Fn.tfw(), None, None, u, u.clone(), u.clone(),
+                                   u.clone())
+    finally:
+        B.of_grid_destroy(hp)
+        B.of_grid_destroy(hv)
+
+
 def test_fixed_point_on_u_matches_golden():
     # the alternative fixed point of Sec. 5.3 (Anderson mixing of u instead of V_LR) reaches
     # the same ground state
