@@ -31,5 +31,7 @@ from .scf import (hamiltonian_apply, inner_energy, nlcg, anderson_update, scf_gr
 from .forces import forces
 from .relax import relax, RelaxResult
 from .vacancy import vacancy_cell, vacancy_formation, VacancyResult
+from .overlap import (repulsive_correction_grid, repulsive_correction_grid_forces,
+                      repulsive_correction_pairs)
 
 __all__ = [n for n in dir() if not n.startswith("_")]
