@@ -103,6 +103,12 @@ typedef struct {
                                the paper's construction from the potential (Sec. 4), V_J sampled
                                on each ion's box widened by N points (the self energy with it;
                                forces keep the closed-form gradient of b_J) */
+    double sigma_ref;       /* overlap correction E_c^* and f^c (App. B): 0 = point reference
+                               charges, the closed form 1/2 sum Z_I Z_J erfc(R/2 sigma)/R;
+                               > 0 = evaluated on the grid (Eq. RepulsiveCorrection2) with
+                               Gaussian reference charges of this width within rc_ref, V_c from
+                               one periodic Poisson solve (needs b_from_potential = 0) */
+    double rc_ref;          /* cutoff of the reference charges (used when sigma_ref > 0) */
 } of_system;
 
 /* Kinetic functional T_TF + lambda T_vW + mu T_LR (Eq. KineticEnergyComponents).  The

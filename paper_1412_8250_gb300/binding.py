@@ -37,7 +37,7 @@ class of_solve_info(C.Structure):
 class of_system(C.Structure):
     _fields_ = [("n_atoms", C.c_int), ("R", C.POINTER(C.c_double)),
                 ("Z", C.POINTER(C.c_double)), ("sigma", C.c_double), ("rc", C.c_double),
-                ("b_from_potential", C.c_int)]
+                ("b_from_potential", C.c_int), ("sigma_ref", C.c_double), ("rc_ref", C.c_double)]
 
 
 class of_functional(C.Structure):
@@ -249,12 +249,14 @@ def of_kernel_solve(h, f, P, Q, kf2, W, opts=None, allow=()):
     return info
 
 
-def make_system(R, Z, sigma, rc, b_from_potential=False):
-    """of_system from numpy arrays (kept alive on the returned object)."""
+def make_system(R, Z, sigma, rc, b_from_potential=False, sigma_ref=0.0, rc_ref=0.0):
+    """of_system from numpy arrays (kept alive on the returned object).  sigma_ref > 0: the
+    overlap correction on the grid with reference charges of that width within rc_ref."""
     R = np.ascontiguousarray(np.asarray(R, dtype=np.float64).reshape(-1, 3))
     Z = np.ascontiguousarray(np.asarray(Z, dtype=np.float64).reshape(-1))
     s = of_system(int(Z.size), R.ctypes.data_as(C.POINTER(_D)), Z.ctypes.data_as(C.POINTER(_D)),
-                  float(sigma), float(rc), int(bool(b_from_potential)))
+                  float(sigma), float(rc), int(bool(b_from_potential)), float(sigma_ref),
+                  float(rc_ref))
     s._keep = (R, Z)
     return s
 

@@ -212,6 +212,100 @@ __global__ void k_overlap(int M, const AtomBox* boxes, double L1, double L2, dou
     fc[3 * I + 2] = f2;
 }
 
+// ---- E_c^* and f^c on the grid with Gaussian reference charges (App. B)
+// Reference charges b~_J of width sigma_ref within rc_ref, with the sign of b_J, so that
+// b~ - b is neutral; V_c solves -(1/4pi) L_h V_c = b~ - b, and
+//   E_c^* = 1/2 int (b~ + b) V_c + 1/2 sum_J int b_J V_J - 1/2 sum_J int b~_J V~_J.
+// f^c follows the expression printed after Eq. RepulsiveCorrection2:
+//   f_J = 1/2 sum_J' int [ grad b~_J' (V_c - V~_J') + grad b_J' (V_c + V_J')
+//                          + grad(V~_J' - V_J') (b~ + b) + b_J' grad V_J' - b~_J' grad V~_J' ].
+
+// (1/r) dV/dr of V = -Z erf(r/(sqrt2 s))/r, so that grad V = g(r) (x - R); near r = 0 the
+// series Z v0/(3 s^2) (1 - 3 r^2/(10 s^2)) avoids the cancellation of the two terms.
+__device__ __forceinline__ double gauss_gradV_over_r(double r2, double Z, const Gauss& q) {
+    const double x2 = r2 * q.inv2s2;   // (r / (sqrt2 s))^2
+    if (x2 < 1e-4) return Z * q.v0 * (2.0 * q.inv2s2) / 3.0 * (1.0 - 0.6 * x2);
+    const double r = sqrt(r2);
+    return -Z * (q.v0 * exp(-x2) / r - erf(r * q.erfscale) / r2) / r;
+}
+
+// Block (J, plane) of the box of radius `cut` (>= rc, rc_ref): the three components of the
+// integrand above summed over the plane (the factor dV/2 is applied by k_sum_planes).
+// Vc: the grid potential with its constant; bsum: b~ + b.
+__global__ void __launch_bounds__(256) k_overlap_grid_forces(Dims d, double h1, double h2, double h3,
+                                                             const AtomBox* boxes, Gauss q, Gauss qt,
+                                                             double cut, const double* Vc,
+                                                             const double* bsum, double* part,
+                                                             int max_planes) {
+    const int J = blockIdx.x, pl = blockIdx.y;
+    const AtomBox B = boxes[J];
+    double f[3] = {0.0, 0.0, 0.0};
+    if (pl < B.len[2]) {
+        const int k = B.lo[2] + pl;
+        const double dz = k * h3 - B.R[2];
+        const int kw = wrap_index(k, d.n3);
+        const int nxy = B.len[0] * B.len[1];
+        const double cut2 = cut * cut, rc2 = q.rc * q.rc, rct2 = qt.rc * qt.rc;
+        const double inv_s2 = 2.0 * q.inv2s2, inv_st2 = 2.0 * qt.inv2s2;
+        for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
+            const int jj = t / B.len[0];
+            const int i = B.lo[0] + (t - jj * B.len[0]);
+            const int j = B.lo[1] + jj;
+            const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > cut2) continue;
+            const long long idx = wrap_index(i, d.n1) +
+                                  (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+            const double g = gauss_gradV_over_r(r2, B.Z, q);
+            const double gt = gauss_gradV_over_r(r2, B.Z, qt);
+            // grad (V~_J - V_J) (b~ + b)
+            double w = (gt - g) * bsum[idx];
+            if (r2 <= rc2 || r2 <= rct2) {
+                const double vc = Vc[idx];
+                const double r = sqrt(r2);
+                if (r2 <= rc2) {   // grad b_J (V_c + V_J) + b_J grad V_J, grad b_J = -b_J (x-R)/s^2
+                    const double bj = gauss_b(r2, B.Z, q);
+                    w += -bj * inv_s2 * (vc + gauss_V(r, B.Z, q)) + bj * g;
+                }
+                if (r2 <= rct2) {  // grad b~_J (V_c - V~_J) - b~_J grad V~_J
+                    const double btj = gauss_b(r2, B.Z, qt);
+                    w += -btj * inv_st2 * (vc - gauss_V(r, B.Z, qt)) - btj * gt;
+                }
+            }
+            f[0] += w * dx;
+            f[1] += w * dy;
+            f[2] += w * dz;
+        }
+    }
+    __shared__ double sh[8][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double s = warp_sum(f[c]);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w][threadIdx.x];
+        part[((long long)J * max_planes + pl) * 3 + threadIdx.x] = s;
+    }
+}
+
+// out = alpha x + beta y
+__global__ void k_axpby_fields(long long n, double alpha, const double* x, double beta,
+                               const double* y, double* out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = alpha * x[i] + beta * y[i];
+}
+
+// x += c
+__global__ void k_add_constant(long long n, double* x, double c) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] += c;
+}
+
 // ---- b_J = -(1/4pi) L_h V_J (the paper's construction from the potential, Sec. 4)
 // V_J sampled on the ion's ball box widened by N points each way: box point (i, j, k), with
 // i = 0 .. n[0] - 1 standing for grid index lo[0] - N + i (unwrapped)
@@ -327,8 +421,96 @@ static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, doubl
     }
 }
 
+// sum over the ions and their periodic images of (V~_J - V_J)(x0), terms beyond `cut` dropped
+static double potential_difference_at(const double x0[3], const of_system* sys, const double L[3],
+                                      double cut) {
+    const double es = 1.0 / (std::sqrt(2.0) * sys->sigma), est = 1.0 / (std::sqrt(2.0) * sys->sigma_ref);
+    int reps[3];
+    for (int c = 0; c < 3; ++c) reps[c] = (int)std::ceil(cut / L[c]) + 1;
+    double s = 0.0;
+    for (int J = 0; J < sys->n_atoms; ++J)
+        for (int a = -reps[0]; a <= reps[0]; ++a)
+            for (int b = -reps[1]; b <= reps[1]; ++b)
+                for (int c = -reps[2]; c <= reps[2]; ++c) {
+                    const double dx = x0[0] - sys->R[3 * J] - a * L[0];
+                    const double dy = x0[1] - sys->R[3 * J + 1] - b * L[1];
+                    const double dz = x0[2] - sys->R[3 * J + 2] - c * L[2];
+                    const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+                    if (r > cut) continue;
+                    // V~_J - V_J = -Z (erf(r e~) - erf(r e)) / r, limit -Z (2/sqrt pi)(e~ - e)
+                    s += r < 1e-12 ? -sys->Z[J] * 2.0 / std::sqrt(M_PI) * (est - es)
+                                   : -sys->Z[J] * (std::erf(r * est) - std::erf(r * es)) / r;
+                }
+    return s;
+}
+
+// E_c^* and f^c of App. B on the grid (the comment above k_overlap_grid_forces)
+static void overlap_correction_grid(of_grid* g, const of_system* sys, double* e_c, double* fc_host) {
+    OF_REQUIRE(sys->rc_ref > 0 && !sys->b_from_potential, OF_EINVAL,
+               "overlap correction on the grid: needs rc_ref > 0 and b_from_potential = 0");
+    const long long n = g->d.n;
+    const int nb = red_blocks(n, 256 * 4);
+    double* f = (double*)ws(g, WS_OVL, sizeof(double) * 4 * (size_t)n);
+    double *b = f, *bt = f + n, *rho = f + 2 * n, *Vc = f + 3 * n;
+    of_system sb = *sys;   // the ions' charges as sampled from their closed form
+    sb.b_from_potential = 0;
+    of_system st = sb;     // the reference charges
+    st.sigma = sys->sigma_ref;
+    st.rc = sys->rc_ref;
+    double self_b = 0.0, self_bt = 0.0;   // -1/2 sum_J int b_J V_J, and for b~
+    pseudocharge_impl(g, &sb, b, &self_b);
+    pseudocharge_impl(g, &st, bt, &self_bt);
+    launch(k_axpby_fields, nb, 256, g->stream, n, 1.0, (const double*)bt, -1.0, (const double*)b, rho);
+    OF_LAUNCH_CHECK();
+    OF_CUDA(cudaMemsetAsync(Vc, 0, sizeof(double) * n, g->stream));
+    KrylovOpts ko = krylov_opts(nullptr);
+    ko.precision = OF_F32;   // FP32 multigrid passes refined in FP64
+    ko.tol = 1e-12;
+    const of_status ps = poisson(g, rho, Vc, ko, nullptr);
+    OF_REQUIRE(ps == OF_OK, ps, "overlap correction on the grid: Poisson solve for V_c failed");
+    // the constant of V_c: its value at the grid point x = 0 is the lattice sum of V~_J - V_J
+    const double cut = 12.0 * std::max(sys->sigma, sys->sigma_ref);
+    const double x0[3] = {0.0, 0.0, 0.0};
+    const double s0 = potential_difference_at(x0, sys, g->L, cut);
+    double v00 = 0.0;
+    OF_CUDA(cudaMemcpyAsync(&v00, Vc, sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    OF_CUDA(cudaStreamSynchronize(g->stream));
+    const double c = s0 - v00;
+    // b~ + b into rho
+    launch(k_axpby_fields, nb, 256, g->stream, n, 1.0, (const double*)bt, 1.0, (const double*)b, rho);
+    launch(k_add_constant, nb, 256, g->stream, n, Vc, c);
+    OF_LAUNCH_CHECK();
+    if (e_c) {
+        launch(k_sum_product, nb, 256, g->stream, n, (const double*)rho, (const double*)Vc,
+               red_ctx(g, 117));
+        OF_LAUNCH_CHECK();
+        double sv = 0.0;
+        fetch_scalars(g, 117, 1, &sv);
+        *e_c = 0.5 * g->dV * sv - self_b + self_bt;
+    }
+    if (fc_host) {
+        of_system sc = sb;   // boxes of radius cut around each ion
+        sc.rc = std::max(cut, std::max(sys->rc, sys->rc_ref));
+        AtomSet a = upload_atoms(g, &sc);
+        const int M = a.n_atoms;
+        const size_t nparts = (size_t)M * a.max_planes * 3;
+        double* part = (double*)ws(g, WS_OVLP, sizeof(double) * (nparts + 3 * (size_t)M + 8));
+        double* per_atom = part + nparts;
+        launch(k_overlap_grid_forces, dim3(M, a.max_planes), 256, g->stream, g->d, g->h[0], g->h[1],
+               g->h[2], (const AtomBox*)a.d_boxes, gauss(&sb), gauss(&st), sc.rc,
+               (const double*)Vc, (const double*)rho, part, a.max_planes);
+        launch(k_sum_planes, (3 * M + 127) / 128, 128, g->stream, M, a.max_planes, 3,
+               (const double*)part, 0.5 * g->dV, per_atom);
+        OF_LAUNCH_CHECK();
+        OF_CUDA(cudaMemcpyAsync(fc_host, per_atom, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost,
+                                g->stream));
+        OF_CUDA(cudaStreamSynchronize(g->stream));
+    }
+}
+
 // E_c^* and f^c into host outputs (either may be null)
 void overlap_correction(of_grid* g, const of_system* sys, double* e_c, double* fc_host) {
+    if (sys && sys->sigma_ref > 0.0) return overlap_correction_grid(g, sys, e_c, fc_host);
     AtomSet a = upload_atoms(g, sys);
     const int M = a.n_atoms;
     const double cutoff = 14.0 * sys->sigma;
@@ -356,6 +538,12 @@ void pseudocharge(of_grid* g, const of_system* sys, double* b, double* e_self) {
 }
 
 void forces(of_grid* g, const of_system* sys, const double* phi, double* F) {
+    OF_REQUIRE(sys && sys->n_atoms >= 1, OF_EINVAL, "invalid of_system");
+    std::vector<double> fc(3 * (size_t)sys->n_atoms);
+    // f^c on the grid samples charges and solves for V_c in this handle's scratch (the ion
+    // boxes and partial sums below reuse it), so it goes first; the closed form goes last
+    const bool fc_on_grid = sys->sigma_ref > 0.0;
+    if (fc_on_grid) overlap_correction(g, sys, nullptr, fc.data());   // synchronises the stream
     AtomSet a = upload_atoms(g, sys);
     Gauss q = gauss(sys);
     const int M = a.n_atoms;
@@ -368,8 +556,7 @@ void forces(of_grid* g, const of_system* sys, const double* phi, double* F) {
     launch(k_sum_planes, (3 * M + 127) / 128, 128, g->stream, M, a.max_planes, 3, part, g->dV,
                                                             per_atom);
     OF_LAUNCH_CHECK();
-    std::vector<double> fc(3 * (size_t)M);
-    overlap_correction(g, sys, nullptr, fc.data());   // synchronises the stream
+    if (!fc_on_grid) overlap_correction(g, sys, nullptr, fc.data());   // synchronises the stream
     OF_CUDA(cudaMemcpyAsync(F, per_atom, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, g->stream));
     OF_CUDA(cudaStreamSynchronize(g->stream));
     for (size_t i = 0; i < fc.size(); ++i) F[i] += fc[i];

@@ -243,6 +243,8 @@ enum Slot {
     WS_AND,      // Anderson history
     WS_ATOM,     // per-atom device data
     WS_ATOMBOX,  // one ion's widened box (pseudocharge from the potential)
+    WS_OVL,      // reference charges, V_c and its right-hand side (overlap correction on the grid)
+    WS_OVLP,     // per-(ion, plane) partial forces of that correction
     WS_MG,       // multigrid hierarchy
     WS_NSLOTS
 };
