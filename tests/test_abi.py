@@ -49,3 +49,41 @@ def test_default_options(lib):
     o = B.of_default_scf_opts()
     assert o.nlcg_tol == 1e-7 and o.anderson_m == 7 and o.anderson_zeta == 0.3
     assert o.poisson.tol == 1e-10 and o.kernel.max_iter == 20000
+
+
+STRUCTS = ["of_solve_opts", "of_solve_info", "of_system", "of_functional", "of_scf_opts",
+           "of_scf_result", "of_relax_opts", "of_relax_result", "of_vacancy_result",
+           "of_kernel_stat"]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # every record the binding passes across the boundary has the header's size and field
+    # offsets (a C program built from include/of.h prints them)
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "of.h"', 'int main(void) {']
+    for name in STRUCTS:
+        cls = getattr(B, name)
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            cname = "lambda" if fname == "lambda_" else fname
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {cname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        name, field, value = line.split()
+        cls = getattr(B, name)
+        got = C.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert got == int(value), (name, field, got, value)
+        seen += 1
+    assert seen > 60
