@@ -42,6 +42,11 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.of_laplacian_apply(None, 0, None, None) == B.OF_EINVAL
     assert lib.of_poisson_solve(None, None, None, None, None) == B.OF_EINVAL
     assert lib.of_forces(None, None, None, None, None) == B.OF_EINVAL
+    assert lib.of_relax(None, None, None, None, None, None, None, None, None, None) == B.OF_EINVAL
+    assert "of_relax" in B.of_last_error()
+    assert lib.of_vacancy_formation(None, None, None, 0, None, None, None, None, None, None, None,
+                                    None, None) == B.OF_EINVAL
+    assert "of_vacancy_formation" in B.of_last_error()
     assert lib.of_grid_destroy(None) == B.OF_OK
 
 
