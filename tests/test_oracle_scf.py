@@ -200,19 +200,25 @@ def test_vw_energy_gradient_form_plane_wave_and_limit():
     assert gaps[0] < 1e-3 and gaps[1] < gaps[0] / 100, gaps
 
 
-def test_ground_state_energy_converges_at_order_2n():
+def test_ground_state_energy_and_forces_converge_at_order_2n():
     # Sec. 5.1: on the 4-atom cell with the corner atom moved to (0.80, 0.56, 0.42), the
-    # ground-state energy error against a fine order-12 reference falls as h^{2N} (measured
-    # rates between 16, 20 and 24 points per 7.6 bohr: 2.01 / 3.9 / 5.7 for N = 1 / 2 / 3).
-    # A wrong weight, a dropped stencil term or an energy term inconsistent with the
-    # Hamiltonian lowers the order.
+    # errors of the ground-state energy and of the forces against a fine order-12 reference
+    # fall as h^{2N} (measured rates between 16, 20 and 24 points per 7.6 bohr: energy 2.01 /
+    # 3.9 / 5.7, forces 1.99 / 3.9 / 5.6 for N = 1 / 2 / 3).  A wrong weight, a dropped
+    # stencil term or an energy term inconsistent with the Hamiltonian lowers the order.
     fn = O.tfw_functional()
     c = W.al4_displaced_cell(points_per_cell=16)
-    ref = O.scf_ground_state(O.Grid((40, 40, 40), c.L, 6), c.R, c.Z, c.sigma, c.rc, fn,
-                             nlcg_tol=1e-10).energy
+    g = O.Grid((40, 40, 40), c.L, 6)
+    r = O.scf_ground_state(g, c.R, c.Z, c.sigma, c.rc, fn, nlcg_tol=1e-10)
+    E_ref, F_ref = r.energy, O.forces(r.phi, c.R, c.Z, c.sigma, c.rc, g)
     ns = (16, 20, 24)
     for N in (1, 2, 3):
-        errs = [abs(O.scf_ground_state(O.Grid((n, n, n), c.L, N), c.R, c.Z, c.sigma, c.rc, fn,
-                                       nlcg_tol=1e-10).energy - ref) for n in ns]
-        rates = [np.log(errs[i] / errs[i + 1]) / np.log(ns[i + 1] / ns[i]) for i in range(2)]
-        assert min(rates) > 2 * N - 0.5, (N, errs, rates)
+        e_err, f_err = [], []
+        for n in ns:
+            gn = O.Grid((n, n, n), c.L, N)
+            rn = O.scf_ground_state(gn, c.R, c.Z, c.sigma, c.rc, fn, nlcg_tol=1e-10)
+            e_err.append(abs(rn.energy - E_ref))
+            f_err.append(np.abs(O.forces(rn.phi, c.R, c.Z, c.sigma, c.rc, gn) - F_ref).max())
+        for errs in (e_err, f_err):
+            rates = [np.log(errs[i] / errs[i + 1]) / np.log(ns[i + 1] / ns[i]) for i in range(2)]
+            assert min(rates) > 2 * N - 0.5, (N, errs, rates)
