@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--relax", action="store_true",
                    help="measure a geometry relaxation of the 108-atom 96^3 cell instead of the "
                         "benchmark step")
+    p.add_argument("--convergence", action="store_true",
+                   help="mesh convergence of the energy and forces with the FD order (4-atom "
+                        "cell, orders 2, 6, 12) instead of the benchmark step")
     p.add_argument("--vacancy", action="store_true",
                    help="vacancy formation energy of the 108-atom 96^3 cell (unrelaxed and "
                         "relaxed) instead of the benchmark step")
@@ -504,6 +507,60 @@ def relax_case(args):
     return 0
 
 
+def convergence_case(args):
+    """Sec. 5.1's study on the GPU: ground-state energy and forces of the 4-atom TFW cell with
+    the corner atom at (0.80, 0.56, 0.42) for 16..48 points per 7.6 bohr and FD orders 2, 6, 12,
+    errors against the order-12 result on 64 points, and the fitted rates.  Prints one JSON
+    line."""
+    import numpy as np
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    stream = torch.cuda.current_stream()
+    fn = Fn.tfw()
+
+    def run(n, N):
+        c = W.al4_displaced_cell(points_per_cell=n)
+        h = B.of_grid_create(c.n, c.L, N, stream)
+        try:
+            o = B.of_default_scf_opts()
+            o.nlcg_tol = 1e-10
+            u = torch.ones(c.shape, dtype=torch.float64, device="cuda")
+            phi = torch.zeros_like(u)
+            sysd = B.make_system(c.R, c.Z, c.sigma, c.rc)
+            res = B.of_scf_ground_state(h, sysd, fn, o, u, phi)
+            F = B.of_forces(h, sysd, u, phi)
+        finally:
+            B.of_grid_destroy(h)
+        return res.energy / c.n_atoms, F
+
+    t0 = time.time()
+    E_ref, F_ref = run(64, 6)
+    ns = (16, 20, 24, 32, 40, 48)
+    out = {}
+    for N in (1, 3, 6):
+        rows = []
+        for n in ns:
+            E, F = run(n, N)
+            rows.append({"points_per_edge": n, "h_bohr": 7.6 / n,
+                         "energy_error_ha_per_atom": abs(E - E_ref),
+                         "force_error_ha_per_bohr": float(np.abs(F - F_ref).max())})
+        for key in ("energy_error_ha_per_atom", "force_error_ha_per_bohr"):
+            e = [r[key] for r in rows]
+            ok = [i for i in range(len(ns)) if e[i] > 1e-11]
+            rate = (float(np.polyfit(np.log([7.6 / ns[i] for i in ok]), np.log([e[i] for i in ok]), 1)[0])
+                    if len(ok) >= 2 else None)
+            out.setdefault(f"order_{2 * N}", {})[key.split("_error")[0] + "_rate"] = rate
+        out[f"order_{2 * N}"]["rows"] = rows
+    line = {"metric": "mesh convergence rates of the energy and forces (Sec. 5.1)", "unit": "rate",
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "4-atom FCC Al-like cell, a=7.6 bohr, corner atom at (0.80, 0.56, 0.42), "
+                                   "TFW, reference: order 12 on 64 points per edge"},
+            "wall_s": time.time() - t0, "result": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def vacancy_case(args):
     """Vacancy formation energy (Sec. 5.6) of the perfect 108-atom 3x3x3 FCC cell (a = 7.6,
     96^3, WT-type functional, mixed form, the benchmark's options), the site nearest the centre
@@ -828,6 +885,8 @@ def main():
         return wgc(args)
     if args.relax:
         return relax_case(args)
+    if args.convergence:
+        return convergence_case(args)
     if args.vacancy:
         return vacancy_case(args)
     if args.mixing_study:
