@@ -17,6 +17,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -99,7 +100,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples: $OF_CLOCKS_DIR if set (to keep them), else the temporary directory
+        out_dir = os.environ.get("OF_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"of_clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
