@@ -213,9 +213,11 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
  * device array of about 10.6 MB that every GPU loading the library holds until exit, which
  * limits the grid to n1*n2*n3 <= 262144 points (OF_EINVAL beyond).  All calls share that array,
  * so calls whose GPU work overlaps (on different streams or threads) race; serialise them.
+ * Nor does it create streams, events or CUDA graphs: every CG iteration is launched directly.
  * The first call on a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.  Synchronises the stream
- * before returning. */
+ * device current); make that first call before any stream capture.  Every call reads solver
+ * scalars back to the host, synchronising the stream, at each convergence check and before
+ * returning. */
 of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1, double L2, double L3,
                                    int fd_half_order, void* stream, const double* rho,
                                    double* phi, const of_solve_opts* opts, of_solve_info* info);
@@ -366,6 +368,12 @@ int of_precond_num_params(void);
 /* Copies params (host, 7809 floats) to a new handle.  OF_EINVAL on a wrong count. */
 of_status of_precond_create(const float* params, int nparams, of_precond** out);
 of_status of_precond_destroy(of_precond* P);
+/* Failure detection: the tensor-core kernels give up waiting for an MMA completion after
+ * `seconds` (default 2; 0 <= seconds <= 60), then let the MMAs in flight finish (waiting up to
+ * the default limit), free their tensor memory and return; the call that launched them returns
+ * OF_ETIMEOUT and the grid and the handle stay usable.  0 makes every such wait give up at
+ * once, which exercises that path without a fault. */
+of_status of_precond_set_wait_limit(of_precond* P, double seconds);
 /* Current FP32 master parameters to host params[7809]. */
 of_status of_precond_get_params(of_precond* P, float* params, int nparams);
 /* z = s net(r / s) for device float fields r, z (r != z).  Synchronises. */
@@ -392,6 +400,9 @@ const char* of_last_error(void);
 
 /* ---- measurement hooks (no counterpart in the paper) ----
  * of_launch_count: kernel launches made by this library so far in the process.
+ * of_resource_count: device buffers, pinned host buffers, streams, events and executable CUDA
+ * graphs this library has created so far in the process (a call that creates none leaves it
+ * unchanged).
  * of_profile_enable: time every sample_every-th launch of each kernel class on the grid's
  * stream with CUDA events (0 stops timing, counting continues); resets the statistics.
  * of_profile_read: synchronises the stream, fills up to max records (one per kernel class
@@ -409,6 +420,7 @@ typedef struct {
 } of_kernel_stat;
 
 unsigned long long of_launch_count(void);
+unsigned long long of_resource_count(void);
 const char* of_kernel_class_name(int kernel_class);
 of_status of_profile_enable(of_grid* g, int sample_every);
 int of_profile_read(of_grid* g, of_kernel_stat* out, int max);

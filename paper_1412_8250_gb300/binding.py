@@ -129,12 +129,14 @@ _SIGNATURES = {
     "of_precond_num_params": (_I, []),
     "of_precond_create": (_I, [C.POINTER(C.c_float), _I, C.POINTER(_P)]),
     "of_precond_destroy": (_I, [_P]),
+    "of_precond_set_wait_limit": (_I, [_P, _D]),
     "of_precond_get_params": (_I, [_P, C.POINTER(C.c_float), _I]),
     "of_precond_apply": (_I, [_P, _P, _P, _P]),
     "of_precond_loss_grad": (_I, [_P, _P, _P, C.POINTER(_D), C.POINTER(C.c_float)]),
     "of_precond_train": (_I, [_P, _P, _P, _I, C.POINTER(_I), _I, _I, C.c_float, C.POINTER(_D)]),
     "of_precond_collect": (_I, [_P, _P, _I, _I, _P, C.POINTER(_I)]),
     "of_launch_count": (C.c_ulonglong, []),
+    "of_resource_count": (C.c_ulonglong, []),
     "of_kernel_class_name": (C.c_char_p, [_I]),
     "of_profile_enable": (_I, [_P, _I]),
     "of_profile_read": (_I, [_P, C.POINTER(of_kernel_stat), _I]),
@@ -386,6 +388,10 @@ def of_launch_count():
     return int(load().of_launch_count())
 
 
+def of_resource_count():
+    return int(load().of_resource_count())
+
+
 def of_kernel_class_name(cls):
     return load().of_kernel_class_name(int(cls)).decode()
 
@@ -451,6 +457,10 @@ def of_precond_get_params(P):
     _check(load().of_precond_get_params(P, out.ctypes.data_as(C.POINTER(C.c_float)), int(out.size)),
            "of_precond_get_params")
     return out
+
+
+def of_precond_set_wait_limit(P, seconds):
+    return _check(load().of_precond_set_wait_limit(P, float(seconds)), "of_precond_set_wait_limit")
 
 
 def of_precond_apply(h, P, r, z):

@@ -39,6 +39,7 @@ static AtomSet upload_atoms(of_grid* g, const of_system* sys) {
     for (int J = 0; J < a.n_atoms; ++J) {
         AtomBox& b = a.h[J];
         b.Z = sys->Z[J];
+        OF_REQUIRE(std::isfinite(b.Z), OF_EINVAL, "ion %d has a non-finite charge", J);
         for (int c = 0; c < 3; ++c) {
             b.R[c] = sys->R[3 * J + c];
             OF_REQUIRE(std::isfinite(b.R[c]), OF_EINVAL, "ion %d has a non-finite position", J);
@@ -575,6 +576,8 @@ of_status of_pseudocharge(of_grid* g, const of_system* sys, double* b, double* e
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -587,6 +590,8 @@ of_status of_forces(of_grid* g, const of_system* sys, const double* u, const dou
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 

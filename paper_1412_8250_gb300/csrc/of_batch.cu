@@ -369,6 +369,8 @@ static int tune_cz(of_grid* g0, BatchPlan& P, int N) {
     cudaEvent_t e0, e1;
     OF_CUDA(cudaEventCreate(&e0));
     OF_CUDA(cudaEventCreate(&e1));
+    note_resource();
+    note_resource();
     for (int cz : cand) {
         layout(P, cz);
         if (P.sblocks > P.S.stride) continue;
@@ -476,12 +478,19 @@ static of_status poisson_batched(int nc, of_grid* const* gs, const double* const
         OF_CUDA(cudaMemcpyAsync(all.data(), P.states, sizeof(KState) * 2 * nc, cudaMemcpyDeviceToHost,
                                 g0->stream));
         OF_CUDA(cudaStreamSynchronize(g0->stream));
-        bool all_done = true;
+        bool all_done = true, finite = true;
         for (int c = 0; c < nc; ++c) {
             h64[c] = all[2 * c];
             ++refinements[c];
             if (!(h64[c].rr <= h64[c].tol2)) all_done = false;
+            if (!std::isfinite(h64[c].rr) || !std::isfinite(h64[c].tol2)) {
+                if (finite)
+                    set_error("batched Poisson solve: cell %d has a non-finite right-hand side or "
+                              "residual", c);
+                finite = false;
+            }
         }
+        if (!finite) { status = OF_EINVAL; break; }
         if (all_done) break;
         int max_it = 0;
         for (int c = 0; c < nc; ++c) max_it = std::max(max_it, iters[c]);
@@ -566,5 +575,7 @@ extern "C" of_status of_poisson_solve_batched(int ncells, of_grid* const* grids,
         return poisson_batched(ncells, grids, rho, phi, o, infos);
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }

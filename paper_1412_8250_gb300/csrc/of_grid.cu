@@ -1,6 +1,8 @@
 // Grid handle, workspace, error reporting and the plain Laplacian entry point.
 #include <atomic>
 #include <cstdarg>
+#include <exception>
+#include <new>
 #include <cstring>
 #include <cmath>
 
@@ -9,6 +11,7 @@
 namespace of {
 
 unsigned long long g_launch_count = 0;
+unsigned long long g_resource_count = 0;
 thread_local double g_capture_bytes = 0.0;
 thread_local bool g_capturing = false;
 static thread_local char g_err[1024] = "";
@@ -18,6 +21,21 @@ void set_error(const char* fmt, ...) {
     va_start(ap, fmt);
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
+}
+
+of_status unexpected_exception() {
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return OF_ENOMEM;
+    } catch (const std::exception& e) {
+        set_error("unexpected host exception: %s", e.what());
+        return OF_ECUDA;
+    } catch (...) {
+        set_error("unexpected host exception");
+        return OF_ECUDA;
+    }
 }
 
 int num_sms() {
@@ -47,6 +65,7 @@ void* ws(of_grid* g, int slot, size_t bytes) {
             set_error("cudaMalloc(%zu) for workspace slot %d: %s", bytes, slot, cudaGetErrorString(e));
             throw Error{OF_ENOMEM};
         }
+        note_resource();
         b.bytes = bytes;
     }
     return b.ptr;
@@ -61,7 +80,7 @@ void fetch_scalars(of_grid* g, int first, int count, double* out) {
 
 // Weights of Eq. FD:Laplacian:
 //   w_0 = -(1/h^2) sum_{q=1}^N 1/q^2,  w_p = 2 (-1)^{p+1} (N!)^2 / (h^2 p^2 (N-p)! (N+p)!).
-static void fd_weights(int N, double h, double* w) {
+void fd_weights(int N, double h, double* w) {
     double s = 0.0;
     for (int q = 1; q <= N; ++q) s += 1.0 / ((double)q * q);
     w[0] = -s / (h * h);
@@ -143,6 +162,7 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
         OF_CUDA(cudaMalloc(&g->s.partials, sizeof(double) * OF_RED_SLOTS * OF_MAX_RED_BLOCKS));
         OF_CUDA(cudaMalloc(&g->s.counter, sizeof(unsigned int) * 4));
         OF_CUDA(cudaMalloc(&g->s.scalars, sizeof(double) * 256));
+        for (int k = 0; k < 3; ++k) note_resource();
         // zeroed on the handle's stream and finished before the handle is returned: a plain
         // cudaMemset runs on the legacy default stream, which the non-blocking streams the
         // handle later runs on (stream pool, twin handle) do not wait for, and a reduction
@@ -151,11 +171,15 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
         OF_CUDA(cudaMemsetAsync(g->s.scalars, 0, sizeof(double) * 256, g->stream));
         OF_CUDA(cudaStreamSynchronize(g->stream));
         OF_CUDA(cudaMallocHost(&g->s.host, sizeof(double) * 256));
+        note_resource();
         *out = g;
         return OF_OK;
     } catch (const Error& e) {
         of_grid_destroy(g);
         return e.code;
+    } catch (...) {
+        of_grid_destroy(g);
+        return unexpected_exception();
     }
 }
 
@@ -192,11 +216,17 @@ of_status of_laplacian_apply(of_grid* g, of_dtype dtype, const void* x, void* y)
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
 unsigned long long of_launch_count(void) {
     return __atomic_load_n(&of::g_launch_count, __ATOMIC_RELAXED);
+}
+
+unsigned long long of_resource_count(void) {
+    return __atomic_load_n(&of::g_resource_count, __ATOMIC_RELAXED);
 }
 
 const char* of_kernel_class_name(int cls) {
@@ -226,6 +256,8 @@ of_status of_profile_enable(of_grid* g, int sample_every) {
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 

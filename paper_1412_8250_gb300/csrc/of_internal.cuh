@@ -22,6 +22,9 @@ void set_error(const char* fmt, ...);
 struct Error {
     of_status code;
 };
+// Status for an exception other than Error that reached a C entry point (called inside the
+// catch block): OF_ENOMEM for a failed host allocation, OF_ECUDA otherwise, with a message.
+of_status unexpected_exception();
 
 #define OF_CUDA(call)                                                                    \
     do {                                                                                 \
@@ -37,6 +40,11 @@ struct Error {
 
 // Kernel launches by this library (process-wide), for the launch accounting of callers.
 extern unsigned long long g_launch_count;
+
+// Resources this library has created (process-wide): device and pinned host buffers, streams,
+// events and executable graphs.  Every creation site calls note_resource() after it succeeds.
+extern unsigned long long g_resource_count;
+inline void note_resource() { __atomic_add_fetch(&g_resource_count, 1ull, __ATOMIC_RELAXED); }
 
 // Every kernel of the library is launched through this wrapper (no dynamic shared memory).
 template <typename... KArgs, typename... Args>
@@ -119,6 +127,7 @@ struct Prof {
         if (pool.empty()) {
             cudaEvent_t e;
             OF_CUDA(cudaEventCreate(&e));
+            note_resource();
             return e;
         }
         cudaEvent_t e = pool.back();
@@ -190,6 +199,9 @@ struct of_grid {
     cudaStream_t twin_stream = nullptr;
     cudaEvent_t twin_in = nullptr, twin_out = nullptr;
     void* graphs = nullptr;              // cached CUDA graphs (of_krylov.cu)
+    // the Krylov loops launch every iteration directly instead of capturing and caching CUDA
+    // graphs (which create a capture stream and executable graphs)
+    bool no_graphs = false;
 };
 
 namespace of {
@@ -250,6 +262,9 @@ enum Slot {
 };
 
 void* ws(of_grid* g, int slot, size_t bytes);   // grow-only
+
+// Weights w_0..w_N of Eq. FD:Laplacian for spacing h (w_p = 0 for N < p <= OF_MAX_N).
+void fd_weights(int N, double h, double* w);
 
 // Reduction bookkeeping: how many blocks a grid-sized kernel uses
 inline int red_blocks(long long work_items, int per_block) {

@@ -294,7 +294,7 @@ static KState iterate(of_grid* g, int st_off, T* x, T* r, T* pa, T* pb, T* Ap,
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(T) * n, g->stream));
     KState h;
-    if (std::getenv("OF_NO_GRAPHS") == nullptr) {
+    if (!g->no_graphs && std::getenv("OF_NO_GRAPHS") == nullptr) {
         Graphs& G = graphs(g);
         const void* key[8] = {x, r, pa, pb, Ap, st, &W, (const void*)(uintptr_t)sizeof(T)};
         const double consts[3] = {(double)a, Q.x, Q.y};
@@ -394,7 +394,7 @@ static KState iterate_pcocg(of_grid* g, int st_off, float2* x, float2* r, float2
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float2) * n, g->stream));
     KState h;
-    if (std::getenv("OF_NO_GRAPHS") == nullptr) {
+    if (!g->no_graphs && std::getenv("OF_NO_GRAPHS") == nullptr) {
         Graphs& G = graphs(g);
         const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
         const double consts[4] = {(double)a, Q.x, Q.y, sigma};
@@ -442,7 +442,7 @@ static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa,
     const long long n = g->d.n;
     OF_CUDA(cudaMemsetAsync(pa, 0, sizeof(float) * n, g->stream));
     KState h;
-    const bool use_graphs = std::getenv("OF_NO_GRAPHS") == nullptr;
+    const bool use_graphs = !g->no_graphs && std::getenv("OF_NO_GRAPHS") == nullptr;
     if (use_graphs) {
         PcgGraphs& G = graphs(g).pcg;
         const void* key[8] = {x, r, pa, pb, Ap, z, st, g->mg};
@@ -499,6 +499,11 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     KState h;
     fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
     const double bb = h.tol2 / (o.tol * o.tol);
+    // a NaN or an infinity would compare false against every tolerance and pass for a zero
+    // right-hand side or a converged start: refuse it instead
+    OF_REQUIRE(std::isfinite(bb), OF_EINVAL, "Krylov solve: the right-hand side is not finite");
+    OF_REQUIRE(std::isfinite(h.rr), OF_EINVAL,
+               "Krylov solve: the initial guess gives a non-finite residual");
     int total_iters = 0, refinements = 1;
     double net_steps = 0.0;
     of_status status = OF_OK;
@@ -677,6 +682,8 @@ of_status of_poisson_solve(of_grid* g, const double* rho, double* phi, const of_
         return poisson(g, rho, phi, krylov_opts(opts), info);
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -706,6 +713,8 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
         return worst;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -793,25 +802,16 @@ extern "C" of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1,
         g.N = fd_half_order;
         g.w64.centre = 0.0;
         for (int a = 0; a < 3; ++a) {
-            // Eq. FD:Laplacian weights
-            double s = 0.0;
-            for (int q = 1; q <= g.N; ++q) s += 1.0 / ((double)q * q);
-            g.w64.w[a][0] = -s / (g.h[a] * g.h[a]);
-            for (int p = 1; p <= OF_MAX_N; ++p) {
-                double w = 0.0;
-                if (p <= g.N) {
-                    double ratio = 1.0;
-                    for (int k = 1; k <= p; ++k) ratio *= (double)(g.N - p + k) / (double)(g.N + k);
-                    w = 2.0 * ((p % 2) ? 1.0 : -1.0) * ratio / (g.h[a] * g.h[a] * p * p);
-                }
-                g.w64.w[a][p] = w;
-            }
+            fd_weights(g.N, g.h[a], g.w64.w[a]);
             g.w64.centre += 2.0 * g.w64.w[a][0];
             for (int p = 0; p <= OF_MAX_N; ++p) g.w32.w[a][p] = (float)g.w64.w[a][p];
         }
         g.w32.centre = (float)g.w64.centre;
         g.stream = (cudaStream_t)stream;
         g.device = device;
+        // no CUDA graphs: capturing one creates a capture stream and an executable graph, and
+        // this handle, which never reaches of_grid_destroy, could not release them
+        g.no_graphs = true;
         double host_scalars[256];
         g.s.partials = base + NOALLOC_PARTIALS;
         g.s.scalars = base + NOALLOC_SCALARS;
@@ -838,6 +838,10 @@ extern "C" of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1,
         KState h;
         fetch_scalars(&g, KS64, KSTATE_DOUBLES, (double*)&h);
         const double bb = h.tol2 / (o.tol * o.tol);
+        OF_REQUIRE(std::isfinite(bb), OF_EINVAL,
+                   "of_poisson_solve_noalloc: the right-hand side is not finite");
+        OF_REQUIRE(std::isfinite(h.rr), OF_EINVAL,
+                   "of_poisson_solve_noalloc: the initial guess gives a non-finite residual");
         of_status status = OF_OK;
         int iters = 0, refinements = 1;
         if (!(bb > 0.0)) {
@@ -868,5 +872,7 @@ extern "C" of_status of_poisson_solve_noalloc(int n1, int n2, int n3, double L1,
         return status;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }

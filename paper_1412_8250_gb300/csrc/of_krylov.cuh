@@ -452,7 +452,10 @@ inline Graphs& graphs(of_grid* g) {
 template <class Body>
 inline cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kernels,
                                double& bytes) {
-    if (!g->cap_stream) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    if (!g->cap_stream) {
+        OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        note_resource();
+    }
     cudaStream_t saved = g->stream;
     Prof* saved_prof = g->prof;
     g->stream = g->cap_stream;
@@ -484,6 +487,7 @@ inline cudaGraphExec_t capture(of_grid* g, Body&& body, unsigned long long& kern
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     OF_CUDA(e);
+    note_resource();
     return exec;
 }
 
@@ -499,8 +503,14 @@ template <class Init, class Pair>
 inline cudaGraphExec_t capture_loop(of_grid* g, KState* st, Init&& init, Pair&& pair,
                                     unsigned long long& init_kernels, double& init_bytes,
                                     unsigned long long& pair_kernels, double& pair_bytes) {
-    if (!g->cap_stream) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
-    if (!g->cap_stream2) OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream2, cudaStreamNonBlocking));
+    if (!g->cap_stream) {
+        OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+        note_resource();
+    }
+    if (!g->cap_stream2) {
+        OF_CUDA(cudaStreamCreateWithFlags(&g->cap_stream2, cudaStreamNonBlocking));
+        note_resource();
+    }
     cudaStream_t saved = g->stream;
     Prof* saved_prof = g->prof;
     g->prof = nullptr;
@@ -569,6 +579,7 @@ inline cudaGraphExec_t capture_loop(of_grid* g, KState* st, Init&& init, Pair&& 
     cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     OF_CUDA(e);
+    note_resource();
     return exec;
 }
 

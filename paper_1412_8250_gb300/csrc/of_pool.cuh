@@ -39,10 +39,13 @@ of_status run_on_stream_pool(int ncells, of_grid* const* grids, Body&& body) {
     };
     try {
         OF_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+        note_resource();
         OF_CUDA(cudaEventRecord(start, shared));
         for (int t = 0; t < T; ++t) {
             OF_CUDA(cudaStreamCreateWithFlags(&wstream[t], cudaStreamNonBlocking));
             OF_CUDA(cudaEventCreateWithFlags(&wdone[t], cudaEventDisableTiming));
+            note_resource();
+            note_resource();
             OF_CUDA(cudaStreamWaitEvent(wstream[t], start, 0));
         }
     } catch (const Error& e) {

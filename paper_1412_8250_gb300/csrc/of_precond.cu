@@ -32,6 +32,8 @@ struct of_precond {
     float* v = nullptr;
     int step = 0;                 // Adam step count
     int device = 0;
+    // limit of the tensor-core kernels' waits for an MMA completion (of_precond_set_wait_limit)
+    unsigned long long wait_ns = 2000000000ull;
 };
 
 namespace of {
@@ -166,8 +168,10 @@ __device__ __forceinline__ unsigned long long now_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// bounded wait for the phase of parity `parity` of an mbarrier
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// bounded wait for the phase of parity `parity` of an mbarrier: false once limit_ns have passed
+// (at once for limit_ns = 0, without polling)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    if (limit_ns == 0) return false;
     const unsigned long long t0 = now_ns();
     for (int k = 0; k < (1 << 22); ++k) {
         uint32_t done;
@@ -177,7 +181,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done) : "r"(bar), "r"(parity) : "memory");
         if (done) return true;
-        if ((k & 63) == 63 && now_ns() - t0 > WAIT_NS) return false;
+        if ((k & 63) == 63 && now_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
                                                              const __nv_bfloat16* __restrict__ P,
                                                              __nv_bfloat16* zout, __nv_bfloat16* aout,
                                                              float* rnout, const double* s_dev, float sgn,
-                                                             double* err) {
+                                                             double* err, unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* As = sm;
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
                         tc::desc(b_base + h * tc::B_TAP, tc::B_LBO, tc::B_SBO), h > 0 ? 1u : 0u);
             mma_commit(bar_a);
         }
-        const bool seen = tc::mbar_wait(bar_a, phase);
+        const bool seen = tc::mbar_wait(bar_a, phase, wait_ns);
         phase ^= 1u;
         ok = __syncthreads_and(seen) != 0;
         tc::fence_after();
@@ -418,7 +422,9 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
     }
     if (!ok) {
         if (tid == 0) *err = 1.0;
-        tc::mbar_wait(bar_a, phase ^ 1u);   // let MMAs still in flight finish (bounded)
+        // let the MMAs still in flight finish (bounded by the full limit, whatever wait_ns was)
+        // before the tensor memory they write is freed
+        tc::mbar_wait(bar_a, phase ^ 1u, tc::WAIT_NS);
     }
     tc::fence_before();
     __syncthreads();
@@ -435,7 +441,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, in
                                                             const __nv_bfloat16* __restrict__ in,
                                                             const __nv_bfloat16* __restrict__ P,
                                                             __nv_bfloat16* zout, __nv_bfloat16* aout,
-                                                            float* yout, const double* s_dev, double* err) {
+                                                            float* yout, const double* s_dev, double* err,
+                                                            unsigned long long wait_ns) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* As = sm;                              // two A buffers
@@ -509,7 +516,7 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, in
                 }
             mma_commit(bar_m);
         }
-        const bool done = tc::mbar_wait(bar_m, phase);
+        const bool done = tc::mbar_wait(bar_m, phase, wait_ns);
         ok = __syncthreads_and(done) != 0;
         tc::fence_after();
         if (!ok) break;
@@ -553,7 +560,9 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, in
     asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
     if (!ok) {
         if (tid == 0) *err = 1.0;
-        tc::mbar_wait(bar_m, phase);   // let MMAs still in flight finish (bounded)
+        // let the MMAs still in flight finish (bounded by the full limit, whatever wait_ns was)
+        // before the tensor memory they write is freed
+        tc::mbar_wait(bar_m, phase, tc::WAIT_NS);
     }
     tc::fence_before();
     __syncthreads();
@@ -1036,8 +1045,7 @@ static void net_check_error(of_grid* g) {
     double e = 0.0;
     fetch_scalars(g, SC_NET_ERR, 1, &e);
     OF_REQUIRE(e == 0.0, OF_ETIMEOUT,
-               "tensor-core convolution: an MMA completion was not seen within %.1f s",
-               tc::WAIT_NS * 1e-9);
+               "tensor-core convolution: an MMA completion was not seen within the wait limit");
 }
 
 // The tensor-core layers: x-rows cut into segments of at most 128 points, persistent grids
@@ -1051,7 +1059,8 @@ static void conv_geometry(of_grid* g, int& nseg, int& lseg, long long& tiles) {
 }
 
 static void launch_conv1_tc(of_grid* g, const float* r, const __nv_bfloat16* P, __nv_bfloat16* z1,
-                            __nv_bfloat16* a1, float* rn, const double* rms, float sgn) {
+                            __nv_bfloat16* a1, float* rn, const double* rms, float sgn,
+                            unsigned long long wait_ns) {
     static int configured_device = -1;
     if (configured_device != g->device) {
         OF_CUDA(cudaFuncSetAttribute(k_conv1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM1));
@@ -1062,12 +1071,13 @@ static void launch_conv1_tc(of_grid* g, const float* r, const __nv_bfloat16* P, 
     conv_geometry(g, nseg, lseg, tiles);
     const int grid = (int)std::max(1LL, std::min(tiles, 4LL * num_sms()));
     launch_smem(k_conv1_tc, grid, tc::THREADS, tc::SMEM1, g->stream, g->d, nseg, lseg, r, P, z1, a1, rn,
-                rms, sgn, g->s.scalars + SC_NET_ERR);
+                rms, sgn, g->s.scalars + SC_NET_ERR, wait_ns);
 }
 
 template <int LAYER>
 static void launch_conv_tc(of_grid* g, const __nv_bfloat16* in, const __nv_bfloat16* P,
-                           __nv_bfloat16* zout, __nv_bfloat16* aout, float* y, const double* s_dev) {
+                           __nv_bfloat16* zout, __nv_bfloat16* aout, float* y, const double* s_dev,
+                           unsigned long long wait_ns) {
     static int configured_device = -1;
     if (configured_device != g->device) {
         OF_CUDA(cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
@@ -1078,7 +1088,7 @@ static void launch_conv_tc(of_grid* g, const __nv_bfloat16* in, const __nv_bfloa
     conv_geometry(g, nseg, lseg, tiles);
     const int grid = (int)std::max(1LL, std::min(tiles, 2LL * num_sms()));
     launch_smem(k_conv_tc<LAYER>, grid, tc::THREADS, tc::SMEM, g->stream, g->d, nseg, lseg, in, P, zout,
-                aout, y, s_dev, g->s.scalars + SC_NET_ERR);
+                aout, y, s_dev, g->s.scalars + SC_NET_ERR, wait_ns);
 }
 
 // algorithmic bytes of one application: r read by the RMS pass and by layer 1, a1 and a2
@@ -1093,9 +1103,10 @@ static void net_forward(of_grid* g, of_precond* P, const float* r, float* out, c
     const double* rms = g->s.scalars + SC_NET + 1;
     launch(k_rms32, vec_blocks(n), 256, g->stream, n, r, red_ctx(g, SC_NET));
     const __nv_bfloat16* W = P->pbf;
-    launch_conv1_tc(g, r, W, training ? B.z1 : nullptr, B.a1, training ? B.rn : nullptr, rms, sgn);
-    launch_conv_tc<2>(g, B.a1, W, training ? B.z2 : nullptr, B.a2, nullptr, nullptr);
-    launch_conv_tc<3>(g, B.a2, W, nullptr, nullptr, out, training ? nullptr : rms);
+    launch_conv1_tc(g, r, W, training ? B.z1 : nullptr, B.a1, training ? B.rn : nullptr, rms, sgn,
+                    P->wait_ns);
+    launch_conv_tc<2>(g, B.a1, W, training ? B.z2 : nullptr, B.a2, nullptr, nullptr, P->wait_ns);
+    launch_conv_tc<3>(g, B.a2, W, nullptr, nullptr, out, training ? nullptr : rms, P->wait_ns);
 }
 
 // loss sums (scalars 112, 113) and gradient accumulation (scaled) for one residual, taken
@@ -1222,6 +1233,8 @@ of_status of_precond_create(const float* params, int nparams, of_precond** out) 
         OF_CUDA(cudaGetDevice(&P->device));
         OF_CUDA(cudaMalloc(&P->params, sizeof(float) * NPAR * 4));
         OF_CUDA(cudaMalloc(&P->pbf, sizeof(__nv_bfloat16) * NPAR));
+        note_resource();
+        note_resource();
         P->grad = P->params + NPAR;
         P->m = P->params + 2 * NPAR;
         P->v = P->params + 3 * NPAR;
@@ -1231,11 +1244,17 @@ of_status of_precond_create(const float* params, int nparams, of_precond** out) 
         OF_CUDA(cudaDeviceSynchronize());
         *out = P;
         return OF_OK;
-    } catch (const Error& e) {
+    } catch (...) {
         if (P->params) cudaFree(P->params);
         if (P->pbf) cudaFree(P->pbf);
         delete P;
-        return e.code;
+        try {
+            throw;
+        } catch (const Error& e) {
+            return e.code;
+        } catch (...) {
+            return unexpected_exception();
+        }
     }
 }
 
@@ -1245,6 +1264,15 @@ of_status of_precond_destroy(of_precond* P) {
     cudaFree(P->params);
     cudaFree(P->pbf);
     delete P;
+    return OF_OK;
+}
+
+of_status of_precond_set_wait_limit(of_precond* P, double seconds) {
+    if (!P || !(seconds >= 0.0) || seconds > 60.0) {
+        set_error("of_precond_set_wait_limit: need a handle and 0 <= seconds <= 60");
+        return OF_EINVAL;
+    }
+    P->wait_ns = (unsigned long long)(seconds * 1e9);
     return OF_OK;
 }
 
@@ -1259,6 +1287,8 @@ of_status of_precond_get_params(of_precond* P, float* params, int nparams) {
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1276,6 +1306,8 @@ of_status of_precond_apply(of_grid* g, of_precond* P, const float* r, float* z) 
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1300,6 +1332,8 @@ of_status of_precond_loss_grad(of_grid* g, of_precond* P, const float* r, double
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1346,6 +1380,8 @@ of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int 
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1375,6 +1411,8 @@ of_status of_precond_collect(of_grid* g, const double* rho, int stride, int max_
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 

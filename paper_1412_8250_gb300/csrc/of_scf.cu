@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -597,6 +598,7 @@ static of_grid* twin_of(of_grid* g) {
         OF_CUDA(cudaStreamCreateWithFlags(&g->twin_stream, cudaStreamNonBlocking));
         OF_CUDA(cudaEventCreateWithFlags(&g->twin_in, cudaEventDisableTiming));
         OF_CUDA(cudaEventCreateWithFlags(&g->twin_out, cudaEventDisableTiming));
+        for (int k = 0; k < 3; ++k) note_resource();
         const of_status s = of_grid_create(g->d.n1, g->d.n2, g->d.n3, g->L[0], g->L[1], g->L[2], g->N,
                                            g->twin_stream, &t);
         if (s != OF_OK) throw Error{s};
@@ -635,6 +637,12 @@ static void run_pair(of_grid* g, First&& first, Second&& second) {
         first(g);
     } catch (const Error& e) {
         err1 = e.code;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed in a paired solve");
+        err1 = OF_ENOMEM;
+    } catch (...) {   // whatever it was, the worker is joined before anything leaves
+        set_error("unexpected exception in a paired solve");
+        err1 = OF_ECUDA;
     }
     worker.join();
     OF_CUDA(cudaEventRecord(g->twin_out, t->stream));
@@ -1266,6 +1274,8 @@ of_status of_hamiltonian_apply(of_grid* g, const of_functional* fn, const double
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1289,6 +1299,8 @@ of_status of_lr_potential(of_grid* g, const of_functional* fn, double kf2, const
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1322,6 +1334,8 @@ of_status of_scf_ground_state_batched(int ncells, of_grid* const* grids, const o
         });
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1437,6 +1451,8 @@ of_status of_relax(of_grid* g, const of_system* sys, const of_functional* fn,
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1530,6 +1546,8 @@ of_status of_vacancy_formation(of_grid* perfect, of_grid* vacancy, const of_syst
         return st;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 
@@ -1552,6 +1570,8 @@ of_status of_scf_ground_state(of_grid* g, const of_system* sys, const of_functio
         return OF_OK;
     } catch (const Error& e) {
         return e.code;
+    } catch (...) {
+        return unexpected_exception();
     }
 }
 

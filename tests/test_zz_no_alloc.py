@@ -62,3 +62,30 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     o.precision = B.OF_F32
     with pytest.raises(B.OfError):
         B.of_poisson_solve_noalloc((8, 8, 8), (7.6, 7.6, 7.6), 6, None, x, x, o)
+
+
+def test_noalloc_repeated_calls_create_and_leak_nothing():
+    # 200 calls: the library creates no buffer, stream, event or graph (its own resource
+    # counter stays put) and the device's free memory does not move
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    n, L = (32, 32, 32), (7.6, 7.6, 7.6)
+    grid = O.Grid(n, L, 6)
+    rho = W.random_field(grid.shape, seed=5, kind="smooth")
+    rd = torch.from_numpy(rho).cuda()
+    phi = torch.zeros_like(rd)
+    stream = torch.cuda.current_stream()
+    B.of_poisson_solve_noalloc(n, L, 6, stream, rd, phi, _opts(1e-10))   # device address lookup
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    res0 = B.of_resource_count()
+    for _ in range(200):
+        phi.zero_()
+        info = B.of_poisson_solve_noalloc(n, L, 6, stream, rd, phi, _opts(1e-10))
+        assert info.rel_residual <= 1e-10
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert B.of_resource_count() == res0
+    assert free1 == free0, (free0, free1)
+    exact = O.poisson_solve(rho, grid)
+    assert np.max(np.abs(phi.cpu().numpy() - exact)) <= 1e-8 * np.max(np.abs(exact))
