@@ -25,13 +25,60 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "s per SCF ground state & stencil GPts/s: chosen vs plain FP64 CG, at 1e-6 Ha/atom"
-# Step counts of the exact scheme the oracle runs (every inner solve to tolerance, Anderson
-# m = 3, zeta = 1) on this workload, from a converged run of the same iteration; used to
-# extrapolate the oracle's per-step times to one ground state.
-ORACLE_NLCG_STEPS, ORACLE_OUTER = 537, 12
 UNIT = "s/ground-state"
 WORKLOAD = ("108-atom FCC Al-like cell (3x3x3, a=7.6 bohr, +-0.1 bohr displacements, seed 2), "
             "96^3 grid, 12th-order FD, WT-type kernel functional, ground state + forces")
+# what else defines the step (the options of make_case)
+WORKLOAD_DETAIL = {
+    "ions": "normalised Gaussian pseudocharges Z=3, sigma=1.2 bohr, r_c=10 bohr (sigma=0.7 "
+            "gives the kernel functional no minimiser with u >= 0)",
+    "functional": "TF + vW (lambda=1) + WT-type kernel (mu=1, alpha,beta=(5+-sqrt5)/6, the "
+                  "K_00 rows of the WGC table) + PZ LDA",
+    "anderson": {"m": 3, "zeta": 1.0, "fixed_point_tol": 1e-6, "variable": "V_LR"},
+    "nlcg": {"tol": 1e-7, "line_search": "root of dE/ds (secant), line_tol 1e-3",
+             "inexact": "NLCG of outer step k stops at max(1e-7, 0.1 x fixed-point error of "
+                        "step k-1); the last outer step at 1e-7"},
+    "poisson": {"tol": 1e-10, "form": "FP32 multigrid-preconditioned CG passes to 1e-4 of "
+                                      "their starting residual, FP64 refinement"},
+    "kernel_solves": {"form": "FP32 COCG preconditioned by the V-cycle of -L + kf2 |Q|, FP64 "
+                              "refinement", "tol": "max(1e-10, min(1e-6, 1e-3 x previous "
+                                                  "fixed-point error))"},
+}
+GOLDEN_AL108 = os.path.join(ROOT, "tests", "golden", "al108_wt.json")
+GOLDEN_SMALL = os.path.join(ROOT, "tests", "golden", "ground_states.json")
+
+
+def golden_al108():
+    """The oracle's ground state of this workload (tests/golden/al108_wt.json, written by
+    tests/golden/make_golden.py from the oracle alone), or None if absent."""
+    if not os.path.exists(GOLDEN_AL108):
+        return None
+    with open(GOLDEN_AL108) as f:
+        return json.load(f)["al108_wt"]
+
+
+def oracle_counts():
+    """NLCG steps and kernel maps (one per outer iteration) of the oracle's own ground state of
+    this workload, from its stored record: the constants that scale the oracle's timed sample
+    to one ground state."""
+    rec = golden_al108()
+    if rec is None:
+        raise RuntimeError("tests/golden/al108_wt.json is missing: run "
+                           "python tests/golden/make_golden.py --al108")
+    return int(sum(rec["nlcg_iterations"])), int(rec["outer_iterations"])
+
+
+def errors_vs_oracle(res, F, n_atoms):
+    """Energy (Ha/atom) and largest force-component (Ha/bohr) difference from the oracle's
+    stored ground state of this workload."""
+    import numpy as np
+    rec = golden_al108()
+    if rec is None:
+        return None
+    return {"energy_error_vs_oracle_ha_per_atom": abs(res.energy - rec["energy"]) / n_atoms,
+            "max_force_error_vs_oracle_ha_per_bohr": float(np.max(np.abs(F - np.array(rec["forces"])))),
+            "oracle_energy_per_atom_ha": rec["energy_per_atom"],
+            "tolerances": {"energy_ha_per_atom": 1e-6, "force_ha_per_bohr": 1e-5}}
 
 
 def parse():
@@ -41,8 +88,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
-    p.add_argument("--compare-f64", action="store_true",
-                   help="also time one plain FP64 CG ground state and report it")
+    p.add_argument("--no-compare-f64", action="store_true",
+                   help="skip the plain FP64 CG ground state (same options) timed beside the step")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--config3", action="store_true",
                    help="batched ground states of the first --cells cells of the 64-cell set")
@@ -177,7 +224,9 @@ def run_step(B, h, sysd, fn, o, u, phi, u0):
 def stencil_rates(torch, B, shape, L, reps=30):
     """Device time of one of_laplacian_apply sweep (FP32 and FP64) on this grid: `reps` sweeps
     captured in one CUDA graph on a grid handle of their own, replayed between CUDA events
-    (host launch overhead excluded; consecutive sweeps keep the fields in L2)."""
+    (host launch overhead excluded).  At 96^3 consecutive sweeps keep the fields in L2; at
+    320^3 each FP32 field (131 MB) is larger than L2, so the sweeps stream from HBM.  GB/s
+    counts the algorithmic traffic (read x, write y); frac is that over the measured HBM peak."""
     out = {}
     s = torch.cuda.Stream()
     h = B.of_grid_create(shape, L, 6, s)
@@ -203,8 +252,9 @@ def stencil_rates(torch, B, shape, L, reps=30):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             n = x.numel()
-            out[name] = {"gpts": n / (ms * 1e-3) / 1e9, "ms": ms,
-                         "gbs": 2 * n * x.element_size() / (ms * 1e-3) / 1e9}
+            gbs = 2 * n * x.element_size() / (ms * 1e-3) / 1e9
+            out[name] = {"gpts": n / (ms * 1e-3) / 1e9, "ms": ms, "gbs": gbs,
+                         "frac_of_hbm": gbs / measured_peaks()[0]}
             del graph
     finally:
         torch.cuda.synchronize()
@@ -358,57 +408,157 @@ def learned_compare(torch, B, W, steps=400, theta=0.3):
     return out
 
 
-def cpu_sample(cell, nlcg_steps_per_gs, outer_per_gs, budget_s=25.0):
-    """Time the oracle on a bounded sample of the same workload and extrapolate to one
-    ground state: setup (pseudocharges, Poisson of b) + NLCG steps x (oracle time per NLCG
-    step) + outer iterations x (oracle time of one kernel map V[u]).  Step counts are those of
-    the same algorithm run to convergence on the GPU."""
+def cpu_setup(cell):
+    """The oracle's once-per-ground-state work on this cell, timed: nuclear charge, its
+    potential, self energy and overlap correction; and the forces (whose cost does not depend
+    on the potential's values).  Returns (state, setup seconds, forces seconds)."""
     import numpy as np
     import oracle as O
     t0 = time.time()
     grid = O.Grid(cell.n, cell.L, 6)
     b = O.pseudocharge(cell.R, cell.Z, cell.sigma, cell.rc, grid)
     phib = O.poisson_solve(b, grid)
+    O.self_energy(cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    O.repulsive_correction(cell.R, cell.Z, cell.sigma, grid.L)
     t_setup = time.time() - t0
+    t1 = time.time()
+    O.forces(phib, cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    t_forces = time.time() - t1
     Ne = cell.n_electrons
     u = np.full(grid.shape, np.sqrt(Ne / grid.volume))
+    return (grid, b, phib, u), t_setup, t_forces
+
+
+def cpu_iteration(cell, state, nlcg_steps=1):
+    """One kernel map V[u] and `nlcg_steps` NLCG steps of the oracle on this cell, timed.
+    Returns (seconds per kernel map, seconds per NLCG step, state with the advanced u)."""
+    import numpy as np
+    import oracle as O
+    grid, b, phib, u = state
+    Ne = cell.n_electrons
     fn = O.wt_functional()
     kf2 = O.kf2_of(Ne, grid.volume)
     t1 = time.time()
-    V, _, _, _ = O.lr_potential(u + 0.01 * np.cos(np.arange(grid.shape[2]) * 0.3), grid, fn, kf2)
-    t_lr = time.time() - t1
-    steps = 0
+    V, _, _, _ = O.lr_potential(u * (1.0 + 0.01 * np.cos(np.arange(grid.shape[2]) * 0.3)), grid,
+                                fn, kf2)
+    t_map = time.time() - t1
     t2 = time.time()
-    while steps < 2 or (time.time() - t0 < budget_s and steps < 6):
-        u, _, info = O.nlcg(u, V, b, phib, grid, fn, Ne, tol=1e-30, max_iter=1)
-        steps += 1
-    t_step = (time.time() - t2) / steps
-    est = t_setup + nlcg_steps_per_gs * t_step + outer_per_gs * t_lr
-    sample = (f"oracle (numpy FP64, FFT-exact solves) on the 108-atom 96^3 cell: setup {t_setup:.1f} s, "
-              f"{steps} NLCG steps at {t_step:.2f} s each, one kernel map V[u] {t_lr:.2f} s; "
-              f"extrapolated with {nlcg_steps_per_gs} NLCG steps and {outer_per_gs} outer "
-              f"iterations per ground state")
+    for _ in range(nlcg_steps):
+        u, _, _ = O.nlcg(u, V, b, phib, grid, fn, Ne, tol=1e-30, max_iter=1)
+    t_step = (time.time() - t2) / nlcg_steps
+    return t_map, t_step, (grid, b, phib, u)
+
+
+def cpu_estimate(t_setup, t_forces, t_map, t_step, counts):
+    """Oracle seconds per ground state + forces: setup + NLCG steps x (time per step) + kernel
+    maps x (time per map) + forces, with the step and map counts of the oracle's own run."""
+    nlcg_total, maps = counts
+    return t_setup + nlcg_total * t_step + maps * t_map + t_forces
+
+
+def cpu_sample(cell, budget_s=20.0):
+    """The oracle on a bounded sample of the benchmark cell (setup, forces, one kernel map and
+    a few NLCG steps, about budget_s of host time), scaled to one ground state + forces with
+    the NLCG-step and kernel-map counts of the oracle's own converged run of this cell
+    (tests/golden/al108_wt.json)."""
+    counts = oracle_counts()
+    t0 = time.time()
+    state, t_setup, t_forces = cpu_setup(cell)
+    t_map, t_step, state = cpu_iteration(cell, state, 1)
+    steps = [t_step]
+    while time.time() - t0 < budget_s and len(steps) < 6:
+        t, state = cpu_nlcg_only(cell, state)
+        steps.append(t)
+    t_step = statistics.median(steps)
+    est = cpu_estimate(t_setup, t_forces, t_map, t_step, counts)
+    sample = (f"oracle (numpy FP64, FFT-exact solves, one host core) on the 108-atom 96^3 cell: "
+              f"setup {t_setup:.1f} s, forces {t_forces:.1f} s, one kernel map {t_map:.2f} s, "
+              f"{len(steps)} NLCG steps at {t_step:.2f} s (median); scaled with the oracle's own "
+              f"run of this cell ({counts[0]} NLCG steps, {counts[1]} kernel maps, "
+              f"tests/golden/al108_wt.json)")
     return est, sample, time.time() - t0
 
 
+def cpu_nlcg_only(cell, state):
+    """One NLCG step of the oracle at zero V_LR, timed (a line-search step costs the same
+    whatever V_LR is).  Returns (seconds, state)."""
+    import numpy as np
+    import oracle as O
+    grid, b, phib, u = state
+    t = time.time()
+    u, _, _ = O.nlcg(u, np.zeros(grid.shape), b, phib, grid, O.wt_functional(), cell.n_electrons,
+                     tol=1e-30, max_iter=1)
+    return time.time() - t, (grid, b, phib, u)
+
+
+def config1_measured(torch, B, Fn, W):
+    """A like-for-like measured pair on the small cell the oracle finishes in seconds: the
+    4-atom FCC cell of the TFW configuration (a = 7.6, sigma = 0.7, 32^3, order 12, uniform
+    start), one full ground state + forces by the oracle on one host core and by the GPU in
+    both forms (after one untimed run)."""
+    import numpy as np
+    import oracle as O
+    cell = W.al4_cell()
+    grid = O.Grid(cell.n, cell.L, 6)
+    t = time.time()
+    ref = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.tfw_functional(),
+                             nlcg_tol=1e-7)
+    O.forces(ref.phi, cell.R, cell.Z, cell.sigma, cell.rc, grid)
+    t_oracle = time.time() - t
+    out = {"workload": "4-atom FCC cell, a=7.6 bohr, Gaussian ions Z=3 sigma=0.7 r_c=7, 32^3, "
+                       "12th-order FD, TFW (lambda=1/5) + PZ LDA, ground state + forces",
+           "oracle_s": t_oracle, "oracle_cores": 1}
+    h = B.of_grid_create(cell.n, cell.L, 6, torch.cuda.current_stream())
+    sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+    for name, prec in (("gpu_mixed_s", B.OF_F32), ("gpu_plain_f64_cg_s", B.OF_F64)):
+        o = B.of_default_scf_opts()
+        o.precision = prec
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(u)
+        for k in range(2):
+            u.fill_(1.0)
+            phi.zero_()
+            torch.cuda.synchronize()
+            t = time.time()
+            res = B.of_scf_ground_state(h, sysd, Fn.tfw(), o, u, phi)
+            B.of_forces(h, sysd, u, phi)
+            torch.cuda.synchronize()
+            dt = time.time() - t
+        out[name] = dt
+        out[name.replace("_s", "_energy_error_vs_oracle_ha_per_atom")] = \
+            abs(res.energy - ref.energy) / cell.n_atoms
+    B.of_grid_destroy(h)
+    out["oracle_over_gpu_mixed"] = t_oracle / out["gpu_mixed_s"]
+    return out
+
+
 def reference_arm(args, rank, world):
+    """The oracle as the reference arm: rank 0 only.  Untimed: the setup and forces (timed once,
+    their seconds enter every step's estimate) and --warmup NLCG steps.  Each of --steps steps
+    then times one kernel map and one NLCG step of the oracle on the benchmark cell; the step's
+    value is the per-ground-state estimate from those times and the oracle's own step counts."""
     if rank != 0:
         return 0
     from paper_1412_8250_gb300 import workloads as W
     cell = W.al108_cell()
-    nlcg_steps, outer = ORACLE_NLCG_STEPS, ORACLE_OUTER
+    counts = oracle_counts()
+    state, t_setup, t_forces = cpu_setup(cell)
+    for _ in range(args.warmup):
+        _, state = cpu_nlcg_only(cell, state)
     vals = []
-    sample = ""
-    for _ in range(args.warmup):   # untimed, shorter samples
-        cpu_sample(cell, nlcg_steps, outer, budget_s=3.0)
     for _ in range(max(1, args.steps)):
-        est, sample, _ = cpu_sample(cell, nlcg_steps, outer, budget_s=20.0)
-        vals.append(est)
+        t_map, t_step, state = cpu_iteration(cell, state, 1)
+        vals.append(cpu_estimate(t_setup, t_forces, t_map, t_step, counts))
     v = statistics.median(vals)
+    sample = (f"oracle (numpy FP64, FFT-exact solves, one host core) on the 108-atom 96^3 cell: "
+              f"setup {t_setup:.1f} s and forces {t_forces:.1f} s once, then per step one kernel "
+              f"map and one NLCG step; each step scaled to a ground state with the oracle's own "
+              f"run of this cell ({counts[0]} NLCG steps, {counts[1]} kernel maps, "
+              f"tests/golden/al108_wt.json)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "data": "synthetic", "config": {"workload": WORKLOAD, **WORKLOAD_DETAIL},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -961,21 +1111,36 @@ def main():
     d2h = 2 * out_u.numel() * 8 + F_e2e.size * 8
 
     stencil = stencil_rates(torch, B, cell.shape, cell.L)
+    stencil320 = None if rank != 0 else stencil_rates(torch, B, (320, 320, 320), (76.0, 76.0, 76.0),
+                                                      reps=20)
     batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
     learned = None if (args.no_learned or rank != 0) else learned_compare(torch, B, W)
     compare = None
-    if args.compare_f64 and rank == 0:
+    if not args.no_compare_f64 and rank == 0:
+        # the plain FP64 CG / COCG form with the same options (the chosen form's counterpart),
+        # one ground state + forces timed whole
         _, h64, s64, fn64, o64 = make_case(torch, B, Fn, W, "f64")
+        flush.fill_(1.0)
         torch.cuda.synchronize()
         t = time.time()
         u.copy_(u0)
         r64 = B.of_scf_ground_state(h64, s64, fn64, o64, u, phi)
-        B.of_forces(h64, s64, u, phi)
+        F64 = B.of_forces(h64, s64, u, phi)
         torch.cuda.synchronize()
-        compare = {"plain_fp64_cg_s_per_ground_state": time.time() - t,
+        t64 = time.time() - t
+        compare = {"plain_fp64_cg_s_per_ground_state": t64,
+                   "chosen_s_per_ground_state": value,
+                   "speedup_chosen_vs_plain_fp64": t64 / value,
                    "energy_difference_ha_per_atom": abs(r64.energy - res.energy) / cell.n_atoms,
-                   "plain_fp64_poisson_iterations": r64.poisson_iterations}
+                   "max_force_difference_ha_per_bohr": float(np.max(np.abs(F64 - F))),
+                   "plain_fp64": {"outer_iterations": r64.outer_iterations,
+                                  "nlcg_steps": r64.nlcg_iterations,
+                                  "poisson_iterations": r64.poisson_iterations,
+                                  "kernel_iterations": r64.kernel_iterations},
+                   "plain_fp64_vs_oracle": errors_vs_oracle(r64, F64, cell.n_atoms)}
         B.of_grid_destroy(h64)
+    config1 = None if (rank != 0 or world > 1 or args.no_cpu_baseline) else \
+        config1_measured(torch, B, Fn, W)
 
     # roofline of the dominant kernel class (largest extrapolated time in the timed region)
     peak, peak_kind = measured_peaks()
@@ -992,29 +1157,30 @@ def main():
     clocks = clk.summary()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, sample, wall = cpu_sample(cell, ORACLE_NLCG_STEPS, ORACLE_OUTER)
+        est, sample, wall = cpu_sample(cell)
         cpu = {"value": est, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "wall_s": wall}
+               "wall_s": wall, "measured_small_cell": config1}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "form": args.precision,
+                "config": {"workload": WORKLOAD, **WORKLOAD_DETAIL, "form": args.precision,
                            "l2": "flushed between steps (256 MiB write)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
-                "stencil_96": stencil,
+                "stencil_96": stencil, "stencil_320": stencil320,
                 "result": {"energy_ha": res.energy, "energy_per_atom_ha": res.energy / cell.n_atoms,
                            "outer_iterations": res.outer_iterations,
                            "nlcg_steps": res.nlcg_iterations,
                            "poisson_iterations": res.poisson_iterations,
                            "kernel_iterations": res.kernel_iterations,
-                           "fp_error": res.fp_error, "max_force": float(np.abs(F).max())},
+                           "fp_error": res.fp_error, "max_force": float(np.abs(F).max()),
+                           **(errors_vs_oracle(res, F, cell.n_atoms) or {})},
                 "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched,
                 "learned_preconditioner": learned}
         if compare:
