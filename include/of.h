@@ -65,8 +65,9 @@ typedef struct of_precond of_precond;   /* learned preconditioner (of_precond_cr
 
 /* Krylov solve options.  tol is the target of the true FP64 relative residual
  * ||b - A x|| / ||b||.  precision OF_F64: CG/COCG entirely in FP64.  OF_F32: iterative
- * refinement -- FP64 residual, FP32 Krylov solve of the correction to inner_tol, FP64
- * update -- repeated until tol; the FP32 Poisson CG is preconditioned by a multigrid
+ * refinement -- FP64 residual, FP32 Krylov solve of the correction to inner_tol (or only to
+ * half of what the solve still needs, when that is less), FP64 update -- repeated until tol;
+ * the FP32 Poisson CG is preconditioned by a multigrid
  * V-cycle unless no_multigrid is set, or by the learned network when precond is set (see
  * of_precond_create).  Zero fields take defaults (tol 1e-10, max_iter 20000, inner_tol 1e-5,
  * check_every 8, precond_theta 0.3). */

@@ -542,8 +542,15 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             constexpr int MG_PASS_CAP = 100;
             const int pass_max = pcg ? std::min(MG_PASS_CAP, o.max_iter - total_iters)
                                      : o.max_iter - total_iters;
+            // The pass reduces its residual by inner_tol, or by less when less is left to do: a
+            // pass that started at relative residual rho only needs tol / rho, and one taken
+            // further would overshoot the target (a second pass of a 1e-5 solve ran on to 1e-9).
+            // The factor 0.5 leaves room for the gap between the FP32 recurrence and the true
+            // residual.
+            const double need = std::sqrt(h.tol2 / h.rr);   // tol / current relative residual
+            const double itol = std::max(o.inner_tol, std::min(0.5, 0.5 * need));
             launch(k_demote<T64, T32>, vec_blocks(n), 256, g->stream,
-                n, r, r32, e32, o.inner_tol, st, s32, pass_max, red_ctx(g, 0));
+                n, r, r32, e32, itol, st, s32, pass_max, red_ctx(g, 0));
             OF_LAUNCH_CHECK();
             KState hi;
             PendingLoop pending;   // a loop graph whose state is read with the outer residual

@@ -100,6 +100,27 @@ def test_laplacian_fp32_large_grids(n, L):
         assert np.max(np.abs(host(yd) - ref)) <= 8 * 2**-24 * wsum * np.max(np.abs(x))
 
 
+# more fast-path grids, tiled whole by its 32 x 32 tiles: 128^3 exactly at the threshold, a
+# non-cubic grid cut into several z chunks, and a z-thin grid whose register queue wraps in z
+# more than once
+WHOLE_TILE_CASES = [((128, 128, 128), (30.4, 30.4, 30.4)), ((320, 96, 80), (76.0, 22.8, 19.0)),
+                    ((256, 1024, 9), (60.8, 243.2, 2.1375))]
+
+
+@pytest.mark.parametrize("n,L", WHOLE_TILE_CASES)
+def test_laplacian_fp32_whole_tile_grids(n, L):
+    with G(n, L, 6) as g:
+        x = W.random_field(g.shape, seed=11).astype(np.float32)
+        xd = dev(x, torch.float32)
+        yd = torch.full_like(xd, float("nan"))
+        B.of_laplacian_apply(g.h, B.OF_F32, xd, yd)
+        ref = O.laplacian(x.astype(np.float64), g.grid)
+        wsum = sum(np.abs(O.fd_laplacian_weights(6, hd)).sum() * 2 for hd in g.grid.h)
+        got = host(yd)
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref)) <= 8 * 2**-24 * wsum * np.max(np.abs(x))
+
+
 @pytest.mark.parametrize("n,L", LARGE_CASES[:1])
 def test_poisson_mixed_large_grid(n, L):
     # the mixed solve's FP32 Krylov and V-cycle sweeps run on the fast path at this size

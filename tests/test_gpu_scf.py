@@ -249,6 +249,63 @@ def test_line_searches_reach_the_same_ground_state():
     assert per_step[B.OF_LINE_SLOPE] < 0.6 * per_step[B.OF_LINE_BRENT], per_step
 
 
+def _bench_like_opts(o):
+    # the benchmark's options (bench.make_case): Anderson m = 3, zeta = 1, fixed point to 1e-6,
+    # inexact inner solves (NLCG to 0.1 x the previous fixed-point error, FP32 Poisson passes
+    # to 1e-4)
+    o.fp_tol = 1e-6
+    o.anderson_m = 3
+    o.anderson_zeta = 1.0
+    o.nlcg_tol_rel = 1e-1
+    o.poisson.inner_tol = 1e-4
+    return o
+
+
+def test_wt_small_cell_with_the_benchmark_options_against_golden():
+    rec = _golden()["al4_wt"]
+    cell = _cell_from(rec)
+    h = B.of_grid_create(cell.n, cell.L, 6, torch.cuda.current_stream())
+    try:
+        sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+        o = _bench_like_opts(B.of_default_scf_opts())
+        o.precision = B.OF_F32
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(u)
+        res = B.of_scf_ground_state(h, sysd, Fn.wt(), o, u, phi)
+        F = B.of_forces(h, sysd, u, phi)
+    finally:
+        B.of_grid_destroy(h)
+    assert res.converged
+    assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
+    assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
+
+
+@pytest.mark.parametrize("form", ["mixed", "f64"])
+def test_benchmark_cell_against_the_oracle(form):
+    # the benchmark step itself -- 108 atoms, 96^3, WT-type kernel, exactly bench.make_case's
+    # options and call sequence -- against the oracle's ground state of the same cell
+    # (tests/golden/al108_wt.json, written by tests/golden/make_golden.py from the oracle alone)
+    import bench
+    path = os.path.join(HERE, "golden", "al108_wt.json")
+    with open(path) as f:
+        rec = json.load(f)["al108_wt"]
+    cell, h, sysd, fn, o = bench.make_case(torch, B, Fn, W, form)
+    try:
+        assert np.array_equal(np.array(rec["R"]), cell.R)       # same seeded positions
+        assert rec["sigma"] == cell.sigma and rec["rc"] == cell.rc and list(rec["n"]) == list(cell.n)
+        u0 = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        u = torch.empty_like(u0)
+        phi = torch.zeros_like(u0)
+        res, F = bench.run_step(B, h, sysd, fn, o, u, phi, u0)
+    finally:
+        B.of_grid_destroy(h)
+    assert res.converged
+    assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
+    for k in ("tf", "vw", "lr", "xc", "es", "self", "corr"):
+        assert abs(getattr(res, "e_" + k) - rec["terms"][k]) / cell.n_atoms <= 1e-5, k
+    assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
+
+
 def test_wt_108_atoms_full_size_properties():
     cell = W.al108_cell()
     res, F, u, phi = _run(cell, Fn.wt(), B.OF_F32, fp_tol=1e-6)
