@@ -45,6 +45,9 @@ WORKLOAD_DETAIL = {
                                                   "fixed-point error))"},
 }
 GOLDEN_AL108 = os.path.join(ROOT, "tests", "golden", "al108_wt.json")
+# DRAM bytes (read + write) of one FP32 order-12 sweep of a 320^3 grid by the fast-path stencil,
+# from the ncu capture summarised in profiles/stencil_fp32_320.md (145.9 + 91.9 MB)
+STENCIL320_DRAM_BYTES = 237.8e6
 GOLDEN_SMALL = os.path.join(ROOT, "tests", "golden", "ground_states.json")
 
 
@@ -93,7 +96,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--config3", action="store_true",
                    help="batched ground states of the first --cells cells of the 64-cell set")
-    p.add_argument("--cells", type=int, default=16)
+    p.add_argument("--cells", type=int, default=64)
     p.add_argument("--config5", action="store_true",
                    help="measure the 3999-atom 320^3 ground state instead of the benchmark step")
     p.add_argument("--wgc", action="store_true",
@@ -113,7 +116,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
     p.add_argument("--no-batched", action="store_true",
-                   help="skip the 64-cell batched-vs-sequential Poisson comparison")
+                   help="skip the 64-cell batched-vs-sequential comparisons (Poisson solves and "
+                        "ground states)")
     p.add_argument("--kernel-case", default=None, choices=["poisson96", "stencil96", "stencil320", "scf", "net160", "scf96_short"],
                    help="run only a bounded piece of the step (for profiler captures) and exit: "
                         "poisson96 = 4 mixed Poisson solves on the benchmark grid; stencil96 / "
@@ -902,16 +906,14 @@ def whole_job_value(step_ms, steps, world, device="cuda"):
     return total_ms, total_ms / 1e3 / (steps * world)
 
 
-def config3(args):
-    """Ground states + forces of the first --cells cells of the 64-cell set (reps 2..4 per axis,
+def batched_ground_states(torch, B, Fn, W, ncells):
+    """Ground states + forces of the first ncells cells of the 64-cell set (reps 2..4 per axis,
     64-128 points per axis, half with a vacancy, +-0.1 bohr, seed 3; WT-type kernel, the
-    benchmark's options): one batched call (cells on a pool of streams) against the same ground
-    states one after another.  Prints one JSON line."""
-    import numpy as np
-    import torch
-    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
-    B.load()
-    cells = W.batched_cells()[:args.cells]
+    benchmark's options): one batched call (each cell's solver on its own stream of a pool,
+    driven by its own host thread) against the same ground states one after another.  An
+    untimed batched call cut short (one outer iteration of three NLCG steps) first creates
+    every cell's workspace, multigrid hierarchy and graphs."""
+    cells = W.batched_cells()[:ncells]
     stream = torch.cuda.current_stream()
     grids = [B.of_grid_create(c.n, c.L, 6, stream) for c in cells]
     systems = [B.make_system(c.R, c.Z, c.sigma, c.rc) for c in cells]
@@ -921,14 +923,13 @@ def config3(args):
     us = [torch.ones(c.shape, dtype=torch.float64, device="cuda") for c in cells]
     phis = [torch.zeros_like(x) for x in us]
 
-    def batched():
+    def batched(opts, allow=()):
         for x, p in zip(us, phis):
             x.fill_(1.0)
             p.zero_()
-        r = B.of_scf_ground_state_batched(grids, systems, fn, o, us, phis)
-        for g, s, x, p in zip(grids, systems, us, phis):
-            B.of_forces(g, s, x, p)
-        return r
+        r = B.of_scf_ground_state_batched(grids, systems, fn, opts, us, phis, allow=allow)
+        forces = [B.of_forces(g, s, x, p) for g, s, x, p in zip(grids, systems, us, phis)]
+        return r, forces
 
     def sequential():
         out = []
@@ -939,11 +940,13 @@ def config3(args):
             B.of_forces(g, s, x, p)
         return out
 
-    batched()   # warm-up: workspaces, multigrid hierarchies, graphs
+    short = B.of_scf_opts.from_buffer_copy(o)
+    short.fp_max_iter, short.nlcg_max_iter = 1, 3
+    batched(short, allow=(B.OF_ENOCONV,))
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         t = time.time()
-        rb = batched()
+        rb, _ = batched(o)
         torch.cuda.synchronize()
         tb = time.time() - t
         t = time.time()
@@ -951,19 +954,30 @@ def config3(args):
         torch.cuda.synchronize()
         ts = time.time() - t
     de = max(abs(a.energy - b.energy) / c.n_atoms for a, b, c in zip(rb, rs, cells))
-    line = {"metric": "s per batch of ground states + forces", "unit": "s", "higher_is_better": False,
-            "data": "synthetic",
-            "config": {"workload": f"first {len(cells)} cells of the 64-cell set (seed 3), "
-                                   "WT-type kernel, ground state + forces each",
-                       "points": int(sum(c.n_points for c in cells)),
-                       "atoms": int(sum(c.n_atoms for c in cells))},
-            "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
-            "max_energy_difference_ha_per_atom": de,
-            "energies_per_atom_ha": [r.energy / c.n_atoms for r, c in zip(rb, cells)],
-            "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    out = {"workload": f"first {len(cells)} cells of the 64-cell set (seed 3), WT-type kernel, "
+                       "ground state + forces each",
+           "cells": len(cells), "points": int(sum(c.n_points for c in cells)),
+           "atoms": int(sum(c.n_atoms for c in cells)),
+           "batched_s": tb, "sequential_s": ts, "speedup": ts / tb,
+           "all_converged": all(r.converged for r in rb),
+           "max_energy_difference_ha_per_atom": de,
+           "energies_per_atom_ha": [r.energy / c.n_atoms for r, c in zip(rb, cells)],
+           "clocks": clk.summary()}
     for g in grids:
         B.of_grid_destroy(g)
+    return out
+
+
+def config3(args):
+    """--config3: the batched ground states of the first --cells cells as one JSON line."""
+    import torch
+    from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
+    B.load()
+    r = batched_ground_states(torch, B, Fn, W, args.cells)
+    line = {"metric": "s per batch of ground states + forces", "unit": "s", "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": r["workload"], "points": r["points"],
+                                            "atoms": r["atoms"]}, **r}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -1114,6 +1128,7 @@ def main():
     stencil320 = None if rank != 0 else stencil_rates(torch, B, (320, 320, 320), (76.0, 76.0, 76.0),
                                                       reps=20)
     batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
+    batched_gs = None if (args.no_batched or rank != 0) else batched_ground_states(torch, B, Fn, W, 64)
     learned = None if (args.no_learned or rank != 0) else learned_compare(torch, B, W)
     compare = None
     if not args.no_compare_f64 and rank == 0:
@@ -1152,7 +1167,27 @@ def main():
                     "frac": achieved / peak, "traffic": None, "kernel": dom["kernel"],
                     "peak_kind": peak_kind,
                     "launches": dom["launches"], "mean_us": dom["mean_ms"] * 1e3,
-                    "bytes_per_launch": dom["bytes_per_launch"]}
+                    "bytes_per_launch": dom["bytes_per_launch"],
+                    "bytes_model": "every field a fused sweep reads or writes, once per point of "
+                                   "its level (CG iteration 10 words, Chebyshev step 6, residual "
+                                   "3, transfers 1-2 per fine point), halos not counted"}
+        if dom["kernel"] == "mg_pcg_pass_graph" and prof:
+            # the same time against the CG iterations' own bytes only (10 FP32 words per point
+            # per iteration), the V-cycle's sweeps left out
+            passes = sum(p["launches"] for p in prof if p["kernel"] == "mg_pcg_pass_graph")
+            its = res.poisson_iterations * args.steps / max(1, passes)
+            cg_bytes = its * 40.0 * cell.n_points
+            roofline["cg_iterations_per_launch"] = its
+            roofline["frac_cg_bytes_only"] = cg_bytes / (dom["mean_ms"] * 1e-3) / 1e9 / peak
+            roofline["note"] = ("latency-bound: at 96^3 every field stays in L2 and one "
+                                "preconditioned iteration is a chain of ~17 dependent launches")
+    roofline_320 = None
+    if stencil320:
+        roofline_320 = {"kernel": "stencil2_kernel (of_laplacian_apply, FP32, order 12, 320^3)",
+                        "bound": "hbm", "achieved": stencil320["f32"]["gbs"], "peak": peak,
+                        "unit": "GB/s", "frac": stencil320["f32"]["gbs"] / peak,
+                        "traffic": STENCIL320_DRAM_BYTES, "bytes_per_launch": 8.0 * 320 ** 3,
+                        "peak_kind": peak_kind}
 
     clocks = clk.summary()
     cpu = None
@@ -1172,7 +1207,8 @@ def main():
                 "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+                "roofline": roofline, "roofline_stencil_320": roofline_320,
+                "cpu_baseline": cpu, "clocks": clocks,
                 "stencil_96": stencil, "stencil_320": stencil320,
                 "result": {"energy_ha": res.energy, "energy_per_atom_ha": res.energy / cell.n_atoms,
                            "outer_iterations": res.outer_iterations,
@@ -1182,6 +1218,7 @@ def main():
                            "fp_error": res.fp_error, "max_force": float(np.abs(F).max()),
                            **(errors_vs_oracle(res, F, cell.n_atoms) or {})},
                 "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched,
+                "batched_ground_states_64": batched_gs,
                 "learned_preconditioner": learned}
         if compare:
             line["compare"] = compare

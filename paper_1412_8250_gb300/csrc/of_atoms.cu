@@ -78,6 +78,24 @@ __device__ __forceinline__ double gauss_V(double r, double Z, const Gauss& q) {
     return r < 1e-12 ? -Z * q.v0 : -Z * erf(r * q.erfscale) / r;
 }
 
+// The Gaussian factorises: exp(-r^2 / 2s^2) = ex(dx) ey(dy) ez(dz).  A block (J, plane) takes
+// ex and ey of its box columns and rows from shared memory (one exp each per block) instead of
+// one exp per point; boxes wider than GX_MAX fall back to the direct form.
+constexpr int GX_MAX = 512;
+
+__device__ __forceinline__ void gauss_axis_tables(const AtomBox& B, double h1, double h2, const Gauss& q,
+                                                  double* ex, double* ey) {
+    if (B.len[0] > GX_MAX || B.len[1] > GX_MAX) return;
+    for (int t = threadIdx.x; t < B.len[0]; t += blockDim.x) {
+        const double dx = (B.lo[0] + t) * h1 - B.R[0];
+        ex[t] = exp(-dx * dx * q.inv2s2);
+    }
+    for (int t = threadIdx.x; t < B.len[1]; t += blockDim.x) {
+        const double dy = (B.lo[1] + t) * h2 - B.R[1];
+        ey[t] = exp(-dy * dy * q.inv2s2);
+    }
+}
+
 // Block (J, plane): scatter b_J into b (atomic: boxes of different ions overlap) and reduce
 // dV * sum b_J V_J for the self energy.
 __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double h2, double h3,
@@ -85,21 +103,27 @@ __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double 
                                                       double* e_self_part, int max_planes) {
     const int J = blockIdx.x, pl = blockIdx.y;
     const AtomBox B = boxes[J];
+    __shared__ double ex[GX_MAX], ey[GX_MAX];
+    const bool tables = B.len[0] <= GX_MAX && B.len[1] <= GX_MAX;
+    if (pl < B.len[2]) gauss_axis_tables(B, h1, h2, q, ex, ey);
+    __syncthreads();
     double acc = 0.0;
     if (pl < B.len[2]) {
         const int k = B.lo[2] + pl;
         const double dz = k * h3 - B.R[2];
+        const double cz = -B.Z * q.norm * exp(-dz * dz * q.inv2s2);
         const int kw = wrap_index(k, d.n3);
         const int nxy = B.len[0] * B.len[1];
         const double rc2 = q.rc * q.rc;
         for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
             const int jj = t / B.len[0];
-            const int i = B.lo[0] + (t - jj * B.len[0]);
+            const int ii = t - jj * B.len[0];
+            const int i = B.lo[0] + ii;
             const int j = B.lo[1] + jj;
             const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= rc2) {
-                const double bj = gauss_b(r2, B.Z, q);
+                const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
                 const long long idx = wrap_index(i, d.n1) +
                                       (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
                 atomicAdd(b + idx, bj);
@@ -124,25 +148,32 @@ __global__ void __launch_bounds__(256) k_forces(Dims d, double h1, double h2, do
                                                 double* part, int max_planes) {
     const int J = blockIdx.x, pl = blockIdx.y;
     const AtomBox B = boxes[J];
+    __shared__ double ex[GX_MAX], ey[GX_MAX];
+    const bool tables = B.len[0] <= GX_MAX && B.len[1] <= GX_MAX;
+    if (pl < B.len[2]) gauss_axis_tables(B, h1, h2, q, ex, ey);
+    __syncthreads();
     double f[3] = {0.0, 0.0, 0.0};
     if (pl < B.len[2]) {
         const int k = B.lo[2] + pl;
         const double dz = k * h3 - B.R[2];
+        const double cz = -B.Z * q.norm * exp(-dz * dz * q.inv2s2);
         const int kw = wrap_index(k, d.n3);
         const int nxy = B.len[0] * B.len[1];
         const double rc2 = q.rc * q.rc;
         const double inv_s2 = 2.0 * q.inv2s2;
         for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
             const int jj = t / B.len[0];
-            const int i = B.lo[0] + (t - jj * B.len[0]);
+            const int ii = t - jj * B.len[0];
+            const int i = B.lo[0] + ii;
             const int j = B.lo[1] + jj;
             const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= rc2) {
                 const long long idx = wrap_index(i, d.n1) +
                                       (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+                const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
                 // grad b_J = -b_J (x - R_J) / sigma^2
-                const double w = -gauss_b(r2, B.Z, q) * inv_s2 * (phi[idx] - gauss_V(sqrt(r2), B.Z, q));
+                const double w = -bj * inv_s2 * (phi[idx] - gauss_V(sqrt(r2), B.Z, q));
                 f[0] += w * dx;
                 f[1] += w * dy;
                 f[2] += w * dz;
@@ -176,41 +207,55 @@ __global__ void k_sum_planes(int n_atoms, int max_planes, int stride, const doub
 
 // E_c^* (per-ion halves) and f^c for Gaussian charges with point reference charges:
 // E_c^* = 1/2 sum_I sum_{(J,T) != (I,0)} Z_I Z_J erfc(r/(2s))/r, f^c_I = -dE_c^*/dR_I.
-__global__ void k_overlap(int M, const AtomBox* boxes, double L1, double L2, double L3,
-                          double sigma, double cutoff, int t1, int t2, int t3, double* e_part,
-                          double* fc) {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= M) return;
+// One block per ion I; its threads take the (J, image) pairs in a fixed stride and the block
+// sums them in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_overlap(int M, const AtomBox* boxes, double L1, double L2,
+                                                 double L3, double sigma, double cutoff, int t1,
+                                                 int t2, int t3, double* e_part, double* fc) {
+    const int I = blockIdx.x;
     const AtomBox A = boxes[I];
-    double e = 0.0, f0 = 0.0, f1 = 0.0, f2 = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // e, f0, f1, f2
     const double inv2s = 1.0 / (2.0 * sigma), c2 = cutoff * cutoff;
     const double gp0 = 1.0 / (sigma * sqrt(M_PI));
-    for (int J = 0; J < M; ++J) {
+    const int na = 2 * t1 + 1, nb = 2 * t2 + 1, nc = 2 * t3 + 1;
+    const int nimg = na * nb * nc;
+    const long long total = (long long)M * nimg;
+    for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+        const int J = (int)(t / nimg);
+        int rem = (int)(t - (long long)J * nimg);
+        const int a = rem / (nb * nc) - t1;
+        rem %= nb * nc;
+        const int bb = rem / nc - t2, c = rem % nc - t3;
+        if (J == I && a == 0 && bb == 0 && c == 0) continue;
         const AtomBox B = boxes[J];
-        for (int a = -t1; a <= t1; ++a)
-            for (int bb = -t2; bb <= t2; ++bb)
-                for (int c = -t3; c <= t3; ++c) {
-                    if (J == I && a == 0 && bb == 0 && c == 0) continue;
-                    const double dx = A.R[0] - B.R[0] - a * L1;
-                    const double dy = A.R[1] - B.R[1] - bb * L2;
-                    const double dz = A.R[2] - B.R[2] - c * L3;
-                    const double r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 > c2) continue;
-                    const double r = sqrt(r2);
-                    const double ec = erfc(r * inv2s);
-                    e += 0.5 * A.Z * B.Z * ec / r;
-                    // g'(r) = -exp(-r^2/(4 s^2)) / (s sqrt(pi) r) - erfc(r/2s)/r^2
-                    const double gp = -exp(-r2 * inv2s * inv2s) * gp0 / r - ec / r2;
-                    const double w = -A.Z * B.Z * gp / r;
-                    f0 += w * dx;
-                    f1 += w * dy;
-                    f2 += w * dz;
-                }
+        const double dx = A.R[0] - B.R[0] - a * L1;
+        const double dy = A.R[1] - B.R[1] - bb * L2;
+        const double dz = A.R[2] - B.R[2] - c * L3;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 > c2) continue;
+        const double r = sqrt(r2);
+        const double ec = erfc(r * inv2s);
+        acc[0] += 0.5 * A.Z * B.Z * ec / r;
+        // g'(r) = -exp(-r^2/(4 s^2)) / (s sqrt(pi) r) - erfc(r/2s)/r^2
+        const double gp = -exp(-r2 * inv2s * inv2s) * gp0 / r - ec / r2;
+        const double w = -A.Z * B.Z * gp / r;
+        acc[1] += w * dx;
+        acc[2] += w * dy;
+        acc[3] += w * dz;
     }
-    e_part[I] = e;
-    fc[3 * I + 0] = f0;
-    fc[3 * I + 1] = f1;
-    fc[3 * I + 2] = f2;
+    __shared__ double sh[8][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double v = warp_sum(acc[k]);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[w][threadIdx.x];
+        if (threadIdx.x == 0) e_part[I] = v;
+        else fc[3 * I + threadIdx.x - 1] = v;
+    }
 }
 
 // ---- E_c^* and f^c on the grid with Gaussian reference charges (App. B)
@@ -519,8 +564,8 @@ void overlap_correction(of_grid* g, const of_system* sys, double* e_c, double* f
     const int t2 = (int)std::ceil(cutoff / g->L[1]) + 1;
     const int t3 = (int)std::ceil(cutoff / g->L[2]) + 1;
     double* buf = (double*)ws(g, WS_S14, sizeof(double) * (4 * (size_t)M + 8));
-    launch(k_overlap, (M + 127) / 128, 128, g->stream, M, a.d_boxes, g->L[0], g->L[1], g->L[2],
-                                                     sys->sigma, cutoff, t1, t2, t3, buf, buf + M);
+    launch(k_overlap, M, 256, g->stream, M, a.d_boxes, g->L[0], g->L[1], g->L[2], sys->sigma,
+           cutoff, t1, t2, t3, buf, buf + M);
     OF_LAUNCH_CHECK();
     if (e_c) {
         launch(k_sum_product, 1, 256, g->stream, M, buf, nullptr, red_ctx(g, 118));

@@ -348,3 +348,36 @@ def test_batched_ground_states_match_single_cell_calls():
     finally:
         for g in grids:
             B.of_grid_destroy(g)
+
+
+def test_batched_wt_ground_states_of_uneven_cells_match_the_oracle():
+    # the batched call on cells of different shapes and atom counts, one with a vacancy, with
+    # the WT-type kernel term and the benchmark's options: every cell's energy and forces
+    # against the oracle's own ground state of that cell
+    cells = [W.fcc_supercell((1, 1, 1), points_per_cell=16, displacement=0.1, seed=11,
+                             sigma=1.2, rc=10.0, name="c111"),
+             W.fcc_supercell((2, 1, 1), points_per_cell=12, displacement=0.1, seed=12,
+                             vacancy="random", sigma=1.2, rc=10.0, name="c211v"),
+             W.fcc_supercell((1, 2, 1), points_per_cell=12, displacement=0.1, seed=13,
+                             sigma=1.2, rc=10.0, name="c121")]
+    stream = torch.cuda.current_stream()
+    grids = [B.of_grid_create(c.n, c.L, 6, stream) for c in cells]
+    try:
+        systems = [B.make_system(c.R, c.Z, c.sigma, c.rc) for c in cells]
+        o = _bench_like_opts(B.of_default_scf_opts())
+        o.precision = B.OF_F32
+        us = [torch.ones(c.shape, dtype=torch.float64, device="cuda") for c in cells]
+        phis = [torch.zeros_like(x) for x in us]
+        results = B.of_scf_ground_state_batched(grids, systems, Fn.wt(), o, us, phis)
+        for k, c in enumerate(cells):
+            assert results[k].converged, c.name
+            F = B.of_forces(grids[k], systems[k], us[k], phis[k])
+            grid = O.Grid(c.n, c.L, 6)
+            ref = O.scf_ground_state(grid, c.R, c.Z, c.sigma, c.rc, O.wt_functional(),
+                                     nlcg_tol=1e-7, fp_tol=1e-7, anderson_m=3, zeta=1.0)
+            Fref = O.forces(ref.phi, c.R, c.Z, c.sigma, c.rc, grid)
+            assert abs(results[k].energy - ref.energy) / c.n_atoms <= E_TOL, c.name
+            assert np.max(np.abs(F - Fref)) <= F_TOL, c.name
+    finally:
+        for g in grids:
+            B.of_grid_destroy(g)
