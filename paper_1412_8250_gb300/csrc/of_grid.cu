@@ -185,6 +185,7 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
 
 of_status of_grid_destroy(of_grid* g) {
     if (!g) return OF_OK;
+    if (g->worker) g->worker_destroy(g->worker);
     if (g->twin) of_grid_destroy(g->twin);
     if (g->twin_stream) cudaStreamDestroy(g->twin_stream);
     if (g->twin_in) cudaEventDestroy(g->twin_in);
@@ -264,8 +265,9 @@ of_status of_profile_enable(of_grid* g, int sample_every) {
 int of_profile_read(of_grid* g, of_kernel_stat* out, int max) {
     if (!g || !g->prof) return 0;
     try {
-        // the timed launches of this handle and of its twin (whose solves ran beside it)
-        Prof* ps[2] = {g->prof, g->twin ? g->twin->prof : nullptr};
+        // the timed launches of this handle and of its twin chain (whose solves ran beside it)
+        std::vector<Prof*> ps;
+        for (of_grid* h = g; h; h = h->twin) ps.push_back(h->prof);
         OF_CUDA(cudaStreamSynchronize(g->stream));
         for (Prof* pp : ps) {
             if (!pp) continue;

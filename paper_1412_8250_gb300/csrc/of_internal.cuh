@@ -198,6 +198,10 @@ struct of_grid {
     of_grid* twin = nullptr;
     cudaStream_t twin_stream = nullptr;
     cudaEvent_t twin_in = nullptr, twin_out = nullptr;
+    // host thread that runs the twin's half of paired solves (of_scf.cu), started with the
+    // first pair and joined by worker_destroy when the handle is destroyed
+    void* worker = nullptr;
+    void (*worker_destroy)(void*) = nullptr;
     void* graphs = nullptr;              // cached CUDA graphs (of_krylov.cu)
     // the Krylov loops launch every iteration directly instead of capturing and caching CUDA
     // graphs (which create a capture stream and executable graphs)

@@ -18,6 +18,9 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -609,20 +612,83 @@ static of_grid* twin_of(of_grid* g) {
     return g->twin;
 }
 
+// The host thread that runs the second half of every pair on a handle: started with the
+// handle's first pair, idle on a condition variable between pairs, joined when the handle is
+// destroyed (a thread per pair cost a thread start every NLCG step and kernel map).
+struct PairWorker {
+    std::thread th;
+    std::mutex m;
+    std::condition_variable cv;
+    std::function<void()> task;
+    bool has_task = false, busy = false, stop = false;
+    explicit PairWorker(int device) {
+        th = std::thread([this, device]() {
+            cudaSetDevice(device);
+            for (;;) {
+                std::function<void()> f;
+                {
+                    std::unique_lock<std::mutex> lk(m);
+                    cv.wait(lk, [this] { return has_task || stop; });
+                    if (!has_task) return;
+                    f = std::move(task);
+                    has_task = false;
+                }
+                f();   // never throws: the tasks of run_pair catch everything
+                {
+                    std::lock_guard<std::mutex> lk(m);
+                    busy = false;
+                }
+                cv.notify_all();
+            }
+        });
+    }
+    void post(std::function<void()> f) {
+        {
+            std::lock_guard<std::mutex> lk(m);
+            task = std::move(f);
+            has_task = true;
+            busy = true;
+        }
+        cv.notify_all();
+    }
+    void wait() {
+        std::unique_lock<std::mutex> lk(m);
+        cv.wait(lk, [this] { return !busy; });
+    }
+    ~PairWorker() {
+        {
+            std::lock_guard<std::mutex> lk(m);
+            stop = true;
+        }
+        cv.notify_all();
+        th.join();
+    }
+};
+
+static void destroy_pair_worker(void* p) { delete static_cast<PairWorker*>(p); }
+
+static PairWorker* pair_worker(of_grid* g) {
+    if (!g->worker) {
+        g->worker = new PairWorker(g->device);
+        g->worker_destroy = destroy_pair_worker;
+    }
+    return static_cast<PairWorker*>(g->worker);
+}
+
 // Two independent pieces of work at once: first(g) on g's stream in this thread, second(t) on
-// the twin handle t (its own stream and workspace) in a second host thread.  Both are
+// the twin handle t (its own stream and workspace) in the handle's worker thread.  Both are
 // latency-bound solves at the benchmark's sizes, so they overlap on the GPU.  The twin's
 // stream starts after the work queued on g's stream, which waits for the twin before it goes
 // on.  An error of either side is rethrown after both have finished.
 template <class First, class Second>
 static void run_pair(of_grid* g, First&& first, Second&& second) {
     of_grid* t = twin_of(g);
+    PairWorker* w = pair_worker(g);
     OF_CUDA(cudaEventRecord(g->twin_in, g->stream));
     OF_CUDA(cudaStreamWaitEvent(t->stream, g->twin_in, 0));
     of_status err2 = OF_OK;
     std::string msg2;
-    std::thread worker([&]() {
-        cudaSetDevice(g->device);
+    w->post([&]() {
         try {
             second(t);
         } catch (const Error& e) {
@@ -630,6 +696,7 @@ static void run_pair(of_grid* g, First&& first, Second&& second) {
             msg2 = of_last_error();
         } catch (...) {
             err2 = OF_ECUDA;
+            msg2 = "unexpected exception in the second solve of a pair";
         }
     });
     of_status err1 = OF_OK;
@@ -640,11 +707,11 @@ static void run_pair(of_grid* g, First&& first, Second&& second) {
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed in a paired solve");
         err1 = OF_ENOMEM;
-    } catch (...) {   // whatever it was, the worker is joined before anything leaves
+    } catch (...) {   // whatever it was, the worker finishes before anything leaves
         set_error("unexpected exception in a paired solve");
         err1 = OF_ECUDA;
     }
-    worker.join();
+    w->wait();
     OF_CUDA(cudaEventRecord(g->twin_out, t->stream));
     OF_CUDA(cudaStreamWaitEvent(g->stream, g->twin_out, 0));
     if (err1 != OF_OK) throw Error{err1};
@@ -652,6 +719,61 @@ static void run_pair(of_grid* g, First&& first, Second&& second) {
         set_error("%s", msg2.c_str());
         throw Error{err2};
     }
+}
+
+// Up to GROUP_MAX independent solves at once: task 0 on g in this thread, task i on the i-th
+// handle of g's twin chain (g->twin, its twin, ...) in the worker thread of the handle before
+// it.  The chain's streams start after the work queued on g's stream, which waits for all of
+// them before it goes on.  The first error is rethrown after every task has finished.
+constexpr int GROUP_MAX = 4;
+
+static void run_group(of_grid* g, int ntasks, const std::function<void(of_grid*, int)>& task) {
+    OF_REQUIRE(ntasks >= 1 && ntasks <= GROUP_MAX, OF_EINVAL, "run_group: %d tasks", ntasks);
+    of_grid* H[GROUP_MAX] = {g};
+    for (int i = 1; i < ntasks; ++i) H[i] = twin_of(H[i - 1]);
+    if (ntasks > 1) {
+        OF_CUDA(cudaEventRecord(g->twin_in, g->stream));
+        for (int i = 1; i < ntasks; ++i) OF_CUDA(cudaStreamWaitEvent(H[i]->stream, g->twin_in, 0));
+    }
+    of_status err[GROUP_MAX] = {};
+    std::string msg[GROUP_MAX];
+    PairWorker* w[GROUP_MAX] = {};
+    for (int i = 1; i < ntasks; ++i) {
+        w[i] = pair_worker(H[i - 1]);
+        w[i]->post([&, i]() {
+            try {
+                task(H[i], i);
+            } catch (const Error& e) {
+                err[i] = e.code;
+                msg[i] = of_last_error();
+            } catch (...) {
+                err[i] = OF_ECUDA;
+                msg[i] = "unexpected exception in a grouped solve";
+            }
+        });
+    }
+    try {
+        task(g, 0);
+    } catch (const Error& e) {
+        err[0] = e.code;
+        msg[0] = of_last_error();
+    } catch (const std::bad_alloc&) {
+        err[0] = OF_ENOMEM;
+        msg[0] = "host allocation failed in a grouped solve";
+    } catch (...) {   // whatever it was, the workers finish before anything leaves
+        err[0] = OF_ECUDA;
+        msg[0] = "unexpected exception in a grouped solve";
+    }
+    for (int i = 1; i < ntasks; ++i) w[i]->wait();
+    for (int i = 1; i < ntasks; ++i) {
+        OF_CUDA(cudaEventRecord(H[i - 1]->twin_out, H[i]->stream));
+        OF_CUDA(cudaStreamWaitEvent(g->stream, H[i - 1]->twin_out, 0));
+    }
+    for (int i = 0; i < ntasks; ++i)
+        if (err[i] != OF_OK) {
+            set_error("%s", msg[i].c_str());
+            throw Error{err[i]};
+        }
 }
 
 // The two line-energy Poisson solves of products, phi1 for rho = a1 b1 and phi2 for
@@ -914,15 +1036,12 @@ static double lr_potential_l2(of_grid* g, const of_functional* fn, double kf2, c
         S.W[p][r] = W;
         return shifted(h, f, P, Q, kf2, W, ko, &si);
     };
-    for (int job = 0; job < njobs; job += 2) {
-        of_solve_info si[2] = {};
-        of_status sj[2] = {OF_OK, OF_OK};
-        if (job + 1 < njobs)
-            run_pair(g, [&](of_grid* h) { sj[0] = solve(h, job, si[0]); },
-                     [&](of_grid* h) { sj[1] = solve(h, job + 1, si[1]); });
-        else
-            sj[0] = solve(g, job, si[0]);
-        for (int q = 0; q < 2; ++q) {
+    for (int job = 0; job < njobs; job += GROUP_MAX) {
+        const int k = std::min(GROUP_MAX, njobs - job);
+        of_solve_info si[GROUP_MAX] = {};
+        of_status sj[GROUP_MAX] = {};
+        run_group(g, k, [&](of_grid* h, int q) { sj[q] = solve(h, job + q, si[q]); });
+        for (int q = 0; q < k; ++q) {
             if (sj[q] != OF_OK && sj[q] != OF_ENOCONV) throw Error{sj[q]};
             st.kernel += si[q].iterations;
             add_info(info_out, si[q]);
@@ -954,27 +1073,30 @@ static double lr_potential_impl(of_grid* g, const of_functional* fn, double kf2,
     launch_stencil<double, 2>(g, g->w64, OpScaledLap{gb, fb, -1.0 / kf2});
     PairPtrs W{};
     W.npairs = npairs;
+    // the shifted solves (two exponents x npairs shifts), up to GROUP_MAX at once on the grid
+    // and its twin chain
+    const int njobs = 2 * npairs;
+    double2* Wj[2 * 4];
+    for (int j = 0; j < njobs; ++j) Wj[j] = (double2*)Wws + (size_t)j * n;   // even: u^{2 alpha}
     for (int k = 0; k < npairs; ++k) {
-        const double2 P = make_double2(fn->P[4 * k], fn->P[4 * k + 1]);
-        const double2 Q = make_double2(fn->Q[4 * k], fn->Q[4 * k + 1]);
-        double2* Wa = (double2*)Wws + (size_t)(2 * k) * n;       // from u^{2 alpha}
-        double2* Wb = (double2*)Wws + (size_t)(2 * k + 1) * n;   // from u^{2 beta}
-        of_solve_info ia{}, ib{};
-        of_status s1 = OF_OK, s2 = OF_OK;
-        // the two exponents' solves at once, the second on the twin handle
-        run_pair(g, [&](of_grid* h) { s1 = shifted(h, fa, P, Q, kf2, Wa, ko, &ia); },
-                 [&](of_grid* h) { s2 = shifted(h, fb, P, Q, kf2, Wb, ko, &ib); });
-        if (s1 != OF_OK && s1 != OF_ENOCONV) throw Error{s1};
-        if (s2 != OF_OK && s2 != OF_ENOCONV) throw Error{s2};
-        st.kernel += ia.iterations + ib.iterations;
-        if (info_out) {
-            info_out->iterations += ia.iterations + ib.iterations;
-            info_out->refinements += ia.refinements + ib.refinements;
-            info_out->rel_residual = std::max(info_out->rel_residual,
-                                              std::max(ia.rel_residual, ib.rel_residual));
+        W.Wa[k] = Wj[2 * k];
+        W.Wb[k] = Wj[2 * k + 1];
+    }
+    for (int job = 0; job < njobs; job += GROUP_MAX) {
+        const int kk = std::min(GROUP_MAX, njobs - job);
+        of_solve_info si[GROUP_MAX] = {};
+        of_status sj[GROUP_MAX] = {};
+        run_group(g, kk, [&](of_grid* h, int q) {
+            const int j = job + q, k = j / 2;
+            const double2 P = make_double2(fn->P[4 * k], fn->P[4 * k + 1]);
+            const double2 Q = make_double2(fn->Q[4 * k], fn->Q[4 * k + 1]);
+            sj[q] = shifted(h, (j & 1) ? fb : fa, P, Q, kf2, Wj[j], ko, &si[q]);
+        });
+        for (int q = 0; q < kk; ++q) {
+            if (sj[q] != OF_OK && sj[q] != OF_ENOCONV) throw Error{sj[q]};
+            st.kernel += si[q].iterations;
+            add_info(info_out, si[q]);
         }
-        W.Wa[k] = Wa;
-        W.Wb[k] = Wb;
     }
     launch(k_lr_assemble, nb, 256, g->stream, n, u, W, fn->alpha, fn->beta, vlr, red_ctx(g, SC_TLR));
     OF_LAUNCH_CHECK();
