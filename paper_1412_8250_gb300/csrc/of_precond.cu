@@ -34,6 +34,8 @@ struct of_precond {
     int device = 0;
     // limit of the tensor-core kernels' waits for an MMA completion (of_precond_set_wait_limit)
     unsigned long long wait_ns = 2000000000ull;
+    // BF16 weights of the backward pass in the forward layout (k_backward_weights)
+    __nv_bfloat16* pbw = nullptr;
 };
 
 namespace of {
@@ -321,16 +323,43 @@ __device__ __forceinline__ void stage_planes(uint32_t abuf, const __nv_bfloat16*
 }
 
 // Layer 1: z1 = W1 * (sgn r / s) + b1, a1 = GELU(z1), as the GEMM D[128 x 16] = A B^T with
+// Data-gradient epilogue (the backward pass runs the forward kernels with the mirrored,
+// transposed weights of of_precond's backward array): the convolution's 8 channels ch*8 ..
+// of point i times GELU' of the forward pre-activation zin, to gout (FP32, [x][16], for the
+// weight gradients) and, when aout is set, to aout (BF16 planar, the next convolution's input).
+__device__ __forceinline__ void epilogue_bwd(const float (&acc)[8], const __nv_bfloat16* zin, float* gout,
+                                             __nv_bfloat16* aout, long long n, long long i, int ch) {
+    float z[8];
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(zin + ((long long)ch * n + i) * 8));
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(h[k]);
+        z[2 * k] = f.x;
+        z[2 * k + 1] = f.y;
+    }
+    float g[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) g[o] = acc[o] * gelu_grad_f(z[o]);
+    float4* go = reinterpret_cast<float4*>(gout + i * NC + 8 * ch);
+    go[0] = make_float4(g[0], g[1], g[2], g[3]);
+    go[1] = make_float4(g[4], g[5], g[6], g[7]);
+    if (aout) store8(aout + ((long long)ch * n + i) * 8, g);
+}
+
 // A[m][k] = (sgn r / s)(x_m + t_k) (taps k < 27, zero up to 32) and B[o][k] = W1[o][t_k]: two
 // MMAs of K = 16.  The nine plane rows of r are staged in FP32 (plain loads), each thread
 // builds half of its A row in BF16.  rnout: the input as rounded to BF16 (training).  One CTA
 // of 256 threads per tile; thread tid owns row m = tid % 128 and channels 8 (tid / 128) .. + 7.
+template <bool BWD>
 __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, int lseg,
                                                              const float* __restrict__ rin,
                                                              const __nv_bfloat16* __restrict__ P,
                                                              __nv_bfloat16* zout, __nv_bfloat16* aout,
                                                              float* rnout, const double* s_dev, float sgn,
-                                                             double* err, unsigned long long wait_ns) {
+                                                             double* err, unsigned long long wait_ns,
+                                                             const __nv_bfloat16* __restrict__ zin,
+                                                             float* gout) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* As = sm;
@@ -355,7 +384,8 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
     tc::fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t a_base = tc::smem_addr(As), b_base = tc::smem_addr(Bs);
-    const double rms = *s_dev;
+    // the input scaled by sgn / RMS (forward), or as it is (data gradient)
+    const double rms = BWD ? 1.0 : *s_dev;
     const float inv = rms > 0.0 ? sgn * (float)(1.0 / rms) : 0.f;   // 0 for a zero residual
     const long long ntiles = (long long)d.n2 * d.n3 * nseg;
     float* rs = reinterpret_cast<float*>(As + tc::L1_STAGE);
@@ -409,14 +439,18 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
         tc::ld8(tmem + ((uint32_t)((warp & 3) * 32) << 16) + 8 * ch, acc);
         if (m < L) {
             const long long i = (long long)rowi * d.n1 + x0 + m;
-            float zv[8], g[8];
+            if (BWD)
+                epilogue_bwd(acc, zin, gout, aout, d.n, i, ch);
+            else {
+                float zv[8], g[8];
 #pragma unroll
-            for (int o = 0; o < 8; ++o) {
-                zv[o] = acc[o] + bias[8 * ch + o];
-                g[o] = gelu_f(zv[o]);
+                for (int o = 0; o < 8; ++o) {
+                    zv[o] = acc[o] + bias[8 * ch + o];
+                    g[o] = gelu_f(zv[o]);
+                }
+                if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
+                store8(aout + ((long long)ch * d.n + i) * 8, g);
             }
-            if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
-            store8(aout + ((long long)ch * d.n + i) * 8, g);
         }
         tc::fence_before();
     }
@@ -436,13 +470,15 @@ __global__ void __launch_bounds__(tc::THREADS, 4) k_conv1_tc(Dims d, int nseg, i
 // y = scale (W3 * a2 + b3), scale = *s_dev (1 with s_dev null).  The next tile's plane rows are
 // copied into the other A buffer while the current tile's MMAs and epilogue run; one CTA of 256
 // threads per tile, persistent; err as for layer 1.
-template <int LAYER>
+template <int LAYER, bool BWD>
 __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, int lseg,
                                                             const __nv_bfloat16* __restrict__ in,
                                                             const __nv_bfloat16* __restrict__ P,
                                                             __nv_bfloat16* zout, __nv_bfloat16* aout,
                                                             float* yout, const double* s_dev, double* err,
-                                                            unsigned long long wait_ns) {
+                                                            unsigned long long wait_ns,
+                                                            const __nv_bfloat16* __restrict__ zin,
+                                                            float* gout) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
     unsigned char* As = sm;                              // two A buffers
@@ -536,14 +572,18 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, in
 #pragma unroll
                 for (int o = 0; o < 8; ++o) acc[o] += __uint_as_float(part[q][o]);
             if (m < L) {
-                float zv[8], g[8];
+                if (BWD)
+                    epilogue_bwd(acc, zin, gout, aout, d.n, i, ch);
+                else {
+                    float zv[8], g[8];
 #pragma unroll
-                for (int o = 0; o < 8; ++o) {
-                    zv[o] = acc[o] + bias[8 * ch + o];
-                    g[o] = gelu_f(zv[o]);
+                    for (int o = 0; o < 8; ++o) {
+                        zv[o] = acc[o] + bias[8 * ch + o];
+                        g[o] = gelu_f(zv[o]);
+                    }
+                    if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
+                    store8(aout + ((long long)ch * d.n + i) * 8, g);
                 }
-                if (zout) store8(zout + ((long long)ch * d.n + i) * 8, zv);
-                store8(aout + ((long long)ch * d.n + i) * 8, g);
             }
         } else if (ch == 0) {
             uint32_t part[9];
@@ -571,84 +611,8 @@ __global__ void __launch_bounds__(tc::THREADS, 2) k_conv_tc(Dims d, int nseg, in
 }
 
 // ---------------------------------------------------------------- backward
-// gz2[x][c] = GELU'(z2[x][c]) sum_t W3[c][t] gy[x - t]
-__global__ void __launch_bounds__(256) k_net_l3_bwd(Dims d, const float* __restrict__ gy,
-                                                    const __nv_bfloat16* __restrict__ z2,
-                                                    const __nv_bfloat16* __restrict__ P, float* gz2) {
-    __shared__ float W[NT * NC];   // [t][c]
-    for (int k = threadIdx.x; k < NT * NC; k += blockDim.x)
-        W[k] = __bfloat162float(P[OW3 + (k % NC) * NT + k / NC]);
-    __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const Nb nb = neighbours(d, i);
-    float acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-        const float g = __ldg(gy + nb.at(NT - 1 - t));   // x - t is the mirrored tap
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fmaf(W[t * NC + c], g, acc[c]);
-    }
-    float z[NC];
-    load16p(z2, d.n, i, z);
-    float4* out = reinterpret_cast<float4*>(gz2 + i * NC);
-#pragma unroll
-    for (int q = 0; q < NC / 4; ++q)
-        out[q] = make_float4(acc[4 * q] * gelu_grad_f(z[4 * q]), acc[4 * q + 1] * gelu_grad_f(z[4 * q + 1]),
-                             acc[4 * q + 2] * gelu_grad_f(z[4 * q + 2]),
-                             acc[4 * q + 3] * gelu_grad_f(z[4 * q + 3]));
-}
-
-// gz1[x][c] = GELU'(z1[x][c]) sum_t sum_o W2[o][c][t] gz2[x - t][o]; W2 staged as [t][o][c]
-__global__ void __launch_bounds__(256) k_net_l2_bwd(Dims d, const float* __restrict__ gz2,
-                                                    const __nv_bfloat16* __restrict__ z1,
-                                                    const __nv_bfloat16* __restrict__ P, float* gz1) {
-    __shared__ __align__(16) float W[NT * NC * NC];
-    for (int k = threadIdx.x; k < NT * NC * NC; k += blockDim.x) {
-        const int t = k / (NC * NC), o = (k / NC) % NC, c = k % NC;
-        W[k] = __bfloat162float(P[OW2 + (o * NC + c) * NT + t]);
-    }
-    __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= d.n) return;
-    const Nb nb = neighbours(d, i);
-    float acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-#pragma unroll 1
-    for (int t = 0; t < NT; ++t) {
-        const float4* g4 = reinterpret_cast<const float4*>(gz2 + nb.at(NT - 1 - t) * NC);
-        const float4* Wt = reinterpret_cast<const float4*>(W + t * NC * NC);
-#pragma unroll
-        for (int oq = 0; oq < NC / 4; ++oq) {
-            const float4 gq = __ldg(g4 + oq);
-            const float go[4] = {gq.x, gq.y, gq.z, gq.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int o = 4 * oq + k;
-#pragma unroll
-                for (int q = 0; q < NC / 4; ++q) {
-                    const float4 w = Wt[o * (NC / 4) + q];
-                    acc[4 * q] = fmaf(w.x, go[k], acc[4 * q]);
-                    acc[4 * q + 1] = fmaf(w.y, go[k], acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmaf(w.z, go[k], acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmaf(w.w, go[k], acc[4 * q + 3]);
-                }
-            }
-        }
-    }
-    float z[NC];
-    load16p(z1, d.n, i, z);
-    float4* out = reinterpret_cast<float4*>(gz1 + i * NC);
-#pragma unroll
-    for (int q = 0; q < NC / 4; ++q)
-        out[q] = make_float4(acc[4 * q] * gelu_grad_f(z[4 * q]), acc[4 * q + 1] * gelu_grad_f(z[4 * q + 1]),
-                             acc[4 * q + 2] * gelu_grad_f(z[4 * q + 2]),
-                             acc[4 * q + 3] * gelu_grad_f(z[4 * q + 3]));
-}
-
+// The data gradients run on the tensor-core kernels above (k_backward_weights); the weight
+// and bias gradients here, on the CUDA cores in FP32.
 // Weight and bias gradients.  A persistent grid walks tiles of WT consecutive points; per
 // tile and tap t the shifted activations a1(x+t), a2(x+t), rn(x+t) are gathered into shared
 // memory, and
@@ -797,6 +761,25 @@ __global__ void k_adam(float* params, __nv_bfloat16* pbf, float* grad, float* m,
     params[p] = w;
     pbf[p] = __float2bfloat16(w);
     grad[p] = 0.f;
+}
+
+// The data gradients of layers 3 and 2 are convolutions of the same shape as layers 1 and 2:
+//   ga2[c](x) = sum_t W3[c][t] gy(x - t) = sum_t' W3[c][mirror t'] gy(x + t')        (1 -> 16)
+//   ga1[c](x) = sum_o sum_t W2[o][c][t] gz2[o](x - t) = sum_t' sum_o W2[o][c][mirror t'] gz2[o](x + t')
+// so they run on the forward tensor-core kernels with W1' = mirrored W3 and W2' = W2 with its
+// channels transposed and taps mirrored (mirror t = NT - 1 - t negates the offset), zero biases.
+__global__ void k_backward_weights(const __nv_bfloat16* __restrict__ P, __nv_bfloat16* __restrict__ Q) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NPAR) return;
+    __nv_bfloat16 v = __float2bfloat16(0.f);
+    if (k >= OW1 && k < OB1) {
+        const int c = (k - OW1) / NT, t = (k - OW1) % NT;
+        v = P[OW3 + c * NT + (NT - 1 - t)];
+    } else if (k >= OW2 && k < OB2) {
+        const int j = k - OW2, cc = j / (NC * NT), o = (j / NT) % NC, t = j % NT;
+        v = P[OW2 + (o * NC + cc) * NT + (NT - 1 - t)];
+    }
+    Q[k] = v;
 }
 
 __global__ void k_to_bf16(int n, const float* a, __nv_bfloat16* b) {
@@ -986,7 +969,7 @@ __global__ void __launch_bounds__(256) k_sumsq64(long long n, const double* __re
 
 // ---------------------------------------------------------------- host side
 struct NetBufs {
-    __nv_bfloat16 *a1, *a2, *z1, *z2;
+    __nv_bfloat16 *a1, *a2, *z1, *z2, *gz2b;   // gz2b: gz2 in BF16, input of the layer-2 data gradient
     float *y, *Ay, *gy, *rn, *gz2, *gz1, *part;
     int wblocks;
 };
@@ -1005,7 +988,7 @@ static NetBufs net_bufs(of_grid* g, bool training) {
     const int wb = wgrad_blocks(g->d.n);
     const size_t act = al256(n * NC * sizeof(__nv_bfloat16));
     const size_t f1 = al256(n * sizeof(float)), f16 = al256(n * NC * sizeof(float));
-    const size_t bytes = training ? 4 * act + 4 * f1 + 2 * f16 + al256((size_t)wb * NPAR * 4) : 2 * act;
+    const size_t bytes = training ? 5 * act + 4 * f1 + 2 * f16 + al256((size_t)wb * NPAR * 4) : 2 * act;
     char* p = (char*)ws(g, WS_K6, bytes);
     NetBufs B{};
     B.a1 = (__nv_bfloat16*)p; p += act;
@@ -1014,6 +997,7 @@ static NetBufs net_bufs(of_grid* g, bool training) {
     if (!training) return B;
     B.z1 = (__nv_bfloat16*)p; p += act;
     B.z2 = (__nv_bfloat16*)p; p += act;
+    B.gz2b = (__nv_bfloat16*)p; p += act;
     B.y = (float*)p; p += f1;
     B.Ay = (float*)p; p += f1;
     B.gy = (float*)p; p += f1;
@@ -1033,8 +1017,6 @@ struct OpNegLap32 {
     __device__ void store(long long i, float, float lap) { y[i] = -lap; }
     __device__ void end() {}
 };
-
-static inline unsigned pt_blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
 constexpr int SC_NET_ERR = SC_NET + 4;   // set by k_net_l2_tc when a wait gave up
 
@@ -1058,37 +1040,43 @@ static void conv_geometry(of_grid* g, int& nseg, int& lseg, long long& tiles) {
                "grid too large for the network kernels (%lld row segments)", tiles);
 }
 
+// BWD: the data gradient (the kernel's weights P are then the backward array, its input the
+// gradient of the layer above, zin the forward pre-activation and gout the FP32 output)
+template <bool BWD = false>
 static void launch_conv1_tc(of_grid* g, const float* r, const __nv_bfloat16* P, __nv_bfloat16* z1,
                             __nv_bfloat16* a1, float* rn, const double* rms, float sgn,
-                            unsigned long long wait_ns) {
+                            unsigned long long wait_ns, const __nv_bfloat16* zin = nullptr,
+                            float* gout = nullptr) {
     static int configured_device = -1;
     if (configured_device != g->device) {
-        OF_CUDA(cudaFuncSetAttribute(k_conv1_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM1));
+        OF_CUDA(cudaFuncSetAttribute(k_conv1_tc<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM1));
         configured_device = g->device;
     }
     int nseg, lseg;
     long long tiles;
     conv_geometry(g, nseg, lseg, tiles);
     const int grid = (int)std::max(1LL, std::min(tiles, 4LL * num_sms()));
-    launch_smem(k_conv1_tc, grid, tc::THREADS, tc::SMEM1, g->stream, g->d, nseg, lseg, r, P, z1, a1, rn,
-                rms, sgn, g->s.scalars + SC_NET_ERR, wait_ns);
+    launch_smem(k_conv1_tc<BWD>, grid, tc::THREADS, tc::SMEM1, g->stream, g->d, nseg, lseg, r, P, z1, a1,
+                rn, rms, sgn, g->s.scalars + SC_NET_ERR, wait_ns, zin, gout);
 }
 
-template <int LAYER>
+template <int LAYER, bool BWD = false>
 static void launch_conv_tc(of_grid* g, const __nv_bfloat16* in, const __nv_bfloat16* P,
                            __nv_bfloat16* zout, __nv_bfloat16* aout, float* y, const double* s_dev,
-                           unsigned long long wait_ns) {
+                           unsigned long long wait_ns, const __nv_bfloat16* zin = nullptr,
+                           float* gout = nullptr) {
     static int configured_device = -1;
     if (configured_device != g->device) {
-        OF_CUDA(cudaFuncSetAttribute(k_conv_tc<LAYER>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM));
+        OF_CUDA(cudaFuncSetAttribute(k_conv_tc<LAYER, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     tc::SMEM));
         configured_device = g->device;
     }
     int nseg, lseg;
     long long tiles;
     conv_geometry(g, nseg, lseg, tiles);
     const int grid = (int)std::max(1LL, std::min(tiles, 2LL * num_sms()));
-    launch_smem(k_conv_tc<LAYER>, grid, tc::THREADS, tc::SMEM, g->stream, g->d, nseg, lseg, in, P, zout,
-                aout, y, s_dev, g->s.scalars + SC_NET_ERR, wait_ns);
+    launch_smem(k_conv_tc<LAYER, BWD>, grid, tc::THREADS, tc::SMEM, g->stream, g->d, nseg, lseg, in, P,
+                zout, aout, y, s_dev, g->s.scalars + SC_NET_ERR, wait_ns, zin, gout);
 }
 
 // algorithmic bytes of one application: r read by the RMS pass and by layer 1, a1 and a2
@@ -1118,10 +1106,11 @@ static void net_loss_grad(of_grid* g, of_precond* P, const float* r, const NetBu
     launch_stencil<float, 2>(g, g->w32, OpNegLap32{B.y, B.Ay});
     launch(k_net_loss, vec_blocks(n), 256, g->stream, n, (const float*)B.y, (const float*)B.Ay,
            (const float*)B.rn, B.gy, red_ctx(g, SC_NET + 2));
-    launch(k_net_l3_bwd, pt_blocks(n), 256, g->stream, g->d, (const float*)B.gy,
-           (const __nv_bfloat16*)B.z2, (const __nv_bfloat16*)P->pbf, B.gz2);
-    launch(k_net_l2_bwd, pt_blocks(n), 256, g->stream, g->d, (const float*)B.gz2,
-           (const __nv_bfloat16*)B.z1, (const __nv_bfloat16*)P->pbf, B.gz1);
+    // data gradients on the tensor cores (BF16 operands, FP32 accumulation): gz2 from gy with
+    // the mirrored W3, gz1 from gz2 with the transposed, mirrored W2
+    launch(k_backward_weights, (NPAR + 255) / 256, 256, g->stream, (const __nv_bfloat16*)P->pbf, P->pbw);
+    launch_conv1_tc<true>(g, B.gy, P->pbw, nullptr, B.gz2b, nullptr, nullptr, 1.f, P->wait_ns, B.z2, B.gz2);
+    launch_conv_tc<2, true>(g, B.gz2b, P->pbw, nullptr, nullptr, nullptr, nullptr, P->wait_ns, B.z1, B.gz1);
     launch(k_net_wgrad, B.wblocks, 256, g->stream, g->d, (const float*)B.rn, (const __nv_bfloat16*)B.a1,
            (const __nv_bfloat16*)B.a2, (const float*)B.gz1, (const float*)B.gz2, (const float*)B.gy,
            B.part);
@@ -1233,6 +1222,8 @@ of_status of_precond_create(const float* params, int nparams, of_precond** out) 
         OF_CUDA(cudaGetDevice(&P->device));
         OF_CUDA(cudaMalloc(&P->params, sizeof(float) * NPAR * 4));
         OF_CUDA(cudaMalloc(&P->pbf, sizeof(__nv_bfloat16) * NPAR));
+        OF_CUDA(cudaMalloc(&P->pbw, sizeof(__nv_bfloat16) * NPAR));
+        note_resource();
         note_resource();
         note_resource();
         P->grad = P->params + NPAR;
@@ -1247,6 +1238,7 @@ of_status of_precond_create(const float* params, int nparams, of_precond** out) 
     } catch (...) {
         if (P->params) cudaFree(P->params);
         if (P->pbf) cudaFree(P->pbf);
+        if (P->pbw) cudaFree(P->pbw);
         delete P;
         try {
             throw;
@@ -1263,6 +1255,7 @@ of_status of_precond_destroy(of_precond* P) {
     cudaDeviceSynchronize();
     cudaFree(P->params);
     cudaFree(P->pbf);
+    cudaFree(P->pbw);
     delete P;
     return OF_OK;
 }
