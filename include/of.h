@@ -157,6 +157,12 @@ typedef struct {
                                whose gradient is the Hamiltonian's; OF_VW_GRADIENT (lambda/2)
                                int |grad_h u|^2 with the order-2N gradient (Eq.
                                gradient:approximate).  The minimisation is the same. */
+    double nlcg_precond_shift;  /* > 0: the NLCG direction is preconditioned by one multigrid
+                               V-cycle of -L_h + shift (bohr^-2) applied to the gradient, with the
+                               Polak-Ribiere update in its preconditioned form: the real-space
+                               preconditioner for Algorithm NLCG that Sec. 5.5 calls for.  Needs a
+                               grid the multigrid can coarsen (else ignored).  0 (default): the
+                               plain NLCG of App. C */
 } of_scf_opts;
 
 typedef struct {

@@ -29,7 +29,7 @@ from math import pi, sqrt
 import numpy as np
 from scipy.optimize import brent
 
-from .fd import Grid, gradient, laplacian, integrate, poisson_solve
+from .fd import Grid, gradient, laplacian, integrate, poisson_solve, solve_shifted_spectral
 from .functional import tf_energy_density, tf_potential, xc_energy_density, v_xc
 from .kernel import Functional, lr_potential, kf2_of
 from .pseudo import pseudocharge, self_energy, repulsive_correction
@@ -109,14 +109,20 @@ class NlcgInfo:
 
 
 def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
-         max_iter=2000, n_restart=50, s_init=1e-2):
+         max_iter=2000, n_restart=50, s_init=1e-2, precond_shift=0.0):
     """Constrained non-linear CG with Polak-Ribiere update and Brent line search (App. C,
-    Algorithm NLCG).  Returns (u, phi, info) with phi the Poisson solution for u."""
+    Algorithm NLCG).  Returns (u, phi, info) with phi the Poisson solution for u.
+
+    precond_shift > 0: the real-space preconditioner for the NLCG that Sec. 5.5 calls for, in
+    its plainest form: the direction is built from z = (-L_h + precond_shift)^{-1} r (solved
+    exactly here) with the preconditioned Polak-Ribiere coefficient
+    xi = <z, r - r_prev> / <z_prev, r_prev>; the line search and the stopping test are those of
+    the plain method, so the minimum reached is the same."""
     Ne = float(n_electrons)
     u = u0 * sqrt(Ne / inner(u0, u0, grid))
     phi = poisson_solve(u * u + b, grid)
     info = NlcgInfo()
-    r_prev = d_prev = None
+    r_prev = d_prev = z_prev = None
     s_prev = s_init
     for q in range(max_iter + 1):
         Hu = hamiltonian_apply(u, phi, V_LR, grid, fn)
@@ -129,11 +135,13 @@ def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
             break
         if q == max_iter:
             break
+        z = (solve_shifted_spectral(r, grid, 1.0, precond_shift).real if precond_shift > 0.0
+             else r)
         if q == 0 or q % n_restart == 0:
-            d = r
+            d = z
         else:
-            xi = inner(r - r_prev, r, grid) / inner(r_prev, r_prev, grid)
-            d = r if xi <= 0.0 else r + xi * d_prev
+            xi = inner(r - r_prev, z, grid) / inner(r_prev, z_prev, grid)
+            d = z if xi <= 0.0 else z + xi * d_prev
         phi_uu = phi - phi_b
         phi_ud = poisson_solve(u * d, grid)
         phi_dd = poisson_solve(d * d, grid)
@@ -158,7 +166,7 @@ def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
         u = sqrt(Ne / inner(w, w, grid)) * w
         phi = poisson_solve(u * u + b, grid)
         info.steps.append(s)
-        r_prev, d_prev = r, d
+        r_prev, d_prev, z_prev = r, d, z
         s_prev = s if s != 0.0 else s_init
     return u, phi, info
 
@@ -216,7 +224,7 @@ def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c
 
 def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_tol=1e-7,
                      fp_tol=1e-7, max_outer=50, anderson_m=7, zeta=0.3, n_restart=50,
-                     max_nlcg=5000, fixed_point="V", vw_energy="laplacian"):
+                     max_nlcg=5000, fixed_point="V", vw_energy="laplacian", precond_shift=0.0):
     """Fixed point V_LR = V[U(V_LR)] (Eqs. FixedPoint:Map1, MVF) with Anderson mixing
     (App. D); V_LR,0 = 0.  Returns the ground state and its energy.
 
@@ -238,7 +246,7 @@ def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_
     T_LR = 0.0
     for k in range(max_outer):
         u, phi, info = nlcg(u, V, b, phi_b, grid, fn, Ne, tol=nlcg_tol, max_iter=max_nlcg,
-                            n_restart=n_restart)
+                            n_restart=n_restart, precond_shift=precond_shift)
         its.append(info.iterations)
         if fn.mu == 0.0:
             break

@@ -262,6 +262,7 @@ enum Slot {
     WS_OVL,      // reference charges, V_c and its right-hand side (overlap correction on the grid)
     WS_OVLP,     // per-(ion, plane) partial forces of that correction
     WS_MG,       // multigrid hierarchy
+    WS_NLCGP,    // preconditioned NLCG: the gradient in FP32, its V-cycle, the FP64 direction
     WS_NSLOTS
 };
 

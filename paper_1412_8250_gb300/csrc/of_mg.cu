@@ -717,6 +717,10 @@ static bool vcycle(of_grid* g, const T* r, T* z, const double* done, double sigm
     return fs >= 1 && m.deg >= 1;   // the last sweep was level 0's, and carried the fusion
 }
 
+void mg_vcycle_real_shifted(of_grid* g, const float* r, float* z, const double* done, double sigma) {
+    vcycle<float>(g, r, z, done, sigma);
+}
+
 void mg_vcycle(of_grid* g, const float* r, float* z, const double* done) {
     vcycle<float>(g, r, z, done, 0.0);
 }

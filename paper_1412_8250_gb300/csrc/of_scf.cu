@@ -43,7 +43,9 @@ enum {
     SC_EN = 26,        // 4 energy sums
     SC_TLR = 30,
     SC_FP = 32,        // |f|^2, |Vhat|^2
-    SC_GRAM = 40       // Anderson Gram entries
+    SC_GRAM = 40,      // Anderson Gram entries
+    SC_ZR = 104,       // <z, r>, <z, r_prev> of the preconditioned NLCG
+    SC_ZERO = 106      // always 0: the V-cycle's stop flag in the preconditioned NLCG
 };
 
 static inline int vb(long long n) { return red_blocks(n, 256 * 4); }
@@ -157,6 +159,43 @@ __global__ void __launch_bounds__(256) k_direction(long long n, const double* r,
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     GRID_LOOP(i, n) {
         const double v = (xi != 0.0 && dprev) ? r[i] + xi * dprev[i] : r[i];
+        d[i] = v;
+        acc[0] += r[i] * v;
+        acc[1] += u[i] * v;
+        acc[2] += v * v;
+        acc[3] += u[i] * u[i];
+    }
+    grid_reduce<4>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// ---- preconditioned NLCG (nlcg_precond_shift > 0)
+// r32 = r / s with s = RMS of r (from the reduced |r|^2), so that the FP32 V-cycle sees unit scale
+__global__ void __launch_bounds__(256) k_grad_demote(long long n, const double* r, const double* rr,
+                                                     float* r32) {
+    const double inv = rsqrt(fmax(*rr / (double)n, 1e-300));
+    GRID_LOOP(i, n) r32[i] = (float)(r[i] * inv);
+}
+// z = s z32 (the preconditioned gradient); sums <z, r>, <z, r_prev>
+__global__ void __launch_bounds__(256) k_grad_promote(long long n, const float* z32, const double* rr,
+                                                      const double* r, const double* rprev, double* z,
+                                                      RedCtx rc) {
+    const double s = sqrt(fmax(*rr / (double)n, 1e-300));
+    double acc[2] = {0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double v = s * (double)z32[i];
+        z[i] = v;
+        acc[0] += v * r[i];
+        if (rprev) acc[1] += v * rprev[i];
+    }
+    grid_reduce<2>(acc, rc.partials, rc.counter, rc.out);
+}
+// d = z + xi d_prev ; sums <r,d> (the descent test and dE/ds at s = 0), <u,d>, <d,d>, <u,u>
+__global__ void __launch_bounds__(256) k_direction_z(long long n, const double* z, const double* r,
+                                                     const double* dprev, double xi, const double* u,
+                                                     double* d, RedCtx rc) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    GRID_LOOP(i, n) {
+        const double v = (xi != 0.0 && dprev) ? z[i] + xi * dprev[i] : z[i];
         d[i] = v;
         acc[0] += r[i] * v;
         acc[1] += u[i] * v;
@@ -803,9 +842,23 @@ static void poisson_pair(of_grid* g, const double* a1, const double* b1, double*
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
 static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
                  const double* V, double tol, int max_iter, int n_restart, double line_tol,
-                 int line_search, const KrylovOpts& po, ScfStats& st) {
+                 int line_search, const KrylovOpts& po, ScfStats& st, double pshift) {
     const long long n = g->d.n;
     const double dV = g->dV;
+    // preconditioned NLCG: buffers of the gradient in FP32, its V-cycle and the FP64 direction
+    struct {
+        float *r32 = nullptr, *z32 = nullptr;
+        double* z = nullptr;
+    } pc;
+    double zr_prev = 0.0;
+    if (pshift > 0.0 && mg_available(g)) {
+        char* p = (char*)ws(g, WS_NLCGP, (sizeof(float) * 2 + sizeof(double)) * (size_t)n + 256);
+        pc.z = (double*)p;
+        pc.r32 = (float*)(p + sizeof(double) * (size_t)n);
+        pc.z32 = pc.r32 + n;
+    } else {
+        pshift = 0.0;
+    }
     const int nb = vb(n);
     // normalise u and solve for its potential
     launch(k_sum_product, nb, 256, g->stream, n, u, u, red_ctx(g, SC_UU));
@@ -833,16 +886,40 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         if (st.last_residual < tol) { converged = true; break; }
         if (q == max_iter) break;
         double xi = 0.0;
-        if (q > 0 && q % n_restart != 0) {
-            xi = (rr - rrp) / rr_prev;
-            if (!(xi > 0.0)) xi = 0.0;
-        }
-        launch(k_direction, nb, 256, g->stream, n, v.r, v.dp, xi, u, v.d, red_ctx(g, SC_RD));
-        OF_LAUNCH_CHECK();
         double m[4];
-        fetch_scalars(g, SC_RD, 4, m);
-        if (!(m[0] > 0.0) && xi != 0.0) {   // not a descent direction: restart along r
-            xi = 0.0;
+        if (pshift > 0.0) {
+            // preconditioned direction: z = M^{-1} r with M one V-cycle of -L_h + pshift (FP32
+            // on the gradient scaled to unit RMS), Polak-Ribiere in the preconditioned form
+            // xi = <z, r - r_prev> / <z_prev, r_prev>, d = z + xi d_prev
+            launch(k_grad_demote, nb, 256, g->stream, n, (const double*)v.r,
+                   (const double*)(g->s.scalars + SC_RR), pc.r32);
+            mg_vcycle_real_shifted(g, pc.r32, pc.z32, g->s.scalars + SC_ZERO, pshift);
+            launch(k_grad_promote, nb, 256, g->stream, n, (const float*)pc.z32,
+                   (const double*)(g->s.scalars + SC_RR), (const double*)v.r,
+                   q > 0 ? (const double*)v.rp : nullptr, pc.z, red_ctx(g, SC_ZR));
+            OF_LAUNCH_CHECK();
+            double zr[2];
+            fetch_scalars(g, SC_ZR, 2, zr);
+            if (q > 0 && q % n_restart != 0 && zr_prev > 0.0) {
+                xi = (zr[0] - zr[1]) / zr_prev;
+                if (!(xi > 0.0)) xi = 0.0;
+            }
+            zr_prev = zr[0];
+            launch(k_direction_z, nb, 256, g->stream, n, (const double*)pc.z, (const double*)v.r,
+                   (const double*)v.dp, xi, u, v.d, red_ctx(g, SC_RD));
+            OF_LAUNCH_CHECK();
+            fetch_scalars(g, SC_RD, 4, m);
+        } else {
+            if (q > 0 && q % n_restart != 0) {
+                xi = (rr - rrp) / rr_prev;
+                if (!(xi > 0.0)) xi = 0.0;
+            }
+            launch(k_direction, nb, 256, g->stream, n, v.r, v.dp, xi, u, v.d, red_ctx(g, SC_RD));
+            OF_LAUNCH_CHECK();
+            fetch_scalars(g, SC_RD, 4, m);
+        }
+        if (!(m[0] > 0.0) && (xi != 0.0 || pshift > 0.0)) {   // not a descent direction: restart
+            xi = 0.0;                                            // along r
             launch(k_direction, nb, 256, g->stream, n, v.r, v.dp, 0.0, u, v.d, red_ctx(g, SC_RD));
             OF_LAUNCH_CHECK();
             fetch_scalars(g, SC_RD, 4, m);
@@ -1282,7 +1359,7 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         }
         inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, tol_k, o->nlcg_max_iter,
                         std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3,
-                        o->line_search, po, st);
+                        o->line_search, po, st, o->nlcg_precond_shift);
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
         if (fp_u) {

@@ -740,6 +740,8 @@ void destroy_graphs(void* graphs);
 // multigrid preconditioner (of_mg.cu): z = one V-cycle applied to r (FP32 fine-level fields)
 bool mg_available(of_grid* g);
 void mg_vcycle(of_grid* g, const float* r, float* z, const double* done);
+// z = one V-cycle of (-L_h + sigma) applied to r, sigma > 0 (real fields)
+void mg_vcycle_real_shifted(of_grid* g, const float* r, float* z, const double* done, double sigma);
 // the same for complex fields and A = -L + sigma (sigma > 0), real and imaginary parts alike
 void mg_vcycle_shifted(of_grid* g, const float2* r, float2* z, const double* done, double sigma);
 

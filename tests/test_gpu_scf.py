@@ -79,6 +79,27 @@ def test_tfw_config1_against_golden(prec):
     assert abs(np.sum(u * u) * np.prod(np.array(cell.L) / np.array(cell.n)) - cell.n_electrons) < 1e-10
 
 
+@pytest.mark.parametrize("prec", [B.OF_F64, B.OF_F32])
+def test_preconditioned_nlcg_reaches_the_golden_minimum(prec):
+    # the NLCG preconditioned by one V-cycle of -L_h + 8 on the gradient (Sec. 5.5's real-space
+    # preconditioner) ends at the oracle's plain-NLCG minimum, in fewer steps than the plain
+    # NLCG on the GPU
+    rec = _golden()["al4_tfw"]
+    cell = _cell_from(rec)
+    plain, _, _, _ = _run(cell, Fn.tfw(), prec)
+    res, F, u, phi = _run(cell, Fn.tfw(), prec, nlcg_precond_shift=8.0)
+    assert res.converged
+    assert abs(res.energy - rec["energy"]) / cell.n_atoms <= E_TOL
+    assert np.max(np.abs(F - np.array(rec["forces"]))) <= F_TOL
+    assert res.nlcg_iterations < 0.7 * plain.nlcg_iterations, (res.nlcg_iterations, plain.nlcg_iterations)
+    wrec = _golden()["al4_wt"]
+    wcell = _cell_from(wrec)
+    wres, wF, _, _ = _run(wcell, Fn.wt(), prec, anderson_m=3, anderson_zeta=1.0, nlcg_precond_shift=8.0)
+    assert wres.converged
+    assert abs(wres.energy - wrec["energy"]) / wcell.n_atoms <= E_TOL
+    assert np.max(np.abs(wF - np.array(wrec["forces"]))) <= F_TOL
+
+
 @pytest.mark.parametrize("prec,inexact", [(B.OF_F64, 0.0), (B.OF_F32, 0.0), (B.OF_F32, 1e-3)])
 def test_wt_small_cell_against_golden(prec, inexact):
     rec = _golden()["al4_wt"]
@@ -258,6 +279,7 @@ def _bench_like_opts(o):
     o.anderson_zeta = 1.0
     o.nlcg_tol_rel = 1e-1
     o.poisson.inner_tol = 1e-4
+    o.nlcg_precond_shift = 8.0   # the chosen form's NLCG preconditioner (one V-cycle)
     return o
 
 
