@@ -1343,9 +1343,9 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         const double tol_k = (lr && o->nlcg_tol_rel > 0.0)
                                  ? std::max(o->nlcg_tol, o->nlcg_tol_rel * prev_err)
                                  : o->nlcg_tol;
-        // the kernel map's tolerance: 1e-3 of the previous fixed-point error, at most 1e-6
+        // the kernel map's tolerance: 1e-2 of the previous fixed-point error, at most 1e-5
         KrylovOpts kk = ko;
-        kk.tol = std::max(ko.tol, std::min(1e-6, 1e-3 * prev_err));
+        kk.tol = std::max(ko.tol, std::min(1e-5, 1e-2 * prev_err));
         if (fp_u) {
             // u_k normalised to N_e (mixing does not keep the norm), V = V[u_k], u_k kept
             launch(k_sum_product, nb, 256, g->stream, n, u, u, red_ctx(g, SC_UU));

@@ -277,7 +277,7 @@ def _bench_like_opts(o):
     o.fp_tol = 1e-6
     o.anderson_m = 3
     o.anderson_zeta = 1.0
-    o.nlcg_tol_rel = 1e-1
+    o.nlcg_tol_rel = 3e-2
     o.poisson.inner_tol = 1e-4
     o.nlcg_precond_shift = 8.0   # the chosen form's NLCG preconditioner (one V-cycle)
     return o
