@@ -821,10 +821,12 @@ def mixing_study(args):
 
 def config5(args):
     """The 3999-atom cell (10x10x10 FCC minus the centre site, +-0.1 bohr displacements, seed 5),
-    320^3 grid (32.8 M points): one ground state + forces in the mixed form, timed whole; the
-    plain FP64 CG form timed on bounded samples (the first outer iteration stopped after 2 and
-    after 4 NLCG steps, and one FP64 kernel map) and extrapolated with the mixed run's NLCG
-    and outer counts (both forms run the same algorithm).  Prints one JSON line."""
+    320^3 grid (32.8 M points): one ground state + forces in the chosen form (mixed precision,
+    the benchmark's options, preconditioned NLCG), timed whole; the same with the paper's plain
+    NLCG, timed whole; the plain FP64 CG form timed on bounded samples (the first outer
+    iteration stopped after 2 and after 4 NLCG steps, and one FP64 kernel map) and
+    extrapolated with the plain-NLCG mixed run's NLCG and outer counts (both run the same
+    algorithm).  Prints one JSON line."""
     import numpy as np
     import torch
     from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W
@@ -835,14 +837,15 @@ def config5(args):
     sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
     fn = Fn.wt()
 
-    def opts(prec):
+    def opts(prec, pshift=0.0):
         o = B.of_default_scf_opts()
         o.precision = prec
         o.fp_tol = 1e-6
         o.anderson_m = 3
         o.anderson_zeta = 1.0
-        o.nlcg_tol_rel = 1e-1       # the benchmark's inexact schedule (make_case)
+        o.nlcg_tol_rel = 3e-2       # the benchmark's inexact schedule (make_case)
         o.poisson.inner_tol = 1e-4
+        o.nlcg_precond_shift = pshift
         return o
 
     u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
@@ -850,11 +853,19 @@ def config5(args):
     with ClockSampler(0) as clk:
         torch.cuda.synchronize()
         t = time.time()
-        res = B.of_scf_ground_state(h, sysd, fn, opts(B.OF_F32), u, phi)
+        res = B.of_scf_ground_state(h, sysd, fn, opts(B.OF_F32, NLCG_PRECOND_SHIFT), u, phi)
         F = B.of_forces(h, sysd, u, phi)
         torch.cuda.synchronize()
         t_mixed = time.time() - t
         u_gs = u.clone()
+        u.fill_(1.0)
+        phi.zero_()
+        torch.cuda.synchronize()
+        t = time.time()
+        res_p = B.of_scf_ground_state(h, sysd, fn, opts(B.OF_F32), u, phi)
+        B.of_forces(h, sysd, u, phi)
+        torch.cuda.synchronize()
+        t_plain_nlcg = time.time() - t
         samples = {}
         for k in (2, 4):
             o = opts(B.OF_F64)
@@ -876,7 +887,7 @@ def config5(args):
         torch.cuda.synchronize()
         kmap = time.time() - t
     per_step = (samples[4] - samples[2]) / 2.0
-    est = samples[2] + per_step * (res.nlcg_iterations - 2) + kmap * (res.outer_iterations - 1)
+    est = samples[2] + per_step * (res_p.nlcg_iterations - 2) + kmap * (res_p.outer_iterations - 1)
     stencil = stencil_rates(torch, B, cell.shape, cell.L, reps=10)
     line = {"metric": METRIC, "unit": UNIT, "higher_is_better": False, "dtype": "f64+f32",
             "data": "synthetic",
@@ -885,6 +896,11 @@ def config5(args):
                                    "12th-order FD, WT-type kernel (sigma=1.2, r_c=10); ground "
                                    "state + forces"},
             "mixed_multigrid_s": t_mixed,
+            "mixed_multigrid_plain_nlcg_s": t_plain_nlcg,
+            "plain_nlcg_counts": {"outer_iterations": res_p.outer_iterations,
+                                  "nlcg_steps": res_p.nlcg_iterations,
+                                  "energy_difference_ha_per_atom":
+                                      abs(res_p.energy - res.energy) / cell.n_atoms},
             "plain_fp64_cg_s_estimate": est,
             "plain_fp64_sample": {"first_outer_2_nlcg_steps_s": samples[2],
                                   "first_outer_4_nlcg_steps_s": samples[4],
