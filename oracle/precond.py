@@ -9,13 +9,22 @@ t over the 27 offsets (dz, dy, dx) in {-1,0,1}^3 in that nesting order, indices 
 
 Loss for one residual r (normalised to unit RMS): the A-norm error of the correction y = net(r)
 against the exact correction e = A^{-1} r, up to the constant 1/2 e^T A e:
-    loss = 1/2 y^T A y - y^T r,   A = -L_h (Eq. FD:Laplacian),   d loss / d y = A y - r.
+    loss = 1/2 y^T A y - y^T r,   A = -L_h + c (Eq. FD:Laplacian),   d loss / d y = A y - r,
+with c = 0 for the Poisson operator and c > 0 for a network that stands in for the inverse of
+the real positive operator -L_h + c that approximates a shifted kernel system (Sec. 3.1,
+-(1/kf2) L_h W + Q W = P f, scaled by kf2: c = kf2 |Q|).
+
+The shifted systems are complex symmetric; flexible_cocg solves them by a truncated flexible
+COCG whose preconditioner applies the real network to the real and imaginary parts of the
+residual separately.
 
 Pins (tests/test_oracle_precond.py): every gradient against central finite differences of the
-loss; the periodic convolution against an explicit loop over offsets; the loss against the
-A-norm error of the spectral solution; the flexible CG against the spectral solution without a
-preconditioner, in one step with the exact inverse, step for step equal to CG when every
-network step is refused, and faster than CG with a linear SPD preconditioner.
+loss (c = 0 and c > 0); the periodic convolution against an explicit loop over offsets; the loss
+against the A-norm error of the spectral solution (c = 0 and c > 0); the flexible CG against the
+spectral solution without a preconditioner, in one step with the exact inverse, step for step
+equal to CG when every network step is refused, and faster than CG with a linear SPD
+preconditioner; the flexible COCG the same way against the spectral solution of the shifted
+system.
 """
 from __future__ import annotations
 
@@ -85,12 +94,12 @@ def forward(P, r):
     return y, (a0, z1, a1, z2, a2)
 
 
-def loss_and_grads(P, r, grid: Grid):
+def loss_and_grads(P, r, grid: Grid, shift=0.0):
     """A-norm loss of one residual (r is normalised here to unit RMS) and its parameter
-    gradients.  Returns (loss, grads dict)."""
+    gradients, A = -L_h + shift.  Returns (loss, grads dict)."""
     r = r / np.sqrt(np.mean(r * r))
     y, (a0, z1, a1, z2, a2) = forward(P, r)
-    Ay = -laplacian(y, grid)
+    Ay = -laplacian(y, grid) + shift * y
     loss = 0.5 * float(np.sum(y * Ay)) - float(np.sum(y * r))
     gy = (Ay - r)[None]
     dW3, db3, ga2 = conv_backward(a2, P["W3"], gy)
@@ -151,4 +160,55 @@ def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, preco
         p = z.copy()
         for (pj, Apj, pApj) in past:
             p -= (float(np.sum(z * Apj)) / pApj) * pj
+    return x, max_iter, net_steps
+
+
+def flexible_cocg(f, grid: Grid, a, Q, P=None, tol=1e-8, theta=0.3, max_iter=5000, precond=None,
+                  m=4):
+    """Flexible COCG on the complex symmetric system a (-L_h) x + Q x = f (the shifted kernel
+    systems of Sec. 3.1 with a = 1/kf2), truncated after m directions like flexible_cg, with
+    the unconjugated bilinear form u^T v = sum u v in place of the real inner product.
+
+    The preconditioned vector z (the real network applied to the real and imaginary parts,
+    z = apply(P, Re r) + i apply(P, Im r), or `precond(r)` when given) is kept while
+    Re <r, z> > theta |r| |z| (Hermitian product); otherwise the step takes z = r (Jacobi: the
+    diagonal of A is a constant).  Directions p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j, step
+    alpha = p^T r / p^T A p.  Stops at |r| < tol |f| (Hermitian norms).  Returns
+    (x, iterations, network steps)."""
+    def A(v):
+        return -a * (laplacian(v.real, grid) + 1j * laplacian(v.imag, grid)) + Q * v
+
+    def choose(r):
+        if P is None and precond is None:
+            return r.copy(), False
+        z = precond(r) if precond is not None else apply(P, r.real) + 1j * apply(P, r.imag)
+        nz = np.linalg.norm(z)
+        if nz > 0 and np.vdot(r, z).real > theta * np.linalg.norm(r) * nz:
+            return z, True
+        return r.copy(), False
+
+    f = np.asarray(f, dtype=complex)
+    x = np.zeros_like(f)
+    r = f.copy()
+    nb = np.linalg.norm(r)
+    if nb == 0.0:
+        return x, 0, 0
+    z, used = choose(r)
+    net_steps = int(used)
+    p = z
+    past = []   # (p_j, A p_j, p_j^T A p_j), newest last
+    for it in range(1, max_iter + 1):
+        Ap = A(p)
+        pAp = np.sum(p * Ap)
+        alpha = np.sum(p * r) / pAp
+        x += alpha * p
+        r = r - alpha * Ap
+        past = (past + [(p, Ap, pAp)])[-m:]
+        if np.linalg.norm(r) < tol * nb:
+            return x, it, net_steps
+        z, used = choose(r)
+        net_steps += int(used)
+        p = z.copy()
+        for (pj, Apj, pApj) in past:
+            p -= (np.sum(z * Apj) / pApj) * pj
     return x, max_iter, net_steps

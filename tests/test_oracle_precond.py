@@ -23,13 +23,14 @@ def test_conv_matches_explicit_offsets():
         assert abs(y[o, z, yy, x] - s) < 1e-12
 
 
-def test_gradients_match_finite_differences():
+@pytest.mark.parametrize("shift", [0.0, 1.7])
+def test_gradients_match_finite_differences(shift):
     grid = O.Grid((6, 7, 8), (1.5, 1.7, 1.9), 3)
     P = NP.init_params(seed=1, channels=4)
     for k in P:
         P[k] = P[k] + 0.05 * np.random.default_rng(3).normal(size=P[k].shape)
     r = W.random_field(grid.shape, seed=5)
-    loss, G = NP.loss_and_grads(P, r, grid)
+    loss, G = NP.loss_and_grads(P, r, grid, shift)
     rng = np.random.default_rng(9)
     e = 1e-6
     for name in P:
@@ -39,7 +40,7 @@ def test_gradients_match_finite_differences():
             Pm = {k: v.copy() for k, v in P.items()}
             Pp[name][idx] += e
             Pm[name][idx] -= e
-            fd = (NP.loss_and_grads(Pp, r, grid)[0] - NP.loss_and_grads(Pm, r, grid)[0]) / (2 * e)
+            fd = (NP.loss_and_grads(Pp, r, grid, shift)[0] - NP.loss_and_grads(Pm, r, grid, shift)[0]) / (2 * e)
             assert abs(fd - G[name][idx]) < 1e-5 * max(1.0, abs(fd)), (name, idx)
 
 
@@ -112,3 +113,86 @@ def test_flexible_cg_keeps_conjugacy_with_more_directions():
     M = lambda r: O.solve_shifted_spectral(r, grid, 1.0, 2.0)  # noqa: E731
     counts = [NP.flexible_cg(b, grid, tol=1e-10, theta=0.0, precond=M, m=m)[1] for m in (1, 4, 8)]
     assert max(counts) - min(counts) <= 1, counts
+
+
+def test_shifted_loss_is_a_norm_error_up_to_a_constant():
+    # A = -L_h + c is positive definite: 1/2 y^T A y - y^T r + 1/2 e^T A e = 1/2 (y-e)^T A (y-e)
+    grid = O.Grid((8, 8, 8), (2.0, 2.0, 2.0), 6)
+    c = 2.5
+    P = NP.init_params(seed=2, channels=4)
+    r = W.random_field(grid.shape, seed=6)
+    loss, _ = NP.loss_and_grads(P, r, grid, c)
+    rn = r / np.sqrt(np.mean(r * r))
+    e = O.solve_shifted_spectral(rn, grid, 1.0, c)
+    y, _ = NP.forward(P, rn)
+    d = y - e
+    A = lambda v: -O.laplacian(v, grid) + c * v  # noqa: E731
+    lhs = loss + 0.5 * float(np.sum(e * A(e)))
+    rhs = 0.5 * float(np.sum(d * A(d)))
+    assert abs(lhs - rhs) < 1e-9 * max(1.0, abs(rhs))
+
+
+A_SC, Q_SH = 1.0 / 3.5, 0.3 + 0.5j   # a = 1/kf2 of an aluminium-like density, a complex shift
+
+
+def _shifted_case(n=12, seed=21):
+    grid = O.Grid((n, n, n), (0.2375 * n,) * 3, 6)
+    f = W.random_field(grid.shape, seed=seed, kind="smooth") + 0.3 * W.random_field(grid.shape, seed=seed + 1)
+    return grid, f, O.solve_shifted_spectral(f.astype(complex), grid, A_SC, Q_SH)
+
+
+def _textbook_cocg(f, grid, tol):
+    """COCG (CG with the unconjugated bilinear form) written out from its definition."""
+    A = lambda v: -A_SC * (O.laplacian(v.real, grid) + 1j * O.laplacian(v.imag, grid)) + Q_SH * v  # noqa: E731
+    x = np.zeros(f.shape, complex)
+    r = f.astype(complex)
+    p = r.copy()
+    rho = np.sum(r * r)
+    nb = np.linalg.norm(r)
+    for it in range(1, 5000):
+        q = A(p)
+        alpha = rho / np.sum(p * q)
+        x += alpha * p
+        r -= alpha * q
+        if np.linalg.norm(r) < tol * nb:
+            return x, it
+        rho_new = np.sum(r * r)
+        p = r + (rho_new / rho) * p
+        rho = rho_new
+    raise AssertionError("COCG did not converge")
+
+
+def test_flexible_cocg_without_preconditioner_is_cocg():
+    grid, f, x_exact = _shifted_case()
+    x, its, used = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10)
+    x_ref, its_ref = _textbook_cocg(f, grid, 1e-10)
+    assert used == 0 and abs(its - its_ref) <= 1 and 5 < its < 500
+    assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
+    assert np.linalg.norm(x_ref - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
+
+
+def test_flexible_cocg_with_exact_inverse_takes_one_step():
+    grid, f, x_exact = _shifted_case()
+    inv = lambda r: O.solve_shifted_spectral(r, grid, A_SC, Q_SH)  # noqa: E731
+    x, its, used = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10, precond=inv)
+    assert its == 1 and used == 1
+    assert np.linalg.norm(x - x_exact) <= 1e-10 * np.linalg.norm(x_exact)
+
+
+def test_flexible_cocg_falls_back_on_an_ascent_direction():
+    grid, f, _ = _shifted_case()
+    _, its_plain, _ = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10)
+    _, its, used = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10, precond=lambda r: -r)
+    assert used == 0 and its == its_plain
+
+
+def test_flexible_cocg_with_the_real_positive_preconditioner_beats_cocg():
+    # the real operator -L_h + kf2 |Q| inverted on real and imaginary parts: the preconditioner
+    # the network is trained to stand in for (and the one the multigrid V-cycle approximates)
+    grid, f, x_exact = _shifted_case()
+    c = abs(Q_SH) / A_SC
+    M = lambda r: O.solve_shifted_spectral(r, grid, 1.0, c)  # noqa: E731
+    _, its_plain, _ = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10)
+    x, its, used = NP.flexible_cocg(f, grid, A_SC, Q_SH, tol=1e-10, theta=0.0, precond=M)
+    assert used == its and its < its_plain / 2
+    assert np.linalg.norm(x - x_exact) <= 1e-8 * np.linalg.norm(x_exact)
