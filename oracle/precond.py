@@ -14,17 +14,18 @@ with c = 0 for the Poisson operator and c > 0 for a network that stands in for t
 the real positive operator -L_h + c that approximates a shifted kernel system (Sec. 3.1,
 -(1/kf2) L_h W + Q W = P f, scaled by kf2: c = kf2 |Q|).
 
-The shifted systems are complex symmetric; flexible_cocg solves them by a truncated flexible
-COCG whose preconditioner applies the real network to the real and imaginary parts of the
-residual separately.
+The shifted systems are complex symmetric; flexible_gmres solves them by flexible GMRES(m)
+whose preconditioner applies the real network to the real and imaginary parts of the residual
+separately.
 
 Pins (tests/test_oracle_precond.py): every gradient against central finite differences of the
 loss (c = 0 and c > 0); the periodic convolution against an explicit loop over offsets; the loss
 against the A-norm error of the spectral solution (c = 0 and c > 0); the flexible CG against the
 spectral solution without a preconditioner, in one step with the exact inverse, step for step
 equal to CG when every network step is refused, and faster than CG with a linear SPD
-preconditioner; the flexible COCG the same way against the spectral solution of the shifted
-system.
+preconditioner; the flexible GMRES against the minimal residual over the Krylov space (a dense
+least-squares solve on a tiny grid), in one step with the exact inverse, step for step equal to
+GMRES when every network step is refused, and faster with the real positive preconditioner.
 """
 from __future__ import annotations
 
@@ -163,52 +164,66 @@ def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, preco
     return x, max_iter, net_steps
 
 
-def flexible_cocg(f, grid: Grid, a, Q, P=None, tol=1e-8, theta=0.3, max_iter=5000, precond=None,
-                  m=4):
-    """Flexible COCG on the complex symmetric system a (-L_h) x + Q x = f (the shifted kernel
-    systems of Sec. 3.1 with a = 1/kf2), truncated after m directions like flexible_cg, with
-    the unconjugated bilinear form u^T v = sum u v in place of the real inner product.
+def flexible_gmres(f, grid: Grid, a, Q, P=None, tol=1e-8, theta=0.3, m=8, max_iter=5000,
+                   precond=None):
+    """Flexible GMRES(m) with right preconditioning (Saad's FGMRES) on the shifted system
+    a (-L_h) x + Q x = f (the kernel systems of Sec. 3.1 with a = 1/kf2), complex.
 
-    The preconditioned vector z (the real network applied to the real and imaginary parts,
-    z = apply(P, Re r) + i apply(P, Im r), or `precond(r)` when given) is kept while
-    Re <r, z> > theta |r| |z| (Hermitian product); otherwise the step takes z = r (Jacobi: the
-    diagonal of A is a constant).  Directions p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j, step
-    alpha = p^T r / p^T A p.  Stops at |r| < tol |f| (Hermitian norms).  Returns
-    (x, iterations, network steps)."""
+    The system is complex symmetric, not Hermitian, and the network is neither linear nor
+    complex-homogeneous (it acts on the real and imaginary parts separately), so no short
+    recurrence stays valid; FGMRES keeps every preconditioned vector z_j of a cycle and takes
+    the iterate that minimises the residual over their span, whatever they are.  Per step j:
+    z_j = apply(P, Re v_j) + i apply(P, Im v_j) (or `precond(v_j)` when given), kept when
+    Re <v_j, z_j> > theta |z_j| (v_j has unit norm), else z_j = v_j (Jacobi: the diagonal of A is
+    a constant); w = A z_j orthogonalised against v_0..v_j by modified Gram-Schmidt (Hermitian
+    products) gives column j of the Hessenberg matrix H and v_{j+1}; the least-squares residual
+    min_y |beta e_1 - H y| is the residual of x_0 + Z y.  After m steps, or once that residual
+    is below tol |f|, x takes the minimiser and the cycle restarts from the true residual.
+    Returns (x, iterations, network steps)."""
     def A(v):
         return -a * (laplacian(v.real, grid) + 1j * laplacian(v.imag, grid)) + Q * v
 
-    def choose(r):
+    def choose(v):
         if P is None and precond is None:
-            return r.copy(), False
-        z = precond(r) if precond is not None else apply(P, r.real) + 1j * apply(P, r.imag)
+            return v.copy(), False
+        z = precond(v) if precond is not None else apply(P, v.real) + 1j * apply(P, v.imag)
         nz = np.linalg.norm(z)
-        if nz > 0 and np.vdot(r, z).real > theta * np.linalg.norm(r) * nz:
+        if nz > 0 and np.vdot(v, z).real > theta * nz:
             return z, True
-        return r.copy(), False
+        return v.copy(), False
 
     f = np.asarray(f, dtype=complex)
     x = np.zeros_like(f)
-    r = f.copy()
-    nb = np.linalg.norm(r)
+    nb = np.linalg.norm(f)
     if nb == 0.0:
         return x, 0, 0
-    z, used = choose(r)
-    net_steps = int(used)
-    p = z
-    past = []   # (p_j, A p_j, p_j^T A p_j), newest last
-    for it in range(1, max_iter + 1):
-        Ap = A(p)
-        pAp = np.sum(p * Ap)
-        alpha = np.sum(p * r) / pAp
-        x += alpha * p
-        r = r - alpha * Ap
-        past = (past + [(p, Ap, pAp)])[-m:]
+    r = f.copy()
+    it = net_steps = 0
+    while it < max_iter:
+        beta = np.linalg.norm(r)
+        V = [r / beta]
+        Z = []
+        H = np.zeros((m + 1, m), dtype=complex)
+        for j in range(m):
+            z, used = choose(V[j])
+            net_steps += int(used)
+            Z.append(z)
+            w = A(z)
+            for i in range(j + 1):
+                H[i, j] = np.vdot(V[i], w)
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            it += 1
+            k = j + 1
+            e1 = np.zeros(k + 1, dtype=complex)
+            e1[0] = beta
+            y = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)[0]
+            est = np.linalg.norm(e1 - H[:k + 1, :k] @ y)
+            if est < tol * nb or H[j + 1, j] == 0.0 or it >= max_iter:
+                break
+            V.append(w / H[j + 1, j])
+        x = x + sum(yi * zi for yi, zi in zip(y, Z))
+        r = f - A(x)
         if np.linalg.norm(r) < tol * nb:
-            return x, it, net_steps
-        z, used = choose(r)
-        net_steps += int(used)
-        p = z.copy()
-        for (pj, Apj, pApj) in past:
-            p -= (np.sum(z * Apj) / pApj) * pj
-    return x, max_iter, net_steps
+            break
+    return x, it, net_steps
