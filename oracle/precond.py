@@ -15,17 +15,18 @@ the real positive operator -L_h + c that approximates a shifted kernel system (S
 -(1/kf2) L_h W + Q W = P f, scaled by kf2: c = kf2 |Q|).
 
 The shifted systems are complex symmetric; flexible_gmres solves them by flexible GMRES(m)
-whose preconditioner applies the real network to the real and imaginary parts of the residual
-separately.
+preconditioned by a few steps of flexible CG with the network on -L_h + c, applied to the real
+and imaginary parts of each Arnoldi vector separately.
 
 Pins (tests/test_oracle_precond.py): every gradient against central finite differences of the
 loss (c = 0 and c > 0); the periodic convolution against an explicit loop over offsets; the loss
 against the A-norm error of the spectral solution (c = 0 and c > 0); the flexible CG against the
 spectral solution without a preconditioner, in one step with the exact inverse, step for step
 equal to CG when every network step is refused, and faster than CG with a linear SPD
-preconditioner; the flexible GMRES against the minimal residual over the Krylov space (a dense
-least-squares solve on a tiny grid), in one step with the exact inverse, step for step equal to
-GMRES when every network step is refused, and faster with the real positive preconditioner.
+preconditioner, and the shifted flexible CG against the spectral solution of -L_h + c; the
+flexible GMRES against the minimal residual over the Krylov space (a dense least-squares solve
+on a tiny grid), in one step with the exact inverse, and faster with the real positive
+preconditioner, exact or by inner CG.
 """
 from __future__ import annotations
 
@@ -119,27 +120,31 @@ def apply(P, r):
     return s * forward(P, r / s)[0]
 
 
-def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, precond=None, m=4):
-    """Flexible CG on A x = b, A = -L_h on mean-free fields (truncated FCG(m) after Notay).
+def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, precond=None, m=4,
+                shift=0.0):
+    """Flexible CG on A x = b, A = -L_h + shift (truncated FCG(m) after Notay); for shift = 0
+    (the Poisson operator) on mean-free fields.
 
-    The preconditioned vector z (the network z = s net(r / s), or `precond(r)` when given, mean
-    removed) is kept only while it is a clear descent direction, cos(r, z) > theta; otherwise
-    that iteration takes the plain direction z = r (Jacobi: the diagonal of A is a constant, so
-    its inverse is a multiple of the identity, which the step length absorbs).  The direction
-    is z made A-conjugate to the last m directions, p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j,
-    and the step is alpha = r^T p / p^T A p.  Returns (x, iterations, network steps)."""
+    The preconditioned vector z (the network z = s net(r / s), or `precond(r)` when given, its
+    mean removed when shift = 0) is kept only while it is a clear descent direction,
+    cos(r, z) > theta; otherwise that iteration takes the plain direction z = r (Jacobi: the
+    diagonal of A is a constant, so its inverse is a multiple of the identity, which the step
+    length absorbs).  The direction is z made A-conjugate to the last m directions,
+    p = z - sum_j (z^T A p_j / p_j^T A p_j) p_j, and the step is alpha = r^T p / p^T A p.
+    Returns (x, iterations, network steps)."""
     def choose(r):
         if P is None and precond is None:
             return r.copy(), False
         z = precond(r) if precond is not None else apply(P, r)
-        z = z - z.mean()
+        if shift == 0.0:
+            z = z - z.mean()
         nz = np.linalg.norm(z)
         if nz > 0 and float(np.sum(r * z)) > theta * np.linalg.norm(r) * nz:
             return z, True
         return r.copy(), False
 
     x = np.zeros_like(b)
-    r = b - b.mean()
+    r = b - b.mean() if shift == 0.0 else b.copy()
     nb = np.linalg.norm(r)
     if nb == 0.0:
         return x, 0, 0
@@ -148,7 +153,7 @@ def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, preco
     p = z
     past = []   # (p_j, A p_j, p_j^T A p_j), newest last
     for it in range(1, max_iter + 1):
-        Ap = -laplacian(p, grid)
+        Ap = -laplacian(p, grid) + shift * p
         pAp = float(np.sum(p * Ap))
         alpha = float(np.sum(r * p)) / pAp
         x += alpha * p
@@ -164,49 +169,56 @@ def flexible_cg(b, grid: Grid, P=None, tol=1e-8, theta=0.5, max_iter=5000, preco
     return x, max_iter, net_steps
 
 
-def flexible_gmres(f, grid: Grid, a, Q, P=None, tol=1e-8, theta=0.3, m=8, max_iter=5000,
-                   precond=None):
+def flexible_gmres(f, grid: Grid, a, Q, P=None, tol=1e-8, m=8, max_iter=5000, precond=None,
+                   inner=False, inner_tol=0.1, inner_max=40, theta=0.3):
     """Flexible GMRES(m) with right preconditioning (Saad's FGMRES) on the shifted system
     a (-L_h) x + Q x = f (the kernel systems of Sec. 3.1 with a = 1/kf2), complex.
 
-    The system is complex symmetric, not Hermitian, and the network is neither linear nor
-    complex-homogeneous (it acts on the real and imaginary parts separately), so no short
-    recurrence stays valid; FGMRES keeps every preconditioned vector z_j of a cycle and takes
-    the iterate that minimises the residual over their span, whatever they are.  Per step j:
-    z_j = apply(P, Re v_j) + i apply(P, Im v_j) (or `precond(v_j)` when given), kept when
-    Re <v_j, z_j> > theta |z_j| (v_j has unit norm), else z_j = v_j (Jacobi: the diagonal of A is
-    a constant); w = A z_j orthogonalised against v_0..v_j by modified Gram-Schmidt (Hermitian
-    products) gives column j of the Hessenberg matrix H and v_{j+1}; the least-squares residual
-    min_y |beta e_1 - H y| is the residual of x_0 + Z y.  After m steps, or once that residual
-    is below tol |f|, x takes the minimiser and the cycle restarts from the true residual.
-    Returns (x, iterations, network steps)."""
+    Preconditioner z_j = M(v_j): `precond(v_j)` when given; with inner=True, flexible CG with
+    the network P (plain CG when P is None) on the real positive operator -L_h + c, c = |Q| / a,
+    applied to the real and imaginary parts of v_j separately and stopped at relative residual
+    inner_tol (or after inner_max steps); otherwise z_j = v_j (GMRES).  The system is complex
+    symmetric, not Hermitian, and M is neither linear nor complex-homogeneous, so no short
+    recurrence stays valid: FGMRES keeps every z_j of a cycle and takes the iterate that
+    minimises the residual over their span.  w = A z_j orthogonalised against v_0..v_j by
+    modified Gram-Schmidt (Hermitian products) gives column j of the Hessenberg matrix H and
+    v_{j+1}; min_y |beta e_1 - H y| is the residual of x_0 + Z y.  After m steps, or once that
+    residual is below tol |f|, x takes the minimiser and the cycle restarts from the true
+    residual.  Returns (x, outer iterations, inner iterations, network steps)."""
     def A(v):
         return -a * (laplacian(v.real, grid) + 1j * laplacian(v.imag, grid)) + Q * v
 
-    def choose(v):
-        if P is None and precond is None:
-            return v.copy(), False
-        z = precond(v) if precond is not None else apply(P, v.real) + 1j * apply(P, v.imag)
-        nz = np.linalg.norm(z)
-        if nz > 0 and np.vdot(v, z).real > theta * nz:
-            return z, True
-        return v.copy(), False
+    c = abs(Q) / a
+    counts = [0, 0]   # inner iterations, network steps
+
+    def M(v):
+        if precond is not None:
+            return precond(v)
+        if not inner:
+            return v.copy()
+        parts = []
+        for part in (v.real, v.imag):
+            zp, its, used = flexible_cg(part, grid, P=P, tol=inner_tol, theta=theta,
+                                        max_iter=inner_max, shift=c)
+            counts[0] += its
+            counts[1] += used
+            parts.append(zp)
+        return parts[0] + 1j * parts[1]
 
     f = np.asarray(f, dtype=complex)
     x = np.zeros_like(f)
     nb = np.linalg.norm(f)
     if nb == 0.0:
-        return x, 0, 0
+        return x, 0, 0, 0
     r = f.copy()
-    it = net_steps = 0
+    it = 0
     while it < max_iter:
         beta = np.linalg.norm(r)
         V = [r / beta]
         Z = []
         H = np.zeros((m + 1, m), dtype=complex)
         for j in range(m):
-            z, used = choose(V[j])
-            net_steps += int(used)
+            z = M(V[j])
             Z.append(z)
             w = A(z)
             for i in range(j + 1):
@@ -226,4 +238,4 @@ def flexible_gmres(f, grid: Grid, a, Q, P=None, tol=1e-8, theta=0.3, m=8, max_it
         r = f - A(x)
         if np.linalg.norm(r) < tol * nb:
             break
-    return x, it, net_steps
+    return x, it, counts[0], counts[1]
