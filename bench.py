@@ -52,6 +52,9 @@ GOLDEN_AL108 = os.path.join(ROOT, "tests", "golden", "al108_wt.json")
 # DRAM bytes (read + write) of one FP32 order-12 sweep of a 320^3 grid by the fast-path stencil,
 # from the ncu capture summarised in profiles/stencil_fp32_320.md (145.9 + 91.9 MB)
 STENCIL320_DRAM_BYTES = 237.8e6
+# algorithmic FP64 arithmetic of one order-12 Laplacian point: 3 axes x 12 neighbours + the
+# centre, one multiply-add (2 flops) each
+STENCIL_F64_FLOPS_PER_POINT = 2 * (3 * 12 + 1)
 GOLDEN_SMALL = os.path.join(ROOT, "tests", "golden", "ground_states.json")
 
 
@@ -235,6 +238,14 @@ def run_step(B, h, sysd, fn, o, u, phi, u0):
     return res, F
 
 
+def alu_peaks(B, torch):
+    """Measured FMA rates of the CUDA cores (TFLOP/s): FP64, FP32 and packed FP32x2."""
+    s = torch.cuda.current_stream()
+    return {"fp64_tflops": B.of_alu_peak(B.OF_PEAK_F64, s) / 1e12,
+            "fp32_tflops": B.of_alu_peak(B.OF_PEAK_F32, s) / 1e12,
+            "fp32x2_tflops": B.of_alu_peak(B.OF_PEAK_F32X2, s) / 1e12}
+
+
 def stencil_rates(torch, B, shape, L, reps=30):
     """Device time of one of_laplacian_apply sweep (FP32 and FP64) on this grid: `reps` sweeps
     captured in one CUDA graph on a grid handle of their own, replayed between CUDA events
@@ -408,6 +419,7 @@ def learned_compare(torch, B, W, steps=400, theta=0.3):
         out[name] = {"s": time.time() - t, "iterations": info.iterations,
                      "refinements": info.refinements, "network_steps": info.net_steps,
                      "rel_residual": info.rel_residual}
+    out["shifted"] = learned_shifted_compare(torch, B, W, g, cell, steps, theta)
     r = torch.randn(cell.shape, dtype=torch.float32, device="cuda")
     z = torch.empty_like(r)
     B.of_precond_apply(g, net, r, z)
@@ -418,6 +430,88 @@ def learned_compare(torch, B, W, steps=400, theta=0.3):
     torch.cuda.synchronize()
     out["network_apply_ms"] = (time.time() - t) / 10 * 1e3
     B.of_grid_destroy(g)
+    B.of_precond_destroy(net)
+    return out
+
+
+def _kernel_rhs(torch, B, W, g, cell, kf2, seed):
+    """A kernel-map right-hand side f = -(1/kf2) L_h q (the m = n = 0 form of Sec. 3.1) of a
+    smooth positive seeded field q standing in for u^{2 alpha}, formed on the device."""
+    q = torch.from_numpy(1.0 + 0.5 * W.random_field(cell.shape, seed=seed, kind="smooth")).cuda()
+    f = torch.empty_like(q)
+    B.of_laplacian_apply(g, B.OF_F64, q, f)
+    return f * (-1.0 / kf2)
+
+
+def learned_shifted_compare(torch, B, W, g864, cell864, steps, theta):
+    """The learned preconditioner for a shifted kernel system: a network trained for the real
+    operator -L_h + c, c = kf2 |Q| of the WT kernel's second shift (Q = 0.066 - 0.260i), on
+    every CG residual of that real system on the 108-atom 96^3 cell (four right-hand sides,
+    2 x steps Adam steps), then used in the inner flexible CG on that operator that preconditions
+    the FP32 flexible GMRES(8) of the same shifted system on the 864-atom 192^3 grid (a
+    right-hand side not trained on) to true relative residual 1e-10; against the same solver
+    with every network step refused (plain inner CG), plain FP32 COCG, plain FP64 COCG and
+    multigrid-preconditioned FP32 COCG.  Iterations count the inner steps too."""
+    import numpy as np
+    from paper_1412_8250_gb300 import functionals as Fn
+    fn = Fn.wt()
+    Pk, Qk = complex(fn.P[4], fn.P[5]), complex(fn.Q[4], fn.Q[5])
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    cell = W.al108_cell()
+    kf2 = Fn.kf2(cell.n_electrons, float(np.prod(cell.L)))
+    c = kf2 * abs(Qk)
+    net = B.of_precond_create(W.initial_network(4))
+    B.of_precond_set_shift(net, c)
+    g = B.of_grid_create(cell.n, cell.L, 6, stream)
+    sets = []
+    for seed in (41, 43, 45, 49):
+        s = torch.empty((48,) + cell.shape, dtype=torch.float32, device="cuda")
+        cnt = B.of_precond_collect(g, _kernel_rhs(torch, B, W, g, cell, kf2, seed), 1, 48, s, shift=c)
+        sets += [s[k] for k in range(cnt)]
+    S = torch.stack(sets).contiguous()
+    cnt = S.shape[0]
+    rng = np.random.default_rng(4)
+    for rnd in range(4):
+        st = 2 * steps // 4
+        B.of_precond_train(g, net, S, cnt, rng.integers(0, cnt, size=st * 4), st, 4,
+                           3e-3 if rnd < 3 else 1e-3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    B.of_grid_destroy(g)
+    del sets
+    kf2_864 = Fn.kf2(cell864.n_electrons, float(np.prod(cell864.L)))
+    f = _kernel_rhs(torch, B, W, g864, cell864, kf2_864, 47)
+    Wc = torch.zeros(cell864.shape + (2,), dtype=torch.float64, device="cuda")
+
+    def opts(prec, no_mg, use_net, th=theta):
+        o = B.of_default_solve_opts()
+        o.tol, o.precision, o.no_multigrid, o.inner_tol = 1e-10, prec, no_mg, 1e-4
+        if use_net:
+            o.precond, o.precond_theta = net, th
+        return o
+
+    out = {"workload": "al864 shifted kernel system -(1/kf2) L_h W + Q W = P f, Q = 0.066 - 0.260i "
+                       "(the WT kernel's second shift), 192^3, tol 1e-10",
+           "network_shift_c": c, "training_s": train_s, "training_steps": 2 * steps,
+           "training_data": "%d CG residuals of -L_h + c on the 108-atom 96^3 cell, four "
+                            "right-hand sides" % cnt}
+    for name, o in (("plain_cocg_mixed", opts(B.OF_F32, 1, False)),
+                    ("learned_fgmres_mixed", opts(B.OF_F32, 1, True)),
+                    ("fgmres_plain_inner_cg_mixed", opts(B.OF_F32, 1, True, 2.0)),
+                    ("plain_cocg_f64", opts(B.OF_F64, 1, False)),
+                    ("multigrid_pcocg_mixed", opts(B.OF_F32, 0, False))):
+        Wc.zero_()
+        B.of_kernel_solve(g864, f, [Pk], [Qk], kf2_864, Wc, o)     # workspace, graphs
+        Wc.zero_()
+        torch.cuda.synchronize()
+        t = time.time()
+        info = B.of_kernel_solve(g864, f, [Pk], [Qk], kf2_864, Wc, o)
+        torch.cuda.synchronize()
+        out[name] = {"s": time.time() - t, "iterations": info.iterations,
+                     "refinements": info.refinements, "network_steps": info.net_steps,
+                     "rel_residual": info.rel_residual}
     B.of_precond_destroy(net)
     return out
 
@@ -1221,13 +1315,24 @@ def main():
             roofline["frac_cg_bytes_only"] = cg_bytes / (dom["mean_ms"] * 1e-3) / 1e9 / peak
             roofline["note"] = ("latency-bound: at 96^3 every field stays in L2 and one "
                                 "preconditioned iteration is a chain of ~17 dependent launches")
-    roofline_320 = None
+    roofline_320 = roofline_320_f64 = alu = None
     if stencil320:
         roofline_320 = {"kernel": "stencil2_kernel (of_laplacian_apply, FP32, order 12, 320^3)",
                         "bound": "hbm", "achieved": stencil320["f32"]["gbs"], "peak": peak,
                         "unit": "GB/s", "frac": stencil320["f32"]["gbs"] / peak,
                         "traffic": STENCIL320_DRAM_BYTES, "bytes_per_launch": 8.0 * 320 ** 3,
                         "peak_kind": peak_kind}
+        # the FP64 sweep (the refinement residuals) is bound by FP64 arithmetic, not by HBM:
+        # its roofline is the measured DFMA rate of this GPU
+        alu = alu_peaks(B, torch)
+        achieved = stencil320["f64"]["gpts"] * 1e9 * STENCIL_F64_FLOPS_PER_POINT
+        roofline_320_f64 = {"kernel": "stencil_kernel<double> (of_laplacian_apply, FP64, order "
+                                      "12, 320^3)",
+                            "bound": "alu", "achieved": achieved / 1e12,
+                            "peak": alu["fp64_tflops"], "unit": "TFLOP/s",
+                            "frac": achieved / 1e12 / alu["fp64_tflops"], "traffic": None,
+                            "flops_per_point": STENCIL_F64_FLOPS_PER_POINT,
+                            "peak_kind": "measured (of_alu_peak: DFMA chains on every SM, this run)"}
 
     clocks = clk.summary()
     cpu = None
@@ -1248,6 +1353,7 @@ def main():
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
                 "roofline": roofline, "roofline_stencil_320": roofline_320,
+                "roofline_stencil_320_f64": roofline_320_f64, "alu_peaks": alu,
                 "cpu_baseline": cpu, "clocks": clocks,
                 "stencil_96": stencil, "stencil_320": stencil320,
                 "result": {"energy_ha": res.energy, "energy_per_atom_ha": res.energy / cell.n_atoms,

@@ -78,8 +78,10 @@ typedef struct {
     double inner_tol;
     int check_every;
     int no_multigrid;      /* 1: plain FP32 CG inner solve for Poisson (no V-cycle) */
-    of_precond* precond;   /* non-NULL with OF_F32: the FP32 Poisson inner solve is flexible
-                              CG preconditioned by this network (kernel solves ignore it) */
+    of_precond* precond;   /* non-NULL with OF_F32: the FP32 inner solve is flexible CG
+                              (Poisson) or flexible COCG (shifted kernel systems, the network
+                              applied to the real and imaginary parts of the residual)
+                              preconditioned by this network, in place of the V-cycle */
     double precond_theta;  /* a network direction z is kept when cos(r, z) > theta, else the
                               step is plain CG; default 0.3 */
 } of_solve_opts;
@@ -366,15 +368,19 @@ of_status of_forces(of_grid* g, const of_system* sys, const double* u, const dou
  * t over (dz, dy, dx) in {-1,0,1}^3 with dz outermost and dx innermost.  Parameters are one
  * float array of of_precond_num_params() = 7809 values: W1[16][27], b1[16], W2[16][16][27],
  * b2[16], W3[16][27], b3.  Kernels keep weights and activations in BF16 and sum in FP32.
- * Applied to a residual r as z = s net(r / s), s = RMS of r.  Trained on residuals r (of the
- * grid's Poisson operator A = -L_h) with the loss 1/2 y^T A y - y^T r, y = net(r / s), which
- * equals half the A-norm error of y against A^{-1} r up to a constant.  The handle lives on the
+ * Applied to a residual r as z = s net(r / s), s = RMS of r.  Trained on residuals r with the
+ * loss 1/2 y^T A y - y^T r, y = net(r / s), which equals half the A-norm error of y against
+ * A^{-1} r up to a constant, for A = -L_h + c: c = 0 (the default) for the Poisson operator, or
+ * c = kf2 |Q| > 0 for a network meant for the shifted kernel system of shift Q (Sec. 3.1; the
+ * real positive operator its multigrid preconditioner also inverts).  The handle lives on the
  * current device; every call that takes a grid requires the grid on that device and enqueues
  * on the grid's stream. */
 int of_precond_num_params(void);
 /* Copies params (host, 7809 floats) to a new handle.  OF_EINVAL on a wrong count. */
 of_status of_precond_create(const float* params, int nparams, of_precond** out);
 of_status of_precond_destroy(of_precond* P);
+/* The operator shift c >= 0 of the training loss (above).  OF_EINVAL for c < 0 or not finite. */
+of_status of_precond_set_shift(of_precond* P, double shift);
 /* Failure detection: the tensor-core kernels give up waiting for an MMA completion after
  * `seconds` (default 2; 0 <= seconds <= 60), then let the MMAs in flight finish (waiting up to
  * the default limit), free their tensor memory and return; the call that launched them returns
@@ -394,13 +400,13 @@ of_status of_precond_loss_grad(of_grid* g, of_precond* P, const float* r, double
  * per point.  Synchronises. */
 of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int nsamples,
                            const int* order, int steps, int batch, float lr, double* loss_out);
-/* Training data from the solver itself: runs FP32 CG on the grid's Poisson system for the
- * device density rho (right-hand side 4 pi (rho - mean rho), scaled to unit RMS) and copies
- * every stride-th residual, the first one included, to samples[k * n] (device, room for
- * max_samples fields); stops at relative residual 1e-6 or once max_samples are taken;
- * *count = residuals written.  Synchronises. */
-of_status of_precond_collect(of_grid* g, const double* rho, int stride, int max_samples,
-                             float* samples, int* count);
+/* Training data from the solver itself: runs FP32 CG on (-L_h + shift) x = b, b = the device
+ * field rho scaled to unit RMS -- for shift = 0 the grid's Poisson system, b = 4 pi (rho -
+ * mean rho) -- and copies every stride-th residual, the first one included, to samples[k * n]
+ * (device, room for max_samples fields); stops at relative residual 1e-6 or once max_samples
+ * are taken; *count = residuals written.  OF_EINVAL for shift < 0.  Synchronises. */
+of_status of_precond_collect(of_grid* g, const double* rho, double shift, int stride,
+                             int max_samples, float* samples, int* count);
 
 /* Message of the last failure on this host thread ("" if none). */
 const char* of_last_error(void);
@@ -428,6 +434,16 @@ typedef struct {
 
 unsigned long long of_launch_count(void);
 unsigned long long of_resource_count(void);
+
+/* of_alu_peak: the measured arithmetic rate of this GPU's CUDA cores, the roofline denominator
+ * of kernels bound by arithmetic rather than memory (the FP64 Laplacian sweeps).  kind:
+ * OF_PEAK_F64 (DFMA), OF_PEAK_F32 (FFMA) or OF_PEAK_F32X2 (packed FP32x2 FMA, two lanes per
+ * instruction).  Launches a kernel of 8 independent FMA chains per thread on 8 blocks of 256
+ * threads per SM on the given stream (cudaStream_t or NULL) six times (one warm-up, a few ms
+ * each) and returns the best rate in *flop_per_s (2 flops per FMA lane).  Creates and
+ * destroys two events; synchronises the stream.  OF_EINVAL for an unknown kind. */
+enum { OF_PEAK_F64 = 0, OF_PEAK_F32 = 1, OF_PEAK_F32X2 = 2 };
+of_status of_alu_peak(int kind, void* stream, double* flop_per_s);
 const char* of_kernel_class_name(int kernel_class);
 of_status of_profile_enable(of_grid* g, int sample_every);
 int of_profile_read(of_grid* g, of_kernel_stat* out, int max);

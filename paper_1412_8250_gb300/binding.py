@@ -135,9 +135,11 @@ _SIGNATURES = {
     "of_precond_apply": (_I, [_P, _P, _P, _P]),
     "of_precond_loss_grad": (_I, [_P, _P, _P, C.POINTER(_D), C.POINTER(C.c_float)]),
     "of_precond_train": (_I, [_P, _P, _P, _I, C.POINTER(_I), _I, _I, C.c_float, C.POINTER(_D)]),
-    "of_precond_collect": (_I, [_P, _P, _I, _I, _P, C.POINTER(_I)]),
+    "of_precond_collect": (_I, [_P, _P, _D, _I, _I, _P, C.POINTER(_I)]),
+    "of_precond_set_shift": (_I, [_P, _D]),
     "of_launch_count": (C.c_ulonglong, []),
     "of_resource_count": (C.c_ulonglong, []),
+    "of_alu_peak": (_I, [_I, _P, C.POINTER(_D)]),
     "of_kernel_class_name": (C.c_char_p, [_I]),
     "of_profile_enable": (_I, [_P, _I]),
     "of_profile_read": (_I, [_P, C.POINTER(of_kernel_stat), _I]),
@@ -393,6 +395,16 @@ def of_resource_count():
     return int(load().of_resource_count())
 
 
+OF_PEAK_F64, OF_PEAK_F32, OF_PEAK_F32X2 = 0, 1, 2
+
+
+def of_alu_peak(kind, stream=None):
+    """Measured FMA rate of the CUDA cores in FLOP/s (kind: OF_PEAK_F64 / F32 / F32X2)."""
+    out = _D(0.0)
+    _check(load().of_alu_peak(int(kind), _stream_ptr(stream), C.byref(out)), "of_alu_peak")
+    return out.value
+
+
 def of_kernel_class_name(cls):
     return load().of_kernel_class_name(int(cls)).decode()
 
@@ -464,6 +476,10 @@ def of_precond_set_wait_limit(P, seconds):
     return _check(load().of_precond_set_wait_limit(P, float(seconds)), "of_precond_set_wait_limit")
 
 
+def of_precond_set_shift(P, shift):
+    return _check(load().of_precond_set_shift(P, float(shift)), "of_precond_set_shift")
+
+
 def of_precond_apply(h, P, r, z):
     return _check(load().of_precond_apply(h, P, _ptr(r), _ptr(z)), "of_precond_apply")
 
@@ -488,8 +504,8 @@ def of_precond_train(h, P, samples, nsamples, order, steps, batch, lr):
     return loss.value
 
 
-def of_precond_collect(h, rho, stride, max_samples, samples):
+def of_precond_collect(h, rho, stride, max_samples, samples, shift=0.0):
     count = _I()
-    _check(load().of_precond_collect(h, _ptr(rho), int(stride), int(max_samples), _ptr(samples),
-                                     C.byref(count)), "of_precond_collect")
+    _check(load().of_precond_collect(h, _ptr(rho), float(shift), int(stride), int(max_samples),
+                                     _ptr(samples), C.byref(count)), "of_precond_collect")
     return count.value

@@ -161,16 +161,16 @@ of_status of_grid_create(int n1, int n2, int n3, double L1, double L2, double L3
         g->pool.resize(WS_NSLOTS);
         OF_CUDA(cudaMalloc(&g->s.partials, sizeof(double) * OF_RED_SLOTS * OF_MAX_RED_BLOCKS));
         OF_CUDA(cudaMalloc(&g->s.counter, sizeof(unsigned int) * 4));
-        OF_CUDA(cudaMalloc(&g->s.scalars, sizeof(double) * 256));
+        OF_CUDA(cudaMalloc(&g->s.scalars, sizeof(double) * OF_NSCALARS));
         for (int k = 0; k < 3; ++k) note_resource();
         // zeroed on the handle's stream and finished before the handle is returned: a plain
         // cudaMemset runs on the legacy default stream, which the non-blocking streams the
         // handle later runs on (stream pool, twin handle) do not wait for, and a reduction
         // that starts before its counter is zeroed miscounts its blocks
         OF_CUDA(cudaMemsetAsync(g->s.counter, 0, sizeof(unsigned int) * 4, g->stream));
-        OF_CUDA(cudaMemsetAsync(g->s.scalars, 0, sizeof(double) * 256, g->stream));
+        OF_CUDA(cudaMemsetAsync(g->s.scalars, 0, sizeof(double) * OF_NSCALARS, g->stream));
         OF_CUDA(cudaStreamSynchronize(g->stream));
-        OF_CUDA(cudaMallocHost(&g->s.host, sizeof(double) * 256));
+        OF_CUDA(cudaMallocHost(&g->s.host, sizeof(double) * OF_NSCALARS));
         note_resource();
         *out = g;
         return OF_OK;

@@ -14,6 +14,7 @@
 #define OF_MAX_N 6
 #define OF_RED_SLOTS 48          // scalars produced by one reduction kernel (max)
 #define OF_MAX_RED_BLOCKS 4096   // partial sums per slot
+#define OF_NSCALARS 384          // device solver scalars per grid handle
 
 namespace of {
 
@@ -162,7 +163,7 @@ struct Weights {
 struct Scratch {
     double* partials = nullptr;       // [OF_RED_SLOTS * OF_MAX_RED_BLOCKS]
     unsigned int* counter = nullptr;  // block-arrival counter (one per reduction kernel)
-    double* scalars = nullptr;        // general device scalars [256]
+    double* scalars = nullptr;        // general device scalars [OF_NSCALARS]
     double* host = nullptr;           // pinned host mirror [256]
 };
 
@@ -263,6 +264,7 @@ enum Slot {
     WS_OVLP,     // per-(ion, plane) partial forces of that correction
     WS_MG,       // multigrid hierarchy
     WS_NLCGP,    // preconditioned NLCG: the gradient in FP32, its V-cycle, the FP64 direction
+    WS_FGM,      // flexible GMRES: Arnoldi and preconditioned vectors
     WS_NSLOTS
 };
 

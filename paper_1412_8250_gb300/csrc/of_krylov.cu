@@ -530,7 +530,10 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 // -0.512 - 0.027i took 6,000-8,700 preconditioned iterations per solve), so such
                 // shifts take plain COCG
                 const bool near_resonant = Q.x < 0.0 && std::fabs(Q.y) < 0.2 * std::fabs(Q.x);
-                pcg = qabs > 0.0 && !near_resonant && !o.no_multigrid && mg_available(g);
+                // with a learned network: flexible GMRES, the network applied to the real and
+                // imaginary parts of the Arnoldi vectors
+                fcg = o.precond != nullptr && qabs > 0.0;
+                pcg = !fcg && qabs > 0.0 && !near_resonant && !o.no_multigrid && mg_available(g);
             } else {
                 const bool poisson_op = a == 1.0 && Q.x == 0.0 && Q.y == 0.0;
                 fcg = poisson_op && o.precond != nullptr;
@@ -555,8 +558,12 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             KState hi;
             PendingLoop pending;   // a loop graph whose state is read with the outer residual
             if constexpr (std::is_same<T32, float2>::value) {
-                // shifted systems: COCG preconditioned by the V-cycle of -L + |Q| / a
-                if (pcg)
+                // shifted systems: COCG preconditioned by the V-cycle of -L + |Q| / a, or
+                // flexible GMRES with the network
+                if (fcg)
+                    hi = iterate_fgmres(g, o.precond, o.theta, KS32, e32, r32, (float*)ar.z32,
+                                        (float*)ar.pb32, (float)a, Q, &net_steps);
+                else if (pcg)
                     hi = iterate_pcocg(g, KS32, e32, r32, (float2*)ar.pa32, (float2*)ar.pb32,
                                        (float2*)ar.Ap32, (float2*)ar.z32, (float)a, Q, qabs / a,
                                        o.check_every, &pending);
@@ -564,7 +571,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             if constexpr (std::is_same<T32, float>::value) {
                 if (fcg)
                     hi = iterate_fcg(g, o.precond, o.theta, KS32, e32, r32, (float*)ar.pa32,
-                                     (float*)ar.z32, o.check_every, nullptr, &net_steps);
+                                     (float*)ar.z32, o.check_every, nullptr, &net_steps, 0.0);
                 else if (pcg)
                     hi = iterate_pcg(g, KS32, e32, r32, (float*)ar.pa32, (float*)ar.pb32,
                                      (float*)ar.Ap32, (float*)ar.z32, o.check_every, &pending);
@@ -591,7 +598,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
                 status = OF_EBREAKDOWN;
                 set_error("Krylov solve (FP32 inner, %s): breakdown at the start of refinement pass "
                           "%d: inner |r|^2 %.3e, r^T M r %.3e, p^T A p %.3e, outer |r|^2 %.3e, tol2 %.3e",
-                          fcg ? "flexible CG" : pcg ? "multigrid-preconditioned CG/COCG" : "CG/COCG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
+                          fcg ? "flexible CG/GMRES" : pcg ? "multigrid-preconditioned CG/COCG" : "CG/COCG", refinements, hi.rr, hi.rho_re, hi.pAp_re,
                           h.rr, h.tol2);
                 break;
             }
@@ -713,6 +720,7 @@ of_status of_kernel_solve(of_grid* g, const double* f, int nshift, const double*
             if (info) {
                 info->iterations += one.iterations;
                 info->refinements += one.refinements;
+                info->net_steps += one.net_steps;
                 info->rel_residual = std::max(info->rel_residual, one.rel_residual);
             }
             if (st != OF_OK && worst == OF_OK) worst = st;

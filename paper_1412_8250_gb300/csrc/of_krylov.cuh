@@ -30,6 +30,8 @@ struct KState {
 constexpr int KSTATE_DOUBLES = sizeof(KState) / sizeof(double);
 constexpr int KS64 = 128;   // offsets in g->s.scalars
 constexpr int KS32 = 160;
+constexpr int KS_NEST = 256;   // inner solves of the flexible-GMRES preconditioner
+static_assert(KS_NEST + KSTATE_DOUBLES <= OF_NSCALARS, "grid scalars");
 
 inline KState* kstate(of_grid* g, int off) { return (KState*)(g->s.scalars + off); }
 
@@ -386,10 +388,19 @@ inline Arena arena(of_grid* g) {
 }
 
 
-// Flexible CG with the learned preconditioner (of_precond.cu); P == nullptr: plain CG.
+// Flexible CG with the learned preconditioner (of_precond.cu) on -L_h + shift; P == nullptr:
+// plain CG.
 struct Sink;
 KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x, float* r,
-                   float* ra, float* z, int check_every, Sink* sink, double* net_steps);
+                   float* ra, float* z, int check_every, Sink* sink, double* net_steps,
+                   double shift);
+// Flexible GMRES(8) on the shifted system a (-L_h) x + Q x = b, preconditioned by flexible CG
+// with the learned network on the real positive operator -L_h + |Q| / a, applied to the real
+// and imaginary parts (x = 0 on entry; the KState at st_off holds |b|^2, tol2 and maxit and is
+// read, not written).  x, b: n complex; z, rs: 2n floats of scratch.  Returns the outer plus
+// inner iterations and the final |b - A x|^2 in rr.
+KState iterate_fgmres(of_grid* g, of_precond* P, double theta, int st_off, float2* x, const float2* b,
+                      float* z, float* rs, float a, double2 Q, double* net_steps);
 
 // CUDA graphs of the preconditioned CG: "init" (V-cycle + first r^T z) and "pair" (two full
 // iterations, ping and pong of the direction buffers).  Every kernel reads its scalars and the

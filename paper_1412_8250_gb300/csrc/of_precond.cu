@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -36,6 +37,8 @@ struct of_precond {
     unsigned long long wait_ns = 2000000000ull;
     // BF16 weights of the backward pass in the forward layout (k_backward_weights)
     __nv_bfloat16* pbw = nullptr;
+    // the network stands in for the inverse of -L_h + shift (0: the Poisson operator)
+    double shift = 0.0;
 };
 
 namespace of {
@@ -48,6 +51,7 @@ constexpr int OW3 = OB2 + NC, OB3 = OW3 + NC * NT;        // W3[c][t], b3
 constexpr int NPAR = OB3 + 1;                // 7809
 constexpr int SC_NET = 110;                  // scalars: 110 sum r^2, 111 RMS, 112/113 loss sums
 constexpr int FS_OFF = 200;                  // FCG state (FState) in the grid's scalars
+constexpr int FDOTS_OFF = 180;               // sums of the flexible CG / COCG direction choice
 
 // Flexible-CG scalars, next to the inner KState.  Directions are kept A-conjugate to the last
 // FCG_M ones (truncated FCG, Notay), held in a ring of FCG_M (p, A p) pairs.
@@ -798,6 +802,7 @@ struct OpFcgA {
     FState* fs;
     int slot;
     RedCtx rc;
+    float shift;   // A = -L_h + shift
     float acc[2];
     __device__ bool begin() {
         if (st->done != 0.0) return false;
@@ -807,8 +812,9 @@ struct OpFcgA {
     __device__ float load(long long i) const { return p[i]; }
     __device__ float2 load2(long long i) const { return *reinterpret_cast<const float2*>(p + i); }
     __device__ void store(long long i, float c, float lap) {
-        Ap[i] = -lap;
-        acc[0] = fmaf(c, -lap, acc[0]);
+        const float q = fmaf(shift, c, -lap);
+        Ap[i] = q;
+        acc[0] = fmaf(c, q, acc[0]);
         acc[1] = fmaf(r[i], c, acc[1]);
     }
     __device__ void end() {
@@ -851,12 +857,16 @@ __global__ void __launch_bounds__(256) k_fcg_update(long long n, float* __restri
 
 // Sums for the choice of the next direction: sum z, sum r, r.z, z.z and, per filled ring slot
 // j < valid, z.Ap_j and r.Ap_j.  The last block keeps the network direction d = z - mean(z)
-// when cos(r, d) > theta, else d = r, and sets c_j = d.Ap_j / p_j.Ap_j (sum Ap_j = 0 for the
+// (project: the Poisson operator, whose null space is the constants; else d = z) when
+// cos(r, d) > theta, else d = r, and sets c_j = d.Ap_j / p_j.Ap_j (sum Ap_j = 0 for the
 // Laplacian, so the mean shift drops out of d.Ap_j).
 constexpr int DOTS_K = 4 + 2 * FCG_M;
+static_assert(KS32 + KSTATE_DOUBLES <= FDOTS_OFF && FDOTS_OFF + DOTS_K <= FS_OFF,
+              "scalar slots of the flexible-CG sums");
 __global__ void __launch_bounds__(256) k_fcg_dots(long long n, const float* __restrict__ r,
-                                                  const float* __restrict__ z, int has_net, double theta,
-                                                  Ring ring, int valid, KState* st, FState* fs, RedCtx rc) {
+                                                  const float* __restrict__ z, int has_net, int project,
+                                                  double theta, Ring ring, int valid, KState* st,
+                                                  FState* fs, RedCtx rc) {
     if (st->done != 0.0) return;
     float s[DOTS_K];
 #pragma unroll
@@ -885,7 +895,7 @@ __global__ void __launch_bounds__(256) k_fcg_dots(long long n, const float* __re
         bool use = false;
         double mean = 0.0;
         if (has_net) {
-            mean = acc[0] / (double)n;
+            mean = project ? acc[0] / (double)n : 0.0;
             const double zz = acc[3] - (double)n * mean * mean;
             const double rzn = acc[2] - mean * acc[1];
             const double c = (zz > 0.0 && rr > 0.0) ? rzn / sqrt(zz * rr) : -1.0;
@@ -930,6 +940,196 @@ __global__ void k_fcg_reset(FState* fs) {
     fs->plain_steps = 0.0;
     fs->cos_last = 0.0;
     for (int j = 0; j < FCG_M; ++j) fs->pAp[j] = fs->c[j] = 0.0;
+}
+
+// ---------------------------------------------------------------- flexible GMRES
+// The shifted kernel systems a (-L_h) x + Q x = b are complex symmetric, not Hermitian.  The
+// network is trained for the real positive operator A_r = -L_h + c, c = |Q| / a, whose inverse
+// applied to the real and imaginary parts separately is a good preconditioner of them (the
+// multigrid path uses a V-cycle of the same operator).  Applied directly, the network is not
+// accurate enough (flexible COCG and flexible GMRES with z = net(v) stagnated): it is used
+// where flexible CG is robust, in a few flexible-CG steps on A_r z = v (to GM_TAU), and those
+// inner solves precondition flexible GMRES(GM_M), which keeps every preconditioned vector of a
+// cycle and takes the iterate of least residual over their span: Arnoldi with classical
+// Gram-Schmidt applied twice (each pass one grid reduction of all projections), the small
+// Hessenberg least-squares problem by Givens rotations on the host.
+constexpr int GM_M = 8;                        // restart length
+constexpr double GM_TAU = 0.1;                 // relative residual of the inner solves
+constexpr int GM_INNER_MAX = 40;               // iterations of one inner solve, at most
+constexpr int GH1 = FS_OFF + (int)(sizeof(FState) / sizeof(double));   // projections, first pass
+constexpr int GH2 = GH1 + 2 * GM_M;            // second pass
+constexpr int GNRM = GH2 + 2 * GM_M;           // |w|^2 after orthogonalisation, or |r|^2
+static_assert(GNRM + 1 <= KS_NEST, "grid scalars");
+
+struct VecSet {
+    float2* v[GM_M + 1];
+};
+struct GmCoef {
+    double2 y[GM_M];
+};
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// out[2k], out[2k+1] = sum_i conj(v_k[i]) w[i] for k < nv, 0 beyond
+__global__ void __launch_bounds__(256) k_gm_dots(long long n, const float2* __restrict__ w, VecSet V,
+                                                 int nv, RedCtx rc) {
+    float s[2 * GM_M];
+#pragma unroll
+    for (int k = 0; k < 2 * GM_M; ++k) s[k] = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 wv = w[i];
+#pragma unroll
+        for (int k = 0; k < GM_M; ++k)
+            if (k < nv) {
+                const float2 v = V.v[k][i];
+                s[2 * k] = fmaf(v.x, wv.x, fmaf(v.y, wv.y, s[2 * k]));
+                s[2 * k + 1] = fmaf(v.x, wv.y, fmaf(-v.y, wv.x, s[2 * k + 1]));
+            }
+    }
+    double acc[2 * GM_M];
+#pragma unroll
+    for (int k = 0; k < 2 * GM_M; ++k) acc[k] = (double)s[k];
+    grid_reduce<2 * GM_M>(acc, rc.partials, rc.counter, rc.out);
+}
+
+// w -= sum_{k < nv} h_k v_k, h_k = (h[2k], h[2k+1]); with norm != 0, |w|^2 into rc.out[0]
+__global__ void __launch_bounds__(256) k_gm_orth(long long n, float2* __restrict__ w, VecSet V, int nv,
+                                                 const double* __restrict__ h, int norm, RedCtx rc) {
+    float2 c[GM_M];
+#pragma unroll
+    for (int k = 0; k < GM_M; ++k)
+        c[k] = k < nv ? make_float2((float)h[2 * k], (float)h[2 * k + 1]) : make_float2(0.f, 0.f);
+    float part = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 x = w[i];
+#pragma unroll
+        for (int k = 0; k < GM_M; ++k)
+            if (k < nv) {
+                const float2 t = cmulf(c[k], V.v[k][i]);
+                x.x -= t.x;
+                x.y -= t.y;
+            }
+        w[i] = x;
+        part = fmaf(x.x, x.x, fmaf(x.y, x.y, part));
+    }
+    if (norm) {
+        double acc[1] = {(double)part};
+        grid_reduce<1>(acc, rc.partials, rc.counter, rc.out);
+    }
+}
+
+// out = s w
+__global__ void __launch_bounds__(256) k_gm_scale(long long n, const float2* __restrict__ w,
+                                                  float2* __restrict__ out, float s) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = w[i];
+        out[i] = make_float2(s * v.x, s * v.y);
+    }
+}
+
+// real and imaginary parts of v as two planes
+__global__ void __launch_bounds__(256) k_split2(long long n, const float2* __restrict__ v, float* __restrict__ rs) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 x = v[i];
+        rs[i] = x.x;
+        rs[n + i] = x.y;
+    }
+}
+
+// Start of an inner solve of A_r x = r: x = 0, |r|^2 and the stopping state (relative tau)
+__global__ void __launch_bounds__(256) k_nest_init(long long n, const float* __restrict__ r,
+                                                   float* __restrict__ x, double tau, int maxit,
+                                                   KState* st, RedCtx rc) {
+    float p = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = r[i];
+        x[i] = 0.f;
+        p = fmaf(v, v, p);
+    }
+    double acc[1] = {(double)p};
+    if (grid_reduce<1>(acc, rc.partials, rc.counter, st->red) && threadIdx.x == 0) {
+        st->rr = acc[0];
+        st->tol2 = tau * tau * acc[0];
+        st->done = acc[0] > 0.0 ? 0.0 : 1.0;
+        st->iters = 0.0;
+        st->maxit = maxit;
+        st->breakdown = 0.0;
+        st->zshift = 0.0;
+    }
+}
+
+// out = z[0..n) + i z[n..2n)
+__global__ void __launch_bounds__(256) k_merge2(long long n, const float* __restrict__ z, float2* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_float2(z[i], z[n + i]);
+}
+
+// w = A z, A = a(-L_h) + Q
+struct OpGmA {
+    static constexpr int kClass = PC_COCG_F32, kWords = 2;
+    const float2* z;
+    float2* w;
+    float a;
+    double2 Q;
+    __device__ bool begin() { return true; }
+    __device__ float2 load(long long i) const { return z[i]; }
+    __device__ void store(long long i, float2 c, float2 lap) { w[i] = apply_A(c, lap, a, Q); }
+    __device__ void end() {}
+};
+
+// r = b - A x and |r|^2 into rc.out[0]
+struct OpGmResid {
+    static constexpr int kClass = PC_COCG_F32, kWords = 3;
+    const float2* x;
+    const float2* b;
+    float2* r;
+    float a;
+    double2 Q;
+    RedCtx rc;
+    float acc;
+    __device__ bool begin() {
+        acc = 0.f;
+        return true;
+    }
+    __device__ float2 load(long long i) const { return x[i]; }
+    __device__ void store(long long i, float2 c, float2 lap) {
+        const float2 q = apply_A(c, lap, a, Q), bv = b[i];
+        const float2 v = make_float2(bv.x - q.x, bv.y - q.y);
+        r[i] = v;
+        acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+    }
+    __device__ void end() {
+        double v[1] = {(double)acc};
+        grid_reduce<1>(v, rc.partials, rc.counter, rc.out);
+    }
+};
+
+// x += sum_{k < m} y_k Z_k
+__global__ void __launch_bounds__(256) k_gm_xupdate(long long n, float2* __restrict__ x, VecSet Z, int m,
+                                                    GmCoef y) {
+    float2 c[GM_M];
+#pragma unroll
+    for (int k = 0; k < GM_M; ++k) c[k] = make_float2((float)y.y[k].x, (float)y.y[k].y);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 v = x[i];
+#pragma unroll
+        for (int k = 0; k < GM_M; ++k)
+            if (k < m) {
+                const float2 t = cmulf(c[k], Z.v[k][i]);
+                v.x += t.x;
+                v.y += t.y;
+            }
+        x[i] = v;
+    }
 }
 
 // FP64 right-hand side -> FP32 at unit RMS (sample collection); fresh inner state
@@ -1009,12 +1209,14 @@ static NetBufs net_bufs(of_grid* g, bool training) {
 }
 
 // y = A x for FP32 fields, A = -L
+// y = -L_h x + shift x
 struct OpNegLap32 {
     const float* x;
     float* y;
+    float shift;
     __device__ bool begin() { return true; }
     __device__ float load(long long i) const { return x[i]; }
-    __device__ void store(long long i, float, float lap) { y[i] = -lap; }
+    __device__ void store(long long i, float c, float lap) { y[i] = fmaf(shift, c, -lap); }
     __device__ void end() {}
 };
 
@@ -1103,7 +1305,7 @@ static void net_loss_grad(of_grid* g, of_precond* P, const float* r, const NetBu
                           float sgn = 1.f) {
     const long long n = g->d.n;
     net_forward(g, P, r, B.y, B, true, sgn);
-    launch_stencil<float, 2>(g, g->w32, OpNegLap32{B.y, B.Ay});
+    launch_stencil<float, 2>(g, g->w32, OpNegLap32{B.y, B.Ay, (float)P->shift});
     launch(k_net_loss, vec_blocks(n), 256, g->stream, n, (const float*)B.y, (const float*)B.Ay,
            (const float*)B.rn, B.gy, red_ctx(g, SC_NET + 2));
     // data gradients on the tensor cores (BF16 operands, FP32 accumulation): gz2 from gy with
@@ -1128,13 +1330,14 @@ struct Sink {
     int stride, max_samples, count;
 };
 
-// Flexible CG on the FP32 inner system A x = r (x = 0 on entry; the KState at st_off holds
-// rr, tol2, maxit, done).  P == nullptr: every step is plain (Jacobi) CG.  Buffers r
-// (overwritten), ra and z of n floats; the direction ring lives in the grid's workspace.  With
-// a sink, every stride-th residual (the initial one first) is copied to sink->buf[k * n], up
-// to max_samples.
+// Flexible CG on the FP32 inner system A x = r, A = -L_h + shift (x = 0 on entry; the KState
+// at st_off holds rr, tol2, maxit, done).  P == nullptr: every step is plain (Jacobi) CG.
+// Buffers r (overwritten), ra and z of n floats; the direction ring lives in the grid's
+// workspace.  With a sink, every stride-th residual (the initial one first) is copied to
+// sink->buf[k * n], up to max_samples.
 KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x, float* r,
-                   float* ra, float* z, int check_every, Sink* sink, double* net_steps) {
+                   float* ra, float* z, int check_every, Sink* sink, double* net_steps,
+                   double shift) {
     const long long n = g->d.n;
     KState* st = kstate(g, st_off);
     FState* fs = fstate(g);
@@ -1161,8 +1364,9 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
     if (net) net_reset_error(g);
     if (sink && sink->count < sink->max_samples) take_sample(r);
     if (net) net_forward(g, P, r, z, B, false);
-    launch(k_fcg_dots, nb, 256, g->stream, n, (const float*)r, (const float*)z, (int)net, theta, ring, 0,
-           st, fs, red_ctx(g, 0));
+    const int project = shift == 0.0;
+    launch(k_fcg_dots, nb, 256, g->stream, n, (const float*)r, (const float*)z, (int)net, project, theta,
+           ring, 0, st, fs, red_ctx(g, FDOTS_OFF));
     launch(k_fcg_direction, nb, 256, g->stream, n, (const float*)r, (const float*)z, ring, 0, ring.p[0],
            (const KState*)st, (const FState*)fs);
     float* rc = r;
@@ -1172,7 +1376,7 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
     for (int it = 1;; ++it) {
         const int slot = (it - 1) % FCG_M;
         launch_stencil<float, 2>(g, g->w32, OpFcgA{ring.p[slot], rc, ring.Ap[slot], st, fs, slot,
-                                                   red_ctx(g, 0)});
+                                                   red_ctx(g, 0), (float)shift});
         {
             ProfScope ps(g, PC_UPDATE, 5.0 * 4.0 * (double)n);
             launch(k_fcg_update, nb, 256, g->stream, n, x, (const float*)rc, rn, (const float*)ring.p[slot],
@@ -1184,8 +1388,8 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
         }
         const int valid = std::min(it, FCG_M);
         if (net) net_forward(g, P, rn, z, B, false);
-        launch(k_fcg_dots, nb, 256, g->stream, n, (const float*)rn, (const float*)z, (int)net, theta, ring,
-               valid, st, fs, red_ctx(g, 0));
+        launch(k_fcg_dots, nb, 256, g->stream, n, (const float*)rn, (const float*)z, (int)net, project,
+               theta, ring, valid, st, fs, red_ctx(g, FDOTS_OFF));
         launch(k_fcg_direction, nb, 256, g->stream, n, (const float*)rn, (const float*)z, ring, valid,
                ring.p[it % FCG_M], (const KState*)st, (const FState*)fs);
         std::swap(rc, rn);
@@ -1200,6 +1404,133 @@ KState iterate_fcg(of_grid* g, of_precond* P, double theta, int st_off, float* x
         fetch_scalars(g, FS_OFF, sizeof(FState) / sizeof(double), (double*)&f);
         *net_steps += f.net_steps;
     }
+    return h;
+}
+
+KState iterate_fgmres(of_grid* g, of_precond* P, double theta, int st_off, float2* x, const float2* b,
+                      float* z, float* rs, float a, double2 Q, double* net_steps) {
+    using cplx = std::complex<double>;
+    const long long n = g->d.n;
+    KState h;
+    fetch_scalars(g, st_off, KSTATE_DOUBLES, (double*)&h);   // |b|^2, tol2, maxit (x = 0)
+    h.iters = 0.0;
+    h.breakdown = 0.0;
+    if (!(h.rr > h.tol2)) {
+        h.done = 1.0;
+        return h;
+    }
+    if (P) require_device(g, P);
+    const size_t vec = al256((size_t)n * sizeof(float2));
+    char* base = (char*)ws(g, WS_FGM, (2 * GM_M + 3) * vec);
+    VecSet V, Zs;
+    for (int k = 0; k <= GM_M; ++k) V.v[k] = (float2*)(base + k * vec);
+    for (int k = 0; k < GM_M; ++k) Zs.v[k] = (float2*)(base + (GM_M + 1 + k) * vec);
+    Zs.v[GM_M] = nullptr;
+    float2* W = (float2*)(base + (2 * GM_M + 1) * vec);
+    float* scr = (float*)(base + (2 * GM_M + 2) * vec);   // two fields of n floats
+    const int nb = vec_blocks(n);
+    const int maxit = (int)h.maxit;
+    double* sc = g->s.scalars;
+    const double c = std::sqrt((double)Q.x * Q.x + (double)Q.y * Q.y) / a;   // A_r = -L_h + c
+    double beta = std::sqrt(h.rr), rr = h.rr;
+    launch(k_gm_scale, nb, 256, g->stream, n, b, V.v[0], (float)(1.0 / beta));
+    int it = 0, inner = 0;
+    for (;;) {   // one restart cycle
+        cplx H[GM_M + 1][GM_M] = {};
+        cplx cs[GM_M], sn[GM_M], gv[GM_M + 1] = {};
+        gv[0] = beta;
+        VecSet Zc{};
+        int k = 0;
+        for (int j = 0; j < GM_M; ++j) {
+            // z_j: flexible CG with the network on A_r z = v_j, real and imaginary parts
+            launch(k_split2, nb, 256, g->stream, n, (const float2*)V.v[j], rs);
+            for (int part = 0; part < 2; ++part) {
+                float* rp = rs + part * n;
+                float* zp = z + part * n;
+                launch(k_nest_init, nb, 256, g->stream, n, (const float*)rp, zp, GM_TAU, GM_INNER_MAX,
+                       kstate(g, KS_NEST), red_ctx(g, 0));
+                const KState hn = iterate_fcg(g, P, theta, KS_NEST, zp, rp, scr, scr + n, 4, nullptr,
+                                              net_steps, c);
+                inner += (int)hn.iters;
+            }
+            launch(k_merge2, nb, 256, g->stream, n, (const float*)z, Zs.v[j]);
+            float2* zj = Zs.v[j];
+            Zc.v[j] = zj;
+            launch_stencil<float2, 1>(g, g->w32, OpGmA{zj, W, a, Q});
+            {
+                ProfScope ps(g, PC_UPDATE, 4.0 * 8.0 * (j + 2) * (double)n);
+                launch(k_gm_dots, nb, 256, g->stream, n, (const float2*)W, V, j + 1, red_ctx(g, GH1));
+                launch(k_gm_orth, nb, 256, g->stream, n, W, V, j + 1, (const double*)(sc + GH1), 0, red_ctx(g, GNRM));
+                launch(k_gm_dots, nb, 256, g->stream, n, (const float2*)W, V, j + 1, red_ctx(g, GH2));
+                launch(k_gm_orth, nb, 256, g->stream, n, W, V, j + 1, (const double*)(sc + GH2), 1, red_ctx(g, GNRM));
+            }
+            double hv[4 * GM_M + 1];
+            fetch_scalars(g, GH1, 4 * GM_M + 1, hv);
+            for (int i = 0; i <= j; ++i)
+                H[i][j] = cplx(hv[2 * i] + hv[2 * GM_M + 2 * i], hv[2 * i + 1] + hv[2 * GM_M + 2 * i + 1]);
+            const double hn = std::sqrt(std::max(hv[4 * GM_M], 0.0));
+            H[j + 1][j] = hn;
+            // the earlier rotations on the new column, then one that zeroes H[j+1][j]
+            for (int i = 0; i < j; ++i) {
+                const cplx t = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+                H[i + 1][j] = -std::conj(sn[i]) * H[i][j] + cs[i] * H[i + 1][j];
+                H[i][j] = t;
+            }
+            const double aa = std::abs(H[j][j]);
+            if (hn == 0.0) {
+                cs[j] = 1.0;
+                sn[j] = 0.0;
+            } else if (aa == 0.0) {
+                cs[j] = 0.0;
+                sn[j] = 1.0;
+            } else {
+                const double t = std::hypot(aa, hn);
+                cs[j] = aa / t;
+                sn[j] = (H[j][j] / aa) * hn / t;
+            }
+            H[j][j] = cs[j] * H[j][j] + sn[j] * H[j + 1][j];
+            H[j + 1][j] = 0.0;
+            gv[j + 1] = -std::conj(sn[j]) * gv[j];
+            gv[j] = cs[j] * gv[j];
+            ++it;
+            k = j + 1;
+            const double est2 = std::norm(gv[j + 1]);
+            if (!std::isfinite(est2) || !std::isfinite(hn)) {
+                h.breakdown = 1.0;
+                break;
+            }
+            if (est2 <= h.tol2 || hn == 0.0 || it >= maxit) break;
+            launch(k_gm_scale, nb, 256, g->stream, n, (const float2*)W, V.v[j + 1], (float)(1.0 / hn));
+        }
+        // x += Z y, y from the triangular system R y = g
+        GmCoef y{};
+        cplx yc[GM_M];
+        for (int i = k - 1; i >= 0; --i) {
+            cplx s = gv[i];
+            for (int l = i + 1; l < k; ++l) s -= H[i][l] * yc[l];
+            if (std::abs(H[i][i]) == 0.0) {
+                h.breakdown = 1.0;
+                yc[i] = 0.0;
+            } else {
+                yc[i] = s / H[i][i];
+            }
+            if (!std::isfinite(std::abs(yc[i]))) {
+                h.breakdown = 1.0;
+                yc[i] = 0.0;
+            }
+        }
+        for (int i = 0; i < k; ++i) y.y[i] = make_double2(yc[i].real(), yc[i].imag());
+        launch(k_gm_xupdate, nb, 256, g->stream, n, x, Zc, k, y);
+        // the true residual of the inner system restarts the next cycle
+        launch_stencil<float2, 1>(g, g->w32, OpGmResid{(const float2*)x, b, W, a, Q, red_ctx(g, GNRM), 0.f});
+        fetch_scalars(g, GNRM, 1, &rr);
+        if (!(rr > h.tol2) || it >= maxit || h.breakdown != 0.0 || !std::isfinite(rr)) break;
+        beta = std::sqrt(rr);
+        launch(k_gm_scale, nb, 256, g->stream, n, (const float2*)W, V.v[0], (float)(1.0 / beta));
+    }
+    h.iters = it + inner;
+    h.rr = rr;
+    h.done = 1.0;
     return h;
 }
 
@@ -1248,6 +1579,15 @@ of_status of_precond_create(const float* params, int nparams, of_precond** out) 
             return unexpected_exception();
         }
     }
+}
+
+of_status of_precond_set_shift(of_precond* P, double shift) {
+    if (!P || !(shift >= 0.0) || !std::isfinite(shift)) {
+        set_error("of_precond_set_shift: need a handle and a finite shift >= 0");
+        return OF_EINVAL;
+    }
+    P->shift = shift;
+    return OF_OK;
 }
 
 of_status of_precond_destroy(of_precond* P) {
@@ -1378,19 +1718,24 @@ of_status of_precond_train(of_grid* g, of_precond* P, const float* samples, int 
     }
 }
 
-of_status of_precond_collect(of_grid* g, const double* rho, int stride, int max_samples,
-                             float* samples, int* count) {
-    if (!g || !rho || stride < 1 || max_samples < 1 || !samples || !count) {
+of_status of_precond_collect(of_grid* g, const double* rho, double shift, int stride,
+                             int max_samples, float* samples, int* count) {
+    if (!g || !rho || stride < 1 || max_samples < 1 || !samples || !count || !(shift >= 0.0) ||
+        !std::isfinite(shift)) {
         set_error("of_precond_collect: bad argument");
         return OF_EINVAL;
     }
     try {
         const long long n = g->d.n;
         Arena ar = arena(g);
-        launch(k_sum_product, vec_blocks(n), 256, g->stream, n, rho, (const double*)nullptr,
-               red_ctx(g, 120));
-        launch(k_form_rhs, vec_blocks(n), 256, g->stream, n, rho, (const double*)nullptr,
-               (const double*)(g->s.scalars + 120), 4.0 * M_PI, (double*)ar.b64);
+        if (shift == 0.0) {
+            launch(k_sum_product, vec_blocks(n), 256, g->stream, n, rho, (const double*)nullptr,
+                   red_ctx(g, 120));
+            launch(k_form_rhs, vec_blocks(n), 256, g->stream, n, rho, (const double*)nullptr,
+                   (const double*)(g->s.scalars + 120), 4.0 * M_PI, (double*)ar.b64);
+        } else {
+            OF_CUDA(cudaMemcpyAsync(ar.b64, rho, sizeof(double) * n, cudaMemcpyDeviceToDevice, g->stream));
+        }
         launch(k_sumsq64, vec_blocks(n), 256, g->stream, n, (const double*)ar.b64, red_ctx(g, 121));
         const long long maxit = std::min<long long>(20000, (long long)stride * max_samples);
         launch(k_unit32, vec_blocks(n), 256, g->stream, n, (const double*)ar.b64, (float*)ar.r32,
@@ -1398,7 +1743,7 @@ of_status of_precond_collect(of_grid* g, const double* rho, int stride, int max_
                red_ctx(g, 0));
         Sink sink{samples, stride, max_samples, 0};
         iterate_fcg(g, nullptr, 0.0, KS32, (float*)ar.e32, (float*)ar.r32, (float*)ar.pa32,
-                    (float*)ar.z32, 8, &sink, nullptr);
+                    (float*)ar.z32, 8, &sink, nullptr, shift);
         OF_CUDA(cudaStreamSynchronize(g->stream));
         *count = sink.count;
         return OF_OK;

@@ -1039,6 +1039,7 @@ static void add_info(of_solve_info* out, const of_solve_info& a) {
     if (!out) return;
     out->iterations += a.iterations;
     out->refinements += a.refinements;
+    out->net_steps += a.net_steps;
     out->rel_residual = std::max(out->rel_residual, a.rel_residual);
 }
 

@@ -643,7 +643,9 @@ template <typename T, int N, class Op>
 void launch_brick(of_grid* g, dim3 grid, dim3 block, const Dims& d, const Weights<float>& W, Op op) {
     constexpr int BZ = BrickDepth<N>::value;
     constexpr size_t smem = brick_smem_bytes<T, N, BZ>();
-    if constexpr (smem > 48 * 1024) {   // above the default limit: raise it once per thread
+    // near or above the default 48 KB limit, which counts the op's static shared memory (its
+    // reduction buffers) too: raise it once per thread
+    if constexpr (smem > 40 * 1024) {
         static thread_local int configured_device = -1;
         if (configured_device != g->device) {
             OF_CUDA(cudaFuncSetAttribute(brick_kernel<T, N, BZ, Op>,

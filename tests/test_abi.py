@@ -47,6 +47,10 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.of_vacancy_formation(None, None, None, 0, None, None, None, None, None, None, None,
                                     None, None) == B.OF_EINVAL
     assert "of_vacancy_formation" in B.of_last_error()
+    x = C.c_double(1.0)
+    assert lib.of_alu_peak(7, None, C.byref(x)) == B.OF_EINVAL
+    assert "kind 7" in B.of_last_error()
+    assert lib.of_alu_peak(B.OF_PEAK_F64, None, None) == B.OF_EINVAL
     assert lib.of_grid_destroy(None) == B.OF_OK
 
 

@@ -319,3 +319,15 @@ def test_forces_for_given_potential(cell):
         F = B.of_forces(g.h, sysd, None, dev(phi))
         ref = O.forces(phi, cell.R, cell.Z, cell.sigma, cell.rc, g.grid)
         assert np.max(np.abs(F - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_alu_peak_probe_gives_plausible_rates():
+    # the roofline denominator of the FP64 stencil: a measured DFMA rate, between the FP64 rate
+    # a Blackwell part could plausibly have and the FP32 rate, and an FP32 rate of the order of
+    # 152 SMs x 128 lanes x 2 flops x ~2 GHz
+    f64 = B.of_alu_peak(B.OF_PEAK_F64)
+    f32 = B.of_alu_peak(B.OF_PEAK_F32)
+    f32x2 = B.of_alu_peak(B.OF_PEAK_F32X2)
+    assert 1e11 < f64 < f32
+    assert 2e13 < f32 < 2e14
+    assert 0.8 * f32 < f32x2 < 2.5 * f32
