@@ -109,7 +109,7 @@ class NlcgInfo:
 
 
 def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
-         max_iter=2000, n_restart=50, s_init=1e-2, precond_shift=0.0):
+         max_iter=2000, n_restart=50, s_init=1e-2, precond_shift=0.0, precond_low=0.0):
     """Constrained non-linear CG with Polak-Ribiere update and Brent line search (App. C,
     Algorithm NLCG).  Returns (u, phi, info) with phi the Poisson solution for u.
 
@@ -117,7 +117,13 @@ def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
     its plainest form: the direction is built from z = (-L_h + precond_shift)^{-1} r (solved
     exactly here) with the preconditioned Polak-Ribiere coefficient
     xi = <z, r - r_prev> / <z_prev, r_prev>; the line search and the stopping test are those of
-    the plain method, so the minimum reached is the same."""
+    the plain method, so the minimum reached is the same.
+
+    precond_low > 0 as well: z = (-L_h + precond_low) (-L_h + precond_shift)^{-2} r.  The
+    energy's curvature along a density wave of wave number k grows like k^2 at large k (the vW
+    term) and like 16 pi rho_bar / k^2 at small k (the Hartree term, which a larger cell reaches
+    with smaller k); this form decays like 1/k^2 at large k and flattens at small k, so that it
+    follows both ends."""
     Ne = float(n_electrons)
     u = u0 * sqrt(Ne / inner(u0, u0, grid))
     phi = poisson_solve(u * u + b, grid)
@@ -135,8 +141,14 @@ def nlcg(u0, V_LR, b, phi_b, grid: Grid, fn: Functional, n_electrons, tol=1e-6,
             break
         if q == max_iter:
             break
-        z = (solve_shifted_spectral(r, grid, 1.0, precond_shift).real if precond_shift > 0.0
-             else r)
+        if precond_shift > 0.0 and precond_low > 0.0:
+            t = solve_shifted_spectral(solve_shifted_spectral(r, grid, 1.0, precond_shift).real,
+                                       grid, 1.0, precond_shift).real
+            z = -laplacian(t, grid) + precond_low * t
+        elif precond_shift > 0.0:
+            z = solve_shifted_spectral(r, grid, 1.0, precond_shift).real
+        else:
+            z = r
         if q == 0 or q % n_restart == 0:
             d = z
         else:
@@ -224,7 +236,8 @@ def ground_state_energy(u, phi, b, grid: Grid, fn: Functional, T_LR, E_self, E_c
 
 def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_tol=1e-7,
                      fp_tol=1e-7, max_outer=50, anderson_m=7, zeta=0.3, n_restart=50,
-                     max_nlcg=5000, fixed_point="V", vw_energy="laplacian", precond_shift=0.0):
+                     max_nlcg=5000, fixed_point="V", vw_energy="laplacian", precond_shift=0.0,
+                     precond_low=0.0):
     """Fixed point V_LR = V[U(V_LR)] (Eqs. FixedPoint:Map1, MVF) with Anderson mixing
     (App. D); V_LR,0 = 0.  Returns the ground state and its energy.
 
@@ -246,7 +259,8 @@ def scf_ground_state(grid: Grid, R, Z, sigma, rc, fn: Functional, u0=None, nlcg_
     T_LR = 0.0
     for k in range(max_outer):
         u, phi, info = nlcg(u, V, b, phi_b, grid, fn, Ne, tol=nlcg_tol, max_iter=max_nlcg,
-                            n_restart=n_restart, precond_shift=precond_shift)
+                            n_restart=n_restart, precond_shift=precond_shift,
+                            precond_low=precond_low)
         its.append(info.iterations)
         if fn.mu == 0.0:
             break

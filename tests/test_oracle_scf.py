@@ -238,6 +238,14 @@ def test_preconditioned_nlcg_reaches_the_same_minimum_in_fewer_steps():
     assert np.max(np.abs(pre.u - plain.u)) < 1e-5 * np.max(plain.u)
     assert sum(pre.nlcg_iterations) < 0.6 * sum(plain.nlcg_iterations), (
         sum(pre.nlcg_iterations), sum(plain.nlcg_iterations))
+    # the two-shift form (-L_h + 0.1)(-L_h + 1.2)^{-2}, which also follows the Hartree term's
+    # 1/k^2 curvature at small k: the same minimum, fewer steps still (measured 59 against 86)
+    two = O.scf_ground_state(grid, cell.R, cell.Z, cell.sigma, cell.rc, O.wt_functional(),
+                             precond_shift=1.2, precond_low=0.1, **kw)
+    assert abs(two.energy - plain.energy) / cell.n_atoms < 1e-9
+    assert np.max(np.abs(two.u - plain.u)) < 1e-5 * np.max(plain.u)
+    assert sum(two.nlcg_iterations) < 0.8 * sum(pre.nlcg_iterations), (
+        sum(two.nlcg_iterations), sum(pre.nlcg_iterations))
     # the TFW functional (no outer loop) as well
     tcell = W.al4_displaced_cell(points_per_cell=16)
     tgrid = O.Grid(tcell.n, tcell.L, 6)
