@@ -26,7 +26,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s per SCF ground state & stencil GPts/s: chosen vs plain FP64 CG, at 1e-6 Ha/atom"
 UNIT = "s/ground-state"
-NLCG_PRECOND_SHIFT = 8.0   # bohr^-2
+NLCG_PRECOND_SHIFT = 1.5   # bohr^-2
+NLCG_PRECOND_LOW = 0.01    # bohr^-2
 WORKLOAD = ("108-atom FCC Al-like cell (3x3x3, a=7.6 bohr, +-0.1 bohr displacements, seed 2), "
             "96^3 grid, 12th-order FD, WT-type kernel functional, ground state + forces")
 # what else defines the step (the options of make_case)
@@ -39,9 +40,10 @@ WORKLOAD_DETAIL = {
     "nlcg": {"tol": 1e-7, "line_search": "root of dE/ds (secant), line_tol 1e-3",
              "inexact": "NLCG of outer step k stops at max(1e-7, 0.03 x fixed-point error of "
                         "step k-1); the last outer step at 1e-7",
-             "preconditioner": "chosen form: one multigrid V-cycle of -L_h + 8 bohr^-2 on the "
-                               "gradient, preconditioned Polak-Ribiere (the real-space NLCG "
-                               "preconditioner Sec. 5.5 calls for); plain FP64 form: none"},
+             "preconditioner": "chosen form: (-L_h + 0.01) (-L_h + 1.5)^-2 on the gradient (two "
+                               "multigrid V-cycles and one FP32 sweep), preconditioned "
+                               "Polak-Ribiere (the real-space NLCG preconditioner Sec. 5.5 calls "
+                               "for); plain FP64 form: none"},
     "poisson": {"tol": 1e-10, "form": "FP32 multigrid-preconditioned CG passes to 1e-4 of "
                                       "their starting residual, FP64 refinement"},
     "kernel_solves": {"form": "FP32 COCG preconditioned by the V-cycle of -L + kf2 |Q|, FP64 "
@@ -223,11 +225,15 @@ def make_case(torch, B, Fn, W, precision):
     # 0.41 s per ground state, the same energy to 1e-11 Ha/atom)
     o.nlcg_tol_rel = 3e-2
     o.poisson.inner_tol = 1e-4
-    # the chosen form preconditions the NLCG with one V-cycle of -L_h + 8 bohr^-2 on the
-    # gradient (tuned on this cell: shifts 6 / 8 / 12 / 16 / 32 / 64 gave 0.40 / 0.37 / 0.37 /
-    # 0.39 / 0.39 / 0.50 s per ground state, against 0.79 s without); the plain FP64 form keeps
-    # the paper's unpreconditioned NLCG
+    # the chosen form preconditions the NLCG with (-L_h + 0.01)(-L_h + 1.5)^{-2} on the
+    # gradient, two V-cycles and one sweep, which follows the energy's curvature both at large
+    # wave numbers (~k^2, vW) and at small ones (~16 pi rho_bar / k^2, Hartree).  Tuned on this
+    # cell and on the 3999-atom cell (s per ground state, 108 / 3999 atoms): one V-cycle of
+    # -L_h + 8: 0.328 / 18.3; two-shift (1.5, 0.01): 0.325 / 12.4; (1.5, 0.02): 0.323 / 14.6;
+    # (1.2, 0.02): 0.327 / 15.5; (2.0, 0.05): 0.371 / 14.3; without: 0.79 / 27.0.  The plain FP64
+    # form keeps the paper's unpreconditioned NLCG
     o.nlcg_precond_shift = NLCG_PRECOND_SHIFT if precision == "mixed" else 0.0
+    o.nlcg_precond_low = NLCG_PRECOND_LOW if precision == "mixed" else 0.0
     return cell, h, sysd, fn, o
 
 
@@ -940,6 +946,7 @@ def config5(args):
         o.nlcg_tol_rel = 3e-2       # the benchmark's inexact schedule (make_case)
         o.poisson.inner_tol = 1e-4
         o.nlcg_precond_shift = pshift
+        o.nlcg_precond_low = NLCG_PRECOND_LOW if pshift > 0.0 else 0.0
         return o
 
     u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
@@ -1267,6 +1274,7 @@ def main():
         # preconditioner alone gains
         o_plain_nlcg = B.of_scf_opts.from_buffer_copy(o)
         o_plain_nlcg.nlcg_precond_shift = 0.0
+        o_plain_nlcg.nlcg_precond_low = 0.0
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t = time.time()

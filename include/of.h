@@ -165,6 +165,11 @@ typedef struct {
                                preconditioner for Algorithm NLCG that Sec. 5.5 calls for.  Needs a
                                grid the multigrid can coarsen (else ignored).  0 (default): the
                                plain NLCG of App. C */
+    double nlcg_precond_low;    /* > 0 with nlcg_precond_shift > 0: the two-shift form
+                               (-L_h + low)(-L_h + shift)^{-2}, two V-cycles and one FP32 sweep,
+                               which follows the energy's curvature at both ends of the spectrum:
+                               ~k^2 at large wave numbers (vW), ~1/k^2 at small ones (Hartree).
+                               0 (default): the one-shift form */
 } of_scf_opts;
 
 typedef struct {

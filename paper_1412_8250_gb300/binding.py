@@ -56,7 +56,8 @@ class of_scf_opts(C.Structure):
                 ("precision", C.c_int), ("poisson", of_solve_opts), ("kernel", of_solve_opts),
                 ("verbose", C.c_int), ("line_tol", C.c_double), ("nlcg_tol_rel", C.c_double),
                 ("line_search", C.c_int), ("fixed_point", C.c_int), ("vw_energy", C.c_int),
-                ("nlcg_precond_shift", C.c_double)]
+                ("nlcg_precond_shift", C.c_double),
+                ("nlcg_precond_low", C.c_double)]
 
 
 class of_scf_result(C.Structure):

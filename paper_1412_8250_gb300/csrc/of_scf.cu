@@ -839,10 +839,21 @@ static void poisson_pair(of_grid* g, const double* a1, const double* b1, double*
     st.poisson += st2.poisson;
 }
 
+// y = -L_h x + s x (FP32), the numerator of the two-shift NLCG preconditioner
+struct OpShiftedNegLap32 {
+    const float* x;
+    float* y;
+    float s;
+    __device__ bool begin() { return true; }
+    __device__ float load(long long i) const { return x[i]; }
+    __device__ void store(long long i, float c, float lap) { y[i] = fmaf(s, c, -lap); }
+    __device__ void end() {}
+};
+
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
 static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
                  const double* V, double tol, int max_iter, int n_restart, double line_tol,
-                 int line_search, const KrylovOpts& po, ScfStats& st, double pshift) {
+                 int line_search, const KrylovOpts& po, ScfStats& st, double pshift, double plow) {
     const long long n = g->d.n;
     const double dV = g->dV;
     // preconditioned NLCG: buffers of the gradient in FP32, its V-cycle and the FP64 direction
@@ -888,12 +899,17 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         double xi = 0.0;
         double m[4];
         if (pshift > 0.0) {
-            // preconditioned direction: z = M^{-1} r with M one V-cycle of -L_h + pshift (FP32
-            // on the gradient scaled to unit RMS), Polak-Ribiere in the preconditioned form
-            // xi = <z, r - r_prev> / <z_prev, r_prev>, d = z + xi d_prev
+            // preconditioned direction: z = M^{-1} r with M^{-1} one V-cycle of -L_h + pshift,
+            // or (-L_h + plow) times two of them (FP32 on the gradient scaled to unit RMS),
+            // Polak-Ribiere in the preconditioned form xi = <z, r - r_prev> / <z_prev, r_prev>,
+            // d = z + xi d_prev
             launch(k_grad_demote, nb, 256, g->stream, n, (const double*)v.r,
                    (const double*)(g->s.scalars + SC_RR), pc.r32);
             mg_vcycle_real_shifted(g, pc.r32, pc.z32, g->s.scalars + SC_ZERO, pshift);
+            if (plow > 0.0) {
+                mg_vcycle_real_shifted(g, pc.z32, pc.r32, g->s.scalars + SC_ZERO, pshift);
+                launch_stencil<float, 2>(g, g->w32, OpShiftedNegLap32{pc.r32, pc.z32, (float)plow});
+            }
             launch(k_grad_promote, nb, 256, g->stream, n, (const float*)pc.z32,
                    (const double*)(g->s.scalars + SC_RR), (const double*)v.r,
                    q > 0 ? (const double*)v.rp : nullptr, pc.z, red_ctx(g, SC_ZR));
@@ -1360,7 +1376,7 @@ static void scf(of_grid* g, const of_system* sys, const of_functional* fn, const
         }
         inner_ok = nlcg(g, fp, Ne, v, u, phi, lr ? v.V : nullptr, tol_k, o->nlcg_max_iter,
                         std::max(1, o->nlcg_restart), o->line_tol > 0 ? o->line_tol : 1e-3,
-                        o->line_search, po, st, o->nlcg_precond_shift);
+                        o->line_search, po, st, o->nlcg_precond_shift, o->nlcg_precond_low);
         res->outer_iterations = k + 1;
         if (!lr) { err = 0.0; break; }
         if (fp_u) {

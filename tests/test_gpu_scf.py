@@ -98,6 +98,12 @@ def test_preconditioned_nlcg_reaches_the_golden_minimum(prec):
     assert wres.converged
     assert abs(wres.energy - wrec["energy"]) / wcell.n_atoms <= E_TOL
     assert np.max(np.abs(wF - np.array(wrec["forces"]))) <= F_TOL
+    # the two-shift form (-L_h + 0.01)(-L_h + 1.5)^{-2}: the same minimum
+    for c, r, fn, kw in ((cell, rec, Fn.tfw(), {}), (wcell, wrec, Fn.wt(), dict(anderson_m=3, anderson_zeta=1.0))):
+        tres, tF, _, _ = _run(c, fn, prec, nlcg_precond_shift=1.5, nlcg_precond_low=0.01, **kw)
+        assert tres.converged
+        assert abs(tres.energy - r["energy"]) / c.n_atoms <= E_TOL
+        assert np.max(np.abs(tF - np.array(r["forces"]))) <= F_TOL
 
 
 @pytest.mark.parametrize("prec,inexact", [(B.OF_F64, 0.0), (B.OF_F32, 0.0), (B.OF_F32, 1e-3)])
@@ -279,7 +285,8 @@ def _bench_like_opts(o):
     o.anderson_zeta = 1.0
     o.nlcg_tol_rel = 3e-2
     o.poisson.inner_tol = 1e-4
-    o.nlcg_precond_shift = 8.0   # the chosen form's NLCG preconditioner (one V-cycle)
+    o.nlcg_precond_shift = 1.5   # the chosen form's NLCG preconditioner,
+    o.nlcg_precond_low = 0.01    # (-L_h + 0.01)(-L_h + 1.5)^{-2}
     return o
 
 
