@@ -850,6 +850,10 @@ struct OpShiftedNegLap32 {
     __device__ void end() {}
 };
 
+// Tolerance of the Poisson re-solve after an NLCG step, relative to the normalised gradient
+// norm (tuned on the 108-atom cell)
+constexpr double RESOLVE_FACTOR = 1e-3;
+
 // Inner minimisation U(V) (App. C).  u, phi in/out.  Returns true when converged.
 static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* u, double* phi,
                  const double* V, double tol, int max_iter, int n_restart, double line_tol,
@@ -1028,7 +1032,13 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         launch(k_step, nb, 256, g->stream, n, u, v.d, phi, v.D, v.B, v.C, s, c);
         launch(k_density_plus, nb, 256, g->stream, n, u, v.b, v.rho);
         OF_LAUNCH_CHECK();
-        poisson_into(g, v.rho, nullptr, phi, po, st);   // re-solve (warm start is nearly exact)
+        // re-solve (the warm start is nearly exact) to what the next gradient needs: phi's
+        // error enters it as 2 u dphi, so a relative accuracy of RESOLVE_FACTOR x the
+        // normalised gradient norm keeps that well below the gradient itself; near convergence
+        // this reaches the full tolerance, which the final energy and forces use
+        KrylovOpts pr = po;
+        pr.tol = std::max(po.tol, std::min(1e-6, RESOLVE_FACTOR * st.last_residual));
+        poisson_into(g, v.rho, nullptr, phi, pr, st);
         std::swap(v.r, v.rp);
         std::swap(v.d, v.dp);
         rr_prev = rr;
