@@ -96,8 +96,9 @@ __device__ __forceinline__ void gauss_axis_tables(const AtomBox& B, double h1, d
     }
 }
 
-// Block (J, plane): scatter b_J into b (atomic: boxes of different ions overlap) and reduce
-// dV * sum b_J V_J for the self energy.
+// Block (J, plane): reduce dV * sum b_J V_J over the plane for the self energy, and with b
+// non-null scatter b_J into b (atomic: boxes of different ions overlap, so the summation order
+// of b, and its last bits, vary from run to run; the gather below is the deterministic form).
 __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double h2, double h3,
                                                       const AtomBox* boxes, Gauss q, double* b,
                                                       double* e_self_part, int max_planes) {
@@ -124,9 +125,11 @@ __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double 
             const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= rc2) {
                 const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
-                const long long idx = wrap_index(i, d.n1) +
-                                      (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
-                atomicAdd(b + idx, bj);
+                if (b) {
+                    const long long idx = wrap_index(i, d.n1) +
+                                          (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+                    atomicAdd(b + idx, bj);
+                }
                 acc += bj * gauss_V(sqrt(r2), B.Z, q);
             }
         }
@@ -140,6 +143,153 @@ __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double 
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
         e_self_part[(long long)J * max_planes + pl] = s;
     }
+}
+
+// ---- the nuclear charge in a fixed summation order
+// One periodic image of an ion: the ion's unwrapped box restricted to the grid by the offset
+// off = m n (grid points) along each axis; its points are the in-grid indices lo..hi, and the
+// displacement of point i is (i + off) h - R, the same arithmetic as in the unwrapped box.
+struct IonImage {
+    double R[3];
+    double Z;
+    int off[3];
+    int lo[3];
+    int hi[3];
+};
+
+constexpr int GT = 8;          // tile edge (points) of the gather
+constexpr int GCAP = 64;       // images whose tables a block holds at once
+
+__device__ __forceinline__ bool tile_overlaps(const IonImage& m, int x0, int y0, int z0) {
+    return m.lo[0] <= x0 + GT - 1 && m.hi[0] >= x0 && m.lo[1] <= y0 + GT - 1 && m.hi[1] >= y0 &&
+           m.lo[2] <= z0 + GT - 1 && m.hi[2] >= z0;
+}
+
+// Block = one 8 x 8 x 8 tile of the grid (z-slab blockIdx.z): b at each point is the sum over
+// the images that reach the tile, taken in image order (ion order, then image offsets), each
+// contribution -Z norm exp(-dz^2/2s^2) (exp(-dx^2/2s^2) exp(-dy^2/2s^2)) within r_c as in the
+// scatter; the images of the slab come from a list built on the host.  Every point is written
+// once, and the order of its sum does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_pseudocharge_gather(Dims d, double h1, double h2, double h3,
+                                                             const IonImage* __restrict__ img,
+                                                             const int* __restrict__ slab_start,
+                                                             const int* __restrict__ slab_img, Gauss q,
+                                                             double* __restrict__ b) {
+    const int x0 = blockIdx.x * GT, y0 = blockIdx.y * GT, z0 = blockIdx.z * GT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tx = tid & 7, ty = (tid >> 3) & 7, tz = tid >> 6;   // points (tx, ty, tz) and (tx, ty, tz + 4)
+    __shared__ int pend[256];
+    __shared__ int wcount[8];
+    __shared__ int npend;
+    __shared__ double ex[GCAP][GT], ey[GCAP][GT], ez[GCAP][GT];   // ez carries -Z norm
+    const double rc2 = q.rc * q.rc;
+    const int i = x0 + tx, j = y0 + ty;
+    double acc[2] = {0.0, 0.0};
+    const int first = slab_start[blockIdx.z], last = slab_start[blockIdx.z + 1];
+    for (int base = first; base < last; base += 256) {
+        // the slab's images that reach this tile, compacted in order
+        const int c = base + tid;
+        const bool hit = c < last && tile_overlaps(img[slab_img[c]], x0, y0, z0);
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) wcount[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < 8; ++w) {
+            if (w < warp) before += wcount[w];
+            total += wcount[w];
+        }
+        if (hit) pend[before + __popc(bal & ((1u << lane) - 1u))] = slab_img[c];
+        if (tid == 0) npend = total;
+        __syncthreads();
+        const int np = npend;
+        for (int p0 = 0; p0 < np; p0 += GCAP) {
+            const int cnt = min(GCAP, np - p0);
+            // axis tables of this batch of images: one exp per (image, axis, tile coordinate)
+            for (int e = tid; e < cnt * 3 * GT; e += 256) {
+                const int m = e / (3 * GT), a = (e / GT) % 3, t = e % GT;
+                const IonImage& I = img[pend[p0 + m]];
+                const double hh = a == 0 ? h1 : (a == 1 ? h2 : h3);
+                const int o = a == 0 ? x0 : (a == 1 ? y0 : z0);
+                const double dv = (o + t + I.off[a]) * hh - I.R[a];
+                const double ev = exp(-dv * dv * q.inv2s2);
+                if (a == 0) ex[m][t] = ev;
+                else if (a == 1) ey[m][t] = ev;
+                else ez[m][t] = -I.Z * q.norm * ev;
+            }
+            __syncthreads();
+            for (int m = 0; m < cnt; ++m) {
+                const IonImage& I = img[pend[p0 + m]];
+                const double dx = (i + I.off[0]) * h1 - I.R[0];
+                const double dy = (j + I.off[1]) * h2 - I.R[1];
+                const double exy = ex[m][tx] * ey[m][ty];
+                const double dxy2 = dx * dx + dy * dy;
+#pragma unroll
+                for (int s2 = 0; s2 < 2; ++s2) {
+                    const int kz = tz + 4 * s2;
+                    const double dz = (z0 + kz + I.off[2]) * h3 - I.R[2];
+                    if (dxy2 + dz * dz <= rc2) acc[s2] += ez[m][kz] * exy;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (i < d.n1 && j < d.n2) {
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int k = z0 + tz + 4 * s2;
+            if (k < d.n3) b[(long long)i + (long long)d.n1 * (j + (long long)d.n2 * k)] = acc[s2];
+        }
+    }
+}
+
+// Periodic images of the ions (each ion's unwrapped box split by the grid period) and, per
+// z-slab of GT planes, the images that reach it, in image order.
+static void build_images(of_grid* g, const AtomSet& a, IonImage*& d_img, int*& d_start, int*& d_list,
+                         int& nslab) {
+    const int n[3] = {g->d.n1, g->d.n2, g->d.n3};
+    auto floor_div = [](int x, int m) { return x >= 0 ? x / m : -((-x + m - 1) / m); };
+    std::vector<IonImage> im;
+    for (const AtomBox& B : a.h) {
+        int mlo[3], mhi[3];
+        for (int c = 0; c < 3; ++c) {
+            mlo[c] = floor_div(B.lo[c], n[c]);
+            mhi[c] = floor_div(B.lo[c] + B.len[c] - 1, n[c]);
+        }
+        for (int mz = mlo[2]; mz <= mhi[2]; ++mz)
+            for (int my = mlo[1]; my <= mhi[1]; ++my)
+                for (int mx = mlo[0]; mx <= mhi[0]; ++mx) {
+                    IonImage I;
+                    const int m[3] = {mx, my, mz};
+                    for (int c = 0; c < 3; ++c) {
+                        I.R[c] = B.R[c];
+                        I.off[c] = m[c] * n[c];
+                        I.lo[c] = std::max(0, B.lo[c] - I.off[c]);
+                        I.hi[c] = std::min(n[c] - 1, B.lo[c] + B.len[c] - 1 - I.off[c]);
+                    }
+                    I.Z = B.Z;
+                    if (I.lo[0] <= I.hi[0] && I.lo[1] <= I.hi[1] && I.lo[2] <= I.hi[2]) im.push_back(I);
+                }
+    }
+    nslab = (n[2] + GT - 1) / GT;
+    std::vector<int> start(nslab + 1, 0), list;
+    for (int s = 0; s < nslab; ++s) {
+        start[s] = (int)list.size();
+        for (int k = 0; k < (int)im.size(); ++k)
+            if (im[k].lo[2] <= s * GT + GT - 1 && im[k].hi[2] >= s * GT) list.push_back(k);
+    }
+    start[nslab] = (int)list.size();
+    const size_t b_img = (sizeof(IonImage) * im.size() + 255) / 256 * 256;
+    const size_t b_start = (sizeof(int) * start.size() + 255) / 256 * 256;
+    char* base = (char*)ws(g, WS_IMG, b_img + b_start + sizeof(int) * std::max<size_t>(1, list.size()));
+    d_img = (IonImage*)base;
+    d_start = (int*)(base + b_img);
+    d_list = (int*)(base + b_img + b_start);
+    OF_CUDA(cudaMemcpyAsync(d_img, im.data(), sizeof(IonImage) * im.size(), cudaMemcpyHostToDevice, g->stream));
+    OF_CUDA(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, g->stream));
+    if (!list.empty())
+        OF_CUDA(cudaMemcpyAsync(d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, g->stream));
+    // the host vectors go out of scope: finish the copies first
+    OF_CUDA(cudaStreamSynchronize(g->stream));
 }
 
 // Block (J, plane): dV * sum grad b_J (phi - V_J) over the plane, 3 components.
@@ -450,14 +600,20 @@ static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, doubl
     if (sys && sys->b_from_potential) return pseudocharge_fd(g, sys, b, e_self);
     AtomSet a = upload_atoms(g, sys);
     Gauss q = gauss(sys);
-    const size_t nparts = (size_t)a.n_atoms * a.max_planes;
-    double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + a.n_atoms + 8));
-    OF_CUDA(cudaMemsetAsync(b, 0, sizeof(double) * g->d.n, g->stream));
-    OF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * nparts, g->stream));
-    launch(k_pseudocharge, dim3(a.n_atoms, a.max_planes), 256, g->stream, 
-        g->d, g->h[0], g->h[1], g->h[2], a.d_boxes, q, b, part, a.max_planes);
+    IonImage* img = nullptr;
+    int *start = nullptr, *list = nullptr, nslab = 0;
+    build_images(g, a, img, start, list, nslab);
+    launch(k_pseudocharge_gather, dim3((g->d.n1 + GT - 1) / GT, (g->d.n2 + GT - 1) / GT, nslab), 256,
+           g->stream, g->d, g->h[0], g->h[1], g->h[2], (const IonImage*)img, (const int*)start,
+           (const int*)list, q, b);
     OF_LAUNCH_CHECK();
     if (e_self) {
+        const size_t nparts = (size_t)a.n_atoms * a.max_planes;
+        double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + a.n_atoms + 8));
+        OF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * nparts, g->stream));
+        launch(k_pseudocharge, dim3(a.n_atoms, a.max_planes), 256, g->stream, g->d, g->h[0], g->h[1],
+               g->h[2], a.d_boxes, q, (double*)nullptr, part, a.max_planes);
+        OF_LAUNCH_CHECK();
         double* per_atom = part + nparts;
         launch(k_sum_planes, (a.n_atoms + 127) / 128, 128, g->stream, a.n_atoms, a.max_planes, 1,
                                                                     part, -0.5 * g->dV, per_atom);

@@ -265,6 +265,7 @@ enum Slot {
     WS_MG,       // multigrid hierarchy
     WS_NLCGP,    // preconditioned NLCG: the gradient in FP32, its V-cycle, the FP64 direction
     WS_FGM,      // flexible GMRES: Arnoldi and preconditioned vectors
+    WS_IMG,      // periodic images of the ions and their lists per z-slab (nuclear charge)
     WS_NSLOTS
 };
 

@@ -250,6 +250,19 @@ def test_pseudocharge_and_self_energy(cell):
         assert abs(e - eref) <= 1e-12 * abs(eref)
 
 
+def test_pseudocharge_is_bitwise_reproducible():
+    # every point of the nuclear charge is summed over the ions' images in one fixed order, so
+    # two handles give the same bits (a scatter with atomics would not)
+    for cell in (W.al108_cell(), W.al4_cell()):
+        out = []
+        for _ in range(2):
+            with G(cell.n, cell.L) as g:
+                b = torch.empty(g.shape, dtype=torch.float64, device="cuda")
+                e = B.of_pseudocharge(g.h, B.make_system(cell.R, cell.Z, cell.sigma, cell.rc), b)
+                out.append((b, e))
+        assert torch.equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
 @pytest.mark.parametrize("cell", [W.al4_displaced_cell(points_per_cell=24), W.al4_lr_cell(points_per_cell=20)],
                          ids=["al4d", "al4lr"])
 def test_pseudocharge_from_the_potential(cell):

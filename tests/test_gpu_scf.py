@@ -379,6 +379,41 @@ def test_batched_ground_states_match_single_cell_calls():
             B.of_grid_destroy(g)
 
 
+def test_ground_states_are_bitwise_reproducible():
+    # every reduction sums in a fixed order and the nuclear charge is gathered, not scattered:
+    # the same WT ground state with the benchmark's options (twin handles, concurrent kernel-map
+    # solves, the two-shift NLCG preconditioner) on two handles, and inside a batched call
+    # beside another cell, gives the same bits
+    cell = W.al4_lr_cell(points_per_cell=16)
+    other = W.al4_cell(points_per_cell=16)
+    stream = torch.cuda.current_stream()
+    o = _bench_like_opts(B.of_default_scf_opts())
+    o.precision = B.OF_F32
+    sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+    runs = []
+    for _ in range(2):
+        h = B.of_grid_create(cell.n, cell.L, 6, stream)
+        try:
+            u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+            phi = torch.zeros_like(u)
+            res = B.of_scf_ground_state(h, sysd, Fn.wt(), o, u, phi)
+            runs.append((res.energy, u, B.of_forces(h, sysd, u, phi)))
+        finally:
+            B.of_grid_destroy(h)
+    grids = [B.of_grid_create(c.n, c.L, 6, stream) for c in (other, cell)]
+    try:
+        us = [torch.ones(c.shape, dtype=torch.float64, device="cuda") for c in (other, cell)]
+        phis = [torch.zeros_like(x) for x in us]
+        systems = [B.make_system(other.R, other.Z, other.sigma, other.rc), sysd]
+        results = B.of_scf_ground_state_batched(grids, systems, Fn.wt(), o, us, phis)
+    finally:
+        for g in grids:
+            B.of_grid_destroy(g)
+    assert runs[0][0] == runs[1][0] == results[1].energy
+    assert torch.equal(runs[0][1], runs[1][1]) and torch.equal(runs[0][1], us[1])
+    assert np.array_equal(runs[0][2], runs[1][2])
+
+
 def test_batched_wt_ground_states_of_uneven_cells_match_the_oracle():
     # the batched call on cells of different shapes and atom counts, one with a vacancy, with
     # the WT-type kernel term and the benchmark's options: every cell's energy and forces
