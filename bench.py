@@ -124,6 +124,9 @@ def parse():
                    help="fixed point on V_LR vs on u, Anderson m and zeta, on the 108-atom cell")
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-preconditioner comparison (864-atom 192^3 Poisson)")
+    p.add_argument("--no-other-configs", action="store_true",
+                   help="skip the other workloads of the default line (3999-atom cell, full WGC, "
+                        "relaxation, vacancy formation)")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the 64-cell batched-vs-sequential comparisons (Poisson solves and "
                         "ground states)")
@@ -678,6 +681,82 @@ def reference_arm(args, rank, world):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def other_configs(torch, B, Fn, W):
+    """The other workloads, one timed run each in the chosen form with the benchmark's options
+    (their own modes, --config5, --wgc, --relax, --vacancy, add the comparisons): the 3999-atom
+    320^3 ground state + forces; the 108-atom ground state + forces with the full WGC functional
+    (L = 2); the relaxation of the 108-atom cell; the vacancy formation energy of the perfect
+    108-atom cell, unrelaxed and relaxed."""
+    import numpy as np
+    out = {}
+    stream = torch.cuda.current_stream()
+    # 3999 atoms, 320^3
+    cell = W.al3999_cell()
+    h = B.of_grid_create(cell.n, cell.L, 6, stream)
+    sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+    _, h0, _, fn, o = make_case(torch, B, Fn, W, "mixed")
+    B.of_grid_destroy(h0)
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    torch.cuda.synchronize()
+    t = time.time()
+    res = B.of_scf_ground_state(h, sysd, fn, o, u, phi)
+    F = B.of_forces(h, sysd, u, phi)
+    torch.cuda.synchronize()
+    out["large_3999_atoms_320"] = {"s": time.time() - t, "energy_per_atom_ha": res.energy / cell.n_atoms,
+                                   "outer_iterations": res.outer_iterations,
+                                   "nlcg_steps": res.nlcg_iterations, "fp_error": res.fp_error,
+                                   "max_force": float(np.abs(F).max()),
+                                   "max_force_sum": float(np.abs(F.sum(0)).max())}
+    B.of_grid_destroy(h)
+    del u, phi
+    # 108 atoms: WGC, relaxation
+    cell, h, sysd, fn, o = make_case(torch, B, Fn, W, "mixed")
+    u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+    phi = torch.zeros_like(u)
+    torch.cuda.synchronize()
+    t = time.time()
+    res = B.of_scf_ground_state(h, sysd, Fn.wgc(), o, u, phi)
+    F = B.of_forces(h, sysd, u, phi)
+    torch.cuda.synchronize()
+    out["wgc_108_atoms"] = {"s": time.time() - t, "energy_per_atom_ha": res.energy / cell.n_atoms,
+                            "outer_iterations": res.outer_iterations, "nlcg_steps": res.nlcg_iterations,
+                            "kernel_iterations": res.kernel_iterations, "max_force": float(np.abs(F).max())}
+    u.fill_(1.0)
+    phi.zero_()
+    torch.cuda.synchronize()
+    t = time.time()
+    R, F, rres = B.of_relax(h, sysd, fn, o, B.of_default_relax_opts(), u, phi, allow=(B.OF_ENOCONV,))
+    torch.cuda.synchronize()
+    out["relax_108_atoms"] = {"s": time.time() - t, "converged": bool(rres.converged), "steps": rres.steps,
+                              "ground_states": rres.evaluations, "max_force": rres.max_force,
+                              "energy_per_atom_ha": rres.energy / cell.n_atoms}
+    B.of_grid_destroy(h)
+    # vacancy formation, perfect 108-atom cell
+    pc = W.fcc_supercell((3, 3, 3), points_per_cell=32, sigma=W.SIGMA_LR, rc=W.R_CUT_LR, name="al108_perfect")
+    site = int(np.argmin(((pc.R - np.array(pc.L) / 2) ** 2).sum(1)))
+    hp = B.of_grid_create(pc.n, pc.L, 6, stream)
+    hv = B.of_grid_create(pc.n, B.vacancy_cell_lengths(pc.L, pc.n_atoms), 6, stream)
+    psys = B.make_system(pc.R, pc.Z, pc.sigma, pc.rc)
+    fields = [torch.ones(pc.shape, dtype=torch.float64, device="cuda") for _ in range(4)]
+    HA_EV = 27.211386245988
+    for name, ro in (("unrelaxed", None), ("relaxed", B.of_default_relax_opts())):
+        fields[0].fill_(1.0)
+        fields[2].fill_(1.0)
+        fields[1].zero_()
+        fields[3].zero_()
+        torch.cuda.synchronize()
+        t = time.time()
+        _, vres = B.of_vacancy_formation(hp, hv, psys, site, fn, o, ro, *fields)
+        torch.cuda.synchronize()
+        out["vacancy_108_atoms_" + name] = {
+            "s": time.time() - t,
+            "evf_ev": (vres.evf_unrelaxed if ro is None else vres.evf_relaxed) * HA_EV}
+    B.of_grid_destroy(hp)
+    B.of_grid_destroy(hv)
+    return out
 
 
 def wgc(args):
@@ -1257,6 +1336,7 @@ def main():
     batched = None if (args.no_batched or rank != 0) else batched_compare(torch, B, W)
     batched_gs = None if (args.no_batched or rank != 0) else batched_ground_states(torch, B, Fn, W, 64)
     learned = None if (args.no_learned or rank != 0) else learned_compare(torch, B, W)
+    others = None if (args.no_other_configs or rank != 0) else other_configs(torch, B, Fn, W)
     compare = None
     if not args.no_compare_f64 and rank == 0:
         # the plain FP64 CG / COCG form with the same options (the chosen form's counterpart),
@@ -1373,7 +1453,7 @@ def main():
                            **(errors_vs_oracle(res, F, cell.n_atoms) or {})},
                 "kernel_profile": prof, "step_ms": step_ms, "batched_poisson_64_cells": batched,
                 "batched_ground_states_64": batched_gs,
-                "learned_preconditioner": learned}
+                "learned_preconditioner": learned, "other_workloads": others}
         if compare:
             line["compare"] = compare
         print(json.dumps(line), flush=True)

@@ -257,7 +257,9 @@ struct BetaFuse {
     const T* r;
 };
 
-// r = b - A x
+// r = b - A x, and (d0 non-null) the first Chebyshev direction d0 = s0 r beside it: the first
+// smoothing step then reads d0 at the neighbours while it rewrites r at its own points (it
+// must not read r there: other blocks update r while a block stages its halo)
 template <typename T>
 struct OpResid32 {
     static constexpr int kClass = PC_MG_SMOOTH, kWords = 3;
@@ -266,16 +268,23 @@ struct OpResid32 {
     T* r;
     float sigma;
     const double* done;
+    T* d0 = nullptr;
+    float s0 = 0.f;
     __device__ bool begin() { return *done == 0.0; }
     __device__ T load(long long i) const { return x[i]; }
     template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
     __device__ float2 load2(long long i) const { return *reinterpret_cast<const float2*>(x + i); }
-    __device__ void store(long long i, T c, T lap) { r[i] = vfma(-sigma, c, vadd(b[i], lap)); }
+    __device__ void store(long long i, T c, T lap) {
+        const T rv = vfma(-sigma, c, vadd(b[i], lap));
+        r[i] = rv;
+        if (d0) d0[i] = vmul(s0, rv);
+    }
     template <typename U = T, typename = std::enable_if_t<std::is_same<U, float>::value>>
     __device__ void store2(long long i, float2 c, float2 lap) {
         const float2 bv = *reinterpret_cast<const float2*>(b + i);
-        *reinterpret_cast<float2*>(r + i) =
-            make_float2(fmaf(-sigma, c.x, bv.x + lap.x), fmaf(-sigma, c.y, bv.y + lap.y));
+        const float2 rv = make_float2(fmaf(-sigma, c.x, bv.x + lap.x), fmaf(-sigma, c.y, bv.y + lap.y));
+        *reinterpret_cast<float2*>(r + i) = rv;
+        if (d0) *reinterpret_cast<float2*>(d0 + i) = make_float2(s0 * rv.x, s0 * rv.y);
     }
     __device__ void end() {}
 };
@@ -598,14 +607,16 @@ static void smooth(of_grid* g, MGLevel& L, int deg, bool zero_guess, const doubl
     double theta;
     cheby_coeffs(0.15 * S.lmax, 1.05 * S.lmax, deg, a, b, theta);
     T *x = (T*)L.x, *lb = (T*)L.b, *r = (T*)L.r;
-    if (!zero_guess)
-        launch_stencil_dims<T, RY>(g, L.d, L.N, L.W, OpResid32<T>{x, lb, r, (float)sigma, done});
-    T* din = zero_guess ? lb : r;
     T* dbuf[2] = {(T*)L.d0, (T*)L.d1};
+    const float s0 = (float)(S.invD / theta);
+    // from a guess: r and the first direction s0 r (in dbuf[1], which step 0 reads; step 0
+    // writes r in place, so it must not read r at the neighbours)
+    if (!zero_guess)
+        launch_stencil_dims<T, RY>(g, L.d, L.N, L.W, OpResid32<T>{x, lb, r, (float)sigma, done, dbuf[1], s0});
     for (int k = 0; k < deg; ++k) {
         OpCheby<T> op;
-        op.din = (k == 0) ? din : dbuf[(k + 1) & 1];
-        op.dscale = (k == 0) ? (float)(S.invD / theta) : 1.f;
+        op.din = (k == 0 && zero_guess) ? lb : dbuf[(k + 1) & 1];
+        op.dscale = (k == 0 && zero_guess) ? s0 : 1.f;
         op.x = x;
         op.x_init = zero_guess && k == 0;
         op.rin = (k == 0 && zero_guess) ? lb : r;

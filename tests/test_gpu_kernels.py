@@ -250,6 +250,30 @@ def test_pseudocharge_and_self_energy(cell):
         assert abs(e - eref) <= 1e-12 * abs(eref)
 
 
+def test_multigrid_solves_are_bitwise_reproducible():
+    # the multigrid-preconditioned FP32 passes (Poisson and a shifted system) give the same bits
+    # on repeated calls and on another handle.  This caught a data race: the first
+    # post-smoothing step read the residual at its neighbours while other blocks rewrote it.
+    cell = W.al108_cell()
+    rho = torch.from_numpy(W.random_field(cell.shape, seed=5, kind="smooth")
+                           + 0.1 * W.random_field(cell.shape, seed=6)).cuda()
+    f = torch.from_numpy(W.random_field(cell.shape, seed=7, kind="smooth")).cuda()
+    kf2 = Fn.kf2(cell.n_electrons, float(np.prod(cell.L)))
+    fn = Fn.wt()
+    P, Q = [complex(fn.P[4], fn.P[5])], [complex(fn.Q[4], fn.Q[5])]
+    out = []
+    for k in range(3):
+        with G(cell.n, cell.L) as g:
+            for rep in range(1 if k < 2 else 2):
+                phi = torch.zeros_like(rho)
+                B.of_poisson_solve(g.h, rho, phi, _opts(B.OF_F32, 1e-10))
+                Wc = torch.zeros(cell.shape + (2,), dtype=torch.float64, device="cuda")
+                B.of_kernel_solve(g.h, f, P, Q, kf2, Wc, _opts(B.OF_F32, 1e-10))
+                out.append((phi, Wc))
+    for phi, Wc in out[1:]:
+        assert torch.equal(phi, out[0][0]) and torch.equal(Wc, out[0][1])
+
+
 def test_pseudocharge_is_bitwise_reproducible():
     # every point of the nuclear charge is summed over the ions' images in one fixed order, so
     # two handles give the same bits (a scatter with atomics would not)
