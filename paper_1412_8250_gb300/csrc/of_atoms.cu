@@ -78,6 +78,85 @@ __device__ __forceinline__ double gauss_V(double r, double Z, const Gauss& q) {
     return r < 1e-12 ? -Z * q.v0 : -Z * erf(r * q.erfscale) / r;
 }
 
+// V_J(r) = -Z_J g(r^2) with g(s) = erf(a sqrt s) / sqrt s, a = 1 / (sqrt2 sigma): an entire
+// function of s = r^2, the same for every ion.  The self-energy and force kernels evaluate it
+// at every point of every ion's ball, where an FP64 sqrt, erf and division per point set their
+// time; they take it instead from a table of degree-VT_D polynomials on n equal intervals of
+// s in [0, r_c^2] (Chebyshev interpolation at VT_D + 1 nodes per interval, converted to
+// monomials in the interval's local variable x in [-1, 1]).  The interpolation error is below
+// 2 (w / 4)^9 / 9! max |g^(9)| for an interval of width w in s, and |g^(k)| <= 2 a^(2k+1) /
+// (sqrt(pi) (2k + 1)); n = ceil(2 a^2 r_c^2) intervals (w a^2 <= 1/2) keep it near 3e-15 of
+// g(0) (checked for sigma = 0.3 ... 1.5, r_c = 3 ... 12).  Beyond VT_MAX intervals the kernels
+// evaluate erf directly.
+constexpr int VT_MAX = 256;
+constexpr int VT_D = 8;
+struct VTable {
+    double c[VT_MAX][VT_D + 1];
+    double s_scale;   // n / r_c^2
+    int n;            // intervals; 0: evaluate erf directly
+};
+
+static VTable vtable(const of_system* sys) {
+    VTable t{};
+    const double a = 1.0 / (std::sqrt(2.0) * sys->sigma);
+    const double smax = sys->rc * sys->rc;
+    const double want = std::ceil(2.0 * a * a * smax);
+    if (!(want <= VT_MAX)) return t;   // n = 0
+    const int n = std::max(16, (int)want);
+    const double w = smax / n;
+    t.n = n;
+    t.s_scale = n / smax;
+    auto g = [a](double sv) { const double r = std::sqrt(sv); return std::erf(a * r) / r; };
+    constexpr int M = VT_D + 1;
+    // monomial coefficients of the Chebyshev polynomials T_0 .. T_VT_D
+    double T[M][M] = {};
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int k = 2; k < M; ++k)
+        for (int j = 0; j < M; ++j)
+            T[k][j] = (j > 0 ? 2.0 * T[k - 1][j - 1] : 0.0) - T[k - 2][j];
+    for (int i = 0; i < n; ++i) {
+        double f[M], ck[M];
+        for (int j = 0; j < M; ++j) {
+            const double x = std::cos(M_PI * (j + 0.5) / M);
+            f[j] = g(w * (i + 0.5 * (x + 1.0)));   // nodes are interior: s > 0
+        }
+        for (int k = 0; k < M; ++k) {
+            double sum = 0.0;
+            for (int j = 0; j < M; ++j) sum += f[j] * std::cos(M_PI * k * (j + 0.5) / M);
+            ck[k] = (k == 0 ? 1.0 : 2.0) * sum / M;
+        }
+        for (int j = 0; j < M; ++j) {
+            double m = 0.0;
+            for (int k = j; k < M; ++k) m += ck[k] * T[k][j];
+            t.c[i][j] = m;
+        }
+    }
+    return t;
+}
+
+// g(s) from the table (in shared memory); 0 <= s <= r_c^2
+__device__ __forceinline__ double vt_g(const double (*c)[VT_D + 1], double s_scale, int n, double s) {
+    const double u = s * s_scale;
+    const int i = min((int)u, n - 1);
+    const double x = 2.0 * (u - (double)i) - 1.0;
+    const double* q = c[i];
+    double p = q[VT_D];
+#pragma unroll
+    for (int k = VT_D - 1; k >= 0; --k) p = fma(p, x, q[k]);
+    return p;
+}
+
+__device__ __forceinline__ void vt_load(const VTable& t, double (*c)[VT_D + 1]) {
+    for (int e = threadIdx.x; e < t.n * (VT_D + 1); e += blockDim.x) (&c[0][0])[e] = (&t.c[0][0])[e];
+}
+
+// V_J(r) at r^2 = s: from the table, or directly when it has none
+__device__ __forceinline__ double vt_V(const VTable& t, const double (*c)[VT_D + 1], double s, double Z,
+                                       const Gauss& q) {
+    return t.n ? -Z * vt_g(c, t.s_scale, t.n, s) : gauss_V(sqrt(s), Z, q);
+}
+
 // The Gaussian factorises: exp(-r^2 / 2s^2) = ex(dx) ey(dy) ez(dz).  A block (J, plane) takes
 // ex and ey of its box columns and rows from shared memory (one exp each per block) instead of
 // one exp per point; boxes wider than GX_MAX fall back to the direct form.
@@ -101,12 +180,16 @@ __device__ __forceinline__ void gauss_axis_tables(const AtomBox& B, double h1, d
 // of b, and its last bits, vary from run to run; the gather below is the deterministic form).
 __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double h2, double h3,
                                                       const AtomBox* boxes, Gauss q, double* b,
-                                                      double* e_self_part, int max_planes) {
+                                                      double* e_self_part, int max_planes, const VTable vt) {
     const int J = blockIdx.x, pl = blockIdx.y;
     const AtomBox B = boxes[J];
     __shared__ double ex[GX_MAX], ey[GX_MAX];
+    __shared__ double vc[VT_MAX][VT_D + 1];
     const bool tables = B.len[0] <= GX_MAX && B.len[1] <= GX_MAX;
-    if (pl < B.len[2]) gauss_axis_tables(B, h1, h2, q, ex, ey);
+    if (pl < B.len[2]) {
+        gauss_axis_tables(B, h1, h2, q, ex, ey);
+        vt_load(vt, vc);
+    }
     __syncthreads();
     double acc = 0.0;
     if (pl < B.len[2]) {
@@ -114,23 +197,24 @@ __global__ void __launch_bounds__(256) k_pseudocharge(Dims d, double h1, double 
         const double dz = k * h3 - B.R[2];
         const double cz = -B.Z * q.norm * exp(-dz * dz * q.inv2s2);
         const int kw = wrap_index(k, d.n3);
-        const int nxy = B.len[0] * B.len[1];
         const double rc2 = q.rc * q.rc;
-        for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
-            const int jj = t / B.len[0];
-            const int ii = t - jj * B.len[0];
-            const int i = B.lo[0] + ii;
+        // a warp per box row, its lanes along the row: the wrapped x index advances by 32
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        for (int jj = warp; jj < B.len[1]; jj += nwarps) {
             const int j = B.lo[1] + jj;
-            const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 <= rc2) {
-                const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
-                if (b) {
-                    const long long idx = wrap_index(i, d.n1) +
-                                          (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
-                    atomicAdd(b + idx, bj);
+            const double dy = j * h2 - B.R[1];
+            const long long row = (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+            int iw = wrap_index(B.lo[0] + lane, d.n1);
+            for (int ii = lane; ii < B.len[0]; ii += 32) {
+                const double dx = (B.lo[0] + ii) * h1 - B.R[0];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 <= rc2) {
+                    const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
+                    if (b) atomicAdd(b + row + iw, bj);
+                    acc += bj * vt_V(vt, vc, r2, B.Z, q);
                 }
-                acc += bj * gauss_V(sqrt(r2), B.Z, q);
+                iw += 32;
+                while (iw >= d.n1) iw -= d.n1;
             }
         }
     }
@@ -295,12 +379,16 @@ static void build_images(of_grid* g, const AtomSet& a, IonImage*& d_img, int*& d
 // Block (J, plane): dV * sum grad b_J (phi - V_J) over the plane, 3 components.
 __global__ void __launch_bounds__(256) k_forces(Dims d, double h1, double h2, double h3,
                                                 const AtomBox* boxes, Gauss q, const double* phi,
-                                                double* part, int max_planes) {
+                                                double* part, int max_planes, const VTable vt) {
     const int J = blockIdx.x, pl = blockIdx.y;
     const AtomBox B = boxes[J];
     __shared__ double ex[GX_MAX], ey[GX_MAX];
+    __shared__ double vc[VT_MAX][VT_D + 1];
     const bool tables = B.len[0] <= GX_MAX && B.len[1] <= GX_MAX;
-    if (pl < B.len[2]) gauss_axis_tables(B, h1, h2, q, ex, ey);
+    if (pl < B.len[2]) {
+        gauss_axis_tables(B, h1, h2, q, ex, ey);
+        vt_load(vt, vc);
+    }
     __syncthreads();
     double f[3] = {0.0, 0.0, 0.0};
     if (pl < B.len[2]) {
@@ -308,25 +396,28 @@ __global__ void __launch_bounds__(256) k_forces(Dims d, double h1, double h2, do
         const double dz = k * h3 - B.R[2];
         const double cz = -B.Z * q.norm * exp(-dz * dz * q.inv2s2);
         const int kw = wrap_index(k, d.n3);
-        const int nxy = B.len[0] * B.len[1];
         const double rc2 = q.rc * q.rc;
         const double inv_s2 = 2.0 * q.inv2s2;
-        for (int t = threadIdx.x; t < nxy; t += blockDim.x) {
-            const int jj = t / B.len[0];
-            const int ii = t - jj * B.len[0];
-            const int i = B.lo[0] + ii;
+        // a warp per box row, its lanes along the row: the wrapped x index advances by 32
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+        for (int jj = warp; jj < B.len[1]; jj += nwarps) {
             const int j = B.lo[1] + jj;
-            const double dx = i * h1 - B.R[0], dy = j * h2 - B.R[1];
-            const double r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 <= rc2) {
-                const long long idx = wrap_index(i, d.n1) +
-                                      (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
-                const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
-                // grad b_J = -b_J (x - R_J) / sigma^2
-                const double w = -bj * inv_s2 * (phi[idx] - gauss_V(sqrt(r2), B.Z, q));
-                f[0] += w * dx;
-                f[1] += w * dy;
-                f[2] += w * dz;
+            const double dy = j * h2 - B.R[1];
+            const long long row = (long long)d.n1 * (wrap_index(j, d.n2) + (long long)d.n2 * kw);
+            int iw = wrap_index(B.lo[0] + lane, d.n1);
+            for (int ii = lane; ii < B.len[0]; ii += 32) {
+                const double dx = (B.lo[0] + ii) * h1 - B.R[0];
+                const double r2 = dx * dx + dy * dy + dz * dz;
+                if (r2 <= rc2) {
+                    const double bj = tables ? cz * (ex[ii] * ey[jj]) : gauss_b(r2, B.Z, q);
+                    // grad b_J = -b_J (x - R_J) / sigma^2
+                    const double w = -bj * inv_s2 * (phi[row + iw] - vt_V(vt, vc, r2, B.Z, q));
+                    f[0] += w * dx;
+                    f[1] += w * dy;
+                    f[2] += w * dz;
+                }
+                iw += 32;
+                while (iw >= d.n1) iw -= d.n1;
             }
         }
     }
@@ -612,7 +703,7 @@ static void pseudocharge_impl(of_grid* g, const of_system* sys, double* b, doubl
         double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + a.n_atoms + 8));
         OF_CUDA(cudaMemsetAsync(part, 0, sizeof(double) * nparts, g->stream));
         launch(k_pseudocharge, dim3(a.n_atoms, a.max_planes), 256, g->stream, g->d, g->h[0], g->h[1],
-               g->h[2], a.d_boxes, q, (double*)nullptr, part, a.max_planes);
+               g->h[2], a.d_boxes, q, (double*)nullptr, part, a.max_planes, vtable(sys));
         OF_LAUNCH_CHECK();
         double* per_atom = part + nparts;
         launch(k_sum_planes, (a.n_atoms + 127) / 128, 128, g->stream, a.n_atoms, a.max_planes, 1,
@@ -753,7 +844,7 @@ void forces(of_grid* g, const of_system* sys, const double* phi, double* F) {
     double* part = (double*)ws(g, WS_S15, sizeof(double) * (nparts + 3 * (size_t)M + 8));
     double* per_atom = part + nparts;
     launch(k_forces, dim3(M, a.max_planes), 256, g->stream, g->d, g->h[0], g->h[1], g->h[2],
-                                                         a.d_boxes, q, phi, part, a.max_planes);
+                                                         a.d_boxes, q, phi, part, a.max_planes, vtable(sys));
     OF_LAUNCH_CHECK();
     launch(k_sum_planes, (3 * M + 127) / 128, 128, g->stream, M, a.max_planes, 3, part, g->dV,
                                                             per_atom);
