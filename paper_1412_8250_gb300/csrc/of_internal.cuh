@@ -266,6 +266,7 @@ enum Slot {
     WS_NLCGP,    // preconditioned NLCG: the gradient in FP32, its V-cycle, the FP64 direction
     WS_FGM,      // flexible GMRES: Arnoldi and preconditioned vectors
     WS_IMG,      // periodic images of the ions and their lists per z-slab (nuclear charge)
+    WS_FF,       // a field split into double-float pairs (the mixed form's residual sweeps)
     WS_NSLOTS
 };
 

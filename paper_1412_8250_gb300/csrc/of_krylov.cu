@@ -23,6 +23,7 @@
 #include <mutex>
 #include <type_traits>
 
+#include "of_ff.cuh"
 #include "of_krylov.cuh"
 
 namespace of {
@@ -476,9 +477,66 @@ static KState iterate_pcg(of_grid* g, int st_off, float* x, float* r, float* pa,
     return h;
 }
 
+// r = b - A x like OpResidual, with the Laplacian of x from its double-float split xf, summed on
+// the FP32 pipes and returned to FP64 for the rest: within ~1e-13 of the FP64 sweep's value
+// relative to the largest tap term, in half its time (the FP64 sweep is bound by GB300's FP64
+// rate).
+template <typename T64>
+struct OpResidualFF {
+    using TF = typename std::conditional<KT<T64>::cplx, FF2, FF>::type;
+    static constexpr int kClass = KT<T64>::cplx ? PC_COCG_F64 : PC_STENCIL_F64, kWords = 3;
+    const TF* xf;
+    const T64* x;
+    const T64* b;
+    T64* r;
+    KState* st;
+    RedCtx rc;
+    double a;
+    double2 Q;
+    double acc[3];
+    __device__ bool begin() { acc[0] = acc[1] = acc[2] = 0.0; return true; }
+    __device__ TF load(long long i) const { return xf[i]; }
+    __device__ void store(long long i, TF, TF lap) {
+        const T64 rv = vsub(b[i], apply_A(x[i], ff_to(lap), a, Q));
+        r[i] = rv;
+        acc[0] += hn2(rv);
+        const double2 s = bil(rv, rv);
+        acc[1] += s.x;
+        acc[2] += s.y;
+    }
+    __device__ void end() {
+        if (grid_reduce<3>(acc, rc.partials, rc.counter, st->red) &&
+            threadIdx.x == 0 && threadIdx.y == 0) {
+            st->rr = acc[0];
+            st->rho_re = acc[1];
+            st->rho_im = acc[2];
+            st->beta_re = st->beta_im = 0.0;
+            st->breakdown = 0.0;
+            st->zshift = 0.0;
+            st->done = (acc[0] <= st->tol2) ? 1.0 : 0.0;
+        }
+    }
+};
+
+// The double-float sweep's accuracy floor (~1e-13 of the largest tap term) sits well below the
+// tolerances it serves; tighter solves keep the FP64 sweep.
+constexpr double FF_MIN_TOL = 1e-11;
+
+// ff: the Laplacian in double-float arithmetic (the mixed-precision form's refinement
+// residuals); else in FP64
 template <typename T>
-static void residual(of_grid* g, int st_off, const T* x, const T* b, T* r, double a, double2 Q) {
+static void residual(of_grid* g, int st_off, const T* x, const T* b, T* r, double a, double2 Q,
+                     bool ff = false) {
     constexpr int RY = KT<T>::cplx ? 1 : 2;
+    if (ff) {
+        using TF = typename OpResidualFF<T>::TF;
+        const long long n = g->d.n;
+        TF* xf = (TF*)ws(g, WS_FF, sizeof(TF) * (size_t)n);
+        launch(k_ff_split<T, TF>, vec_blocks(n), 256, g->stream, n, x, xf);
+        OpResidualFF<T> op{xf, x, b, r, kstate(g, st_off), red_ctx(g, 0), a, Q};
+        launch_stencil<TF, RY>(g, ff_weights(g->w64), op);
+        return;
+    }
     OpResidual<T> op{x, b, r, kstate(g, st_off), red_ctx(g, 0), (typename KT<T>::R)a, Q};
     launch_stencil<T, RY>(g, g->w64, op);
 }
@@ -495,7 +553,8 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
     launch(k_init_state, 1, 1, g->stream, st, o.max_iter);
     launch(k_norm_to_tol<T64>, vec_blocks(n), 256, g->stream, n, b, o.tol, st, red_ctx(g, 0));
     OF_LAUNCH_CHECK();
-    residual<T64>(g, KS64, x, b, r, a, Q);
+    const bool ff_res = o.precision == OF_F32 && o.tol >= FF_MIN_TOL;
+    residual<T64>(g, KS64, x, b, r, a, Q, ff_res);
     KState h;
     fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
     const double bb = h.tol2 / (o.tol * o.tol);
@@ -584,7 +643,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             if (hi.done == -1.0) {
                 // one read-back for both states: the inner pass and the true residual after it
                 // (a pass that broke down at its start has a zero correction)
-                residual<T64>(g, KS64, x, b, r, a, Q);
+                residual<T64>(g, KS64, x, b, r, a, Q, ff_res);
                 static_assert(KS32 > KS64, "KState layout");
                 double both[KS32 - KS64 + KSTATE_DOUBLES];
                 fetch_scalars(g, KS64, KS32 - KS64 + KSTATE_DOUBLES, both);
@@ -614,7 +673,7 @@ static of_status solve_formed(of_grid* g, T64* x, double a, double2 Q, const Kry
             }
         }
         if (!residual_done) {
-            residual<T64>(g, KS64, x, b, r, a, Q);   // true residual; restarts the recurrence
+            residual<T64>(g, KS64, x, b, r, a, Q, ff_res);   // true residual; restarts the recurrence
             fetch_scalars(g, KS64, KSTATE_DOUBLES, (double*)&h);
         }
         ++refinements;

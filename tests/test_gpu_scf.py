@@ -385,7 +385,7 @@ def test_ground_states_are_bitwise_reproducible():
     # solves, the two-shift NLCG preconditioner) on two handles, and inside a batched call
     # beside another cell, gives the same bits
     cell = W.al4_lr_cell(points_per_cell=16)
-    other = W.al4_cell(points_per_cell=16)
+    other = W.fcc_supercell((1, 1, 1), points_per_cell=16, displacement=0.05, seed=7, sigma=1.2, rc=10.0)
     stream = torch.cuda.current_stream()
     o = _bench_like_opts(B.of_default_scf_opts())
     o.precision = B.OF_F32
