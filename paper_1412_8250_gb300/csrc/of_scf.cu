@@ -279,6 +279,17 @@ __global__ void k_step(long long n, double* u, const double* d, double* phi, con
     }
 }
 
+// Starting points of the next line's Poisson solves from the last ones: with u = c (u_p + s d_p)
+// and d = z + xi d_p, linearity gives phi(u d) = xi c (phi(u_p d_p) + s phi(d_p^2)) + phi(u z) and
+// phi(d^2) = xi^2 phi(d_p^2) + (terms in z); the known parts start the solves.
+__global__ void k_line_guess(long long n, double* B, double* C, double a1, double s, double a2) {
+    GRID_LOOP(i, n) {
+        const double Ci = C[i];
+        B[i] = a1 * (B[i] + s * Ci);
+        C[i] = a2 * Ci;
+    }
+}
+
 __global__ void k_scale(long long n, double* x, double a) {
     GRID_LOOP(i, n) x[i] *= a;
 }
@@ -885,7 +896,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
     OF_LAUNCH_CHECK();
     poisson_into(g, v.rho, nullptr, phi, po, st);
 
-    double rr_prev = 0.0, s_prev = 1e-2;
+    double rr_prev = 0.0, s_prev = 1e-2, c_prev = 0.0;
     bool converged = false;
     for (int q = 0; q <= max_iter; ++q) {
         launch_stencil<double, 2>(g, g->w64,
@@ -949,6 +960,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         // to the full tolerance.  They are solved to min(1e-5, 1e-2 x the normalised gradient
         // norm), which resolves dE/ds well within the line search's tolerance; if the line
         // search finds no decrease, the step is repeated with both solved to the full tolerance.
+        launch(k_line_guess, nb, 256, g->stream, n, v.B, v.C, xi * c_prev, s_prev, xi * xi);
         const double ud = m[1] * dV, dd = m[2] * dV, uu = m[3] * dV;
         double dLd = 0, uLd = 0, uLu_ = 0, M00 = 0, M01 = 0, M02 = 0, M11 = 0, M12 = 0, M22 = 0;
         double N0 = 0, N1 = 0, N2 = 0, Vq0 = 0, Vq1 = 0, Vq2 = 0, bD = 0;
@@ -1043,6 +1055,7 @@ static bool nlcg(of_grid* g, const FnParams& fn, double Ne, ScfVecs& v, double* 
         std::swap(v.d, v.dp);
         rr_prev = rr;
         s_prev = s;
+        c_prev = c;
         st.nlcg += 1;
     }
     return converged;
