@@ -78,12 +78,14 @@ typedef struct {
     double inner_tol;
     int check_every;
     int no_multigrid;      /* 1: plain FP32 CG inner solve for Poisson (no V-cycle) */
-    of_precond* precond;   /* non-NULL with OF_F32: the FP32 inner solve is flexible CG
-                              (Poisson) or flexible COCG (shifted kernel systems, the network
-                              applied to the real and imaginary parts of the residual)
-                              preconditioned by this network, in place of the V-cycle */
+    of_precond* precond;   /* non-NULL with OF_F32, in place of the V-cycle: the FP32 inner
+                              solve is flexible CG preconditioned by this network (Poisson),
+                              or flexible GMRES(8) preconditioned by a few flexible-CG steps
+                              with this network on -L_h + |Q| / a, applied to the real and
+                              imaginary parts of each Arnoldi vector (shifted kernel systems;
+                              train the network for that shift, of_precond_set_shift) */
     double precond_theta;  /* a network direction z is kept when cos(r, z) > theta, else the
-                              step is plain CG; default 0.3 */
+                              (inner) flexible-CG step is the plain CG step; default 0.3 */
 } of_solve_opts;
 
 typedef struct {
