@@ -1442,16 +1442,21 @@ def main():
                     "bytes_model": "every field a fused sweep reads or writes, once per point of "
                                    "its level (CG iteration 10 words, Chebyshev step 6, residual "
                                    "3, transfers 1-2 per fine point), halos not counted"}
-        if dom["kernel"] == "mg_pcg_pass_graph" and prof:
-            # the same time against the CG iterations' own bytes only (10 FP32 words per point
-            # per iteration), the V-cycle's sweeps left out
-            passes = sum(p["launches"] for p in prof if p["kernel"] == "mg_pcg_pass_graph")
-            its = res.poisson_iterations * args.steps / max(1, passes)
-            cg_bytes = its * 40.0 * cell.n_points
+        if dom["kernel"] in ("mg_pcg_pass_graph", "mg_cocg_pass_graph") and prof:
+            # the same time against the Krylov iterations' own bytes only (10 words per point
+            # per iteration: FP32 for CG, complex FP32 for COCG), the V-cycle's sweeps left out
+            cocg = dom["kernel"] == "mg_cocg_pass_graph"
+            passes = sum(p["launches"] for p in prof if p["kernel"] == dom["kernel"])
+            its = (res.kernel_iterations if cocg else res.poisson_iterations) * args.steps / max(1, passes)
+            cg_bytes = its * (80.0 if cocg else 40.0) * cell.n_points
             roofline["cg_iterations_per_launch"] = its
             roofline["frac_cg_bytes_only"] = cg_bytes / (dom["mean_ms"] * 1e-3) / 1e9 / peak
             roofline["note"] = ("latency-bound: at 96^3 every field stays in L2 and one "
-                                "preconditioned iteration is a chain of ~17 dependent launches")
+                                "preconditioned iteration is a chain of ~17 dependent launches"
+                                + ("; up to four shifted systems are solved at once (a chain of "
+                                   "twin handles), so a pass's events also span the passes "
+                                   "beside it and its mean duration overstates its own time"
+                                   if cocg else ""))
     roofline_320 = roofline_320_f64 = alu = None
     if stencil320:
         roofline_320 = {"kernel": "stencil2_kernel (of_laplacian_apply, FP32, order 12, 320^3)",
