@@ -54,6 +54,10 @@ GOLDEN_AL108 = os.path.join(ROOT, "tests", "golden", "al108_wt.json")
 # DRAM bytes (read + write) of one FP32 order-12 sweep of a 320^3 grid by the fast-path stencil,
 # from the ncu capture summarised in profiles/stencil_fp32_320.md (145.9 + 91.9 MB)
 STENCIL320_DRAM_BYTES = 237.8e6
+# DRAM bytes that one V-cycle plus one COCG iteration of the 96^3 complex FP32 pass moves,
+# summed over its kernels launched one by one from a cold L2 (ncu; the kernels' table is in
+# profiles/mg_cocg_pass_kernels_96.md)
+COCG96_DRAM_BYTES_PER_ITERATION = 167e6
 # algorithmic FP64 arithmetic of one order-12 Laplacian point: 3 axes x 12 neighbours + the
 # centre, one multiply-add (2 flops) each
 STENCIL_F64_FLOPS_PER_POINT = 2 * (3 * 12 + 1)
@@ -1451,6 +1455,13 @@ def main():
             cg_bytes = its * (80.0 if cocg else 40.0) * cell.n_points
             roofline["cg_iterations_per_launch"] = its
             roofline["frac_cg_bytes_only"] = cg_bytes / (dom["mean_ms"] * 1e-3) / 1e9 / peak
+            if cocg and cell.n_points == 96 ** 3:
+                roofline["traffic"] = its * COCG96_DRAM_BYTES_PER_ITERATION
+                roofline["traffic_note"] = (
+                    "ncu dram__bytes_read.sum + dram__bytes_write.sum of the pass's kernels "
+                    "launched one by one from a cold L2 (OF_NO_GRAPHS=1, 28 iterations of the "
+                    "first kernel map: 167 MB per V-cycle + COCG iteration), scaled by the "
+                    "iterations per pass; inside the graphs the fields stay in L2")
             roofline["note"] = ("latency-bound: at 96^3 every field stays in L2 and one "
                                 "preconditioned iteration is a chain of ~17 dependent launches"
                                 + ("; up to four shifted systems are solved at once (a chain of "
