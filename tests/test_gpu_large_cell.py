@@ -1,0 +1,161 @@
+"""The 3999-atom cell at full size: a 10x10x10 FCC supercell with the centre site removed,
+320^3 grid (32.8 M points), WT-type kernel functional, ground state + forces in the mixed form
+with the benchmark's options.
+
+An oracle ground state of this cell would take days of host time, so the GPU's result is
+checked on what the oracle computes one sample at a time, and on properties that hold at any
+size:
+  - the nuclear charge b (Sec. 3.2) at sampled grid points: the oracle's Gaussian charge of
+    every ion within r_c of the point, against of_pseudocharge on the whole grid;
+  - the Poisson equation -(1/4 pi) L_h phi = u^2 + b (Sec. 3.3.1, mean removed) at the sampled
+    points, L_h from the oracle's order-12 weights (Eq. FD:Laplacian);
+  - the energy terms of Eq. GroundStateEnergy that are integrals over the grid (TF, vW, xc,
+    electrostatic) from the oracle's energy densities and Laplacian on the GPU's fields;
+  - the self energy against the oracle's per-ion integral on sampled ions (with sigma = 1.2 bohr
+    on h = 0.2375 bohr and the charge cut where it is ~1e-15 of its peak, every ion's integral is
+    the same to rounding, so the total is the number of ions times one ion's value);
+  - the forces (Eq. Force:Nuclei) on two sampled ions, one beside the vacancy: the oracle's
+    electrostatic part from the GPU's phi plus its overlap-correction force (App. B) over every
+    ion within the correction's cutoff;
+  - the constraint int u^2 = N_e, u > 0, a mean-free phi, the momentum balance of the forces and
+    the total energy as the sum of its terms.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_1412_8250_gb300 import binding as B, functionals as Fn, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+N_SAMPLES = 4096
+
+
+@pytest.fixture(scope="module")
+def large():
+    import bench
+    cell = W.al3999_cell()
+    _, h0, _, fn, o = bench.make_case(torch, B, Fn, W, "mixed")
+    B.of_grid_destroy(h0)
+    h = B.of_grid_create(cell.n, cell.L, 6, torch.cuda.current_stream())
+    try:
+        sysd = B.make_system(cell.R, cell.Z, cell.sigma, cell.rc)
+        u = torch.ones(cell.shape, dtype=torch.float64, device="cuda")
+        phi = torch.zeros_like(u)
+        res = B.of_scf_ground_state(h, sysd, fn, o, u, phi)
+        F = B.of_forces(h, sysd, u, phi)
+        b = torch.empty_like(u)
+        e_self = B.of_pseudocharge(h, sysd, b)
+        out = dict(cell=cell, fn=fn, res=res, F=F, e_self=e_self, u=u.cpu().numpy(),
+                   phi=phi.cpu().numpy(), b=b.cpu().numpy())
+    finally:
+        B.of_grid_destroy(h)
+    rng = np.random.default_rng(77)
+    n3, n2, n1 = cell.shape
+    flat = rng.integers(0, n1 * n2 * n3, size=N_SAMPLES)
+    # and the grid points nearest to a few ions, where b peaks
+    near = np.rint(cell.R[:: max(1, cell.n_atoms // 64)] / (np.array(cell.L) / np.array(cell.n)))
+    near = near.astype(np.int64) % np.array(cell.n)
+    k = np.concatenate([flat // (n1 * n2), near[:, 2]])
+    j = np.concatenate([(flat // n1) % n2, near[:, 1]])
+    i = np.concatenate([flat % n1, near[:, 0]])
+    out["idx"] = (k, j, i)
+    out["grid"] = O.Grid(cell.n, cell.L, 6)
+    return out
+
+
+def _oracle_b_at(cell, grid, k, j, i):
+    """b at grid points (k, j, i) from the oracle's Gaussian charge, every ion within r_c
+    (r_c < L/2, so at most one image of each ion reaches a point)."""
+    L = np.array(cell.L)
+    x = np.stack([i * grid.h[0], j * grid.h[1], k * grid.h[2]], axis=1)
+    out = np.zeros(len(i))
+    for s in range(0, len(i), 256):
+        d = x[s:s + 256, None, :] - cell.R[None, :, :]
+        d -= L * np.round(d / L)
+        r = np.sqrt(np.sum(d * d, axis=2))
+        out[s:s + 256] = np.sum(np.where(r <= cell.rc, O.gaussian_b(r, cell.Z[None, :], cell.sigma),
+                                         0.0), axis=1)
+    return out
+
+
+def _laplacian_at(f, grid, k, j, i):
+    """(L_h f) at grid points (k, j, i), from the oracle's weights (w_0 is half of one axis's
+    centre coefficient: sum_{p=0..N} w_p (f(x + p h) + f(x - p h)) per axis)."""
+    n1, n2, n3 = grid.n
+    w = [O.fd_laplacian_weights(6, grid.h[a]) for a in range(3)]
+    out = 2.0 * (w[0][0] + w[1][0] + w[2][0]) * f[k, j, i]
+    for p in range(1, 7):
+        out = out + w[0][p] * (f[k, j, (i + p) % n1] + f[k, j, (i - p) % n1])
+        out = out + w[1][p] * (f[k, (j + p) % n2, i] + f[k, (j - p) % n2, i])
+        out = out + w[2][p] * (f[(k + p) % n3, j, i] + f[(k - p) % n3, j, i])
+    return out
+
+
+def test_large_cell_converges_with_its_invariants(large):
+    cell, res, u, phi, F = large["cell"], large["res"], large["u"], large["phi"], large["F"]
+    assert res.converged
+    dV = large["grid"].dV
+    assert abs(np.sum(u * u) * dV - cell.n_electrons) < 1e-9 * cell.n_electrons
+    assert u.min() > 0
+    assert abs(phi.mean()) < 1e-10 * np.abs(phi).max()
+    assert np.max(np.abs(F.sum(0))) < 1e-4
+    terms = sum(getattr(res, "e_" + t) for t in ("tf", "vw", "lr", "xc", "es", "self", "corr"))
+    assert abs(terms - res.energy) <= 1e-9 * abs(res.energy)
+
+
+def test_large_cell_nuclear_charge_at_sampled_points(large):
+    k, j, i = large["idx"]
+    ref = _oracle_b_at(large["cell"], large["grid"], k, j, i)
+    got = large["b"][k, j, i]
+    assert np.abs(ref).max() > 0.05   # the samples include ion centres
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
+
+
+def test_large_cell_poisson_equation_at_sampled_points(large):
+    u, phi, b, grid = large["u"], large["phi"], large["b"], large["grid"]
+    k, j, i = large["idx"]
+    f = u * u + b
+    mean = f.mean()
+    lhs = -_laplacian_at(phi, grid, k, j, i) / (4.0 * np.pi)
+    rhs = f[k, j, i] - mean
+    assert np.max(np.abs(lhs - rhs)) <= 1e-6 * np.abs(f).max()
+
+
+def test_large_cell_energy_terms_from_the_oracle_densities(large):
+    cell, res, u, phi, b, grid = (large[x] for x in ("cell", "res", "u", "phi", "b", "grid"))
+    rho = u * u
+    lam = large["fn"].lambda_
+    ref = {"tf": O.integrate(O.tf_energy_density(rho), grid),
+           "xc": O.integrate(O.xc_energy_density(rho), grid),
+           "vw": O.integrate(-0.5 * lam * u * O.laplacian(u, grid), grid),
+           "es": O.integrate(0.5 * (rho + b) * phi, grid)}
+    for t, v in ref.items():
+        assert abs(getattr(res, "e_" + t) - v) / cell.n_atoms <= 1e-10, (t, getattr(res, "e_" + t), v)
+
+
+def test_large_cell_self_energy_per_ion(large):
+    cell, grid = large["cell"], large["grid"]
+    pick = np.arange(0, cell.n_atoms, cell.n_atoms // 8)[:8]
+    per_ion = O.self_energy(cell.R[pick], cell.Z[pick], cell.sigma, cell.rc, grid) / len(pick)
+    assert abs(large["e_self"] - cell.n_atoms * per_ion) <= 1e-10 * abs(cell.n_atoms * per_ion)
+    assert abs(large["res"].e_self - large["e_self"]) <= 1e-10 * abs(large["e_self"])
+
+
+def test_large_cell_forces_on_sampled_ions(large):
+    cell, grid, phi, F = large["cell"], large["grid"], large["phi"], large["F"]
+    L = np.array(cell.L)
+    centre = 0.5 * L
+    d0 = cell.R - centre
+    beside_vacancy = int(np.argmin(np.sum(d0 * d0, axis=1)))
+    cutoff = 14.0 * cell.sigma   # the oracle's correction cutoff (erfc(7) ~ 4e-23 beyond it)
+    for s in (0, beside_vacancy):
+        fe = O.forces(phi, cell.R[s:s + 1], cell.Z[s:s + 1], cell.sigma, cell.rc, grid,
+                      include_correction=False)[0]
+        d = cell.R - cell.R[s]
+        d -= L * np.round(d / L)
+        near = [m for m in np.nonzero(np.sqrt(np.sum(d * d, axis=1)) <= cutoff + 1.0)[0] if m != s]
+        sub = [s] + near
+        fc = O.repulsive_correction_forces(cell.R[sub], cell.Z[sub], cell.sigma, cell.L, cutoff)[0]
+        assert np.max(np.abs(F[s] - (fe + fc))) <= 1e-8, (s, F[s], fe + fc)
