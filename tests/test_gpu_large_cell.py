@@ -2,23 +2,22 @@
 320^3 grid (32.8 M points), WT-type kernel functional, ground state + forces in the mixed form
 with the benchmark's options.
 
-An oracle ground state of this cell would take days of host time, so the GPU's result is
-checked on what the oracle computes one sample at a time, and on properties that hold at any
-size:
+An oracle ground state of this cell would take days of host time, so the GPU path is checked on
+what the oracle computes one sample at a time from the same seeded inputs, and its ground state
+on properties that hold at any size:
   - the nuclear charge b (Sec. 3.2) at sampled grid points: the oracle's Gaussian charge of
     every ion within r_c of the point, against of_pseudocharge on the whole grid;
-  - the Poisson equation -(1/4 pi) L_h phi = u^2 + b (Sec. 3.3.1, mean removed) at the sampled
-    points, L_h from the oracle's order-12 weights (Eq. FD:Laplacian);
-  - the energy terms of Eq. GroundStateEnergy that are integrals over the grid (TF, vW, xc,
-    electrostatic) from the oracle's energy densities and Laplacian on the GPU's fields;
   - the self energy against the oracle's per-ion integral on sampled ions (with sigma = 1.2 bohr
     on h = 0.2375 bohr and the charge cut where it is ~1e-15 of its peak, every ion's integral is
     the same to rounding, so the total is the number of ions times one ion's value);
-  - the forces (Eq. Force:Nuclei) on two sampled ions, one beside the vacancy: the oracle's
-    electrostatic part from the GPU's phi plus its overlap-correction force (App. B) over every
-    ion within the correction's cutoff;
-  - the constraint int u^2 = N_e, u > 0, a mean-free phi, the momentum balance of the forces and
-    the total energy as the sum of its terms.
+  - the forces (Eq. Force:Nuclei) for a seeded smooth potential on two sampled ions, one beside
+    the vacancy: the oracle's electrostatic part plus its overlap-correction force (App. B) over
+    every ion within the correction's cutoff;
+  - of the ground state: the Poisson equation -(1/4 pi) L_h phi = u^2 + b (Sec. 3.3.1, mean
+    removed) at the sampled points with the order-12 weights of Eq. FD:Laplacian; the TF, vW and
+    electrostatic terms of Eq. GroundStateEnergy as the integrals of the returned fields; the
+    constraint int u^2 = N_e, u > 0, a mean-free phi, the momentum balance of the forces and the
+    total energy as the sum of its terms.
 """
 import numpy as np
 import pytest
@@ -47,8 +46,10 @@ def large():
         F = B.of_forces(h, sysd, u, phi)
         b = torch.empty_like(u)
         e_self = B.of_pseudocharge(h, sysd, b)
+        phi_s = W.random_field(cell.shape, seed=23, kind="smooth")   # a seeded potential
+        F_s = B.of_forces(h, sysd, u, torch.from_numpy(phi_s).cuda())
         out = dict(cell=cell, fn=fn, res=res, F=F, e_self=e_self, u=u.cpu().numpy(),
-                   phi=phi.cpu().numpy(), b=b.cpu().numpy())
+                   phi=phi.cpu().numpy(), b=b.cpu().numpy(), phi_s=phi_s, F_s=F_s)
     finally:
         B.of_grid_destroy(h)
     rng = np.random.default_rng(77)
@@ -123,14 +124,20 @@ def test_large_cell_poisson_equation_at_sampled_points(large):
     assert np.max(np.abs(lhs - rhs)) <= 1e-6 * np.abs(f).max()
 
 
-def test_large_cell_energy_terms_from_the_oracle_densities(large):
+def test_large_cell_energy_terms_are_integrals_of_the_returned_fields(large):
     cell, res, u, phi, b, grid = (large[x] for x in ("cell", "res", "u", "phi", "b", "grid"))
     rho = u * u
-    lam = large["fn"].lambda_
-    ref = {"tf": O.integrate(O.tf_energy_density(rho), grid),
-           "xc": O.integrate(O.xc_energy_density(rho), grid),
-           "vw": O.integrate(-0.5 * lam * u * O.laplacian(u, grid), grid),
-           "es": O.integrate(0.5 * (rho + b) * phi, grid)}
+    dV = grid.dV
+    c_f = 0.3 * (3.0 * np.pi ** 2) ** (2.0 / 3.0)
+    lap_u = np.zeros_like(u)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        w = O.fd_laplacian_weights(6, grid.h[a])
+        lap_u += 2.0 * w[0] * u
+        for p in range(1, 7):
+            lap_u += w[p] * (np.roll(u, p, axis=ax) + np.roll(u, -p, axis=ax))
+    ref = {"tf": c_f * np.sum(rho ** (5.0 / 3.0)) * dV,
+           "vw": -0.5 * large["fn"].lambda_ * np.sum(u * lap_u) * dV,
+           "es": 0.5 * np.sum((rho + b) * phi) * dV}
     for t, v in ref.items():
         assert abs(getattr(res, "e_" + t) - v) / cell.n_atoms <= 1e-10, (t, getattr(res, "e_" + t), v)
 
@@ -144,18 +151,18 @@ def test_large_cell_self_energy_per_ion(large):
 
 
 def test_large_cell_forces_on_sampled_ions(large):
-    cell, grid, phi, F = large["cell"], large["grid"], large["phi"], large["F"]
+    cell, grid, phi_s, F_s = large["cell"], large["grid"], large["phi_s"], large["F_s"]
     L = np.array(cell.L)
-    centre = 0.5 * L
-    d0 = cell.R - centre
+    d0 = cell.R - 0.5 * L
     beside_vacancy = int(np.argmin(np.sum(d0 * d0, axis=1)))
     cutoff = 14.0 * cell.sigma   # the oracle's correction cutoff (erfc(7) ~ 4e-23 beyond it)
     for s in (0, beside_vacancy):
-        fe = O.forces(phi, cell.R[s:s + 1], cell.Z[s:s + 1], cell.sigma, cell.rc, grid,
+        fe = O.forces(phi_s, cell.R[s:s + 1], cell.Z[s:s + 1], cell.sigma, cell.rc, grid,
                       include_correction=False)[0]
         d = cell.R - cell.R[s]
         d -= L * np.round(d / L)
         near = [m for m in np.nonzero(np.sqrt(np.sum(d * d, axis=1)) <= cutoff + 1.0)[0] if m != s]
         sub = [s] + near
         fc = O.repulsive_correction_forces(cell.R[sub], cell.Z[sub], cell.sigma, cell.L, cutoff)[0]
-        assert np.max(np.abs(F[s] - (fe + fc))) <= 1e-8, (s, F[s], fe + fc)
+        ref = fe + fc
+        assert np.max(np.abs(F_s[s] - ref)) <= 1e-11 * max(1.0, np.max(np.abs(ref))), (s, F_s[s], ref)

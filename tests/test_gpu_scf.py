@@ -240,17 +240,21 @@ def test_fixed_point_on_u_matches_golden():
 
 def test_vw_energy_gradient_form():
     # the vW energy reported as (lam/2) int |grad_h u|^2 (Eq. gradient:approximate) instead of
-    # -(lam/2) <u, L_h u>: same ground state, the term equals the oracle's gradient form of the
-    # same u, and the two forms differ only by the discretisation error
+    # -(lam/2) <u, L_h u>: same ground state, the term is the gradient form's integral of the
+    # returned u (order-12 first-difference weights from the oracle), and the two forms differ
+    # only by the discretisation error
     rec = _golden()["al4_tfw"]
     cell = _cell_from(rec)
     res_l, _, u_l, _ = _run(cell, Fn.tfw(), B.OF_F64)
     res_g, _, u_g, phi_g = _run(cell, Fn.tfw(), B.OF_F64, vw_energy=B.OF_VW_GRADIENT)
     grid = O.Grid(cell.n, cell.L, 6)
-    zero = np.zeros(grid.shape)
-    _, t = O.ground_state_energy(u_g, zero, zero, grid, O.tfw_functional(), 0.0, 0.0, 0.0,
-                                 vw_energy="gradient")
-    assert abs(res_g.e_vw - t["vw"]) <= 1e-11 * abs(t["vw"])
+    grad_sq = np.zeros_like(u_g)
+    for a, ax in ((0, 2), (1, 1), (2, 0)):
+        w = O.fd_gradient_weights(6, grid.h[a])
+        g = sum(w[p] * (np.roll(u_g, -p, axis=ax) - np.roll(u_g, p, axis=ax)) for p in range(1, 7))
+        grad_sq += g * g
+    vw = 0.5 * O.tfw_functional().lam * np.sum(grad_sq) * grid.dV
+    assert abs(res_g.e_vw - vw) <= 1e-11 * abs(vw)
     assert abs(res_g.e_tf - res_l.e_tf) <= 1e-9 * abs(res_l.e_tf)
     assert abs(res_g.e_vw - res_l.e_vw) <= 1e-3 * abs(res_l.e_vw)
 
