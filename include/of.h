@@ -81,7 +81,7 @@ typedef struct {
     of_precond* precond;   /* non-NULL with OF_F32, in place of the V-cycle: the FP32 inner
                               solve is flexible CG preconditioned by this network (Poisson),
                               or flexible GMRES(8) preconditioned by a few flexible-CG steps
-                              with this network on -L_h + |Q| / a, applied to the real and
+                              with this network on -L_h + kf2 |Q|, applied to the real and
                               imaginary parts of each Arnoldi vector (shifted kernel systems;
                               train the network for that shift, of_precond_set_shift) */
     double precond_theta;  /* a network direction z is kept when cos(r, z) > theta, else the
