@@ -16,7 +16,12 @@ al108_wt.json (--al108; about half an hour on one host core):
             steps of every outer iteration and the number of outer iterations (one kernel map
             each), from which a per-ground-state oracle time can be rebuilt from a timed
             sample, and the oracle's own wall time for the whole ground state.
-Usage: python tests/golden/make_golden.py [--al108]
+batched_cells.json (--batched; two processes, each about 15 to 25 minutes on one host core):
+  the two smallest cells of the 64-cell set (W.batched_cells(), seed 3): cell15, 2x2x2 FCC,
+  32 atoms, 64^3, and cell11, 2x2x3 FCC with one site removed, 47 atoms, 64 x 64 x 96; +-0.1
+  bohr displacements, WT-type kernel term, sigma = 1.2, r_c = 10, Anderson m = 3, zeta = 1,
+  every inner solve exact, fixed point to 1e-7; the same record fields as al108_wt.
+Usage: python tests/golden/make_golden.py [--al108 | --batched]
 """
 import json
 import os
@@ -48,7 +53,25 @@ def run(cell, fn, name, **kw):
                 seconds_ground_state=t_gs)
 
 
+BATCHED_GOLDEN = (15, 11)   # indices into W.batched_cells()
+
+
+def run_batched_cell(index):
+    cell = W.batched_cells()[index]
+    return run(cell, O.wt_functional(), cell.name, nlcg_tol=1e-7, fp_tol=1e-7, anderson_m=3,
+               zeta=1.0)
+
+
 if __name__ == "__main__":
+    if "--batched" in sys.argv:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(len(BATCHED_GOLDEN)) as pool:
+            recs = pool.map(run_batched_cell, BATCHED_GOLDEN)
+        with open(os.path.join(HERE, "batched_cells.json"), "w") as f:
+            json.dump({r["name"]: r for r in recs}, f, indent=1)
+        for r in recs:
+            print(r["name"], r["energy"], r["nlcg_iterations"], r["seconds"])
+        sys.exit(0)
     if "--al108" in sys.argv:
         rec = run(W.al108_cell(), O.wt_functional(), "al108_wt", nlcg_tol=1e-7, fp_tol=1e-7,
                   anderson_m=3, zeta=1.0)
